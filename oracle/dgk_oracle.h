@@ -1,0 +1,83 @@
+/*
+ * dgk_oracle.h -- plain FP64 CPU reference ("oracle") of one explicit time step of
+ * the DGSEM discretisation of the relaxed, non-isothermal Navier-Stokes-Korteweg
+ * equations of Keim, Munz & Rohde (arXiv 2208.05310).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or call
+ * this code; only the tests, the smoke check and the CPU-baseline leg of the bench
+ * use it.  It shares no code, header, table or constant generator with the CUDA
+ * library: every formula here is written out again from the paper.
+ *
+ * State layout (conserved variables, structure of arrays):
+ *   U[v][e][n], v = 0..nv-1, e = element, n = node (x index fastest)
+ *   relaxation models (model 1, 2): nv = dim+3, U = (rho, rho*u_1..rho*u_dim, rho*e, c)
+ *   original NSK (model 0):          nv = dim+2, U = (rho, rho*u_1..rho*u_dim, rho*e)
+ * Element e = ix + nx*(iy + ny*iz); node n = i + P*(j + P*k), P = N+1.
+ */
+#ifndef DGK_ORACLE_H
+#define DGK_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int dim;            /* 2 or 3 */
+    int N;              /* polynomial degree */
+    int n[3];           /* elements per direction */
+    double lo[3], hi[3];
+    int periodic[3];
+    /* faces of the box: -x, +x, -y, +y, -z, +z.  kind 0: no wall (direction must be
+       periodic); kind 1: isothermal no-slip wall with static contact angle. */
+    int wall_kind[6];
+    double wall_T[6];
+    double wall_theta_deg[6];
+} or_mesh;
+
+typedef struct {
+    int model;          /* 0 original NSK (periodic boxes only), 1 relaxation model 1, 2 relaxation model 2 */
+    double gammaK, mu, kappa, cv, alpha, beta;
+} or_params;
+
+/* ---- thermodynamics (Sec. 2.1) ---- */
+double or_psi(double rho, double T, double cv);
+double or_pressure(double rho, double T);
+double or_dpdrho_T(double rho, double T);
+double or_cs2(double rho, double T, double cv);
+double or_chem(double rho, double T, double cv);
+double or_inner_energy(double rho, double T, double cv);
+double or_entropy_vol(double rho, double T, double cv);
+int    or_spinodal(double T, double *rho_sv, double *rho_sl);
+int    or_maxwell(double T, double *rho_v, double *rho_l);
+double or_sigma_vl(double T, double cv, double gammaK);
+double or_interface_width(double T, double cv, double gammaK);
+int    or_rho_from_p(double T, double p, int liquid, double *rho);
+double or_wall_dpsi_dc(double c, double rho_v, double rho_l, double sigma, double theta_deg);
+
+/* ---- 1D operators (Sec. 3.1) ---- */
+int  or_gauss_legendre(int npts, double *x, double *w);
+void or_lagrange_at(int N, const double *xi, double x, double *l);
+void or_dmatrix(int N, const double *xi, double *D);
+
+/* ---- discretisation ---- */
+int  or_sizes(const or_mesh *m, const or_params *p, long *nelem, int *np, int *nv);
+int  or_node_coords(const or_mesh *m, double *x);
+int  or_set_primitive(const or_mesh *m, const or_params *p, const double *prim, double *U);
+int  or_temperature(const or_mesh *m, const or_params *p, const double *U, double *T);
+typedef void (*or_forcing_fn)(int dim, const double *x, double t, double *q, void *user);
+int  or_rhs(const or_mesh *m, const or_params *p, const double *U, double *Ut);
+int  or_rhs_forced(const or_mesh *m, const or_params *p, const double *U, double *Ut,
+                   double t, or_forcing_fn f, void *user);
+int  or_rk_coeffs(int rk, int *nstages, double *A, double *B, double *c);
+int  or_run(const or_mesh *m, const or_params *p, double *U, int nsteps, double dt, int rk,
+            double t0, or_forcing_fn f, void *user);
+int  or_max_dt(const or_mesh *m, const or_params *p, const double *U, double cfl, double dfl, double *dt);
+int  or_diagnostics(const or_mesh *m, const or_params *p, const double *U, double *out);
+int  or_num_threads(void);
+
+#define OR_NDIAG 8  /* mass, mom_x, mom_y, mom_z, energy, -entropy, ||rho-c||_2, max|u| */
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,91 @@
+"""Shared test helpers: mesh / parameter specifications as plain data, node permutations
+for the symmetry tests, and the workload recipes used by the parity tests.  None of the
+method's arithmetic lives here: thermodynamic numbers (saturation densities, interface
+width) are always obtained from the side under test."""
+import numpy as np
+
+from paper_2208_05310_gb300 import inputs
+
+PAPER_PARAMS = dict(model=1, gammaK=1e-4, mu=0.01, kappa=1.0 / 150.0, cv=5.0, alpha=100.0, beta=100.0)
+
+
+def mesh_spec(dim, N, n, lo=None, hi=None, periodic=None, walls=None):
+    lo = lo or [0.0] * dim
+    hi = hi or [1.0] * dim
+    periodic = periodic if periodic is not None else [1] * dim
+    return dict(dim=dim, N=N, n=list(n), lo=list(lo), hi=list(hi), periodic=list(periodic), walls=dict(walls or {}))
+
+
+def oracle_objects(orc, mspec, pspec):
+    m = orc.make_mesh(mspec["dim"], mspec["N"], mspec["n"] + [1] * (3 - mspec["dim"]),
+                      mspec["lo"] + [0.0] * (3 - mspec["dim"]), mspec["hi"] + [1.0] * (3 - mspec["dim"]),
+                      mspec["periodic"] + [1] * (3 - mspec["dim"]), mspec["walls"])
+    p = orc.make_params(**pspec)
+    return orc.Oracle(m, p)
+
+
+def quad_weights(w1d, dim, h):
+    """Per-node quadrature weight times the element Jacobian prod(h/2)."""
+    P = len(w1d)
+    W = np.ones(P ** dim)
+    idx = np.arange(P ** dim)
+    for d in range(dim):
+        W = W * w1d[(idx // P ** d) % P]
+    return W * np.prod([0.5 * hh for hh in h])
+
+
+# ---------------- node / element permutations ----------------
+
+def _grid(arr, dim, n, P):
+    """view [v][e][node] as [v][ez][ey][ex][k][j][i] (3D) or [v][ey][ex][j][i] (2D)"""
+    v = arr.shape[0]
+    if dim == 2:
+        return arr.reshape(v, n[1], n[0], P, P)
+    return arr.reshape(v, n[2], n[1], n[0], P, P, P)
+
+
+def mirror(arr, dim, n, P, axis, flip_vars):
+    """Reflect a nodal field across the mid-plane normal to `axis` (0 = x); the
+    components listed in flip_vars change sign."""
+    g = _grid(arr, dim, n, P).copy()
+    e_ax = dim - axis  # element axis index in the grid view (after v)
+    n_ax = 2 * dim - axis
+    g = np.flip(g, axis=e_ax)
+    g = np.flip(g, axis=n_ax)
+    for v in flip_vars:
+        g[v] = -g[v]
+    return np.ascontiguousarray(g.reshape(arr.shape))
+
+
+def transpose_xy(arr, n, P, var_perm):
+    """2D: swap x and y (requires nx == ny).  var_perm maps new variable -> old variable."""
+    g = _grid(arr, 2, n, P)
+    g = np.transpose(g, (0, 2, 1, 4, 3))
+    g = g[list(var_perm)]
+    return np.ascontiguousarray(g.reshape(arr.shape))
+
+
+def cycle_xyz(arr, n, P, var_perm):
+    """3D: new (x, y, z) = old (y, z, x) (requires nx == ny == nz)."""
+    g = _grid(arr, 3, n, P)
+    # grid axes: v, ez, ey, ex, k, j, i ; new x = old y etc.
+    # new[ez', ey', ex'] with ex' = old ey, ey' = old ez, ez' = old ex
+    g = np.transpose(g, (0, 3, 1, 2, 6, 4, 5))
+    g = g[list(var_perm)]
+    return np.ascontiguousarray(g.reshape(arr.shape))
+
+
+# ---------------- workloads ----------------
+
+def droplet_state(x, thermo, T0=0.85, center=None, radius=0.25, perturb_seed=None, lengths=None,
+                  noise_seed=None, noise_amp=0.0, liquid_inside=True, axes=None):
+    """thermo = (rho_v, rho_l, L_i) from the side under test."""
+    rv, rl, L = thermo
+    dim = x.shape[0]
+    center = center if center is not None else [0.5] * dim
+    noise = inputs.uniform_noise(x[0].shape, noise_seed) if noise_seed is not None else None
+    prim = inputs.droplet(x, center, radius, rv, rl, L, T0, liquid_inside=liquid_inside, noise=noise,
+                          noise_amp=noise_amp, axes=axes)
+    if perturb_seed is not None:
+        prim = inputs.perturbed(prim, x, perturb_seed, lengths=lengths)
+    return prim
