@@ -1,0 +1,416 @@
+"""Throughput benchmark of the DGSEM relaxed-NSK time step on GB300.
+
+Workload (default): non-isothermal confined liquid bridge between two parallel walls,
+3D, N = 5 on 64x64x32 elements of [0,2]x[0,2]x[0,1] (28.3 M nodes), periodic in x and
+y, bottom wall 0.95, top wall 0.8 (isothermal no-slip, contact angle 90 deg), T0 = 0.85,
+relaxation model 1 with alpha = beta = 100, the paper's fluid properties, LSRK4 (5
+stages).  Metric: DOF-stage updates per second (nodes x RK stages / time).
+
+Arms:
+  default             libdgk on the GPU (FP32-bulk form as the headline; FP64 form and
+                      end-to-end host-buffer throughput reported beside it)
+  --impl reference    the FP64 CPU oracle on the host cores, on a bounded sub-box of the
+                      same workload (the paper publishes no timing to compare against)
+
+Multi-GPU (torchrun): every rank runs its own replica (independent problems, no data
+exchange); value = total DOF-stage updates of all ranks / max-over-ranks time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-stage updates/s (DGSEM RHS+RK), FP32/batched vs FP64 at stated err; % HBM roof"
+UNIT = "DOF-stage/s"
+
+# Algorithmic bytes per node and launch of each stage kernel: every array element the
+# kernel consumes or produces, once (R = bulk type size; 3D: NV = 6, NL = 5, one face
+# point per node for N = 5).
+def kernel_bytes_per_node(dim, N, rsize):
+    nv, nl = dim + 3, dim + 2
+    f = 2 * dim / (N + 1)  # face points per node (own faces)
+    lift1 = 8 * nv + rsize * nl * f + rsize * 2 * f
+    lift2 = 8 * nv + rsize * nl * f + rsize * 2 * f + rsize * nv + rsize * (2 * nv + 1) * f
+    surf = rsize * (2 * nv + 1) * f + rsize * nv + 8 * nv * 4 + rsize * nl * f
+    return {"k_lift1": lift1, "k_lift2vol": lift2, "k_surf_rk": surf}
+
+
+def workload_c5(scale=1):
+    """Confined heated liquid bridge (3D, N = 5)."""
+    n = [64 // scale, 64 // scale, 32]
+    hi = [2.0 / scale, 2.0 / scale, 1.0]
+    return dict(name="confined heated liquid bridge between walls (0.95 / 0.8 Tc), 3D N=5, "
+                     f"{n[0]}x{n[1]}x{n[2]} elements, LSRK4",
+                mesh=dict(dim=3, N=5, n=n, lo=[0.0, 0.0, 0.0], hi=hi, periodic=[1, 1, 0],
+                          walls={4: (0.95, 90.0), 5: (0.8, 90.0)}),
+                params=dict(model=1, gammaK=1e-4, mu=0.01, kappa=1.0 / 150.0, cv=5.0, alpha=100.0, beta=100.0),
+                rk=4, T0=0.85, radius=0.5, center=[1.0, 1.0, 0.5], axes=(0, 1))
+
+
+def workload_c2():
+    return dict(name="static droplet, 2D N=4, 64x64 elements, LSRK4",
+                mesh=dict(dim=2, N=4, n=[64, 64], lo=[0.0, 0.0], hi=[1.0, 1.0], periodic=[1, 1], walls={}),
+                params=dict(model=1, gammaK=1e-4, mu=0.01, kappa=1.0 / 150.0, cv=5.0, alpha=100.0, beta=100.0),
+                rk=4, T0=0.8, radius=0.25, center=[0.5, 0.5], axes=None, noise=1e-3)
+
+
+WORKLOADS = {"c5": workload_c5, "c5s": lambda: workload_c5(scale=2), "c2": workload_c2}
+
+
+def primitive_state(wl, x, rv, rl, width):
+    from paper_2208_05310_gb300 import inputs
+    noise = inputs.uniform_noise(x[0].shape, 2208) if wl.get("noise") else None
+    return inputs.droplet(x, wl["center"], wl["radius"], rv, rl, width, wl["T0"], liquid_inside=True, noise=noise,
+                          noise_amp=wl.get("noise", 0.0), axes=wl.get("axes"))
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_sources_sha():
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2208_05310_gb300", "csrc")
+    for fn in ("dgk_common.cuh", "dgk_kernels.cuh"):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha1") != kernel_sources_sha():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [s.strip() for s in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax = float(p[2])
+                except ValueError:
+                    continue
+                for nm, val in zip(names, p[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_rate(wl, seconds_target=15.0, steps=None, sub=(6, 6, None)):
+    """FP64 oracle DOF-stage/s on a sub-box of the workload with the same N and element
+    size (periodic laterally, the workload's walls in z)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import numpy as np
+    import oracle as orc
+    m = wl["mesh"]
+    dim = m["dim"]
+    h = [(m["hi"][d] - m["lo"][d]) / m["n"][d] for d in range(dim)]
+    nsub = [sub[d] if sub[d] else m["n"][d] for d in range(dim)]
+    hi = [m["lo"][d] + nsub[d] * h[d] for d in range(dim)]
+    mesh = orc.make_mesh(dim, m["N"], nsub + [1] * (3 - dim), m["lo"] + [0.0] * (3 - dim), hi + [1.0] * (3 - dim),
+                         m["periodic"] + [1] * (3 - dim), m["walls"])
+    o = orc.Oracle(mesh, orc.make_params(**wl["params"]))
+    rv, rl = orc.maxwell(wl["T0"])
+    width = orc.interface_width(wl["T0"], 5.0, wl["params"]["gammaK"])
+    wl2 = dict(wl, center=[0.5 * hi[0], 0.5 * hi[1]] + wl["center"][2:], radius=min(wl["radius"], 0.3 * hi[0]))
+    U = o.set_primitive(primitive_state(wl2, o.node_coords(), rv, rl, width))
+    dt = o.max_dt(U)
+    stages = 5 if wl["rk"] == 4 else 3
+    dof = o.nelem * o.np
+    t0 = time.perf_counter()
+    U = o.run(U, 1, dt, rk=wl["rk"])
+    t1 = time.perf_counter() - t0
+    nsteps = steps if steps is not None else max(0, int(seconds_target / max(t1, 1e-3)) - 1)
+    t0 = time.perf_counter()
+    if nsteps:
+        U = o.run(U, nsteps, dt, rk=wl["rk"])
+    tt = time.perf_counter() - t0
+    total_steps = nsteps if nsteps else 1
+    total_t = tt if nsteps else t1
+    assert np.isfinite(U).all()
+    return dict(rate=dof * stages * total_steps / total_t, cores=orc.num_threads(), dof=dof, steps=total_steps,
+                seconds=total_t, sub=nsub)
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as orc
+    orc.lib()
+    # warm-up steps, then K timed steps; one step = one RK step on the sub-box
+    r_w = oracle_rate(wl, steps=max(args.warmup, 1))
+    r = oracle_rate(wl, steps=max(args.steps, 1))
+    sample = f"one RK step per bench step on a {r['sub']} sub-box of the workload ({r['dof']} nodes)"
+    line = dict(metric=METRIC, value=r["rate"], unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * r["seconds"] / r["steps"], higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=wl["name"], sample=sample, stages_per_step=5 if wl["rk"] == 4 else 3),
+                cpu_baseline=dict(value=r["rate"], unit=UNIT, cores=r["cores"], kind="oracle", sample=sample),
+                e2e=dict(value=r["rate"], unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    del r_w
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, wl, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2208_05310_gb300 import dgk
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    m = wl["mesh"]
+    stages = 5 if wl["rk"] == 4 else 3
+
+    def make_ctx(precision):
+        ctx = dgk.Context(device=local_rank)
+        ctx.set_params(rk=wl["rk"], precision=precision, **wl["params"])
+        dim = m["dim"]
+        ctx.mesh_box(dim, m["N"], m["n"] + [1] * (3 - dim), m["lo"] + [0.0] * (3 - dim), m["hi"] + [1.0] * (3 - dim),
+                     m["periodic"] + [1] * (3 - dim), m["walls"])
+        rv, rl = dgk.maxwell(wl["T0"])
+        width = dgk.interface_width(wl["T0"], wl["params"]["cv"], wl["params"]["gammaK"])
+        ctx.set_primitive(primitive_state(wl, ctx.node_coords(), rv, rl, width))
+        return ctx
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ctx = make_ctx(args.precision)
+    dof = ctx.nelem * ctx.np
+    dt = ctx.max_dt(0.9, 0.4)
+    # warm-up (also captures the step graph)
+    ctx.run(args.warmup, dt)
+    ctx.status()
+
+    # --- pass A: graph-launched steps, headline throughput
+    s = ctx.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        e0.record(s)
+        ctx.run(args.steps, dt)
+        e1.record(s)
+        s.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    ctx.status()
+    ms_max = max_over_ranks(ms)
+    value = dof * stages * args.steps * world / (ms_max / 1e3)
+
+    # --- pass B: the same steps kernel by kernel with per-kernel CUDA events
+    ctx.set_timing(True)
+    barrier()
+    ctx.run(args.steps, dt)
+    ktimes = {}
+    for k, name in enumerate(("k_lift1", "k_lift2vol", "k_surf_rk")):
+        tot, cnt = ctx.kernel_time(k)
+        ktimes[name] = (tot, cnt)
+    ctx.set_timing(False)
+    ctx.status()
+    rsize = 4 if args.precision == "fp32bulk" else 8
+    kb = kernel_bytes_per_node(m["dim"], m["N"], rsize)
+    total_k = sum(t for t, _ in ktimes.values())
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    avg_ms = ktimes[dom][0] / max(ktimes[dom][1], 1)
+    alg_bytes = kb[dom] * dof
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+    traffic = ncu_traffic(dom, args.workload + ("_fp32" if rsize == 4 else "_fp64"))
+    roofline = dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=traffic,
+                    kernel=dom, peak_kind=peak_kind, alg_bytes_per_launch=alg_bytes,
+                    avg_launch_ms=avg_ms,
+                    share={k: ktimes[k][0] / total_k for k in ktimes},
+                    step_bytes_alg=(8 * (m["dim"] + 3) * 4) * dof * stages,
+                    step_frac_alg=(8 * (m["dim"] + 3) * 4) * dof * stages / (ms / args.steps / 1e3) / 1e9 / peak)
+    del ctx
+    torch.cuda.synchronize()
+
+    # --- FP64 form on the same GPU (fewer steps: FP64 is ALU-bound on this part)
+    fp64 = None
+    if args.precision != "fp64" and not args.no_fp64:
+        c64 = make_ctx("fp64")
+        k64 = max(1, args.steps // 4)
+        c64.run(1, dt)
+        c64.status()
+        barrier()
+        e0.record(c64.stream)
+        c64.run(k64, dt)
+        e1.record(c64.stream)
+        c64.stream.synchronize()
+        barrier()
+        ms64 = max_over_ranks(e0.elapsed_time(e1))
+        c64.status()
+        fp64 = dict(value=dof * stages * k64 * world / (ms64 / 1e3), unit=UNIT, steps=k64, ms_per_step=ms64 / k64)
+        del c64
+        torch.cuda.synchronize()
+
+    # --- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(args, make_ctx, dt, dof, stages, world, barrier, max_over_ranks)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_rate(wl, seconds_target=args.cpu_seconds)
+        cpu = dict(value=r["rate"], unit=UNIT, cores=r["cores"], kind="oracle",
+                   sample=f"{r['steps']} RK steps on a {r['sub']} sub-box of the workload ({r['dof']} nodes), "
+                          f"{r['seconds']:.1f} s")
+
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                    ms_per_step=ms_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                    dtype="f32/f64" if args.precision == "fp32bulk" else "f64", data="synthetic",
+                    config=dict(workload=wl["name"], dof=dof, stages_per_step=stages, precision=args.precision,
+                                l2="inputs larger than L2: state %.2f GB" % (dof * (m['dim'] + 3) * 8 / 1e9),
+                                parallelism=f"replicas x{world}"),
+                    e2e=e2e, gpu_launches=3 * stages * args.steps, roofline=roofline, cpu_baseline=cpu,
+                    clocks=clk.summary(), fp64=fp64)
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def end_to_end(args, make_ctx, dt, dof, stages, world, barrier, max_over_ranks):
+    """K steps through the C ABI with pinned host buffers: each step uploads the state,
+    runs one RK step and reads the state back."""
+    import torch
+    ctx = make_ctx(args.precision)
+    host_in = torch.empty(ctx.shape(), dtype=torch.float64, pin_memory=True)
+    host_out = torch.empty(ctx.shape(), dtype=torch.float64, pin_memory=True)
+    ctx.download_state(host_in)
+    ctx.run(1, dt)
+    ctx.status()
+    k_e2e = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        ctx.upload_state(host_in)
+        ctx.run(1, dt)
+        ctx.download_state(host_out)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    ctx.status()
+    nbytes = host_in.numel() * 8
+    del ctx
+    return dict(value=dof * stages * k_e2e * world / t_e2e, unit=UNIT, h2d_bytes_per_step=nbytes,
+                d2h_bytes_per_step=nbytes, steps=k_e2e)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32bulk", choices=["fp32bulk", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = WORKLOADS[args.workload]()
+    if args.impl == "reference":
+        return run_reference(args, wl, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        return run_ours(args, wl, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

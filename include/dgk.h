@@ -1,0 +1,175 @@
+/*
+ * dgk.h -- C ABI of libdgk: one explicit low-storage Runge-Kutta time step of the DGSEM
+ * discretisation of the relaxed, non-isothermal Navier-Stokes-Korteweg equations
+ * (Keim, Munz & Rohde, arXiv 2208.05310), on one GB300 (sm_103a).
+ *
+ * Method (paper references are sections / equations of the paper):
+ *   unknowns U = (rho, rho u_1..rho u_d, rho e, c)        Sec. 2.3, Eq. (navierstokeskorteweg_p)
+ *   van der Waals fluid, R = 8/3, a = 3, b = 1/3           Sec. 2.1, Eq. (helmholtzfreeenergyvol)
+ *   total energy incl. alpha/2 (rho-c)^2 + gamma_K/2 |grad c|^2   Eq. (totalenergyalpha)
+ *   relaxation model 1 (p in the flux, alpha rho grad(c - rho) as a source) or
+ *   model 2 (modified pressure p + alpha/2 rho^2)          Eq. (navierstokeskorteweg_p), (..._palpha)
+ *   DGSEM on Legendre-Gauss nodes, hexahedral (box) meshes, Rusanov flux, BR1 lifting of
+ *   (rho, u, c), then of (T, grad c) for grad T and lap c, point-wise sources      Sec. 3.1
+ *   isothermal no-slip walls with a static contact angle   Sec. 2.4, Eq. (bc_nsk_alpha),
+ *                                                          Eq. (helmfreesurftot_derivative)
+ *   low-storage RK: 3-stage (Williamson) or 5-stage 4th order (Carpenter-Kennedy)  Sec. 3.1
+ *
+ * Conventions for every call:
+ *   - Return value: DGK_OK (0) or a negative DGK_ERR_* code; no call aborts, throws or
+ *     traps.  dgk_status_string() names a code; dgk_last_error() gives details.
+ *   - Array layout: structure of arrays, FP64, X[v][e][n] with v the variable, e the
+ *     element (e = ix + nx*(iy + ny*iz)) and n the node inside the element
+ *     (n = i + P*(j + P*k), P = N+1, i along x).  Sizes from dgk_sizes().
+ *   - on_device != 0: the pointer is device memory of the context's GPU; 0: host memory
+ *     (pageable or pinned).  Caller-owned pointers are only read or written during the
+ *     call (device pointers: in stream order on the context's stream).
+ *   - The context owns all other device memory and releases it in dgk_destroy().
+ *   - All device work is issued on the context's stream; calls that return data to the
+ *     host synchronise that stream.  One context per host thread at a time.
+ *   - Device-detected errors (non-finite state, density outside (0, 1/b), T <= 0) are
+ *     latched in a device status word; dgk_status() synchronises and returns it, then
+ *     clears it.
+ */
+#ifndef DGK_H
+#define DGK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DGK_OK 0
+#define DGK_ERR_ARG (-1)         /* invalid argument (null pointer, size mismatch, bad enum) */
+#define DGK_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define DGK_ERR_NONFINITE (-3)   /* device: non-finite value in the state */
+#define DGK_ERR_DOMAIN (-4)      /* device: density outside (0, 1/b) or temperature <= 0 */
+#define DGK_ERR_STATE (-5)       /* call order: no mesh / params / state yet */
+#define DGK_ERR_UNSUPPORTED (-6) /* dimension / degree / model not compiled in */
+#define DGK_ERR_NOMEM (-7)       /* device allocation failed */
+#define DGK_ERR_THERMO (-8)      /* no saturation states at this temperature (T >= 1) */
+
+#define DGK_PREC_FP64 0      /* every kernel in FP64 */
+#define DGK_PREC_FP32BULK 1  /* lifting, volume and surface in FP32; the energy balance of
+                                the nodal temperature recovery, the RK accumulation and the
+                                diagnostics in FP64 */
+
+#define DGK_NDIAG 8 /* mass, momentum x/y/z, total energy, -int rho eta, ||rho-c||_2, max|u| */
+
+typedef struct dgk_ctx dgk_ctx;
+
+/* Physical and numerical parameters.  Defaults of the paper (Sec. 4, table
+   "fluidproperties"): gammaK 1e-4, mu 0.01, kappa 1/150, cv 5; alpha = beta = 100. */
+typedef struct {
+    int model;       /* 1: relaxation model 1 (Eq. navierstokeskorteweg_p); 2: model 2 (.._palpha) */
+    int rk;          /* 3: three-stage LSRK3, 4: five-stage LSRK4 (the paper's default, Sec. 3.1) */
+    int precision;   /* DGK_PREC_FP64 or DGK_PREC_FP32BULK */
+    double gammaK;   /* capillarity coefficient gamma_K > 0 (Eq. non-dimensionals) */
+    double mu;       /* viscosity, Stokes hypothesis (Sec. 2.2) */
+    double kappa;    /* heat conductivity */
+    double cv;       /* heat capacity ratio cv = c_v/R_gas */
+    double alpha;    /* Korteweg relaxation parameter alpha > 0 (Sec. 2.3) */
+    double beta;     /* order-parameter relaxation rate beta > 0 (Eq. orderparametersourcenskalpha) */
+} dgk_params;
+
+/* One face of the box.  kind 0: none (the direction must be periodic); kind 1:
+   isothermal no-slip wall at temperature T_wall with static contact angle theta_deg
+   (Eq. bc_nsk_alpha with gamma_1 = gamma_2 = gamma_4 = 0; the saturation densities and
+   sigma_vl at T_wall are computed by the library, Eq. surftenscoef). */
+typedef struct {
+    int kind;
+    double T_wall;
+    double theta_deg;
+} dgk_wall;
+
+/* Cartesian box mesh of hexahedral (dim 3) or quadrilateral (dim 2) elements. */
+typedef struct {
+    int dim;            /* 2 or 3 */
+    int N;              /* polynomial degree, 2..5 */
+    int n[3];           /* elements per direction (n[2] ignored for dim 2) */
+    double lo[3], hi[3];
+    int periodic[3];
+    dgk_wall wall[6];   /* faces -x, +x, -y, +y, -z, +z */
+} dgk_box_mesh;
+
+/* ---------------- context ---------------- */
+
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to issue all
+   work on (e.g. PyTorch's current stream), or NULL for a stream owned by the context. */
+int dgk_create(dgk_ctx **out, int device, void *cuda_stream);
+/* Release all device memory and the owned stream.  Accepts NULL. */
+void dgk_destroy(dgk_ctx *ctx);
+/* Set the parameters (copied).  Must precede dgk_mesh_box; may be changed later for
+   the same precision (a state present stays valid). */
+int dgk_set_params(dgk_ctx *ctx, const dgk_params *p);
+/* Build the box mesh: 1D operators on N+1 Legendre-Gauss nodes (Sec. 3.1), wall
+   constants, and device buffers for the state, the RK register and the face traces. */
+int dgk_mesh_box(dgk_ctx *ctx, const dgk_box_mesh *mesh);
+/* Problem sizes: elements, nodes per element (N+1)^dim, conserved variables dim+3. */
+int dgk_sizes(const dgk_ctx *ctx, long long *nelem, int *nodes_per_elem, int *nvar);
+/* Node coordinates x[d][e][n] (dim x nelem x np doubles). */
+int dgk_node_coords(dgk_ctx *ctx, double *x, int on_device);
+
+/* ---------------- state ---------------- */
+
+/* Set the state from nodal primitive variables prim[v][e][n], v = (rho, u_1..u_dim, T, c):
+   rho e = rho (R cv T - a rho) + rho|u|^2/2 + alpha/2 (rho-c)^2 + gamma_K/2 |grad c|^2
+   (Eq. totalenergyalpha) with grad c the BR1-lifted gradient of c, so that the
+   temperature the scheme recovers equals T.  Resets the RK register. */
+int dgk_set_primitive(dgk_ctx *ctx, const double *prim, size_t count, int on_device);
+/* Copy a conserved state in / out (count = nvar*nelem*np).  Upload resets the RK register. */
+int dgk_upload_state(dgk_ctx *ctx, const double *U, size_t count, int on_device);
+int dgk_download_state(dgk_ctx *ctx, double *U, size_t count, int on_device);
+
+/* ---------------- the hot path ---------------- */
+
+/* One evaluation of the semi-discrete right-hand side U_t = R(U) of the current state
+   (all steps of Sec. 3.1: lifting, temperature, second lifting, volume integral with
+   the derivative matrix per direction, Rusanov + viscous surface fluxes, Jacobian, point
+   sources); Ut has count = nvar*nelem*np doubles.  The state is not changed. */
+int dgk_rhs(dgk_ctx *ctx, double *Ut, size_t count, int on_device);
+/* One low-storage RK step of size dt (all stages; per stage G = A_s G + dt R(U),
+   U = U + B_s G, fused into the surface kernel).  Asynchronous. */
+int dgk_rk_step(dgk_ctx *ctx, double dt);
+/* nsteps RK steps of size dt, launched as a captured CUDA graph of one step.
+   Asynchronous; check dgk_status() afterwards. */
+int dgk_run(dgk_ctx *ctx, int nsteps, double dt);
+/* Largest stable step for the current state: min of CFL/((2N+1) max sum_d (|u_d|+s)/h_d),
+   DFL/((2N+1)^2 nu_max sum_d h_d^-2) and 2/(alpha beta); s^2 = c_s^2 + alpha rho. */
+int dgk_max_dt(dgk_ctx *ctx, double cfl, double dfl, double *dt);
+/* Integral diagnostics (Gauss quadrature, FP64, fixed summation order):
+   out[DGK_NDIAG] = mass, momentum x, y, z, total energy, -int rho eta, ||rho - c||_2, max|u|. */
+int dgk_diagnostics(dgk_ctx *ctx, double *out);
+/* Synchronise the stream and return (then clear) the latched device status. */
+int dgk_status(dgk_ctx *ctx);
+/* Event-timed duration (ms) of the last timed launch of each kernel class, for roofline
+   accounting: which = 0 lift1, 1 lift2+volume, 2 surface+RK.  Enabled by dgk_set_timing. */
+int dgk_set_timing(dgk_ctx *ctx, int enable);
+int dgk_kernel_time(dgk_ctx *ctx, int which, double *ms_total, long long *launches);
+
+/* ---------------- thermodynamics (host) ---------------- */
+
+/* Maxwell (saturation) densities at T in (0, 1) (Sec. 2.1). */
+int dgk_maxwell(double T, double *rho_v, double *rho_l);
+/* Equilibrium surface tension, Eq. (surftenscoef) with prefactor sqrt(2 gamma_K),
+   15-point Gauss quadrature (Sec. 3.2). */
+int dgk_sigma_vl(double T, double cv, double gammaK, double *sigma);
+/* Initial interface width L_i = sqrt(2) gamma_K (rho_l - rho_v)^2 / sigma (Sec. 4). */
+int dgk_interface_width(double T, double cv, double gammaK, double *width);
+
+/* Self-check of the library's own binary64 <-> binary32 conversions (integer arithmetic,
+   used by the FP32-bulk kernels to stay off the FP64 pipe) against the GPU's hardware
+   conversions, bit for bit, on the n doubles at x.  *mismatches = number of inputs whose
+   results differ (inputs rounding below the float normal range are skipped).  Allocates
+   and synchronises the current device. */
+int dgk_check_conversions(const double *x, size_t n, int on_device, unsigned long long *mismatches);
+
+const char *dgk_status_string(int status);
+/* Text of the most recent error in this thread (empty if none). */
+const char *dgk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,860 @@
+// dgk_api.cu -- host runtime and C ABI of libdgk (declared in include/dgk.h).
+//
+// The context owns every device buffer of one problem: the FP64 state U and RK register
+// G, the bulk-type volume residual and face traces, a small coefficient block read by
+// the RK kernel (so one captured graph serves every dt), and the device status word.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dgk.h"
+#include "dgk_host_math.h"
+#include "dgk_launch.cuh"
+
+const dgk::KernelTable *dgk_table_2d_f64(int N);
+const dgk::KernelTable *dgk_table_2d_f32(int N);
+const dgk::KernelTable *dgk_table_3d_f64(int N);
+const dgk::KernelTable *dgk_table_3d_f32(int N);
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+#define DGK_CUDA(call)                                                                             \
+    do {                                                                                           \
+        cudaError_t err_ = (call);                                                                 \
+        if (err_ != cudaSuccess)                                                                   \
+            return fail(err_ == cudaErrorMemoryAllocation ? DGK_ERR_NOMEM : DGK_ERR_CUDA,           \
+                        std::string(#call) + ": " + cudaGetErrorString(err_));                     \
+    } while (0)
+
+// LSRK coefficients (Sec. 3.1): Williamson's 3-stage and Carpenter-Kennedy's 5-stage
+// fourth-order 2N-storage schemes.
+void rk_table(int rk, int &ns, double *A, double *B)
+{
+    if (rk == 3) {
+        static const double a[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+        static const double b[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+        ns = 3;
+        for (int s = 0; s < 3; ++s) { A[s] = a[s]; B[s] = b[s]; }
+    } else {
+        static const double a[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                                    -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+        static const double b[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                                    1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                                    2277821191437.0 / 14882151754819.0};
+        ns = 5;
+        for (int s = 0; s < 5; ++s) { A[s] = a[s]; B[s] = b[s]; }
+    }
+}
+
+// primitive (rho, u, T, c) -> partial conserved state; T kept in Tbuf for the energy kernel
+__global__ void k_prim_partial(const double *prim, double *U, double *Tbuf, long long nn, int D)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    const double rho = prim[i];
+    U[i] = rho;
+    for (int k = 0; k < D; ++k) U[(1 + k) * nn + i] = rho * prim[(1 + k) * nn + i];
+    U[(D + 1) * nn + i] = 0.0;
+    U[(D + 2) * nn + i] = prim[(D + 2) * nn + i];
+    Tbuf[i] = prim[(D + 1) * nn + i];
+}
+
+struct NodeInfo {
+    int D, P, NP;
+    double h[3];
+    double J;
+    double w[dgk::kMaxP];
+};
+
+// Largest stable dt contribution per node, reduced with atomicMax on the bit pattern
+// of non-negative doubles (monotone for non-negative values).
+__global__ void k_dt_reduce(const double *U, const double *T, long long ne, NodeInfo ni, dgk::Phys ph,
+                            unsigned long long *lam_max, unsigned long long *nu_max)
+{
+    __shared__ double sl[256], sn[256];
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nn = ne * ni.NP;
+    double lam = 0.0, nu = 0.0;
+    if (i < nn) {
+        const double rho = U[i], t = T[i];
+        double omb = 1.0 - dgk::kBvdw * rho;
+        double s2 = dgk::kRgas * t * (1.0 + 1.0 / ph.cv) / (omb * omb) - 2.0 * dgk::kAvdw * rho + ph.alpha * rho;
+        double s = s2 > 0.0 ? sqrt(s2) : 0.0;
+        for (int k = 0; k < ni.D; ++k) lam += (fabs(U[(1 + k) * nn + i] / rho) + s) / ni.h[k];
+        nu = fmax(4.0 * ph.mu / (3.0 * rho), ph.kap / (rho * dgk::kRgas * ph.cv));
+        nu = fmax(nu, ph.gK * ph.beta);
+        if (!isfinite(lam)) lam = INFINITY;
+    }
+    sl[threadIdx.x] = lam;
+    sn[threadIdx.x] = nu;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sl[threadIdx.x] = fmax(sl[threadIdx.x], sl[threadIdx.x + o]);
+            sn[threadIdx.x] = fmax(sn[threadIdx.x], sn[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicMax(lam_max, (unsigned long long)__double_as_longlong(sl[0]));
+        atomicMax(nu_max, (unsigned long long)__double_as_longlong(sn[0]));
+    }
+}
+
+// Per-block partial sums of the integral diagnostics (fixed tree order; the host sums
+// the blocks in index order, so the result is deterministic).
+__global__ void k_diag_partial(const double *U, const double *T, long long ne, NodeInfo ni, dgk::Phys ph,
+                               double *partial)
+{
+    __shared__ double s[8][256];
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nn = ne * ni.NP;
+    double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (i < nn) {
+        const int n = (int)(i % ni.NP);
+        double W = ni.J;
+        int r = n;
+        for (int k = 0; k < ni.D; ++k) { W *= ni.w[r % ni.P]; r /= ni.P; }
+        const double rho = U[i], t = T[i];
+        q[0] = W * rho;
+        double u2 = 0.0;
+        for (int k = 0; k < ni.D; ++k) {
+            double mk = U[(1 + k) * nn + i];
+            q[1 + k] = W * mk;
+            u2 += (mk / rho) * (mk / rho);
+        }
+        q[4] = W * U[(ni.D + 1) * nn + i];
+        // -rho eta = -(rho R cv ln T - rho R ln(b rho / (1 - b rho)))
+        q[5] = -W * (rho * dgk::kRgas * ph.cv * log(t) - rho * dgk::kRgas * log(dgk::kBvdw * rho / (1.0 - dgk::kBvdw * rho)));
+        double dc = rho - U[(ni.D + 2) * nn + i];
+        q[6] = W * dc * dc;
+        q[7] = sqrt(u2);
+    }
+    for (int k = 0; k < 8; ++k) s[k][threadIdx.x] = q[k];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            for (int k = 0; k < 7; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + o];
+            s[7][threadIdx.x] = fmax(s[7][threadIdx.x], s[7][threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) partial[(long long)blockIdx.x * 8 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+// Bitwise comparison of the integer-arithmetic conversions of dgk_common.cuh with the
+// hardware conversions (round to nearest) on normal-range inputs.
+__global__ void k_check_conv(const double *x, long long n, unsigned long long *bad)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    const float hw = __double2float_rn(v);
+    const float mine = dgk::d2f(v);
+    unsigned long long b = 0;
+    const bool hw_normal = isnan(hw) || isinf(hw) || hw == 0.0f || fabsf(hw) >= 1.17549435e-38f;
+    if (hw_normal && __float_as_uint(hw) != __float_as_uint(mine) && !(isnan(hw) && isnan(mine))) b |= 1ull;
+    const float f = hw;
+    const double back = dgk::f2d(f);
+    if (fabsf(f) >= 1.17549435e-38f || f == 0.0f || isinf(f)) {
+        const double ref = (double)f;
+        if (__double_as_longlong(ref) != __double_as_longlong(back)) b |= 2ull;
+    }
+    if (b) atomicAdd(bad, 1ull);
+}
+
+}  // namespace
+
+struct dgk_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    dgk_params prm{};
+    bool have_params = false;
+    dgk_box_mesh mesh{};
+    bool have_mesh = false;
+    int D = 0, N = 0, P = 0, NP = 0, NFP = 0, NF = 0, NV = 0, NL = 0;
+    long long ne = 0;
+    dgk::host::Operators1D op1{};
+    dgk::KArgs<double> a64{};
+    dgk::KArgs<float> a32{};
+    const dgk::KernelTable *kt = nullptr;
+    size_t rsize = 8;
+    double *U = nullptr, *G = nullptr, *Tbuf = nullptr, *coef = nullptr, *rhsbuf = nullptr, *partial = nullptr;
+    void *Utv = nullptr, *tr1 = nullptr, *tr2 = nullptr, *fd = nullptr;
+    unsigned *status = nullptr;
+    unsigned long long *redbuf = nullptr;
+    double coef_h[11] = {0};
+    bool coef_valid = false;
+    cudaGraphExec_t graph = nullptr;
+    bool timing = false;
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
+    std::vector<int> event_class;
+    double t_ms[3] = {0, 0, 0};
+    long long t_cnt[3] = {0, 0, 0};
+
+    const void *args() const { return prm.precision == DGK_PREC_FP32BULK ? (const void *)&a32 : (const void *)&a64; }
+};
+
+namespace {
+
+void free_buffers(dgk_ctx *c)
+{
+    void *ptrs[] = {c->U, c->G, c->Tbuf, c->coef, c->rhsbuf, c->partial, c->Utv, c->tr1, c->tr2, c->fd, c->status, c->redbuf};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    c->U = c->G = c->Tbuf = c->coef = c->rhsbuf = c->partial = nullptr;
+    c->Utv = c->tr1 = c->tr2 = c->fd = nullptr;
+    c->status = nullptr;
+    c->redbuf = nullptr;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+}
+
+void drop_graph(dgk_ctx *c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+}
+
+template <typename R>
+void fill_args(dgk_ctx *c, dgk::KArgs<R> &a)
+{
+    a.U = c->U;
+    a.G = c->G;
+    a.Utv = (R *)c->Utv;
+    a.tr1 = (R *)c->tr1;
+    a.tr2 = (R *)c->tr2;
+    a.fd = (R *)c->fd;
+    a.out = c->Tbuf;
+    a.coef = c->coef;
+    a.status = c->status;
+}
+
+// constants in the bulk type, derived once on the host
+template <typename R>
+void fill_bulk(dgk::KArgs<R> &a, const dgk::Geom &g, const dgk::Phys &ph, const dgk::Walls &w, const dgk::Ops &o)
+{
+    for (int i = 0; i < dgk::kMaxP * dgk::kMaxP; ++i) a.op.Dh[i] = (R)o.Dhat[i];
+    for (int i = 0; i < dgk::kMaxP; ++i) {
+        a.op.Lp[i] = (R)o.Lp[i];
+        a.op.Lm[i] = (R)o.Lm[i];
+        a.op.lp[i] = (R)o.lp[i];
+        a.op.lm[i] = (R)o.lm[i];
+    }
+    for (int d = 0; d < 3; ++d) a.gr.inv2h[d] = (R)g.inv2h[d];
+    dgk::PhysR<R> &p = a.pr;
+    p.model = ph.model;
+    p.gK = (R)ph.gK;
+    p.mu = (R)ph.mu;
+    p.kap = (R)ph.kap;
+    p.alpha = (R)ph.alpha;
+    p.beta = (R)ph.beta;
+    p.gKbeta = (R)(ph.gK * ph.beta);
+    p.alphabeta = (R)(ph.alpha * ph.beta);
+    p.half_alpha = (R)(0.5 * ph.alpha);
+    p.half_gK = (R)(0.5 * ph.gK);
+    p.two_thirds_mu = (R)(2.0 / 3.0 * ph.mu);
+    p.s_coef = (R)(dgk::kRgas * (1.0 + 1.0 / ph.cv));
+    p.inv_Rcv = (R)(1.0 / (dgk::kRgas * ph.cv));
+    p.half_alpha_p = ph.model == 2 ? (R)(0.5 * ph.alpha) : (R)0;
+    for (int f = 0; f < 6; ++f) {
+        a.wr.K[f] = (R)w.K[f];
+        a.wr.rl[f] = (R)w.rl[f];
+        a.wr.rv[f] = (R)w.rv[f];
+        a.wr.Tw[f] = (R)w.Tw[f];
+    }
+}
+
+// geometry, physics, walls and operators into both argument blocks
+int build_consts(dgk_ctx *c)
+{
+    const dgk_box_mesh &m = c->mesh;
+    dgk::Geom g{};
+    g.ne = c->ne;
+    for (int d = 0; d < 3; ++d) {
+        g.n[d] = d < c->D ? m.n[d] : 1;
+        g.periodic[d] = d < c->D ? m.periodic[d] : 1;
+        g.inv2h[d] = d < c->D ? 2.0 / ((m.hi[d] - m.lo[d]) / m.n[d]) : 0.0;
+    }
+    const dgk_params &q = c->prm;
+    dgk::Phys ph{q.model, q.gammaK, q.mu, q.kappa, q.cv, q.alpha, q.beta,
+                 0.5 * q.alpha, 0.5 * q.gammaK, 1.0 / (dgk::kRgas * q.cv)};
+    dgk::Walls w{};
+    for (int f = 0; f < 2 * c->D; ++f) {
+        int d = f / 2;
+        if (m.periodic[d]) continue;
+        const dgk_wall &wf = m.wall[f];
+        double rv, rl, sig;
+        if (!dgk::host::maxwell(wf.T_wall, rv, rl) || !dgk::host::sigma_vl(wf.T_wall, c->prm.gammaK, sig))
+            return fail(DGK_ERR_THERMO, "wall temperature has no saturation states (need 0 < T_wall < 1)");
+        w.kind[f] = 1;
+        w.Tw[f] = wf.T_wall;
+        w.rv[f] = rv;
+        w.rl[f] = rl;
+        double dr = rl - rv;
+        w.K[f] = -6.0 * sig * std::cos(wf.theta_deg * M_PI / 180.0) / (c->prm.gammaK * dr * dr * dr);
+    }
+    dgk::Ops o{};
+    const int P = c->P;
+    for (int i = 0; i < P; ++i) {
+        for (int j = 0; j < P; ++j) o.Dhat[i * P + j] = c->op1.Dhat[i * P + j];
+        o.Lp[i] = c->op1.lp[i] / c->op1.w[i];
+        o.Lm[i] = c->op1.lm[i] / c->op1.w[i];
+        o.lp[i] = c->op1.lp[i];
+        o.lm[i] = c->op1.lm[i];
+        o.w[i] = c->op1.w[i];
+    }
+    c->a64.g = c->a32.g = g;
+    c->a64.ph = c->a32.ph = ph;
+    fill_bulk(c->a64, g, ph, w, o);
+    fill_bulk(c->a32, g, ph, w, o);
+    return DGK_OK;
+}
+
+int set_coef(dgk_ctx *c, double dt)
+{
+    int ns;
+    double A[5] = {0}, B[5] = {0};
+    rk_table(c->prm.rk, ns, A, B);
+    double h[11];
+    for (int s = 0; s < 5; ++s) { h[s] = A[s]; h[5 + s] = B[s]; }
+    h[10] = dt;
+    if (c->coef_valid && std::memcmp(h, c->coef_h, sizeof(h)) == 0) return DGK_OK;
+    std::memcpy(c->coef_h, h, sizeof(h));
+    DGK_CUDA(cudaMemcpyAsync(c->coef, c->coef_h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+    c->coef_valid = true;
+    return DGK_OK;
+}
+
+int nstages(const dgk_ctx *c) { return c->prm.rk == 3 ? 3 : 5; }
+
+int event_pair(dgk_ctx *c, int cls, cudaEvent_t &a, cudaEvent_t &b)
+{
+    if (c->events_used + 2 > c->events.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            DGK_CUDA(cudaEventCreate(&e));
+            c->events.push_back(e);
+        }
+        c->event_class.resize(c->events.size() / 2, 0);
+    }
+    a = c->events[c->events_used];
+    b = c->events[c->events_used + 1];
+    c->event_class[c->events_used / 2] = cls;
+    c->events_used += 2;
+    return DGK_OK;
+}
+
+// one full RK step, kernel by kernel (optionally bracketed by timing events)
+int launch_step(dgk_ctx *c, bool timed)
+{
+    const void *a = c->args();
+    for (int s = 0; s < nstages(c); ++s) {
+        for (int k = 0; k < 3; ++k) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (timed) {
+                int rc = event_pair(c, k, e0, e1);
+                if (rc) return rc;
+                DGK_CUDA(cudaEventRecord(e0, c->stream));
+            }
+            cudaError_t err = k == 0 ? c->kt->lift1(a, c->stream)
+                              : k == 1 ? c->kt->lift2vol(a, c->stream)
+                                       : c->kt->surf(a, 1, s, c->stream);
+            if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("stage kernel launch: ") + cudaGetErrorString(err));
+            if (timed) DGK_CUDA(cudaEventRecord(e1, c->stream));
+        }
+    }
+    return DGK_OK;
+}
+
+int ready(const dgk_ctx *c)
+{
+    if (!c) return fail(DGK_ERR_ARG, "null context");
+    if (!c->have_params || !c->have_mesh) return fail(DGK_ERR_STATE, "set params and mesh first");
+    return DGK_OK;
+}
+
+int copy_in(dgk_ctx *c, double *dst, const double *src, size_t count, int on_device)
+{
+    DGK_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             c->stream));
+    if (!on_device) DGK_CUDA(cudaStreamSynchronize(c->stream));
+    return DGK_OK;
+}
+
+int after_state_change(dgk_ctx *c)
+{
+    size_t nstate = (size_t)c->NV * c->ne * c->NP;
+    DGK_CUDA(cudaMemsetAsync(c->G, 0, nstate * sizeof(double), c->stream));
+    cudaError_t err = c->kt->traces(c->args(), c->stream);
+    if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("trace kernel: ") + cudaGetErrorString(err));
+    return DGK_OK;
+}
+
+NodeInfo node_info(const dgk_ctx *c)
+{
+    NodeInfo ni{};
+    ni.D = c->D;
+    ni.P = c->P;
+    ni.NP = c->NP;
+    ni.J = 1.0;
+    for (int d = 0; d < c->D; ++d) {
+        ni.h[d] = (c->mesh.hi[d] - c->mesh.lo[d]) / c->mesh.n[d];
+        ni.J *= 0.5 * ni.h[d];
+    }
+    for (int i = 0; i < c->P; ++i) ni.w[i] = c->op1.w[i];
+    return ni;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dgk_last_error(void) { return g_last_error.c_str(); }
+
+const char *dgk_status_string(int s)
+{
+    switch (s) {
+    case DGK_OK: return "ok";
+    case DGK_ERR_ARG: return "invalid argument";
+    case DGK_ERR_CUDA: return "CUDA error";
+    case DGK_ERR_NONFINITE: return "non-finite value in the state";
+    case DGK_ERR_DOMAIN: return "density outside (0, 1/b) or temperature <= 0";
+    case DGK_ERR_STATE: return "call order: missing params, mesh or state";
+    case DGK_ERR_UNSUPPORTED: return "dimension / degree / option not supported";
+    case DGK_ERR_NOMEM: return "device allocation failed";
+    case DGK_ERR_THERMO: return "no saturation states at this temperature";
+    default: return "unknown status";
+    }
+}
+
+int dgk_create(dgk_ctx **out, int device, void *cuda_stream)
+{
+    if (!out) return fail(DGK_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    int ndev = 0;
+    DGK_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(DGK_ERR_ARG, "device index out of range");
+    DGK_CUDA(cudaSetDevice(device));
+    dgk_ctx *c = new (std::nothrow) dgk_ctx();
+    if (!c) return fail(DGK_ERR_NOMEM, "host allocation failed");
+    c->device = device;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t err = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (err != cudaSuccess) {
+            delete c;
+            return fail(DGK_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(err));
+        }
+        c->own_stream = true;
+    }
+    *out = c;
+    return DGK_OK;
+}
+
+void dgk_destroy(dgk_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_buffers(c);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int dgk_set_params(dgk_ctx *c, const dgk_params *p)
+{
+    if (!c || !p) return fail(DGK_ERR_ARG, "null argument");
+    if (p->model != 1 && p->model != 2) return fail(DGK_ERR_UNSUPPORTED, "model must be 1 or 2");
+    if (p->rk != 3 && p->rk != 4) return fail(DGK_ERR_ARG, "rk must be 3 or 4");
+    if (p->precision != DGK_PREC_FP64 && p->precision != DGK_PREC_FP32BULK) return fail(DGK_ERR_ARG, "bad precision");
+    if (!(p->gammaK > 0) || !(p->mu >= 0) || !(p->kappa >= 0) || !(p->cv > 0) || !(p->alpha >= 0) || !(p->beta >= 0))
+        return fail(DGK_ERR_ARG, "parameters out of range");
+    if (c->have_mesh && p->precision != c->prm.precision)
+        return fail(DGK_ERR_STATE, "precision is fixed once the mesh is built");
+    c->prm = *p;
+    c->have_params = true;
+    c->coef_valid = false;
+    drop_graph(c);
+    if (c->have_mesh) return build_consts(c);
+    return DGK_OK;
+}
+
+int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m)
+{
+    if (!c || !m) return fail(DGK_ERR_ARG, "null argument");
+    if (!c->have_params) return fail(DGK_ERR_STATE, "set params before the mesh");
+    if (m->dim != 2 && m->dim != 3) return fail(DGK_ERR_UNSUPPORTED, "dim must be 2 or 3");
+    if (m->N < 2 || m->N > 5) return fail(DGK_ERR_UNSUPPORTED, "N must be 2..5");
+    long long ne = 1;
+    for (int d = 0; d < m->dim; ++d) {
+        if (m->n[d] < 1 || !(m->hi[d] > m->lo[d])) return fail(DGK_ERR_ARG, "bad element count or extent");
+        ne *= m->n[d];
+        if (!m->periodic[d]) {
+            for (int s = 0; s < 2; ++s)
+                if (m->wall[2 * d + s].kind != 1) return fail(DGK_ERR_ARG, "non-periodic direction needs walls on both faces");
+        }
+    }
+    DGK_CUDA(cudaSetDevice(c->device));
+    cudaStreamSynchronize(c->stream);
+    free_buffers(c);
+    c->have_mesh = false;
+    c->mesh = *m;
+    c->D = m->dim;
+    c->N = m->N;
+    c->P = m->N + 1;
+    c->NP = c->D == 2 ? c->P * c->P : c->P * c->P * c->P;
+    c->NFP = c->D == 2 ? c->P : c->P * c->P;
+    c->NF = 2 * c->D;
+    c->NV = c->D + 3;
+    c->NL = c->D + 2;
+    c->ne = ne;
+    if (!dgk::host::dg_operators(c->N, c->op1)) return fail(DGK_ERR_ARG, "operator set-up failed");
+    const bool f32 = c->prm.precision == DGK_PREC_FP32BULK;
+    c->rsize = f32 ? sizeof(float) : sizeof(double);
+    c->kt = c->D == 2 ? (f32 ? dgk_table_2d_f32(c->N) : dgk_table_2d_f64(c->N))
+                      : (f32 ? dgk_table_3d_f32(c->N) : dgk_table_3d_f64(c->N));
+    if (!c->kt) return fail(DGK_ERR_UNSUPPORTED, "no kernels for this (dim, N, precision)");
+    int rc = build_consts(c);
+    if (rc) return rc;
+    DGK_CUDA(c->kt->prepare());
+    const size_t nstate = (size_t)c->NV * ne * c->NP;
+    const size_t nface = (size_t)ne * c->NF * c->NFP;
+    DGK_CUDA(cudaMalloc(&c->U, nstate * sizeof(double)));
+    DGK_CUDA(cudaMalloc(&c->G, nstate * sizeof(double)));
+    DGK_CUDA(cudaMalloc(&c->Tbuf, (size_t)ne * c->NP * sizeof(double)));
+    DGK_CUDA(cudaMalloc(&c->coef, 16 * sizeof(double)));
+    DGK_CUDA(cudaMalloc(&c->status, sizeof(unsigned)));
+    DGK_CUDA(cudaMalloc(&c->redbuf, 2 * sizeof(unsigned long long)));
+    DGK_CUDA(cudaMalloc(&c->Utv, nstate * c->rsize));
+    DGK_CUDA(cudaMalloc(&c->tr1, (size_t)c->NL * nface * c->rsize));
+    DGK_CUDA(cudaMalloc(&c->tr2, (size_t)2 * nface * c->rsize));
+    DGK_CUDA(cudaMalloc(&c->fd, (size_t)(2 * c->NV + 1) * nface * c->rsize));
+    DGK_CUDA(cudaMemsetAsync(c->U, 0, nstate * sizeof(double), c->stream));
+    DGK_CUDA(cudaMemsetAsync(c->G, 0, nstate * sizeof(double), c->stream));
+    DGK_CUDA(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+    DGK_CUDA(cudaMemsetAsync(c->tr1, 0, (size_t)c->NL * nface * c->rsize, c->stream));
+    fill_args(c, c->a64);
+    fill_args(c, c->a32);
+    c->coef_valid = false;
+    c->have_mesh = true;
+    DGK_CUDA(cudaStreamSynchronize(c->stream));
+    return DGK_OK;
+}
+
+int dgk_sizes(const dgk_ctx *c, long long *nelem, int *np, int *nv)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if (nelem) *nelem = c->ne;
+    if (np) *np = c->NP;
+    if (nv) *nv = c->NV;
+    return DGK_OK;
+}
+
+int dgk_node_coords(dgk_ctx *c, double *x, int on_device)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!x) return fail(DGK_ERR_ARG, "null output");
+    const size_t nn = (size_t)c->ne * c->NP;
+    std::vector<double> h((size_t)c->D * nn);
+    for (long long e = 0; e < c->ne; ++e) {
+        long long co[3] = {e % c->mesh.n[0], (e / c->mesh.n[0]) % c->mesh.n[1],
+                           c->D == 3 ? e / ((long long)c->mesh.n[0] * c->mesh.n[1]) : 0};
+        for (int n = 0; n < c->NP; ++n) {
+            int r = n;
+            for (int d = 0; d < c->D; ++d) {
+                const int i = r % c->P;
+                r /= c->P;
+                const double hd = (c->mesh.hi[d] - c->mesh.lo[d]) / c->mesh.n[d];
+                h[(size_t)d * nn + (size_t)e * c->NP + n] = c->mesh.lo[d] + hd * (co[d] + 0.5 * (c->op1.xi[i] + 1.0));
+            }
+        }
+    }
+    DGK_CUDA(cudaMemcpyAsync(x, h.data(), h.size() * sizeof(double), on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
+                             c->stream));
+    DGK_CUDA(cudaStreamSynchronize(c->stream));
+    return DGK_OK;
+}
+
+int dgk_set_primitive(dgk_ctx *c, const double *prim, size_t count, int on_device)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    const size_t nstate = (size_t)c->NV * c->ne * c->NP;
+    if (!prim || count != nstate) return fail(DGK_ERR_ARG, "primitive array has the wrong size");
+    // stage the primitives in G (reset afterwards)
+    rc = copy_in(c, c->G, prim, count, on_device);
+    if (rc) return rc;
+    const long long nn = c->ne * c->NP;
+    k_prim_partial<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->G, c->U, c->Tbuf, nn, c->D);
+    DGK_CUDA(cudaGetLastError());
+    cudaError_t err = c->kt->traces(c->args(), c->stream);
+    if (err != cudaSuccess) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
+    err = c->kt->nodeT(c->args(), 1, c->stream);
+    if (err != cudaSuccess) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
+    rc = after_state_change(c);
+    if (rc) return rc;
+    DGK_CUDA(cudaStreamSynchronize(c->stream));
+    return DGK_OK;
+}
+
+int dgk_upload_state(dgk_ctx *c, const double *U, size_t count, int on_device)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    const size_t nstate = (size_t)c->NV * c->ne * c->NP;
+    if (!U || count != nstate) return fail(DGK_ERR_ARG, "state array has the wrong size");
+    rc = copy_in(c, c->U, U, count, on_device);
+    if (rc) return rc;
+    return after_state_change(c);
+}
+
+int dgk_download_state(dgk_ctx *c, double *U, size_t count, int on_device)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    const size_t nstate = (size_t)c->NV * c->ne * c->NP;
+    if (!U || count != nstate) return fail(DGK_ERR_ARG, "state array has the wrong size");
+    DGK_CUDA(cudaMemcpyAsync(U, c->U, count * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             c->stream));
+    if (!on_device) DGK_CUDA(cudaStreamSynchronize(c->stream));
+    return DGK_OK;
+}
+
+int dgk_rhs(dgk_ctx *c, double *Ut, size_t count, int on_device)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    const size_t nstate = (size_t)c->NV * c->ne * c->NP;
+    if (!Ut || count != nstate) return fail(DGK_ERR_ARG, "output array has the wrong size");
+    double *dst = Ut;
+    if (!on_device) {
+        if (!c->rhsbuf) DGK_CUDA(cudaMalloc(&c->rhsbuf, nstate * sizeof(double)));
+        dst = c->rhsbuf;
+    }
+    cudaError_t err;
+    const void *a = c->args();
+    if ((err = c->kt->lift1(a, c->stream))) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
+    if ((err = c->kt->lift2vol(a, c->stream))) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
+    if (c->prm.precision == DGK_PREC_FP32BULK) {
+        dgk::KArgs<float> b = c->a32;
+        b.out = dst;
+        err = c->kt->surf(&b, 0, 0, c->stream);
+    } else {
+        dgk::KArgs<double> b = c->a64;
+        b.out = dst;
+        err = c->kt->surf(&b, 0, 0, c->stream);
+    }
+    if (err) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
+    if (!on_device) {
+        DGK_CUDA(cudaMemcpyAsync(Ut, dst, nstate * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        DGK_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    return DGK_OK;
+}
+
+int dgk_rk_step(dgk_ctx *c, double dt)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(DGK_ERR_ARG, "dt must be positive");
+    if ((rc = set_coef(c, dt))) return rc;
+    return launch_step(c, c->timing);
+}
+
+int dgk_run(dgk_ctx *c, int nsteps, double dt)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(DGK_ERR_ARG, "nsteps < 0");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(DGK_ERR_ARG, "dt must be positive");
+    if ((rc = set_coef(c, dt))) return rc;
+    if (c->timing) {
+        for (int s = 0; s < nsteps; ++s)
+            if ((rc = launch_step(c, true))) return rc;
+        return DGK_OK;
+    }
+    if (!c->graph && nsteps > 0) {
+        cudaGraph_t g;
+        DGK_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        rc = launch_step(c, false);
+        cudaError_t err = cudaStreamEndCapture(c->stream, &g);
+        if (rc) return rc;
+        if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(err));
+        err = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (err != cudaSuccess) {
+            c->graph = nullptr;
+            return fail(DGK_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(err));
+        }
+    }
+    for (int s = 0; s < nsteps; ++s) DGK_CUDA(cudaGraphLaunch(c->graph, c->stream));
+    return DGK_OK;
+}
+
+int dgk_max_dt(dgk_ctx *c, double cfl, double dfl, double *dt)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!dt || !(cfl > 0) || !(dfl > 0)) return fail(DGK_ERR_ARG, "bad arguments");
+    cudaError_t err = c->kt->nodeT(c->args(), 0, c->stream);
+    if (err) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
+    DGK_CUDA(cudaMemsetAsync(c->redbuf, 0, 2 * sizeof(unsigned long long), c->stream));
+    const long long nn = c->ne * c->NP;
+    dgk::Phys ph = c->a64.ph;
+    k_dt_reduce<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->U, c->Tbuf, c->ne, node_info(c), ph, c->redbuf,
+                                                                     c->redbuf + 1);
+    DGK_CUDA(cudaGetLastError());
+    unsigned long long hv[2];
+    DGK_CUDA(cudaMemcpyAsync(hv, c->redbuf, sizeof(hv), cudaMemcpyDeviceToHost, c->stream));
+    DGK_CUDA(cudaStreamSynchronize(c->stream));
+    double lam, nu;
+    std::memcpy(&lam, &hv[0], 8);
+    std::memcpy(&nu, &hv[1], 8);
+    double ih2 = 0.0;
+    for (int d = 0; d < c->D; ++d) {
+        double h = (c->mesh.hi[d] - c->mesh.lo[d]) / c->mesh.n[d];
+        ih2 += 1.0 / (h * h);
+    }
+    const double k1 = 2.0 * c->N + 1.0;
+    double r = cfl / (k1 * lam);
+    if (nu > 0) r = std::fmin(r, dfl / (k1 * k1 * nu * ih2));
+    if (c->prm.alpha * c->prm.beta > 0) r = std::fmin(r, 2.0 / (c->prm.alpha * c->prm.beta));
+    if (!std::isfinite(r) || !(r > 0)) return fail(DGK_ERR_NONFINITE, "non-finite time step (state invalid)");
+    *dt = r;
+    return DGK_OK;
+}
+
+int dgk_diagnostics(dgk_ctx *c, double *out)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    if (!out) return fail(DGK_ERR_ARG, "null output");
+    cudaError_t err = c->kt->nodeT(c->args(), 0, c->stream);
+    if (err) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
+    const long long nn = c->ne * c->NP;
+    const unsigned nb = (unsigned)((nn + 255) / 256);
+    if (!c->partial) DGK_CUDA(cudaMalloc(&c->partial, (size_t)nb * 8 * sizeof(double)));
+    k_diag_partial<<<nb, 256, 0, c->stream>>>(c->U, c->Tbuf, c->ne, node_info(c), c->a64.ph, c->partial);
+    DGK_CUDA(cudaGetLastError());
+    std::vector<double> h((size_t)nb * 8);
+    DGK_CUDA(cudaMemcpyAsync(h.data(), c->partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    DGK_CUDA(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < DGK_NDIAG; ++k) out[k] = 0.0;
+    for (unsigned b = 0; b < nb; ++b) {
+        for (int k = 0; k < 7; ++k) out[k] += h[(size_t)b * 8 + k];
+        out[7] = std::fmax(out[7], h[(size_t)b * 8 + 7]);
+    }
+    out[6] = std::sqrt(out[6]);
+    return DGK_OK;
+}
+
+int dgk_status(dgk_ctx *c)
+{
+    if (!c) return fail(DGK_ERR_ARG, "null context");
+    DGK_CUDA(cudaStreamSynchronize(c->stream));
+    DGK_CUDA(cudaGetLastError());
+    if (!c->status) return DGK_OK;
+    unsigned s = 0;
+    DGK_CUDA(cudaMemcpy(&s, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    DGK_CUDA(cudaMemset(c->status, 0, sizeof(unsigned)));
+    if (s & dgk::kStatNonFinite) return fail(DGK_ERR_NONFINITE, "device reported a non-finite state");
+    if (s & dgk::kStatDomain) return fail(DGK_ERR_DOMAIN, "device reported a state outside the EoS domain");
+    return DGK_OK;
+}
+
+int dgk_set_timing(dgk_ctx *c, int enable)
+{
+    if (!c) return fail(DGK_ERR_ARG, "null context");
+    c->timing = enable != 0;
+    c->events_used = 0;
+    for (int k = 0; k < 3; ++k) { c->t_ms[k] = 0; c->t_cnt[k] = 0; }
+    return DGK_OK;
+}
+
+int dgk_kernel_time(dgk_ctx *c, int which, double *ms_total, long long *launches)
+{
+    if (!c || which < 0 || which > 2 || !ms_total) return fail(DGK_ERR_ARG, "bad arguments");
+    // resolve outstanding event pairs
+    for (size_t i = 0; i + 1 < c->events_used; i += 2) {
+        DGK_CUDA(cudaEventSynchronize(c->events[i + 1]));
+        float ms = 0.f;
+        DGK_CUDA(cudaEventElapsedTime(&ms, c->events[i], c->events[i + 1]));
+        int cls = c->event_class[i / 2];
+        c->t_ms[cls] += ms;
+        c->t_cnt[cls] += 1;
+    }
+    c->events_used = 0;
+    *ms_total = c->t_ms[which];
+    if (launches) *launches = c->t_cnt[which];
+    return DGK_OK;
+}
+
+int dgk_check_conversions(const double *x, size_t n, int on_device, unsigned long long *mismatches)
+{
+    if (!x || !mismatches) return fail(DGK_ERR_ARG, "null argument");
+    double *dx = nullptr;
+    unsigned long long *dbad = nullptr;
+    DGK_CUDA(cudaMalloc(&dbad, sizeof(unsigned long long)));
+    DGK_CUDA(cudaMemset(dbad, 0, sizeof(unsigned long long)));
+    if (on_device) {
+        dx = const_cast<double *>(x);
+    } else {
+        DGK_CUDA(cudaMalloc(&dx, n * sizeof(double)));
+        DGK_CUDA(cudaMemcpy(dx, x, n * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    if (n) k_check_conv<<<(unsigned)((n + 255) / 256), 256>>>(dx, (long long)n, dbad);
+    cudaError_t err = cudaDeviceSynchronize();
+    if (err == cudaSuccess) err = cudaMemcpy(mismatches, dbad, sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (!on_device) cudaFree(dx);
+    cudaFree(dbad);
+    if (err != cudaSuccess) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
+    return DGK_OK;
+}
+
+int dgk_maxwell(double T, double *rv, double *rl)
+{
+    if (!rv || !rl) return fail(DGK_ERR_ARG, "null output");
+    if (!dgk::host::maxwell(T, *rv, *rl)) return fail(DGK_ERR_THERMO, "no saturation states at this temperature");
+    return DGK_OK;
+}
+
+int dgk_sigma_vl(double T, double cv, double gammaK, double *sigma)
+{
+    (void)cv;  // the cv term of the free energy is linear in rho and drops out
+    if (!sigma || !(gammaK > 0)) return fail(DGK_ERR_ARG, "bad arguments");
+    if (!dgk::host::sigma_vl(T, gammaK, *sigma)) return fail(DGK_ERR_THERMO, "no saturation states at this temperature");
+    return DGK_OK;
+}
+
+int dgk_interface_width(double T, double cv, double gammaK, double *width)
+{
+    double rv, rl, sig;
+    int rc = dgk_maxwell(T, &rv, &rl);
+    if (rc) return rc;
+    if ((rc = dgk_sigma_vl(T, cv, gammaK, &sig))) return rc;
+    if (!width) return fail(DGK_ERR_ARG, "null output");
+    *width = std::sqrt(2.0) * gammaK * (rl - rv) * (rl - rv) / sig;
+    return DGK_OK;
+}
+
+}  // extern "C"

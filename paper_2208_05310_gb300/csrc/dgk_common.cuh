@@ -1,0 +1,359 @@
+// dgk_common.cuh -- device-side data structures, node indexing and the point-wise model
+// of the relaxed non-isothermal NSK equations (Keim, Munz & Rohde, arXiv 2208.05310).
+//
+// R is the "bulk" arithmetic type (double for the FP64 form, float for the FP32-bulk
+// form).  The energy balance of the temperature recovery is always done in double.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dgk {
+
+// van der Waals constants in the paper's non-dimensional form (Sec. 2.1).
+constexpr double kRgas = 8.0 / 3.0;
+constexpr double kAvdw = 3.0;
+constexpr double kBvdw = 1.0 / 3.0;
+constexpr int kMaxP = 6;  // polynomial degree N <= 5
+
+// device status bits (latched with atomicOr, read by dgk_status)
+constexpr unsigned kStatNonFinite = 1u;
+constexpr unsigned kStatDomain = 2u;
+
+struct Phys {
+    int model;  // 1 or 2
+    double gK, mu, kap, cv, alpha, beta;
+    double half_alpha, half_gK, inv_Rcv;  // derived on the host
+};
+
+// The same constants in the bulk type R, derived on the host so that kernels of the
+// FP32-bulk form convert nothing from double per node.
+template <typename R>
+struct PhysR {
+    int model;
+    R gK, mu, kap, alpha, beta;
+    R gKbeta, alphabeta, half_alpha, half_gK, two_thirds_mu;
+    R s_coef;   // R_gas (1 + 1/cv)
+    R inv_Rcv;  // 1 / (R_gas cv)
+    R half_alpha_p;  // alpha/2 in the model-2 pressure, 0 for model 1
+};
+
+// Per box face (-x,+x,-y,+y,-z,+z): isothermal no-slip wall with static contact angle.
+// Contact-angle gradient: grad c . n = K (c - rl)(c - rv), K = -6 sigma cos(theta) /
+// (gamma_K (rl - rv)^3)  (Eq. bc_contactangle_alpha with gamma_1 = 0 and Eq.
+// helmfreesurftot_derivative).
+struct Walls {
+    int kind[6];
+    double Tw[6], rv[6], rl[6], K[6];
+};
+
+struct Geom {
+    int n[3];
+    int periodic[3];
+    double inv2h[3];  // 2 / h_d: d/dx = (2/h) d/dxi on the affine element
+    long long ne;
+};
+
+template <typename R>
+struct GeomR {
+    R inv2h[3];
+};
+
+template <typename R>
+struct WallsR {
+    R K[6], rl[6], rv[6], Tw[6];
+};
+
+// 1D operators on the P = N+1 Legendre-Gauss nodes (Sec. 3.1):
+//   Dhat_ij = -(w_j / w_i) D_ji, Lp_i = l_i(+1)/w_i, Lm_i = l_i(-1)/w_i, lp/lm = l_i(+-1),
+//   w = quadrature weights.
+struct Ops {
+    double Dhat[kMaxP * kMaxP];
+    double Lp[kMaxP], Lm[kMaxP], lp[kMaxP], lm[kMaxP], w[kMaxP];
+};
+
+// ------------------------------------------------------------------ sizes
+
+template <int D, int N>
+struct Shape {
+    static constexpr int P = N + 1;
+    static constexpr int NP = D == 2 ? P * P : P * P * P;   // nodes per element
+    static constexpr int NFP = D == 2 ? P : P * P;          // points per face
+    static constexpr int NF = 2 * D;                        // faces per element
+    static constexpr int NV = D + 3;                        // conserved variables
+    static constexpr int NL = D + 2;                        // pass-1 lifted variables (rho, u, c)
+    static constexpr int NQ = NV + D * D + 2 * D + 1;       // face quantities: U, grad u, grad T, grad c, lap c
+    static constexpr int NFQ = NF * NFP;                    // face points per element
+    static constexpr int EPB = (256 / NP) > 0 ? (256 / NP) : 1;  // elements per block
+    static constexpr int NT = EPB * NP;                     // threads per block
+};
+
+// node n = i + P*(j + P*k); coordinate along direction d
+template <int P>
+__device__ __forceinline__ int ncoord(int n, int d)
+{
+    return d == 0 ? n % P : (d == 1 ? (n / P) % P : n / (P * P));
+}
+
+// face-point index of node n on the faces normal to d (remaining coordinates in order)
+template <int P>
+__device__ __forceinline__ int node_fp(int n, int d)
+{
+    return d == 0 ? n / P : (d == 1 ? (n % P) + P * (n / (P * P)) : n % (P * P));
+}
+
+// first node of the line through face point fp along d, and the stride along d
+template <int P>
+__device__ __forceinline__ int line_base(int fp, int d)
+{
+    return d == 0 ? P * fp : (d == 1 ? (fp % P) + P * P * (fp / P) : fp);
+}
+template <int P>
+__device__ __forceinline__ int line_stride(int d)
+{
+    return d == 0 ? 1 : (d == 1 ? P : P * P);
+}
+
+// neighbours of element e across its 2D faces (f = 2*dir + side); -1 at a wall
+template <int D>
+__device__ __forceinline__ void neighbours(const Geom &g, long long e, long long nb[6])
+{
+    const unsigned ue = (unsigned)e, n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+    int c[3];
+    c[0] = (int)(ue % n0);
+    c[1] = (int)((ue / n0) % n1);
+    c[2] = D == 3 ? (int)(ue / (n0 * n1)) : 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            int cc[3] = {c[0], c[1], c[2]};
+            cc[d] += s ? 1 : -1;
+            long long r;
+            if (cc[d] < 0 || cc[d] >= g.n[d]) {
+                if (!g.periodic[d]) { nb[2 * d + s] = -1; continue; }
+                cc[d] = (cc[d] + g.n[d]) % g.n[d];
+            }
+            r = cc[0] + (long long)g.n[0] * (cc[1] + (long long)g.n[1] * cc[2]);
+            nb[2 * d + s] = r;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ conversions
+//
+// binary64 <-> binary32 conversions written from the IEEE 754 encodings, in integer
+// arithmetic.  On this GPU every FP64-pipe instruction, conversions included, issues at
+// 1/64 of the FP32 rate, so the FP32-bulk kernels convert with integer instructions.
+// d2f rounds to nearest even; results below the float normal range flush to signed
+// zero, results above it round to +-inf, NaN stays NaN.  f2d is exact (subnormal floats
+// become signed zero).
+
+__device__ __forceinline__ float d2f(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const unsigned ed = (hi >> 20) & 0x7ffu;
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // leading 23 fraction bits
+    const unsigned rest = lo & 0x1fffffffu;                  // the 29 dropped bits
+    const int ef = (int)ed - 896;                            // exponent bias 1023 -> 127
+    unsigned r = ((unsigned)ef << 23) + m;
+    r += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    if (ef <= 0) r = 0u;
+    if (ef >= 255) r = 0x7f800000u;
+    if (ed == 0x7ffu) r = (m | rest) ? 0x7fc00000u : 0x7f800000u;
+    return __uint_as_float(sign | r);
+}
+
+__device__ __forceinline__ double f2d(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned sign = u & 0x80000000u, ef = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned hi = sign | ((ef + 896u) << 20) | (m >> 3);
+    unsigned lo = m << 29;
+    if (ef == 0u) { hi = sign; lo = 0u; }
+    if (ef == 255u) { hi = sign | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u); lo = m << 29; }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// bulk <- double and double <- bulk (identity for the FP64 form)
+template <typename R>
+__device__ __forceinline__ R to_bulk(double x)
+{
+    if constexpr (sizeof(R) == 8) return x;
+    else return d2f(x);
+}
+template <typename R>
+__device__ __forceinline__ double to_f64(R x)
+{
+    if constexpr (sizeof(R) == 8) return x;
+    else return f2d(x);
+}
+
+// finiteness of a double from its exponent field (no FP64 instruction)
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return ((((unsigned long long)__double_as_longlong(x)) >> 52) & 0x7ffull) != 0x7ffull;
+}
+
+// ------------------------------------------------------------------ thermodynamics
+
+// Temperature from the total energy, Eq. (totalenergyalpha), with the vdW internal
+// energy rho eps = rho R cv T - a rho^2:
+//   rho R cv T = rho e + a rho^2 - (|m|^2/(2 rho) + alpha/2 (rho-c)^2 + gamma_K/2 |grad c|^2).
+// FP64 form: all in double.  FP32-bulk form: rho e + a rho^2 in double from the FP64
+// state, the small kinetic / relaxation / capillary terms and the scaling by
+// 1/(rho R cv) in float.  irho = 1/rho and d = rho - c in the bulk type; msq = |m|^2,
+// gc2 = |grad c|^2.
+template <typename R>
+__device__ __forceinline__ R temperature(const Phys &ph, const PhysR<R> &pr, double rho, R irho, double E, R d,
+                                         R msq, R gc2)
+{
+    if constexpr (sizeof(R) == 8) {
+        double num = E + kAvdw * rho * rho - 0.5 * msq * irho - ph.half_alpha * d * d - ph.half_gK * gc2;
+        return num * irho * ph.inv_Rcv;
+    } else {
+        const float small = 0.5f * msq * irho + pr.half_alpha * d * d + pr.half_gK * gc2;
+        const float bal = d2f(fma(kAvdw * rho, rho, E));
+        return (bal - small) * irho * pr.inv_Rcv;
+    }
+}
+
+// Pressure in the convective flux, Eq. (pressure), plus alpha/2 rho^2 for model 2
+// (Eq. modified_pressure); iomb = 1/(1 - b rho).
+template <typename R>
+__device__ __forceinline__ R flux_pressure(const PhysR<R> &pr, R rho, R T, R iomb)
+{
+    return rho * R(kRgas) * T * iomb + (pr.half_alpha_p - R(kAvdw)) * rho * rho;
+}
+
+// Signal speed sqrt(c_s^2 + alpha rho) with the vdW isentropic
+// c_s^2 = R T (1 + 1/cv)/(1 - b rho)^2 - 2 a rho (Eq. speedofsound, Sec. 2.3).
+template <typename R>
+__device__ __forceinline__ R signal_speed(const PhysR<R> &pr, R rho, R T, R iomb)
+{
+    R s2 = pr.s_coef * T * iomb * iomb + (pr.alpha - R(2.0 * kAvdw)) * rho;
+    return s2 > R(0) ? sqrt(s2) : R(0);
+}
+
+// ------------------------------------------------------------------ fluxes and sources
+//
+// du[i][k] = d u_k / d x_i, gT = grad T, gc = grad c, lap = lap c.
+
+// F = F^C - F^V in direction dir (Eq. navierstokeskorteweg_p / _palpha):
+//   F^C = (m_dir, m u_dir + p^ e_dir, (rho e + p^) u_dir, c u_dir)
+//   F^V = (0, tau_{., dir}, tau_{dir, .}.u + j_e,dir, gamma_K beta c_dir)
+//   tau = mu (grad u + grad u^T - 2/3 div u I),
+//   j_e = kappa grad T - gamma_K c grad c div u + gamma_K grad c zeta,
+//   zeta = beta (gamma_K lap c + alpha (rho - c)).
+template <int D, typename R>
+__device__ __forceinline__ void flux_dir(const PhysR<R> &ph, int dir, R rho, const R *m, const R *u, R E, R c, R ph_,
+                                         const R du[D][D], const R *gT, const R *gc, R lap, R *F)
+{
+    R divu = R(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) divu += du[k][k];
+    const R mu = ph.mu;
+    R ud = u[dir];
+    R work = R(0);
+    F[0] = m[dir];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        R tau = mu * (du[dir][k] + du[k][dir]);
+        if (k == dir) tau -= ph.two_thirds_mu * divu;
+        work += tau * u[k];
+        F[1 + k] = m[k] * ud - tau;
+        if (k == dir) F[1 + k] += ph_;
+    }
+    R zeta = ph.beta * (ph.gK * lap + ph.alpha * (rho - c));
+    R je = ph.kap * gT[dir] - ph.gK * c * gc[dir] * divu + ph.gK * gc[dir] * zeta;
+    F[D + 1] = (E + ph_) * ud - (work + je);
+    F[D + 2] = c * ud - ph.gKbeta * gc[dir];
+}
+
+// Point-wise source with the lifted gradients (Sec. 3.1); model 1 / model 2 rows of
+// Eq. (navierstokeskorteweg_p) / (..._palpha).  g[i][v]: gradient in direction i of
+// lifted variable v = (rho, u_1..u_D, c).
+template <int D, typename R>
+__device__ __forceinline__ void source_terms(const PhysR<R> &ph, R rho, const R *u, R c, const R g[D][D + 2], R *S)
+{
+    const R al = ph.alpha;
+    R divu = R(0), gc2 = R(0), ccdu = R(0), work = R(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        divu += g[k][1 + k];
+        gc2 += g[k][D + 1] * g[k][D + 1];
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) ccdu += g[i][D + 1] * g[j][D + 1] * g[i][1 + j];
+    S[0] = R(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        R drive = ph.model == 1 ? g[k][D + 1] - g[k][0] : g[k][D + 1];
+        S[1 + k] = al * rho * drive;
+        work += S[1 + k] * u[k];
+    }
+    R pw = ph.model == 1 ? R(0.5) * al * (c * c - rho * rho) : R(0.5) * al * c * c;
+    S[D + 1] = work + pw * divu + ph.gK * (R(0.5) * gc2 * divu - ccdu);
+    S[D + 2] = ph.alphabeta * (rho - c);
+}
+
+// Numerical flux in +e_dir through a wall face whose outward normal is nsign*e_dir
+// (Sec. 2.4, Eq. bc_nsk_alpha, gamma_1 = gamma_2 = gamma_4 = 0): Rusanov flux against
+// the mirrored ghost (rho, m - 2(m.n)n, rho e, c) with equal pressure and signal speed,
+// minus the wall viscous flux (tau(grad u).n, kappa grad T.n - gamma_K c gn div u,
+// gamma_K beta gn) with gn = grad c . n from the contact angle; u_wall = 0, zeta = 0.
+template <int D, typename R>
+__device__ __forceinline__ void wall_flux(const PhysR<R> &ph, int dir, R nsign, R rho, R irho, const R *m, R E, R c,
+                                          R ph_, R lam, const R du[D][D], const R *gT, R gn, R *F)
+{
+    R u[D], mg[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) { u[k] = m[k] * irho; mg[k] = m[k]; }
+    mg[dir] = -m[dir];
+    // convective fluxes of the interior and the ghost state in +e_dir
+    R Fi[D + 3], Fg[D + 3];
+    R ui = u[dir], ug = -u[dir];
+    Fi[0] = m[dir];
+    Fg[0] = mg[dir];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        Fi[1 + k] = m[k] * ui + (k == dir ? ph_ : R(0));
+        Fg[1 + k] = mg[k] * ug + (k == dir ? ph_ : R(0));
+    }
+    Fi[D + 1] = (E + ph_) * ui;
+    Fg[D + 1] = (E + ph_) * ug;
+    Fi[D + 2] = c * ui;
+    Fg[D + 2] = c * ug;
+    R Ui[D + 3], Ug[D + 3];
+    Ui[0] = Ug[0] = rho;
+#pragma unroll
+    for (int k = 0; k < D; ++k) { Ui[1 + k] = m[k]; Ug[1 + k] = mg[k]; }
+    Ui[D + 1] = Ug[D + 1] = E;
+    Ui[D + 2] = Ug[D + 2] = c;
+    const bool plus = nsign > R(0);
+#pragma unroll
+    for (int v = 0; v < D + 3; ++v) {
+        R FL = plus ? Fi[v] : Fg[v], FR = plus ? Fg[v] : Fi[v];
+        R UL = plus ? Ui[v] : Ug[v], UR = plus ? Ug[v] : Ui[v];
+        F[v] = R(0.5) * (FL + FR) - R(0.5) * lam * (UR - UL);
+    }
+    // viscous normal flux (outward), subtracted as nsign * Fv in +e_dir
+    R divu = R(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) divu += du[k][k];
+    const R mu = ph.mu;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        R tau = mu * (du[dir][k] + du[k][dir]);
+        if (k == dir) tau -= ph.two_thirds_mu * divu;
+        F[1 + k] -= tau;  // nsign * (tau * nsign)
+    }
+    F[D + 1] -= ph.kap * gT[dir] - nsign * ph.gK * c * gn * divu;
+    F[D + 2] -= nsign * ph.gKbeta * gn;
+}
+
+}  // namespace dgk

@@ -1,0 +1,822 @@
+// dgk_kernels.cuh -- the three kernels of one RK stage of the DGSEM relaxed-NSK scheme,
+// plus set-up kernels (pass-1 traces of a new state, nodal temperature / energy).
+//
+// One stage = three launches; each kernel depends on face data of its neighbours that
+// the previous launch produced (BR1 pass 1 -> temperature -> pass 2 -> face flux):
+//   k_lift1      lifts c only (the temperature needs grad c), recovers T at the nodes and
+//                writes the face traces of T and of dc/dx_normal (inputs of pass 2)
+//   k_lift2vol   BR1 pass 1 of (rho, u, c) (recomputed, not stored), T, pass 2 (grad T,
+//                lap c), point fluxes and sources, volume integral with Dhat per
+//                direction -> U_t(vol); face traces -> one-sided face data (U-, F-, lambda-)
+//   k_surf_rk    Rusanov + central viscous flux per face point, surface lifting with
+//                l(+-1)/w, Jacobian 2/h, RK stage update in FP64, new pass-1 traces
+//
+// Thread layout: one thread per node for point-wise work (EPB elements per block).  The
+// tensor-product contractions are done line by line ("sum factorisation"): a thread
+// loads the P values of one line into registers and produces all P outputs, and both
+// end-point traces, with the operator entries read as uniform kernel-parameter
+// constants.  Element-local fields are staged in shared memory.
+#pragma once
+
+#include "dgk_common.cuh"
+
+namespace dgk {
+
+// 1D operators in the bulk type (see Ops).
+template <typename R>
+struct OpsR {
+    R Dh[kMaxP * kMaxP];
+    R Lp[kMaxP], Lm[kMaxP], lp[kMaxP], lm[kMaxP];
+};
+
+template <typename R>
+struct KArgs {
+    Geom g;
+    GeomR<R> gr;
+    Phys ph;
+    PhysR<R> pr;
+    WallsR<R> wr;
+    OpsR<R> op;
+    double *U;           // [NV][ne][NP]
+    double *G;           // [NV][ne][NP]
+    R *Utv;              // [NV][ne][NP] volume part of U_t
+    R *tr1;              // [NL][ne][NF][NFP] pass-1 traces of (rho, u, c)
+    R *tr2;              // [2][ne][NF][NFP] traces of T and of d c / d x_normal
+    R *fd;               // [NV+NV+1][ne][NF][NFP] one-sided face data (U, F, lambda)
+    double *out;         // rhs output [NV][ne][NP], or nodal T [ne][NP]
+    const double *coef;  // device [A_0..A_4, B_0..B_4, dt]
+    unsigned *status;
+};
+
+// ------------------------------------------------------------------ line helpers
+
+template <int P, typename R>
+__device__ __forceinline__ void load_line(const R *f, int base, int stride, R x[P])
+{
+#pragma unroll
+    for (int l = 0; l < P; ++l) x[l] = f[base + l * stride];
+}
+
+template <int P, typename R>
+__device__ __forceinline__ void store_line(R *f, int base, int stride, const R y[P])
+{
+#pragma unroll
+    for (int l = 0; l < P; ++l) f[base + l * stride] = y[l];
+}
+
+// BR1 lifting along one line (Sec. 3.1, weak form, collocated Gauss quadrature):
+//   y_i = (2/h) [ sum_l Dhat_il x_l + Lp_i q*_+ - Lm_i q*_- ]
+template <int P, typename R>
+__device__ __forceinline__ void lift_line(const OpsR<R> &o, const R x[P], R qm, R qp, R s, R y[P])
+{
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        R acc = R(0);
+#pragma unroll
+        for (int l = 0; l < P; ++l) acc += o.Dh[i * P + l] * x[l];
+        acc += o.Lp[i] * qp - o.Lm[i] * qm;
+        y[i] = s * acc;
+    }
+}
+
+// y_i = s sum_l Dhat_il x_l (volume integral of one flux line)
+template <int P, typename R>
+__device__ __forceinline__ void dhat_line(const OpsR<R> &o, const R x[P], R s, R y[P])
+{
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        R acc = R(0);
+#pragma unroll
+        for (int l = 0; l < P; ++l) acc += o.Dh[i * P + l] * x[l];
+        y[i] = s * acc;
+    }
+}
+
+// traces of one line at xi = -1 and xi = +1
+template <int P, typename R>
+__device__ __forceinline__ void trace_pair(const OpsR<R> &o, const R x[P], R &tm, R &tp)
+{
+    R am = R(0), ap = R(0);
+#pragma unroll
+    for (int l = 0; l < P; ++l) {
+        am += o.lm[l] * x[l];
+        ap += o.lp[l] * x[l];
+    }
+    tm = am;
+    tp = ap;
+}
+
+template <int NF, int NFP>
+__device__ __forceinline__ long long fidx(long long ne, int v, long long e, int f, int fp)
+{
+    return (((long long)v * ne + e) * NF + f) * NFP + fp;
+}
+
+template <typename R>
+__device__ __forceinline__ void check_state(unsigned *status, R rho, R T, double E)
+{
+    unsigned s = 0;
+    if (!isfinite(rho) || !isfinite(T) || !finite_bits(E)) s |= kStatNonFinite;
+    else if (!(rho > R(0) && rho < R(1.0 / kBvdw) && T > R(0))) s |= kStatDomain;
+    if (s) atomicOr(status, s);
+}
+
+// Common per-thread prologue: local element, node, validity, element coordinates.
+// Neighbours are computed on demand (no per-thread array indexed at run time).
+template <int D, int N>
+struct Slot {
+    using S = Shape<D, N>;
+    int le, n;
+    long long e;
+    bool valid;
+    int cx, cy, cz;
+    __device__ Slot(const Geom &g)
+    {
+        le = threadIdx.x / S::NP;
+        n = threadIdx.x % S::NP;
+        e = (long long)blockIdx.x * S::EPB + le;
+        valid = e < g.ne;
+        const unsigned ue = valid ? (unsigned)e : 0u, n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+        cx = (int)(ue % n0);
+        cy = (int)((ue / n0) % n1);
+        cz = D == 3 ? (int)(ue / (n0 * n1)) : 0;
+    }
+    // neighbour across face f = 2*dir + side, or -1 at a wall
+    __device__ __forceinline__ long long nbr(const Geom &g, int f) const
+    {
+        const int dir = f >> 1;
+        const bool plus = f & 1;
+        const int cd = dir == 0 ? cx : (dir == 1 ? cy : cz);
+        const int nd = dir == 0 ? g.n[0] : (dir == 1 ? g.n[1] : g.n[2]);
+        const int per = dir == 0 ? g.periodic[0] : (dir == 1 ? g.periodic[1] : g.periodic[2]);
+        const long long stride = dir == 0 ? 1LL : (dir == 1 ? (long long)g.n[0] : (long long)g.n[0] * g.n[1]);
+        int cn = cd + (plus ? 1 : -1);
+        if (cn < 0 || cn >= nd) {
+            if (!per) return -1;
+            cn = plus ? 0 : nd - 1;
+        }
+        return e + (long long)(cn - cd) * stride;
+    }
+};
+
+// ------------------------------------------------------------------ c-lifting (k_lift1, k_node_T)
+//
+// Lifts c in every direction (BR1 with central c*, one-sided at walls).  On return
+// sDc[d][n] holds dc/dx_d; with write_tr2 the traces of dc/dx_d on the two faces normal
+// to d are written to tr2[1].
+
+template <int D, int N, typename R>
+struct CLift {
+    using S = Shape<D, N>;
+    static constexpr int smem_per_elem = S::NP + S::NF * S::NFP + D * S::NP + S::NP;  // c, c*, dc, T
+
+    __device__ static void run(const KArgs<R> &a, const Slot<D, N> &t, R *sC, R *sCs, R *sDc, double Ud[S::NV],
+                               bool write_tr2)
+    {
+        constexpr int P = S::P, NP = S::NP, NF = S::NF, NFP = S::NFP, NV = S::NV;
+        const long long ne = a.g.ne;
+        if (t.valid) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Ud[v] = a.U[((long long)v * ne + t.e) * NP + t.n];
+            sC[t.n] = to_bulk<R>(Ud[D + 2]);
+            for (int q = t.n; q < NF * NFP; q += NP) {
+                const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
+                const R own = a.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
+                const long long b = t.nbr(a.g, f);
+                sCs[q] = b >= 0 ? R(0.5) * (own + a.tr1[fidx<NF, NFP>(ne, D + 1, b, 2 * dir + 1 - side, fp)]) : own;
+            }
+        }
+        __syncthreads();
+        if (t.valid) {
+            for (int q = t.n; q < D * NFP; q += NP) {
+                const int dir = q / NFP, line = q % NFP;
+                const int base = line_base<P>(line, dir), stride = line_stride<P>(dir);
+                R x[P], y[P];
+                load_line<P, R>(sC, base, stride, x);
+                lift_line<P, R>(a.op, x, sCs[(2 * dir) * NFP + line], sCs[(2 * dir + 1) * NFP + line], a.gr.inv2h[dir], y);
+                store_line<P, R>(sDc + dir * NP, base, stride, y);
+                if (write_tr2) {
+                    R tm, tp;
+                    trace_pair<P, R>(a.op, y, tm, tp);
+                    a.tr2[fidx<NF, NFP>(ne, 1, t.e, 2 * dir, line)] = tm;
+                    a.tr2[fidx<NF, NFP>(ne, 1, t.e, 2 * dir + 1, line)] = tp;
+                }
+            }
+        }
+        __syncthreads();
+    }
+};
+
+// Bulk-type copies of one node's conserved state.
+template <int D, typename R>
+struct NodeState {
+    R rho, irho, m[D], E, c;
+    __device__ __forceinline__ void load(const double *Ud)
+    {
+        rho = to_bulk<R>(Ud[0]);
+        irho = R(1) / rho;
+#pragma unroll
+        for (int k = 0; k < D; ++k) m[k] = to_bulk<R>(Ud[1 + k]);
+        E = to_bulk<R>(Ud[D + 1]);
+        c = to_bulk<R>(Ud[D + 2]);
+    }
+};
+
+template <int D, typename R>
+__device__ __forceinline__ R node_temperature(const KArgs<R> &a, const double *Ud, const NodeState<D, R> &q,
+                                              const R *gc)
+{
+    R msq = R(0), gc2 = R(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        msq += q.m[k] * q.m[k];
+        gc2 += gc[k] * gc[k];
+    }
+    const R d = sizeof(R) == 8 ? R(Ud[0] - Ud[D + 2]) : q.rho - q.c;
+    return temperature<R>(a.ph, a.pr, Ud[0], q.irho, Ud[D + 1], d, msq, gc2);
+}
+
+// ------------------------------------------------------------------ kernel 1
+
+template <int D, int N, typename R>
+__global__ void __launch_bounds__(Shape<D, N>::NT) k_lift1(KArgs<R> a)
+{
+    using S = Shape<D, N>;
+    using L = CLift<D, N, R>;
+    constexpr int P = S::P, NP = S::NP, NFP = S::NFP, NF = S::NF, NV = S::NV;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const Slot<D, N> t(a.g);
+    R *sC = reinterpret_cast<R *>(smraw) + (size_t)t.le * L::smem_per_elem;
+    R *sCs = sC + NP, *sDc = sCs + NF * NFP, *sT = sDc + D * NP;
+    double Ud[NV];
+    L::run(a, t, sC, sCs, sDc, Ud, true);
+    if (t.valid) {
+        R gc[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) gc[d] = sDc[d * NP + t.n];
+        NodeState<D, R> q;
+        q.load(Ud);
+        const R T = node_temperature<D, R>(a, Ud, q, gc);
+        check_state<R>(a.status, q.rho, T, Ud[D + 1]);
+        sT[t.n] = T;
+    }
+    __syncthreads();
+    if (t.valid) {
+        const long long ne = a.g.ne;
+        for (int q = t.n; q < D * NFP; q += NP) {
+            const int dir = q / NFP, line = q % NFP;
+            R x[P], tm, tp;
+            load_line<P, R>(sT, line_base<P>(line, dir), line_stride<P>(dir), x);
+            trace_pair<P, R>(a.op, x, tm, tp);
+            a.tr2[fidx<NF, NFP>(ne, 0, t.e, 2 * dir, line)] = tm;
+            a.tr2[fidx<NF, NFP>(ne, 0, t.e, 2 * dir + 1, line)] = tp;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ face flux
+
+// Face record of one face point of a face normal to dir, in the order
+//   U (NV) | d u_k / d x_dir (D) | d u_dir / d x_k, k != dir (D-1) | div u | dT/dx_dir |
+//   grad c (D) | lap c
+template <int D>
+struct FaceRec {
+    static constexpr int NV = D + 3;
+    static constexpr int DDU = NV, DUD = NV + D, DIV = NV + 2 * D - 1, GT = NV + 2 * D, GC = NV + 2 * D + 1,
+                         LAP = NV + 3 * D + 1, NQ = NV + 3 * D + 2;
+};
+
+// One-sided flux F(U-, grads-) in direction DIR (interior faces), or the complete wall
+// flux in +e_DIR (wall faces; Sec. 2.4, Eq. bc_nsk_alpha with gamma_1 = gamma_2 =
+// gamma_4 = 0: Rusanov against the mirrored ghost (rho, m - 2(m.n)n, rho e, c) with equal
+// pressure and signal speed, minus the wall viscous flux with u_wall = 0, zeta = 0 and
+// grad c . n from the contact angle), and the Rusanov signal speed |u_DIR| + s.
+template <int D, typename R, int DIR>
+__device__ __forceinline__ void face_flux(const KArgs<R> &a, int f, bool wall, const R *r, R *F, R &lam)
+{
+    using FR = FaceRec<D>;
+    const PhysR<R> &ph = a.pr;
+    const R rho = r[0], E = r[D + 1], c = r[D + 2], irho = R(1) / rho;
+    R m[D], u[D], msq = R(0), gc2 = R(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        m[k] = r[1 + k];
+        u[k] = m[k] * irho;
+        msq += m[k] * m[k];
+        gc2 += r[FR::GC + k] * r[FR::GC + k];
+    }
+    // temperature of the interpolated face state (bulk type: the face state itself is
+    // an interpolation in the bulk type)
+    const R T = (E + R(kAvdw) * rho * rho - R(0.5) * msq * irho - ph.half_alpha * (rho - c) * (rho - c) -
+                 ph.half_gK * gc2) * irho * ph.inv_Rcv;
+    const R iomb = R(1) / (R(1) - R(kBvdw) * rho);
+    const R pf = flux_pressure<R>(ph, rho, T, iomb);
+    lam = fabs(u[DIR]) + signal_speed<R>(ph, rho, T, iomb);
+    const R divu = r[FR::DIV];
+    // viscous stress column tau_{k, DIR} = mu (du_k/dx_DIR + du_DIR/dx_k) - 2/3 mu div u delta
+    R tau[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const R dudk = k == DIR ? r[FR::DDU + DIR] : r[FR::DUD + (k < DIR ? k : k - 1)];
+        tau[k] = ph.mu * (r[FR::DDU + k] + dudk);
+        if (k == DIR) tau[k] -= ph.two_thirds_mu * divu;
+    }
+    const R gTd = r[FR::GT], gcd = r[FR::GC + DIR], lap = r[FR::LAP];
+    if (!wall) {
+        R work = R(0);
+        F[0] = m[DIR];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            work += tau[k] * u[k];
+            F[1 + k] = m[k] * u[DIR] - tau[k] + (k == DIR ? pf : R(0));
+        }
+        const R zeta = ph.beta * (ph.gK * lap + ph.alpha * (rho - c));
+        const R je = ph.kap * gTd - ph.gK * c * gcd * divu + ph.gK * gcd * zeta;
+        F[D + 1] = (E + pf) * u[DIR] - (work + je);
+        F[D + 2] = c * u[DIR] - ph.gKbeta * gcd;
+        return;
+    }
+    const R nsign = (f & 1) ? R(1) : R(-1);
+    const R gn = a.wr.K[f] * (c - a.wr.rl[f]) * (c - a.wr.rv[f]);
+    R Fi[D + 3], Fg[D + 3], Ui[D + 3], Ug[D + 3];
+    const R ui = u[DIR], ug = -u[DIR];
+    Fi[0] = m[DIR];
+    Fg[0] = -m[DIR];
+    Ui[0] = Ug[0] = rho;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const R mg = k == DIR ? -m[k] : m[k];
+        Fi[1 + k] = m[k] * ui + (k == DIR ? pf : R(0));
+        Fg[1 + k] = mg * ug + (k == DIR ? pf : R(0));
+        Ui[1 + k] = m[k];
+        Ug[1 + k] = mg;
+    }
+    Fi[D + 1] = (E + pf) * ui;
+    Fg[D + 1] = (E + pf) * ug;
+    Fi[D + 2] = c * ui;
+    Fg[D + 2] = c * ug;
+    Ui[D + 1] = Ug[D + 1] = E;
+    Ui[D + 2] = Ug[D + 2] = c;
+    const bool plus = nsign > R(0);
+#pragma unroll
+    for (int v = 0; v < D + 3; ++v) {
+        const R FL = plus ? Fi[v] : Fg[v], FRr = plus ? Fg[v] : Fi[v];
+        const R UL = plus ? Ui[v] : Ug[v], UR = plus ? Ug[v] : Ui[v];
+        F[v] = R(0.5) * (FL + FRr) - R(0.5) * lam * (UR - UL);
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) F[1 + k] -= tau[k];
+    F[D + 1] -= ph.kap * gTd - nsign * ph.gK * c * gn * divu;
+    F[D + 2] -= nsign * ph.gKbeta * gn;
+}
+
+// Face record of face point (f, fp) with f normal to DIR, traced from the nodal fields
+// in shared memory along the line through fp (one end), then its face data.
+template <int D, int N, typename R, int DIR>
+__device__ __forceinline__ void face_point(const KArgs<R> &a, long long e, bool wall, int f, int fp, const R *sG,
+                                           const R *sGT, const R *sN)
+{
+    using S = Shape<D, N>;
+    using FR = FaceRec<D>;
+    constexpr int P = S::P, NP = S::NP, NL = S::NL, NV = S::NV, NQ = FR::NQ, NF = S::NF, NFP = S::NFP;
+    const int base = line_base<P>(fp, DIR);
+    constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? P : P * P);
+    const bool side = f & 1;
+    R L[P];
+#pragma unroll
+    for (int l = 0; l < P; ++l) L[l] = side ? a.op.lp[l] : a.op.lm[l];
+    R r[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        const R *src;
+        if (k < FR::DDU) src = sN + k * NP;
+        else if (k < FR::DUD) src = sG + (DIR * NL + 1 + (k - FR::DDU)) * NP;
+        else if (k < FR::DIV) src = sG + (((k - FR::DUD) < DIR ? (k - FR::DUD) : (k - FR::DUD) + 1) * NL + 1 + DIR) * NP;
+        else if (k == FR::DIV) src = sN + NV * NP;
+        else if (k == FR::GT) src = sGT + DIR * NP;
+        else if (k < FR::LAP) src = sG + ((k - FR::GC) * NL + D + 1) * NP;
+        else src = sN + (NV + 1) * NP;
+        R acc = R(0);
+#pragma unroll
+        for (int l = 0; l < P; ++l) acc += L[l] * src[base + l * stride];
+        r[k] = acc;
+    }
+    R F[NV], lam;
+    face_flux<D, R, DIR>(a, f, wall, r, F, lam);
+    const long long ne = a.g.ne;
+    const long long st = ne * NF * NFP;
+    const long long fo = (e * NF + f) * NFP + fp;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        a.fd[v * st + fo] = r[v];
+        a.fd[(NV + v) * st + fo] = F[v];
+    }
+    a.fd[(2 * NV) * st + fo] = lam;
+}
+
+// ------------------------------------------------------------------ kernel 2
+
+template <int D, int N, typename R>
+struct K2Smem {
+    using S = Shape<D, N>;
+    static constexpr int G = D * S::NL * S::NP;  // pass-1 gradients sG[d][v][n]
+    static constexpr int GT = D * S::NP;         // grad T
+    static constexpr int X1 = S::NL * S::NP + S::NF * S::NL * S::NFP;  // prims, q*
+    static constexpr int X2 = S::NP + 2 * S::NF * S::NFP + D * S::NP;  // T, T*, Dc*, lap parts
+    static constexpr int X4 = 2 * S::NV * S::NP;                       // volume: F, acc
+    static constexpr int X3 = X4 + (S::NV + 2) * S::NP;                // nodal U/div/lap after acc
+    static constexpr int XA = X1 > X2 ? X1 : X2;
+    static constexpr int X = XA > X3 ? XA : X3;
+    static constexpr int per_elem = G + GT + X;
+};
+
+template <int D, int N, typename R>
+__global__ void __launch_bounds__(Shape<D, N>::NT) k_lift2vol(KArgs<R> a)
+{
+    using S = Shape<D, N>;
+    using M = K2Smem<D, N, R>;
+    constexpr int P = S::P, NP = S::NP, NFP = S::NFP, NF = S::NF, NL = S::NL, NV = S::NV;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const Slot<D, N> t(a.g);
+    R *sG = reinterpret_cast<R *>(smraw) + (size_t)t.le * M::per_elem;
+    R *sGT = sG + M::G, *sX = sGT + M::GT;
+    const long long ne = a.g.ne;
+    const int n = t.n;
+
+    // ---- pass 1: prims (rho, u, c) and central face values (one-sided rho, c and u* = 0 at walls)
+    R *sQ = sX, *sQs = sX + NL * NP;
+    double Ud[NV];
+    NodeState<D, R> ns;
+    if (t.valid) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Ud[v] = a.U[((long long)v * ne + t.e) * NP + n];
+        ns.load(Ud);
+        sQ[n] = ns.rho;
+#pragma unroll
+        for (int k = 0; k < D; ++k) sQ[(1 + k) * NP + n] = ns.m[k] * ns.irho;
+        sQ[(D + 1) * NP + n] = ns.c;
+        for (int q = n; q < NF * NFP; q += NP) {
+            const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
+            const long long b = t.nbr(a.g, f);
+#pragma unroll
+            for (int v = 0; v < NL; ++v) {
+                const R own = a.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)];
+                R val;
+                if (b >= 0) val = R(0.5) * (own + a.tr1[fidx<NF, NFP>(ne, v, b, 2 * dir + 1 - side, fp)]);
+                else val = (v >= 1 && v <= D) ? R(0) : own;
+                sQs[(f * NL + v) * NFP + fp] = val;
+            }
+        }
+    }
+    __syncthreads();
+    if (t.valid) {
+#pragma unroll
+        for (int dir = 0; dir < D; ++dir) {
+            const int stride = line_stride<P>(dir);
+            for (int q = n; q < NL * NFP; q += NP) {
+                const int v = q / NFP, line = q % NFP;
+                const int base = line_base<P>(line, dir);
+                R x[P], y[P];
+                load_line<P, R>(sQ + v * NP, base, stride, x);
+                lift_line<P, R>(a.op, x, sQs[((2 * dir) * NL + v) * NFP + line], sQs[((2 * dir + 1) * NL + v) * NFP + line],
+                                a.gr.inv2h[dir], y);
+                store_line<P, R>(sG + (dir * NL + v) * NP, base, stride, y);
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- node: gradients, temperature; pass-2 central face values
+    R g[D][D + 2];
+    R T = R(0);
+    R *sT = sX, *sTs = sX + NP, *sDs = sTs + NF * NFP, *sLp = sDs + NF * NFP;
+    if (t.valid) {
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+#pragma unroll
+            for (int v = 0; v < NL; ++v) g[d][v] = sG[(d * NL + v) * NP + n];
+        R gc[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) gc[d] = g[d][D + 1];
+        T = node_temperature<D, R>(a, Ud, ns, gc);
+        sT[n] = T;
+        for (int q = n; q < NF * NFP; q += NP) {
+            const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
+            const long long b = t.nbr(a.g, f);
+            const R ownT = a.tr2[fidx<NF, NFP>(ne, 0, t.e, f, fp)];
+            const R ownD = a.tr2[fidx<NF, NFP>(ne, 1, t.e, f, fp)];
+            R vT, vD;
+            if (b >= 0) {
+                const int fo = 2 * dir + 1 - side;
+                vT = R(0.5) * (ownT + a.tr2[fidx<NF, NFP>(ne, 0, b, fo, fp)]);
+                vD = R(0.5) * (ownD + a.tr2[fidx<NF, NFP>(ne, 1, b, fo, fp)]);
+            } else {
+                const R cm = a.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
+                const R gn = a.wr.K[f] * (cm - a.wr.rl[f]) * (cm - a.wr.rv[f]);
+                vT = a.wr.Tw[f];
+                vD = side ? gn : -gn;
+            }
+            sTs[q] = vT;
+            sDs[q] = vD;
+        }
+    }
+    __syncthreads();
+
+    // ---- pass 2: grad T (-> sGT) and the per-direction parts of lap c (-> sLp);
+    //      tasks 0..D*NFP-1 lift T, the next D*NFP lift dc/dx_dir along dir
+    if (t.valid) {
+        for (int q = n; q < 2 * D * NFP; q += NP) {
+            const bool isT = q < D * NFP;
+            const int qq = isT ? q : q - D * NFP;
+            const int dir = qq / NFP, line = qq % NFP;
+            const int base = line_base<P>(line, dir), stride = line_stride<P>(dir);
+            const R *src = isT ? sT : sG + (dir * NL + D + 1) * NP;
+            const R *qs = isT ? sTs : sDs;
+            R *dst = isT ? sGT + dir * NP : sLp + dir * NP;
+            R x[P], y[P];
+            load_line<P, R>(src, base, stride, x);
+            lift_line<P, R>(a.op, x, qs[(2 * dir) * NFP + line], qs[(2 * dir + 1) * NFP + line], a.gr.inv2h[dir], y);
+            store_line<P, R>(dst, base, stride, y);
+        }
+    }
+    __syncthreads();
+    R gT[D], lap = R(0);
+    R rho = R(0), E = R(0), c = R(0), m[D], u[D], du[D][D], gc[D], S_[NV], pf = R(0);
+    if (t.valid) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            gT[d] = sGT[d * NP + n];
+            lap += sLp[d * NP + n];
+        }
+        rho = ns.rho;
+        E = ns.E;
+        c = ns.c;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            m[k] = ns.m[k];
+            u[k] = m[k] * ns.irho;
+            gc[k] = g[k][D + 1];
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) du[k][kk] = g[k][1 + kk];
+        }
+        pf = flux_pressure<R>(a.pr, rho, T, R(1) / (R(1) - R(kBvdw) * rho));
+        source_terms<D, R>(a.pr, rho, u, c, g, S_);
+    }
+    __syncthreads();  // sT, sTs, sDs, sLp are dead before the volume buffers reuse sX
+
+    // ---- volume integral, direction by direction: acc_i += (2/h) sum_l Dhat_il F_l
+    R *sF = sX, *sAcc = sX + NV * NP;
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir) {
+        if (t.valid) {
+            R F[NV];
+            flux_dir<D, R>(a.pr, dir, rho, m, u, E, c, pf, du, gT, gc, lap, F);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sF[v * NP + n] = F[v];
+        }
+        __syncthreads();
+        if (t.valid) {
+            const int stride = line_stride<P>(dir);
+            for (int q = n; q < NV * NFP; q += NP) {
+                const int v = q / NFP, line = q % NFP;
+                const int base = line_base<P>(line, dir);
+                R x[P], y[P];
+                load_line<P, R>(sF + v * NP, base, stride, x);
+                dhat_line<P, R>(a.op, x, a.gr.inv2h[dir], y);
+                if (dir > 0) {
+#pragma unroll
+                    for (int l = 0; l < P; ++l) y[l] += sAcc[v * NP + base + l * stride];
+                }
+                store_line<P, R>(sAcc + v * NP, base, stride, y);
+            }
+        }
+        __syncthreads();
+    }
+    R *sN = sX + M::X4;  // nodal U, div u, lap c (clear of sF, sAcc)
+    if (t.valid) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) a.Utv[((long long)v * ne + t.e) * NP + n] = S_[v] - sAcc[v * NP + n];
+        sN[n] = rho;
+#pragma unroll
+        for (int k = 0; k < D; ++k) sN[(1 + k) * NP + n] = m[k];
+        sN[(D + 1) * NP + n] = E;
+        sN[(D + 2) * NP + n] = c;
+        R divu = R(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) divu += du[k][k];
+        sN[NV * NP + n] = divu;
+        sN[(NV + 1) * NP + n] = lap;
+    }
+    __syncthreads();
+
+    // ---- face data: one face point per task, its record traced directly from the
+    //      nodal fields (interior: one-sided data; wall: the complete wall flux)
+    if (t.valid) {
+        for (int q = n; q < NF * NFP; q += NP) {
+            const int f = q / NFP, fp = q % NFP, dir = f >> 1;
+            const bool wall = t.nbr(a.g, f) < 0;
+            if (dir == 0) face_point<D, N, R, 0>(a, t.e, wall, f, fp, sG, sGT, sN);
+            else if (D == 2 || dir == 1) face_point<D, N, R, 1>(a, t.e, wall, f, fp, sG, sGT, sN);
+            else face_point<D, N, R, (D == 3 ? 2 : 1)>(a, t.e, wall, f, fp, sG, sGT, sN);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ kernel 3
+
+template <int D, int N, typename R>
+struct K3Smem {
+    using S = Shape<D, N>;
+    static constexpr int a1 = S::NF * S::NV * S::NFP;
+    static constexpr int a2 = S::NL * S::NP;
+    static constexpr int per_elem = a1 > a2 ? a1 : a2;
+};
+
+// New pass-1 traces of (rho, u, c) of the element's state (double U -> bulk type).
+template <int D, int N, typename R>
+__device__ __forceinline__ void write_traces(const KArgs<R> &a, const Slot<D, N> &t, R *sQ, const double *Ud)
+{
+    using S = Shape<D, N>;
+    constexpr int P = S::P, NP = S::NP, NFP = S::NFP, NF = S::NF, NL = S::NL;
+    if (t.valid) {
+        const R rho = to_bulk<R>(Ud[0]), irho = R(1) / rho;
+        sQ[t.n] = rho;
+#pragma unroll
+        for (int k = 0; k < D; ++k) sQ[(1 + k) * NP + t.n] = to_bulk<R>(Ud[1 + k]) * irho;
+        sQ[(D + 1) * NP + t.n] = to_bulk<R>(Ud[D + 2]);
+    }
+    __syncthreads();
+    if (t.valid) {
+        const long long ne = a.g.ne;
+        for (int q = t.n; q < D * NL * NFP; q += NP) {
+            const int dir = q / (NL * NFP), v = (q / NFP) % NL, line = q % NFP;
+            R x[P], tm, tp;
+            load_line<P, R>(sQ + v * NP, line_base<P>(line, dir), line_stride<P>(dir), x);
+            trace_pair<P, R>(a.op, x, tm, tp);
+            a.tr1[fidx<NF, NFP>(ne, v, t.e, 2 * dir, line)] = tm;
+            a.tr1[fidx<NF, NFP>(ne, v, t.e, 2 * dir + 1, line)] = tp;
+        }
+    }
+}
+
+// mode 0: write U_t (double) to a.out; mode 1: RK stage `stage` with coefficients from
+// a.coef (G = A G + dt U_t; U = U + B G) and new traces.
+template <int D, int N, typename R>
+__global__ void __launch_bounds__(Shape<D, N>::NT) k_surf_rk(KArgs<R> a, int mode, int stage)
+{
+    using S = Shape<D, N>;
+    using M = K3Smem<D, N, R>;
+    constexpr int P = S::P, NP = S::NP, NFP = S::NFP, NF = S::NF, NV = S::NV;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const Slot<D, N> t(a.g);
+    R *sFs = reinterpret_cast<R *>(smraw) + (size_t)t.le * M::per_elem;
+    const long long ne = a.g.ne;
+    // issue the node loads first so that their latency overlaps the face phase
+    R utv[NV];
+    double u0[NV], g0[NV];
+    if (t.valid) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const long long idx = ((long long)v * ne + t.e) * NP + t.n;
+            utv[v] = a.Utv[idx];
+            if (mode != 0) {
+                u0[v] = a.U[idx];
+                g0[v] = a.G[idx];
+            }
+        }
+    }
+    if (t.valid) {
+        const long long st = ne * NF * NFP;
+        for (int q = t.n; q < NF * NFP; q += NP) {
+            const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
+            const long long b = t.nbr(a.g, f);
+            const long long oo = ((long long)t.e * NF + f) * NFP + fp;
+            if (b < 0) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sFs[(f * NV + v) * NFP + fp] = a.fd[(NV + v) * st + oo];
+            } else {
+                const long long ob = ((long long)b * NF + (2 * dir + 1 - side)) * NFP + fp;
+                const long long iL = side ? oo : ob, iR = side ? ob : oo;
+                const R lam = fmax(a.fd[(2 * NV) * st + iL], a.fd[(2 * NV) * st + iR]);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const R FL = a.fd[(NV + v) * st + iL], FR = a.fd[(NV + v) * st + iR];
+                    const R UL = a.fd[v * st + iL], UR = a.fd[v * st + iR];
+                    sFs[(f * NV + v) * NFP + fp] = R(0.5) * (FL + FR) - R(0.5) * lam * (UR - UL);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    R Ut[NV];
+    if (t.valid) {
+        // (2/h) l_i(+-1)/w_i of this node's index in each direction, selected into registers
+        R Lp[D], Lm[D];
+        int fpd[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const int i = ncoord<P>(t.n, d);
+            fpd[d] = node_fp<P>(t.n, d);
+            R vp = R(0), vm = R(0);
+#pragma unroll
+            for (int l = 0; l < P; ++l)
+                if (l == i) { vp = a.op.Lp[l]; vm = a.op.Lm[l]; }
+            Lp[d] = vp * a.gr.inv2h[d];
+            Lm[d] = vm * a.gr.inv2h[d];
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            R acc = utv[v];
+#pragma unroll
+            for (int d = 0; d < D; ++d)
+                acc -= Lp[d] * sFs[((2 * d + 1) * NV + v) * NFP + fpd[d]] - Lm[d] * sFs[((2 * d) * NV + v) * NFP + fpd[d]];
+            Ut[v] = acc;
+        }
+    }
+    if (mode == 0) {
+        if (t.valid) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) a.out[((long long)v * ne + t.e) * NP + t.n] = to_f64<R>(Ut[v]);
+        }
+        return;
+    }
+    double Ud[NV];
+    if (t.valid) {
+        // FP64 accumulation: G = A G + dt U_t, U = U + B G (two FP64 FMAs per variable;
+        // in the FP32-bulk form dt U_t is formed in float, as U_t itself is)
+        const double A = a.coef[stage], B = a.coef[5 + stage], dt = a.coef[10];
+        const R dtR = to_bulk<R>(dt);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const long long idx = ((long long)v * ne + t.e) * NP + t.n;
+            double gg;
+            if constexpr (sizeof(R) == 8) gg = A * g0[v] + dt * Ut[v];
+            else gg = fma(A, g0[v], to_f64<R>(dtR * Ut[v]));
+            const double uu = fma(B, gg, u0[v]);
+            a.G[idx] = gg;
+            a.U[idx] = uu;
+            Ud[v] = uu;
+        }
+    }
+    __syncthreads();  // sFs dead; reuse as sQ
+    write_traces<D, N, R>(a, t, sFs, Ud);
+}
+
+// ------------------------------------------------------------------ set-up kernels
+
+// pass-1 traces of the current state
+template <int D, int N, typename R>
+__global__ void __launch_bounds__(Shape<D, N>::NT) k_traces(KArgs<R> a)
+{
+    using S = Shape<D, N>;
+    constexpr int NP = S::NP, NV = S::NV;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const Slot<D, N> t(a.g);
+    R *sQ = reinterpret_cast<R *>(smraw) + (size_t)t.le * (size_t)S::NL * NP;
+    double Ud[NV];
+    if (t.valid) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Ud[v] = a.U[((long long)v * a.g.ne + t.e) * NP + t.n];
+    }
+    write_traces<D, N, R>(a, t, sQ, Ud);
+}
+
+// mode 0: nodal temperature into a.out[ne][NP]; mode 1: set rho e from the temperature in
+// a.out (dgk_set_primitive): rho e = rho (R cv T - a rho) + |m|^2/(2 rho)
+// + alpha/2 (rho - c)^2 + gamma_K/2 |grad c|^2, grad c lifted from the current traces.
+template <int D, int N, typename R>
+__global__ void __launch_bounds__(Shape<D, N>::NT) k_node_T(KArgs<R> a, int mode)
+{
+    using S = Shape<D, N>;
+    using L = CLift<D, N, R>;
+    constexpr int NP = S::NP, NF = S::NF, NFP = S::NFP, NV = S::NV;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const Slot<D, N> t(a.g);
+    R *sC = reinterpret_cast<R *>(smraw) + (size_t)t.le * L::smem_per_elem;
+    R *sCs = sC + NP, *sDc = sCs + NF * NFP;
+    double Ud[NV];
+    L::run(a, t, sC, sCs, sDc, Ud, false);
+    if (!t.valid) return;
+    R gc[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) gc[d] = sDc[d * NP + t.n];
+    const long long idx = t.e * NP + t.n;
+    if (mode == 0) {
+        NodeState<D, R> q;
+        q.load(Ud);
+        a.out[idx] = to_f64<R>(node_temperature<D, R>(a, Ud, q, gc));
+        return;
+    }
+    const double rho = Ud[0], T = a.out[idx];
+    double msq = 0.0, gc2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        msq += Ud[1 + k] * Ud[1 + k];
+        gc2 += (double)gc[k] * (double)gc[k];
+    }
+    const double dc = rho - Ud[D + 2];
+    a.U[((long long)(D + 1) * a.g.ne + t.e) * NP + t.n] =
+        rho * (kRgas * a.ph.cv * T - kAvdw * rho) + 0.5 * msq / rho + 0.5 * a.ph.alpha * dc * dc + 0.5 * a.ph.gK * gc2;
+}
+
+}  // namespace dgk

@@ -1,0 +1,245 @@
+"""Python binding of libdgk (include/dgk.h): argument marshalling only.
+
+Every step of the time step runs in the library's CUDA kernels.  There is no CPU
+fallback: if libdgk.so is missing or no GPU is present, the calls raise.
+
+Host arrays are numpy float64 arrays in the SoA layout [v][e][n]; device arrays are
+torch CUDA float64 tensors of the same shape (on_device paths).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libdgk.so")
+
+DGK_PREC = {"fp64": 0, "fp32bulk": 1}
+NDIAG = 8
+DIAG_NAMES = ("mass", "mom_x", "mom_y", "mom_z", "energy", "neg_entropy", "rho_minus_c_l2", "max_u")
+
+_lib = None
+
+
+class DgkParams(C.Structure):
+    _fields_ = [("model", C.c_int), ("rk", C.c_int), ("precision", C.c_int), ("gammaK", C.c_double),
+                ("mu", C.c_double), ("kappa", C.c_double), ("cv", C.c_double), ("alpha", C.c_double),
+                ("beta", C.c_double)]
+
+
+class DgkWall(C.Structure):
+    _fields_ = [("kind", C.c_int), ("T_wall", C.c_double), ("theta_deg", C.c_double)]
+
+
+class DgkBoxMesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("N", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("periodic", C.c_int * 3), ("wall", DgkWall * 6)]
+
+
+class DgkError(RuntimeError):
+    pass
+
+
+EXPORTS = ("dgk_create", "dgk_destroy", "dgk_set_params", "dgk_mesh_box", "dgk_sizes", "dgk_node_coords",
+           "dgk_set_primitive", "dgk_upload_state", "dgk_download_state", "dgk_rhs", "dgk_rk_step", "dgk_run",
+           "dgk_max_dt", "dgk_diagnostics", "dgk_status", "dgk_set_timing", "dgk_kernel_time", "dgk_maxwell",
+           "dgk_sigma_vl", "dgk_interface_width", "dgk_status_string", "dgk_last_error", "dgk_check_conversions")
+
+
+def lib():
+    """Load libdgk.so (built by paper_2208_05310_gb300.build / __graft_entry__.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise DgkError(f"libdgk.so not found at {LIB_PATH}: run `python -m paper_2208_05310_gb300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, dp, i, d = C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_double
+    sz = C.c_size_t
+    sig = {
+        "dgk_create": (i, [C.POINTER(vp), i, vp]),
+        "dgk_destroy": (None, [vp]),
+        "dgk_set_params": (i, [vp, C.POINTER(DgkParams)]),
+        "dgk_mesh_box": (i, [vp, C.POINTER(DgkBoxMesh)]),
+        "dgk_sizes": (i, [vp, C.POINTER(C.c_longlong), C.POINTER(i), C.POINTER(i)]),
+        "dgk_node_coords": (i, [vp, vp, i]),
+        "dgk_set_primitive": (i, [vp, vp, sz, i]),
+        "dgk_upload_state": (i, [vp, vp, sz, i]),
+        "dgk_download_state": (i, [vp, vp, sz, i]),
+        "dgk_rhs": (i, [vp, vp, sz, i]),
+        "dgk_rk_step": (i, [vp, d]),
+        "dgk_run": (i, [vp, i, d]),
+        "dgk_max_dt": (i, [vp, d, d, dp]),
+        "dgk_diagnostics": (i, [vp, dp]),
+        "dgk_status": (i, [vp]),
+        "dgk_set_timing": (i, [vp, i]),
+        "dgk_kernel_time": (i, [vp, i, dp, C.POINTER(C.c_longlong)]),
+        "dgk_maxwell": (i, [d, dp, dp]),
+        "dgk_sigma_vl": (i, [d, d, d, dp]),
+        "dgk_interface_width": (i, [d, d, d, dp]),
+        "dgk_check_conversions": (i, [vp, sz, i, C.POINTER(C.c_ulonglong)]),
+        "dgk_status_string": (C.c_char_p, [i]),
+        "dgk_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc, what):
+    if rc != 0:
+        L = lib()
+        raise DgkError(f"{what}: {L.dgk_status_string(rc).decode()} ({rc}): {L.dgk_last_error().decode()}")
+
+
+def _ptr(a):
+    """(pointer, count, on_device) of a numpy array or torch tensor of float64."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise DgkError("host arrays must be C-contiguous float64")
+        return a.ctypes.data, a.size, 0
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise DgkError("tensors must be contiguous float64")
+        return a.data_ptr(), a.numel(), 1 if a.is_cuda else 0
+    raise DgkError(f"unsupported array type {type(a)}")
+
+
+# ---------------- thermodynamics (host) ----------------
+
+def maxwell(T):
+    a, b = C.c_double(), C.c_double()
+    _check(lib().dgk_maxwell(T, C.byref(a), C.byref(b)), "dgk_maxwell")
+    return a.value, b.value
+
+
+def sigma_vl(T, cv=5.0, gammaK=1e-4):
+    s = C.c_double()
+    _check(lib().dgk_sigma_vl(T, cv, gammaK, C.byref(s)), "dgk_sigma_vl")
+    return s.value
+
+
+def interface_width(T, cv=5.0, gammaK=1e-4):
+    s = C.c_double()
+    _check(lib().dgk_interface_width(T, cv, gammaK, C.byref(s)), "dgk_interface_width")
+    return s.value
+
+
+def check_conversions(x):
+    """Number of doubles in x whose library conversions differ from the hardware's."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    bad = C.c_ulonglong()
+    _check(lib().dgk_check_conversions(x.ctypes.data, x.size, 0, C.byref(bad)), "dgk_check_conversions")
+    return bad.value
+
+
+# ---------------- context ----------------
+
+class Context:
+    """One problem on one GPU.  stream: a torch.cuda.Stream to issue work on (default: a
+    new non-default stream, so that runs can be captured in a CUDA graph)."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
+        self._h = C.c_void_p()
+        _check(lib().dgk_create(C.byref(self._h), device, C.c_void_p(self.stream.cuda_stream)), "dgk_create")
+        self.dim = self.nelem = self.np = self.nv = None
+
+    def close(self):
+        if self._h:
+            lib().dgk_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, model=1, rk=4, precision="fp64", gammaK=1e-4, mu=0.01, kappa=1.0 / 150.0, cv=5.0,
+                   alpha=100.0, beta=100.0):
+        p = DgkParams(model, rk, DGK_PREC[precision], gammaK, mu, kappa, cv, alpha, beta)
+        _check(lib().dgk_set_params(self._h, C.byref(p)), "dgk_set_params")
+
+    def mesh_box(self, dim, N, n, lo, hi, periodic, walls=None):
+        """walls: {face: (T_wall, theta_deg)}, faces 0..5 = -x,+x,-y,+y,-z,+z."""
+        m = DgkBoxMesh()
+        m.dim, m.N = dim, N
+        for d in range(3):
+            m.n[d] = int(n[d]) if d < dim else 1
+            m.lo[d] = float(lo[d]) if d < dim else 0.0
+            m.hi[d] = float(hi[d]) if d < dim else 1.0
+            m.periodic[d] = int(periodic[d]) if d < dim else 1
+        for f, (Tw, th) in (walls or {}).items():
+            m.wall[f] = DgkWall(1, Tw, th)
+        _check(lib().dgk_mesh_box(self._h, C.byref(m)), "dgk_mesh_box")
+        ne, npn, nv = C.c_longlong(), C.c_int(), C.c_int()
+        _check(lib().dgk_sizes(self._h, C.byref(ne), C.byref(npn), C.byref(nv)), "dgk_sizes")
+        self.dim, self.nelem, self.np, self.nv = dim, ne.value, npn.value, nv.value
+
+    def shape(self):
+        return (self.nv, self.nelem, self.np)
+
+    def node_coords(self):
+        x = np.zeros((self.dim, self.nelem, self.np))
+        _check(lib().dgk_node_coords(self._h, x.ctypes.data, 0), "dgk_node_coords")
+        return x
+
+    def set_primitive(self, prim):
+        ptr, n, dev = _ptr(prim)
+        _check(lib().dgk_set_primitive(self._h, ptr, n, dev), "dgk_set_primitive")
+
+    def upload_state(self, U):
+        ptr, n, dev = _ptr(U)
+        _check(lib().dgk_upload_state(self._h, ptr, n, dev), "dgk_upload_state")
+
+    def download_state(self, out=None):
+        out = np.zeros(self.shape()) if out is None else out
+        ptr, n, dev = _ptr(out)
+        _check(lib().dgk_download_state(self._h, ptr, n, dev), "dgk_download_state")
+        return out
+
+    def rhs(self, out=None):
+        out = np.zeros(self.shape()) if out is None else out
+        ptr, n, dev = _ptr(out)
+        _check(lib().dgk_rhs(self._h, ptr, n, dev), "dgk_rhs")
+        return out
+
+    def rk_step(self, dt):
+        _check(lib().dgk_rk_step(self._h, float(dt)), "dgk_rk_step")
+
+    def run(self, nsteps, dt):
+        _check(lib().dgk_run(self._h, int(nsteps), float(dt)), "dgk_run")
+
+    def max_dt(self, cfl=0.9, dfl=0.4):
+        dt = C.c_double()
+        _check(lib().dgk_max_dt(self._h, cfl, dfl, C.byref(dt)), "dgk_max_dt")
+        return dt.value
+
+    def diagnostics(self):
+        out = np.zeros(NDIAG)
+        _check(lib().dgk_diagnostics(self._h, out.ctypes.data_as(C.POINTER(C.c_double))), "dgk_diagnostics")
+        return dict(zip(DIAG_NAMES, out))
+
+    def status(self):
+        """Synchronise and raise if the device latched an error."""
+        _check(lib().dgk_status(self._h), "dgk_status")
+
+    def status_code(self):
+        return lib().dgk_status(self._h)
+
+    def set_timing(self, enable):
+        _check(lib().dgk_set_timing(self._h, int(bool(enable))), "dgk_set_timing")
+
+    def kernel_time(self, which):
+        ms, cnt = C.c_double(), C.c_longlong()
+        _check(lib().dgk_kernel_time(self._h, which, C.byref(ms), C.byref(cnt)), "dgk_kernel_time")
+        return ms.value, cnt.value

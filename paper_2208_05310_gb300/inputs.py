@@ -100,3 +100,19 @@ def ensemble_specs(nprob, seed, n_range=(16, 96), N_choices=(3, 4, 5), T_range=(
             seed=int(rng.integers(0, 2**31 - 1)),
         ))
     return specs
+
+
+def random_admissible(dim, nelem, np_, seed, rho_range=(0.3, 1.9), T_range=(0.8, 0.95), u_amp=0.05, c_amp=0.01):
+    """Coordinate-free seeded state for exact-input tests: per-element density levels
+    plus per-node variation, small velocities, temperatures in T_range and c = rho
+    perturbed by c_amp.  Both implementations receive the identical array."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    base = rng.uniform(*rho_range, size=(nelem, 1))
+    rho = np.clip(base + 0.1 * rng.uniform(-1, 1, size=(nelem, np_)), rho_range[0], rho_range[1])
+    prim = np.empty((dim + 3, nelem, np_))
+    prim[0] = rho
+    for k in range(dim):
+        prim[1 + k] = u_amp * rng.uniform(-1, 1, size=(nelem, np_))
+    prim[dim + 1] = rng.uniform(*T_range, size=(nelem, np_))
+    prim[dim + 2] = rho * (1.0 + c_amp * rng.uniform(-1, 1, size=(nelem, np_)))
+    return prim

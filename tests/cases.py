@@ -89,3 +89,23 @@ def droplet_state(x, thermo, T0=0.85, center=None, radius=0.25, perturb_seed=Non
     if perturb_seed is not None:
         prim = inputs.perturbed(prim, x, perturb_seed, lengths=lengths)
     return prim
+
+
+def dgk_context(mspec, pspec, precision="fp64", rk=4):
+    """Library context for the same specification (GPU only)."""
+    from paper_2208_05310_gb300 import dgk
+    ctx = dgk.Context()
+    ctx.set_params(rk=rk, precision=precision, **pspec)
+    dim = mspec["dim"]
+    ctx.mesh_box(dim, mspec["N"], mspec["n"] + [1] * (3 - dim), mspec["lo"] + [0.0] * (3 - dim),
+                 mspec["hi"] + [1.0] * (3 - dim), mspec["periodic"] + [1] * (3 - dim), mspec["walls"])
+    return ctx
+
+
+def rel_l2(a, b, floor_frac=1e-3):
+    """Per-variable relative L2 distance ||a - b|| / max(||b||, floor_frac * max_v ||b_v||)."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    nb = np.sqrt((b.reshape(b.shape[0], -1) ** 2).sum(axis=1))
+    den = np.maximum(nb, floor_frac * nb.max())
+    return np.sqrt(((a - b).reshape(b.shape[0], -1) ** 2).sum(axis=1)) / den
