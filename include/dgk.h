@@ -165,6 +165,34 @@ int dgk_interface_width(double T, double cv, double gammaK, double *width);
    and synchronises the current device. */
 int dgk_check_conversions(const double *x, size_t n, int on_device, unsigned long long *mismatches);
 
+/* ---------------- allocation-free right-hand side ----------------
+ *
+ * The paper has no counterpart to this entry point; it is a deployment variant of
+ * dgk_rhs for callers that cannot call cudaMalloc: applications whose device memory is
+ * entirely reserved by another allocator's pool (for example a framework's caching
+ * allocator that owns the GPU), and loops that must never synchronise the device
+ * (cudaMalloc and cudaFree may synchronise implicitly).
+ *
+ * dgk_rhs_static computes exactly what dgk_rhs computes, for the state U (device
+ * pointer, SoA [nvar][nelem][np] FP64, read only) into Ut (device pointer, same layout),
+ * on cuda_stream (NULL: the default stream) of the current device, with the parameters
+ * and mesh passed in.  It creates no context and calls no cudaMalloc, cudaFree or other
+ * allocating routine: every intermediate array lives in one file-scope device array of
+ * DGK_STATIC_SCRATCH_BYTES bytes inside libdgk, which every GPU that loads the library
+ * holds until the process exits.  Asynchronous: synchronise cuda_stream before reading Ut.
+ *   - Size limit: a mesh whose intermediates need more than DGK_STATIC_SCRATCH_BYTES is
+ *     rejected with DGK_ERR_ARG and dgk_last_error() says so (e.g. 3D N = 5 in FP64 fits
+ *     about 1490 elements, in the FP32-bulk form about 2900).
+ *   - The first call on a device looks up the scratch array's device address (once per
+ *     device, with that device current); make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; each call clears
+ *     the only value that must start at zero.  Calls that overlap on the GPU (different
+ *     streams or host threads) race on the array: serialise them.
+ *   - Device-side state checks are latched in the scratch and not reported.
+ */
+#define DGK_STATIC_SCRATCH_BYTES (64u << 20)
+int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *mesh, const double *U, double *Ut, void *cuda_stream);
+
 const char *dgk_status_string(int status);
 /* Text of the most recent error in this thread (empty if none). */
 const char *dgk_last_error(void);

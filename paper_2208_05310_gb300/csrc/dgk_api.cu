@@ -178,6 +178,11 @@ __global__ void k_check_conv(const double *x, long long n, unsigned long long *b
 
 }  // namespace
 
+namespace dgk {
+// Lets other translation units of the library set the text dgk_last_error() returns.
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace dgk
+
 struct dgk_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;

@@ -45,7 +45,8 @@ class DgkError(RuntimeError):
 EXPORTS = ("dgk_create", "dgk_destroy", "dgk_set_params", "dgk_mesh_box", "dgk_sizes", "dgk_node_coords",
            "dgk_set_primitive", "dgk_upload_state", "dgk_download_state", "dgk_rhs", "dgk_rk_step", "dgk_run",
            "dgk_max_dt", "dgk_diagnostics", "dgk_status", "dgk_set_timing", "dgk_kernel_time", "dgk_maxwell",
-           "dgk_sigma_vl", "dgk_interface_width", "dgk_status_string", "dgk_last_error", "dgk_check_conversions")
+           "dgk_sigma_vl", "dgk_interface_width", "dgk_status_string", "dgk_last_error", "dgk_check_conversions",
+           "dgk_rhs_static")
 
 
 def lib():
@@ -80,6 +81,7 @@ def lib():
         "dgk_sigma_vl": (i, [d, d, d, dp]),
         "dgk_interface_width": (i, [d, d, d, dp]),
         "dgk_check_conversions": (i, [vp, sz, i, C.POINTER(C.c_ulonglong)]),
+        "dgk_rhs_static": (i, [C.POINTER(DgkParams), C.POINTER(DgkBoxMesh), vp, vp, vp]),
         "dgk_status_string": (C.c_char_p, [i]),
         "dgk_last_error": (C.c_char_p, []),
     }
@@ -137,6 +139,38 @@ def check_conversions(x):
     bad = C.c_ulonglong()
     _check(lib().dgk_check_conversions(x.ctypes.data, x.size, 0, C.byref(bad)), "dgk_check_conversions")
     return bad.value
+
+
+def make_params(model=1, rk=4, precision="fp64", gammaK=1e-4, mu=0.01, kappa=1.0 / 150.0, cv=5.0, alpha=100.0,
+                beta=100.0):
+    return DgkParams(model, rk, DGK_PREC[precision], gammaK, mu, kappa, cv, alpha, beta)
+
+
+def make_box_mesh(dim, N, n, lo, hi, periodic, walls=None):
+    """walls: {face: (T_wall, theta_deg)}, faces 0..5 = -x,+x,-y,+y,-z,+z."""
+    m = DgkBoxMesh()
+    m.dim, m.N = dim, N
+    for d in range(3):
+        m.n[d] = int(n[d]) if d < dim else 1
+        m.lo[d] = float(lo[d]) if d < dim else 0.0
+        m.hi[d] = float(hi[d]) if d < dim else 1.0
+        m.periodic[d] = int(periodic[d]) if d < dim else 1
+    for f, (Tw, th) in (walls or {}).items():
+        m.wall[f] = DgkWall(1, Tw, th)
+    return m
+
+
+def rhs_static(params, mesh, U, Ut, stream=None):
+    """dgk_rhs_static: right-hand side of the device state U into the device array Ut
+    without any device allocation (see include/dgk.h).  U, Ut: contiguous float64 CUDA
+    tensors of shape (nvar, nelem, np); stream: a torch.cuda.Stream or None (default
+    stream).  Asynchronous."""
+    pu, nu, du = _ptr(U)
+    po, no, do = _ptr(Ut)
+    if not (du and do) or nu != no:
+        raise DgkError("U and Ut must be device tensors of equal size")
+    h = C.c_void_p(stream.cuda_stream) if stream is not None else C.c_void_p()
+    _check(lib().dgk_rhs_static(C.byref(params), C.byref(mesh), pu, po, h), "dgk_rhs_static")
 
 
 # ---------------- context ----------------
