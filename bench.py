@@ -62,7 +62,16 @@ def workload_c2():
                 rk=4, T0=0.8, radius=0.25, center=[0.5, 0.5], axes=None, noise=1e-3)
 
 
-WORKLOADS = {"c5": workload_c5, "c5s": lambda: workload_c5(scale=2), "c2": workload_c2}
+def workload_c4(nprob=256):
+    return dict(name=f"batched ensemble of {nprob} independent 2D droplets / bubbles on contact-angle walls, "
+                     "16x16..96x96 elements, N in {3,4,5}, T in [0.75,0.9] Tc, theta in [30,150] deg, LSRK4",
+                batch=dict(nprob=nprob, seed=2024, n_range=(16, 96)),
+                params=dict(model=1, gammaK=1e-4, mu=0.01, kappa=1.0 / 150.0, cv=5.0, alpha=100.0, beta=100.0),
+                rk=4)
+
+
+WORKLOADS = {"c5": workload_c5, "c5s": lambda: workload_c5(scale=2), "c2": workload_c2, "c4": workload_c4,
+             "c4s": lambda: workload_c4(32)}
 
 
 def primitive_state(wl, x, rv, rl, width):
@@ -199,7 +208,36 @@ def oracle_rate(wl, seconds_target=15.0, steps=None, sub=(6, 6, None)):
     total_t = tt if nsteps else t1
     assert np.isfinite(U).all()
     return dict(rate=dof * stages * total_steps / total_t, cores=orc.num_threads(), dof=dof, steps=total_steps,
-                seconds=total_t, sub=nsub)
+                seconds=total_t, sub=f"a {nsub} sub-box")
+
+
+def oracle_rate_batch(wl, steps, nsample=2):
+    """FP64 oracle DOF-stage/s on the first `nsample` problems of the ensemble (full size),
+    one after the other."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import numpy as np
+    import oracle as orc
+    from paper_2208_05310_gb300 import inputs
+    b = wl["batch"]
+    specs = inputs.ensemble_specs(b["nprob"], b["seed"], n_range=b["n_range"])[:nsample]
+    stages = 5 if wl["rk"] == 4 else 3
+    dof, total = 0, 0.0
+    for sp in specs:
+        m = inputs.ensemble_mesh(sp)
+        o = orc.Oracle(orc.make_mesh(2, m["N"], m["n"] + [1], m["lo"] + [0.0], m["hi"] + [1.0], m["periodic"] + [1],
+                                     m["walls"]), orc.make_params(**wl["params"]))
+        rv, rl = orc.maxwell(sp["T"])
+        U = o.set_primitive(inputs.ensemble_primitive(o.node_coords(), sp, rv, rl,
+                                                      orc.interface_width(sp["T"], wl["params"]["cv"],
+                                                                          wl["params"]["gammaK"])))
+        dt = o.max_dt(U)
+        t0 = time.perf_counter()
+        U = o.run(U, steps, dt, rk=wl["rk"])
+        total += time.perf_counter() - t0
+        assert np.isfinite(U).all()
+        dof += o.nelem * o.np
+    return dict(rate=dof * stages * steps / total, cores=orc.num_threads(), dof=dof, steps=steps, seconds=total,
+                sub=f"first {nsample} problems of the ensemble")
 
 
 def run_reference(args, wl, rank, world):
@@ -209,10 +247,11 @@ def run_reference(args, wl, rank, world):
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as orc
     orc.lib()
-    # warm-up steps, then K timed steps; one step = one RK step on the sub-box
-    r_w = oracle_rate(wl, steps=max(args.warmup, 1))
-    r = oracle_rate(wl, steps=max(args.steps, 1))
-    sample = f"one RK step per bench step on a {r['sub']} sub-box of the workload ({r['dof']} nodes)"
+    # warm-up steps, then K timed steps; one step = one RK step on the sample
+    rate = (lambda k: oracle_rate_batch(wl, k)) if "batch" in wl else (lambda k: oracle_rate(wl, steps=k))
+    r_w = rate(max(args.warmup, 1))
+    r = rate(max(args.steps, 1))
+    sample = f"one RK step per bench step on {r['sub']} of the workload ({r['dof']} nodes)"
     line = dict(metric=METRIC, value=r["rate"], unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=1e3 * r["seconds"] / r["steps"], higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic", impl="reference",
@@ -333,11 +372,16 @@ def run_ours(args, wl, rank, world, local_rank):
     if not args.no_e2e:
         e2e = end_to_end(args, make_ctx, dt, dof, stages, world, barrier, max_over_ranks)
 
+    # --- the batched ensemble (256 independent 2D problems) on the same GPU
+    batched = None
+    if not args.no_batch:
+        batched = batch_measure(WORKLOADS["c4"](), local_rank, max(3, args.steps // 2), 3, unbatched=True)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = oracle_rate(wl, seconds_target=args.cpu_seconds)
         cpu = dict(value=r["rate"], unit=UNIT, cores=r["cores"], kind="oracle",
-                   sample=f"{r['steps']} RK steps on a {r['sub']} sub-box of the workload ({r['dof']} nodes), "
+                   sample=f"{r['steps']} RK steps on {r['sub']} of the workload ({r['dof']} nodes), "
                           f"{r['seconds']:.1f} s")
 
     if rank == 0:
@@ -348,7 +392,141 @@ def run_ours(args, wl, rank, world, local_rank):
                                 l2="inputs larger than L2: state %.2f GB" % (dof * (m['dim'] + 3) * 8 / 1e9),
                                 parallelism=f"replicas x{world}"),
                     e2e=e2e, gpu_launches=3 * stages * args.steps, roofline=roofline, cpu_baseline=cpu,
-                    clocks=clk.summary(), fp64=fp64)
+                    clocks=clk.summary(), fp64=fp64, batched=batched)
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def batch_measure(wl, local_rank, steps, warmup, unbatched=True, e2e=False):
+    """Batched ensemble: autotuned persistent launches per RK stage, timed over `steps`
+    graph-replayed steps; beside it the same problems one context each (FP32-bulk and
+    FP64, every context on its own stream so that small problems may overlap)."""
+    import torch
+    from paper_2208_05310_gb300 import dgk, inputs
+    b = wl["batch"]
+    stages = 5 if wl["rk"] == 4 else 3
+    specs = inputs.ensemble_specs(b["nprob"], b["seed"], n_range=b["n_range"])
+    meshes = [inputs.ensemble_mesh(sp) for sp in specs]
+    thermo = {}
+
+    def prim_of(q, sp):
+        if sp["T"] not in thermo:
+            rv, rl = dgk.maxwell(sp["T"])
+            thermo[sp["T"]] = (rv, rl, dgk.interface_width(sp["T"], wl["params"]["cv"], wl["params"]["gammaK"]))
+        return inputs.ensemble_primitive(q.node_coords(), sp, *thermo[sp["T"]])
+
+    B = dgk.Batch(meshes, device=local_rank, rk=wl["rk"], **wl["params"])
+    prims, dts = [], []
+    for q, sp in zip(B.problems, specs):
+        prims.append(prim_of(q, sp))
+        q.set_primitive(prims[-1])
+        dts.append(0.5 * q.max_dt(0.9, 0.4))
+    B.set_dt(dts)
+    dof_p = [q.nelem * q.np for q in B.problems]
+    dof = sum(dof_p)
+    t0 = time.perf_counter()
+    cfg = B.autotune()
+    t_tune = time.perf_counter() - t0
+    B.run(warmup)
+    B.status()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(B.stream)
+    B.run(steps)
+    e1.record(B.stream)
+    B.stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    B.status()
+    alg = sum(d * sum(kernel_bytes_per_node(2, ms_["N"], 4).values()) for d, ms_ in zip(dof_p, meshes))
+    peak, peak_kind = measured_peak()
+    avg_launch_ms = ms / steps / stages
+    achieved = alg / (avg_launch_ms / 1e3) / 1e9
+    out = dict(value=dof * stages * steps / (ms / 1e3), unit=UNIT, ms_per_step=ms / steps, steps=steps,
+               nodes=dof, problems=len(meshes), autotuned=cfg, autotune_s=t_tune, gpu_launches=stages * steps,
+               roofline=dict(bound="hbm", kernel="k_batch_stage", achieved=achieved, peak=peak, unit="GB/s",
+                             frac=achieved / peak, peak_kind=peak_kind, alg_bytes_per_launch=alg,
+                             avg_launch_ms=avg_launch_ms, traffic=None))
+    if e2e:
+        host_in = [torch.empty(q.shape(), dtype=torch.float64, pin_memory=True) for q in B.problems]
+        host_out = [torch.empty(q.shape(), dtype=torch.float64, pin_memory=True) for q in B.problems]
+        for q, h in zip(B.problems, host_in):
+            q.download_state(h)
+        k_e2e = max(1, min(steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            for q, h in zip(B.problems, host_in):
+                q.upload_state(h)
+            B.run(1)
+            for q, h in zip(B.problems, host_out):
+                q.download_state(h)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        B.status()
+        nbytes = sum(h.numel() * 8 for h in host_in)
+        out["e2e"] = dict(value=dof * stages * k_e2e / t, unit=UNIT, h2d_bytes_per_step=nbytes,
+                          d2h_bytes_per_step=nbytes, steps=k_e2e)
+    B.close()
+    del B
+    torch.cuda.synchronize()
+    if unbatched:
+        for prec, k in (("fp32bulk", steps), ("fp64", max(1, steps // 4))):
+            ctxs = []
+            for ms_, prim in zip(meshes, prims):
+                c = dgk.Context(device=local_rank)
+                c.set_params(rk=wl["rk"], precision=prec, **wl["params"])
+                c.mesh_box(2, ms_["N"], ms_["n"] + [1], ms_["lo"] + [0.0], ms_["hi"] + [1.0], ms_["periodic"] + [1],
+                           ms_["walls"])
+                c.set_primitive(prim)
+                ctxs.append(c)
+            for c, dt in zip(ctxs, dts):
+                c.run(1, dt)  # warm-up, captures each context's step graph
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for c, dt in zip(ctxs, dts):
+                c.run(k, dt)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            for c in ctxs:
+                c.status()
+                c.close()
+            out["unbatched_" + prec] = dict(value=dof * stages * k / t, unit=UNIT, steps=k, ms_per_step=1e3 * t / k,
+                                            launches_per_step=3 * stages * len(ctxs))
+            torch.cuda.synchronize()
+    return out
+
+
+def run_batch(args, wl, rank, world, local_rank):
+    """The batched-ensemble workload as the bench line (replicas under torchrun)."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    if dist is not None:
+        dist.barrier()
+    with ClockSampler(local_rank) as clk:
+        r = batch_measure(wl, local_rank, args.steps, args.warmup, unbatched=not args.no_fp64, e2e=not args.no_e2e)
+    ms = r["ms_per_step"] * args.steps
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    stages = 5 if wl["rk"] == 4 else 3
+    if rank == 0:
+        e2e = r.pop("e2e", None)
+        if e2e is not None:
+            e2e = dict(e2e, value=e2e["value"] * world)
+        line = dict(metric=METRIC, value=r["nodes"] * stages * args.steps * world / (ms / 1e3), unit=UNIT,
+                    n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms / args.steps,
+                    higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32/f64", data="synthetic",
+                    config=dict(workload=wl["name"], dof=r["nodes"], problems=r["problems"], stages_per_step=stages,
+                                precision="fp32bulk", autotuned=r["autotuned"],
+                                l2="inputs larger than L2: state %.2f GB" % (r["nodes"] * 5 * 8 / 1e9),
+                                parallelism=f"replicas x{world}"),
+                    e2e=e2e, gpu_launches=r["gpu_launches"], roofline=r["roofline"], cpu_baseline=None,
+                    clocks=clk.summary(), unbatched_fp32bulk=r.get("unbatched_fp32bulk"),
+                    unbatched_fp64=r.get("unbatched_fp64"))
         print(json.dumps(line), flush=True)
     return 0
 
@@ -390,6 +568,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -405,6 +584,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
+        if "batch" in wl:
+            return run_batch(args, wl, rank, world, local_rank)
         return run_ours(args, wl, rank, world, local_rank)
     finally:
         if world > 1:

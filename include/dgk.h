@@ -49,6 +49,7 @@ extern "C" {
 #define DGK_ERR_UNSUPPORTED (-6) /* dimension / degree / model not compiled in */
 #define DGK_ERR_NOMEM (-7)       /* device allocation failed */
 #define DGK_ERR_THERMO (-8)      /* no saturation states at this temperature (T >= 1) */
+#define DGK_ERR_TIMEOUT (-9)     /* device: a grid barrier of the batched kernel timed out */
 
 #define DGK_PREC_FP64 0      /* every kernel in FP64 */
 #define DGK_PREC_FP32BULK 1  /* lifting, volume and surface in FP32; the energy balance of
@@ -141,6 +142,10 @@ int dgk_max_dt(dgk_ctx *ctx, double cfl, double dfl, double *dt);
 /* Integral diagnostics (Gauss quadrature, FP64, fixed summation order):
    out[DGK_NDIAG] = mass, momentum x, y, z, total energy, -int rho eta, ||rho - c||_2, max|u|. */
 int dgk_diagnostics(dgk_ctx *ctx, double *out);
+/* Nodal temperature (recovered from the total energy with the lifted grad c, as the
+   scheme does) and pressure p(rho, T) (Eq. pressure), each nelem*np doubles [e][n];
+   either pointer may be NULL.  Synchronises. */
+int dgk_node_temperature_pressure(dgk_ctx *ctx, double *T, double *p, size_t count, int on_device);
 /* Synchronise the stream and return (then clear) the latched device status. */
 int dgk_status(dgk_ctx *ctx);
 /* Event-timed duration (ms) of the last timed launch of each kernel class, for roofline
@@ -164,6 +169,47 @@ int dgk_interface_width(double T, double cv, double gammaK, double *width);
    results differ (inputs rounding below the float normal range are skipped).  Allocates
    and synchronises the current device. */
 int dgk_check_conversions(const double *x, size_t n, int on_device, unsigned long long *mismatches);
+
+/* ---------------- batched ensembles ----------------
+ *
+ * Many independent 2D problems (degrees N = 3, 4, 5, any mesh sizes, walls and
+ * temperatures; common physics parameters, FP32-bulk form) advanced together: every RK
+ * stage is ONE persistent cooperative launch that runs the three phases of the stage for
+ * all problems, separated by grid barriers (bounded spin; a timeout is reported as
+ * DGK_ERR_TIMEOUT, never a hang), and one step is replayed as a captured CUDA graph.
+ * Each problem has its own time step.  The problems are ordinary contexts owned by the
+ * batch: use dgk_batch_problem() with the single-problem calls (set-up, download,
+ * diagnostics, max_dt).
+ * All batches of a process share one constant-memory parameter block, rebound at the
+ * start of every step: batches on different streams must not run at the same time.
+ */
+typedef struct dgk_batch dgk_batch;
+/* p: common parameters (precision must be DGK_PREC_FP32BULK); meshes[nprob]: 2D box
+   meshes with N in 3..5.  cuda_stream as for dgk_create (shared by all problems). */
+int dgk_batch_create(dgk_batch **out, int device, void *cuda_stream, const dgk_params *p, int nprob,
+                     const dgk_box_mesh *meshes);
+void dgk_batch_destroy(dgk_batch *b);
+/* The context of problem i (owned by the batch; do not destroy). */
+dgk_ctx *dgk_batch_problem(dgk_batch *b, int i);
+/* Time step of every problem (dt[nprob]). */
+int dgk_batch_set_dt(dgk_batch *b, const double *dt);
+/* nsteps RK steps of every problem: stages x one persistent launch per step, replayed
+   from a captured graph.  Asynchronous. */
+int dgk_batch_run(dgk_batch *b, int nsteps);
+/* Autotuner: times one step for candidate work decompositions -- elements per tile for
+   each degree N (k_N element blocks of the degree's block shape) and resident blocks
+   per SM of the persistent grid -- and keeps the fastest.  Every candidate runs three
+   steps from the current states, which are restored afterwards; the status words are
+   cleared after tuning (tuning refuses to start, returning the error, if a problem
+   already reports one).  out (nullable) = {blocks_per_sm, k_3, k_4, k_5}. */
+int dgk_batch_autotune(dgk_batch *b, int *out);
+/* Set the work decomposition directly: cfg = {blocks_per_sm, k_3, k_4, k_5} (as returned
+   by dgk_batch_autotune; blocks_per_sm in 1..the occupancy limit, k_N >= 1).  Results do
+   not depend on it: every element's arithmetic is the same for any decomposition. */
+int dgk_batch_set_config(dgk_batch *b, const int *cfg);
+/* Synchronise; per_problem (nullable, nprob ints) receives each problem's status.
+   Returns the first error: barrier timeout, then any problem's error. */
+int dgk_batch_status(dgk_batch *b, int *per_problem);
 
 /* ---------------- allocation-free right-hand side ----------------
  *

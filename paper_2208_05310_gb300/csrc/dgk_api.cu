@@ -5,6 +5,7 @@
 // the RK kernel (so one captured graph serves every dt), and the device status word.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -20,6 +21,7 @@ const dgk::KernelTable *dgk_table_2d_f64(int N);
 const dgk::KernelTable *dgk_table_2d_f32(int N);
 const dgk::KernelTable *dgk_table_3d_f64(int N);
 const dgk::KernelTable *dgk_table_3d_f32(int N);
+
 
 namespace {
 
@@ -155,6 +157,15 @@ __global__ void k_diag_partial(const double *U, const double *T, long long ne, N
     if (threadIdx.x < 8) partial[(long long)blockIdx.x * 8 + threadIdx.x] = s[threadIdx.x][0];
 }
 
+// p(rho, T) at the nodes (Eq. pressure), from the nodal temperature in T
+__global__ void k_pressure(const double *U, const double *T, double *p, long long nn)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    const double rho = U[i];
+    p[i] = rho * dgk::kRgas * T[i] / (1.0 - dgk::kBvdw * rho) - dgk::kAvdw * rho * rho;
+}
+
 // Bitwise comparison of the integer-arithmetic conversions of dgk_common.cuh with the
 // hardware conversions (round to nearest) on normal-range inputs.
 __global__ void k_check_conv(const double *x, long long n, unsigned long long *bad)
@@ -239,15 +250,15 @@ void drop_graph(dgk_ctx *c)
 template <typename R>
 void fill_args(dgk_ctx *c, dgk::KArgs<R> &a)
 {
-    a.U = c->U;
-    a.G = c->G;
-    a.Utv = (R *)c->Utv;
-    a.tr1 = (R *)c->tr1;
-    a.tr2 = (R *)c->tr2;
-    a.fd = (R *)c->fd;
-    a.out = c->Tbuf;
-    a.coef = c->coef;
-    a.status = c->status;
+    a.v.U = c->U;
+    a.v.G = c->G;
+    a.v.Utv = (R *)c->Utv;
+    a.v.tr1 = (R *)c->tr1;
+    a.v.tr2 = (R *)c->tr2;
+    a.v.fd = (R *)c->fd;
+    a.v.out = c->Tbuf;
+    a.v.coef = c->coef;
+    a.v.status = c->status;
 }
 
 // constants in the bulk type, derived once on the host
@@ -261,7 +272,7 @@ void fill_bulk(dgk::KArgs<R> &a, const dgk::Geom &g, const dgk::Phys &ph, const 
         a.op.lp[i] = (R)o.lp[i];
         a.op.lm[i] = (R)o.lm[i];
     }
-    for (int d = 0; d < 3; ++d) a.gr.inv2h[d] = (R)g.inv2h[d];
+    for (int d = 0; d < 3; ++d) a.v.gr.inv2h[d] = (R)g.inv2h[d];
     dgk::PhysR<R> &p = a.pr;
     p.model = ph.model;
     p.gK = (R)ph.gK;
@@ -278,10 +289,10 @@ void fill_bulk(dgk::KArgs<R> &a, const dgk::Geom &g, const dgk::Phys &ph, const 
     p.inv_Rcv = (R)(1.0 / (dgk::kRgas * ph.cv));
     p.half_alpha_p = ph.model == 2 ? (R)(0.5 * ph.alpha) : (R)0;
     for (int f = 0; f < 6; ++f) {
-        a.wr.K[f] = (R)w.K[f];
-        a.wr.rl[f] = (R)w.rl[f];
-        a.wr.rv[f] = (R)w.rv[f];
-        a.wr.Tw[f] = (R)w.Tw[f];
+        a.v.wr.K[f] = (R)w.K[f];
+        a.v.wr.rl[f] = (R)w.rl[f];
+        a.v.wr.rv[f] = (R)w.rv[f];
+        a.v.wr.Tw[f] = (R)w.Tw[f];
     }
 }
 
@@ -324,7 +335,7 @@ int build_consts(dgk_ctx *c)
         o.lm[i] = c->op1.lm[i];
         o.w[i] = c->op1.w[i];
     }
-    c->a64.g = c->a32.g = g;
+    c->a64.v.g = c->a32.v.g = g;
     c->a64.ph = c->a32.ph = ph;
     fill_bulk(c->a64, g, ph, w, o);
     fill_bulk(c->a32, g, ph, w, o);
@@ -444,6 +455,7 @@ const char *dgk_status_string(int s)
     case DGK_ERR_UNSUPPORTED: return "dimension / degree / option not supported";
     case DGK_ERR_NOMEM: return "device allocation failed";
     case DGK_ERR_THERMO: return "no saturation states at this temperature";
+    case DGK_ERR_TIMEOUT: return "a grid barrier of the batched kernel timed out";
     default: return "unknown status";
     }
 }
@@ -662,11 +674,11 @@ int dgk_rhs(dgk_ctx *c, double *Ut, size_t count, int on_device)
     if ((err = c->kt->lift2vol(a, c->stream))) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
     if (c->prm.precision == DGK_PREC_FP32BULK) {
         dgk::KArgs<float> b = c->a32;
-        b.out = dst;
+        b.v.out = dst;
         err = c->kt->surf(&b, 0, 0, c->stream);
     } else {
         dgk::KArgs<double> b = c->a64;
-        b.out = dst;
+        b.v.out = dst;
         err = c->kt->surf(&b, 0, 0, c->stream);
     }
     if (err) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
@@ -773,6 +785,26 @@ int dgk_diagnostics(dgk_ctx *c, double *out)
     return DGK_OK;
 }
 
+int dgk_node_temperature_pressure(dgk_ctx *c, double *T, double *p, size_t count, int on_device)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    const size_t nn = (size_t)c->ne * c->NP;
+    if (count != nn || (!T && !p)) return fail(DGK_ERR_ARG, "output arrays must hold nelem*np doubles");
+    cudaError_t err = c->kt->nodeT(c->args(), 0, c->stream);
+    if (err) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (T) DGK_CUDA(cudaMemcpyAsync(T, c->Tbuf, nn * sizeof(double), kind, c->stream));
+    if (p) {
+        if (!c->rhsbuf) DGK_CUDA(cudaMalloc(&c->rhsbuf, (size_t)c->NV * nn * sizeof(double)));
+        k_pressure<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->U, c->Tbuf, c->rhsbuf, (long long)nn);
+        DGK_CUDA(cudaGetLastError());
+        DGK_CUDA(cudaMemcpyAsync(p, c->rhsbuf, nn * sizeof(double), kind, c->stream));
+    }
+    DGK_CUDA(cudaStreamSynchronize(c->stream));
+    return DGK_OK;
+}
+
 int dgk_status(dgk_ctx *c)
 {
     if (!c) return fail(DGK_ERR_ARG, "null context");
@@ -860,6 +892,349 @@ int dgk_interface_width(double T, double cv, double gammaK, double *width)
     if (!width) return fail(DGK_ERR_ARG, "null output");
     *width = std::sqrt(2.0) * gammaK * (rl - rv) * (rl - rv) / sig;
     return DGK_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== batched ensembles
+
+struct dgk_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    dgk_params prm{};
+    std::vector<dgk_ctx *> probs;
+    std::vector<int> probN;
+    dgk::BatchLaunch L{};
+    dgk::KView<float> *d_views = nullptr;
+    int *d_probN = nullptr, *d_tiles = nullptr;
+    unsigned *d_bar = nullptr;  // [0..1] barrier, [2] status
+    void *d_args = nullptr;     // device copy of the kernel parameters
+    int sms = 0, max_bps = 1, bps = 1;
+    int k[3] = {1, 1, 1};
+    size_t tiles_cap = 0;
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+void batch_drop_graph(dgk_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+// tile table: runs of k_N element blocks of one problem, problems interleaved
+int batch_build_tiles(dgk_batch *b)
+{
+    std::vector<int> tp, tb, tl;
+    std::vector<long long> next(b->probs.size(), 0), nblk(b->probs.size());
+    for (size_t p = 0; p < b->probs.size(); ++p) nblk[p] = (b->probs[p]->ne + b->probs[p]->kt->elems_per_block - 1) /
+                                                          b->probs[p]->kt->elems_per_block;
+    bool more = true;
+    while (more) {
+        more = false;
+        for (size_t p = 0; p < b->probs.size(); ++p) {
+            if (next[p] >= nblk[p]) continue;
+            const int kk = b->k[b->probN[p] - 3];
+            const long long len = std::min<long long>(kk, nblk[p] - next[p]);
+            tp.push_back((int)p);
+            tb.push_back((int)next[p]);
+            tl.push_back((int)len);
+            next[p] += len;
+            more = true;
+        }
+    }
+    const size_t nt = tp.size();
+    if (nt > b->tiles_cap) {
+        if (b->d_tiles) cudaFree(b->d_tiles);
+        b->d_tiles = nullptr;
+        DGK_CUDA(cudaMalloc(&b->d_tiles, 3 * nt * sizeof(int)));
+        b->tiles_cap = nt;
+    }
+    std::vector<int> h(3 * nt);
+    std::copy(tp.begin(), tp.end(), h.begin());
+    std::copy(tb.begin(), tb.end(), h.begin() + nt);
+    std::copy(tl.begin(), tl.end(), h.begin() + 2 * nt);
+    DGK_CUDA(cudaMemcpy(b->d_tiles, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice));
+    b->L.tile_prob = b->d_tiles;
+    b->L.tile_blk = b->d_tiles + nt;
+    b->L.tile_len = b->d_tiles + 2 * nt;
+    b->L.ntiles = (int)nt;
+    if (!b->d_args) DGK_CUDA(cudaMalloc(&b->d_args, dgk::batch_args_bytes()));
+    DGK_CUDA(dgk::batch_upload_args(b->L, b->d_args));
+    batch_drop_graph(b);
+    return DGK_OK;
+}
+
+int batch_launch_step(dgk_batch *b)
+{
+    const int ns = b->prm.rk == 3 ? 3 : 5;
+    cudaError_t e0 = dgk::batch_bind_args(b->d_args, b->stream);
+    if (e0 != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("batch parameters: ") + cudaGetErrorString(e0));
+    for (int s = 0; s < ns; ++s) {
+        cudaError_t err = dgk::batch_stage_launch(b->sms * b->bps, s, b->stream);
+        if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("batched stage launch: ") + cudaGetErrorString(err));
+    }
+    return DGK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dgk_batch_create(dgk_batch **out, int device, void *cuda_stream, const dgk_params *p, int nprob,
+                     const dgk_box_mesh *meshes)
+{
+    if (!out || !p || nprob < 1 || !meshes) return fail(DGK_ERR_ARG, "bad arguments");
+    *out = nullptr;
+    if (p->precision != DGK_PREC_FP32BULK) return fail(DGK_ERR_UNSUPPORTED, "batched ensembles run the FP32-bulk form");
+    for (int i = 0; i < nprob; ++i)
+        if (meshes[i].dim != 2 || meshes[i].N < 3 || meshes[i].N > 5)
+            return fail(DGK_ERR_UNSUPPORTED, "batched ensembles take 2D meshes with N = 3..5");
+    DGK_CUDA(cudaSetDevice(device));
+    dgk_batch *b = new (std::nothrow) dgk_batch();
+    if (!b) return fail(DGK_ERR_NOMEM, "host allocation failed");
+    b->device = device;
+    b->prm = *p;
+    int rc = DGK_OK;
+    if (cuda_stream) b->stream = (cudaStream_t)cuda_stream;
+    else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return fail(DGK_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        b->own_stream = true;
+    }
+    for (int i = 0; i < nprob && !rc; ++i) {
+        dgk_ctx *c = nullptr;
+        rc = dgk_create(&c, device, b->stream);
+        if (!rc) b->probs.push_back(c);
+        if (!rc) rc = dgk_set_params(c, p);
+        if (!rc) rc = dgk_mesh_box(c, &meshes[i]);
+        if (!rc) rc = set_coef(c, 1e-6);
+        b->probN.push_back(meshes[i].N);
+    }
+    std::vector<dgk::KView<float>> views;
+    for (dgk_ctx *c : b->probs) views.push_back(c->a32.v);
+    int maxb = 0;
+    if (!rc && dgk::batch_prepare(&maxb) != cudaSuccess) rc = fail(DGK_ERR_CUDA, "batched kernel set-up failed");
+    if (!rc && maxb < 1) rc = fail(DGK_ERR_UNSUPPORTED, "batched kernel does not fit on an SM");
+    if (!rc && (cudaMalloc(&b->d_views, views.size() * sizeof(views[0])) != cudaSuccess ||
+                cudaMalloc(&b->d_probN, b->probN.size() * sizeof(int)) != cudaSuccess ||
+                cudaMalloc(&b->d_bar, 4 * sizeof(unsigned)) != cudaSuccess))
+        rc = fail(DGK_ERR_NOMEM, "batch tables");
+    if (!rc && (cudaMemcpy(b->d_views, views.data(), views.size() * sizeof(views[0]), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(b->d_probN, b->probN.data(), b->probN.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemset(b->d_bar, 0, 4 * sizeof(unsigned)) != cudaSuccess))
+        rc = fail(DGK_ERR_CUDA, "batch table upload");
+    if (!rc) {
+        cudaDeviceProp prop;
+        cudaGetDeviceProperties(&prop, device);
+        b->sms = prop.multiProcessorCount;
+        b->max_bps = maxb;
+        b->bps = maxb;
+        b->L.views = b->d_views;
+        b->L.prob_N = b->d_probN;
+        b->L.ph = b->probs[0]->a32.ph;
+        b->L.pr = b->probs[0]->a32.pr;
+        for (int n = 3; n <= 5; ++n) {
+            dgk::host::Operators1D op;
+            dgk::host::dg_operators(n, op);
+            dgk::OpsR<float> &o = b->L.op[n - 3];
+            std::memset(&o, 0, sizeof(o));
+            for (int i = 0; i <= n; ++i) {
+                for (int j = 0; j <= n; ++j) o.Dh[i * (n + 1) + j] = (float)op.Dhat[i * (n + 1) + j];
+                o.Lp[i] = (float)(op.lp[i] / op.w[i]);
+                o.Lm[i] = (float)(op.lm[i] / op.w[i]);
+                o.lp[i] = (float)op.lp[i];
+                o.lm[i] = (float)op.lm[i];
+            }
+        }
+        b->L.bar = b->d_bar;
+        b->L.status = b->d_bar + 2;
+        b->L.bar_limit = 4000000000LL;  // about 2 s at 2 GHz
+        rc = batch_build_tiles(b);
+    }
+    if (rc) {
+        dgk_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return DGK_OK;
+}
+
+void dgk_batch_destroy(dgk_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    batch_drop_graph(b);
+    for (dgk_ctx *c : b->probs) dgk_destroy(c);
+    if (b->d_views) cudaFree(b->d_views);
+    if (b->d_probN) cudaFree(b->d_probN);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_bar) cudaFree(b->d_bar);
+    if (b->d_args) cudaFree(b->d_args);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+dgk_ctx *dgk_batch_problem(dgk_batch *b, int i)
+{
+    if (!b || i < 0 || i >= (int)b->probs.size()) return nullptr;
+    return b->probs[i];
+}
+
+int dgk_batch_set_dt(dgk_batch *b, const double *dt)
+{
+    if (!b || !dt) return fail(DGK_ERR_ARG, "null argument");
+    for (size_t i = 0; i < b->probs.size(); ++i) {
+        if (!(dt[i] > 0) || !std::isfinite(dt[i])) return fail(DGK_ERR_ARG, "dt must be positive");
+        int rc = set_coef(b->probs[i], dt[i]);
+        if (rc) return rc;
+    }
+    return DGK_OK;
+}
+
+int dgk_batch_run(dgk_batch *b, int nsteps)
+{
+    if (!b || nsteps < 0) return fail(DGK_ERR_ARG, "bad arguments");
+    if (nsteps == 0) return DGK_OK;
+    if (!b->graph) {
+        cudaGraph_t g;
+        DGK_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = batch_launch_step(b);
+        cudaError_t err = cudaStreamEndCapture(b->stream, &g);
+        if (rc) return rc;
+        if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("batched graph capture: ") + cudaGetErrorString(err));
+        err = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (err != cudaSuccess) {
+            b->graph = nullptr;
+            return fail(DGK_ERR_CUDA, std::string("batched graph instantiate: ") + cudaGetErrorString(err));
+        }
+    }
+    for (int s = 0; s < nsteps; ++s) DGK_CUDA(cudaGraphLaunch(b->graph, b->stream));
+    return DGK_OK;
+}
+
+int dgk_batch_set_config(dgk_batch *b, const int *cfg)
+{
+    if (!b || !cfg) return fail(DGK_ERR_ARG, "null argument");
+    if (cfg[0] < 1 || cfg[0] > b->max_bps) return fail(DGK_ERR_ARG, "blocks per SM out of range");
+    for (int i = 1; i < 4; ++i)
+        if (cfg[i] < 1) return fail(DGK_ERR_ARG, "elements per tile must be positive");
+    DGK_CUDA(cudaStreamSynchronize(b->stream));
+    b->bps = cfg[0];
+    for (int i = 0; i < 3; ++i) b->k[i] = cfg[i + 1];
+    return batch_build_tiles(b);
+}
+
+int dgk_batch_status(dgk_batch *b, int *per_problem)
+{
+    if (!b) return fail(DGK_ERR_ARG, "null batch");
+    DGK_CUDA(cudaStreamSynchronize(b->stream));
+    unsigned s = 0;
+    DGK_CUDA(cudaMemcpy(&s, b->d_bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    DGK_CUDA(cudaMemset(b->d_bar + 2, 0, sizeof(unsigned)));
+    // after a timeout the arrival counter is stale: start the next launch from zero
+    if (s & dgk::kStatBarrier) DGK_CUDA(cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned)));
+    int first = (s & dgk::kStatBarrier) ? fail(DGK_ERR_TIMEOUT, "a grid barrier of the batched kernel timed out") : DGK_OK;
+    for (size_t i = 0; i < b->probs.size(); ++i) {
+        const int rc = dgk_status(b->probs[i]);
+        if (per_problem) per_problem[i] = rc;
+        if (!first && rc) first = rc;
+    }
+    return first;
+}
+
+int dgk_batch_autotune(dgk_batch *b, int *out)
+{
+    if (!b) return fail(DGK_ERR_ARG, "null batch");
+    // refuse to tune on a state that already reports an error (the tuning runs clear the
+    // status words at the end)
+    int rc = dgk_batch_status(b, nullptr);
+    if (rc) return rc;
+    // keep the states: U and G of every problem
+    std::vector<double *> keep;
+    for (dgk_ctx *c : b->probs) {
+        const size_t n = (size_t)c->NV * c->ne * c->NP;
+        double *k2 = nullptr;
+        if (cudaMalloc(&k2, 2 * n * sizeof(double)) != cudaSuccess) {
+            for (double *q : keep) cudaFree(q);
+            return fail(DGK_ERR_NOMEM, "autotune backup");
+        }
+        cudaMemcpyAsync(k2, c->U, n * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
+        cudaMemcpyAsync(k2 + n, c->G, n * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
+        keep.push_back(k2);
+    }
+    auto restore = [&]() {
+        for (size_t i = 0; i < b->probs.size(); ++i) {
+            dgk_ctx *c = b->probs[i];
+            const size_t n = (size_t)c->NV * c->ne * c->NP;
+            cudaMemcpyAsync(c->U, keep[i], n * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
+            cudaMemcpyAsync(c->G, keep[i] + n, n * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
+            c->kt->traces(c->args(), b->stream);
+        }
+    };
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // every candidate starts from the kept state: one warm-up step, then two timed steps
+    auto time_config = [&](float &ms) -> int {
+        restore();
+        int r = batch_launch_step(b);
+        if (r) return r;
+        cudaEventRecord(e0, b->stream);
+        for (int k = 0; k < 2 && !r; ++k) r = batch_launch_step(b);
+        cudaEventRecord(e1, b->stream);
+        if (r) return r;
+        if (cudaEventSynchronize(e1) != cudaSuccess) return fail(DGK_ERR_CUDA, "autotune timing");
+        cudaEventElapsedTime(&ms, e0, e1);
+        return DGK_OK;
+    };
+    float best = 1e30f;
+    // resident blocks per SM, then elements per tile for each degree (greedy)
+    int best_bps = b->bps;
+    for (int bps = 1; bps <= b->max_bps && !rc; ++bps) {
+        b->bps = bps;
+        float ms = 0;
+        rc = time_config(ms);
+        if (!rc && ms < best) { best = ms; best_bps = bps; }
+    }
+    b->bps = best_bps;
+    for (int n = 0; n < 3 && !rc; ++n) {
+        bool used = false;
+        for (int q : b->probN) used |= (q == n + 3);
+        if (!used) continue;
+        int best_k = b->k[n];
+        for (int kk : {1, 2, 4}) {
+            b->k[n] = kk;
+            if ((rc = batch_build_tiles(b))) break;
+            float ms = 0;
+            if ((rc = time_config(ms))) break;
+            if (ms < best) { best = ms; best_k = kk; }
+        }
+        b->k[n] = best_k;
+    }
+    if (!rc) rc = batch_build_tiles(b);
+    restore();
+    cudaStreamSynchronize(b->stream);
+    for (double *q : keep) cudaFree(q);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // statuses latched by the tuning runs say nothing about the restored states
+    for (dgk_ctx *c : b->probs)
+        if (c->status) cudaMemset(c->status, 0, sizeof(unsigned));
+    cudaMemset(b->d_bar + 2, 0, sizeof(unsigned));
+    if (out) {
+        out[0] = b->bps;
+        out[1] = b->k[0];
+        out[2] = b->k[1];
+        out[3] = b->k[2];
+    }
+    return rc;
 }
 
 }  // extern "C"

@@ -19,6 +19,7 @@ constexpr int kMaxP = 6;  // polynomial degree N <= 5
 // device status bits (latched with atomicOr, read by dgk_status)
 constexpr unsigned kStatNonFinite = 1u;
 constexpr unsigned kStatDomain = 2u;
+constexpr unsigned kStatBarrier = 4u;  // batched kernel: a grid barrier timed out
 
 struct Phys {
     int model;  // 1 or 2
@@ -74,7 +75,8 @@ struct Ops {
 
 // ------------------------------------------------------------------ sizes
 
-template <int D, int N>
+// EB: elements per block (tile shape); 0 = as many as fit in 256 threads.
+template <int D, int N, int EB = 0>
 struct Shape {
     static constexpr int P = N + 1;
     static constexpr int NP = D == 2 ? P * P : P * P * P;   // nodes per element
@@ -84,7 +86,7 @@ struct Shape {
     static constexpr int NL = D + 2;                        // pass-1 lifted variables (rho, u, c)
     static constexpr int NQ = NV + D * D + 2 * D + 1;       // face quantities: U, grad u, grad T, grad c, lap c
     static constexpr int NFQ = NF * NFP;                    // face points per element
-    static constexpr int EPB = (256 / NP) > 0 ? (256 / NP) : 1;  // elements per block
+    static constexpr int EPB = EB > 0 ? EB : ((256 / NP) > 0 ? (256 / NP) : 1);  // elements per block
     static constexpr int NT = EPB * NP;                     // threads per block
 };
 

@@ -20,7 +20,27 @@
 
 #include "dgk_common.cuh"
 
+// Resident threads per SM requested from the compiler for each stage kernel, as a
+// register budget (65536 / threads).  Measured on the 3D N = 5 FP32-bulk workload:
+// k_lift1 gains 8% at 1728 threads, k_lift2vol 4% at 1080; capping k_surf_rk's
+// registers slows it (its loads in flight need the registers).  0 leaves the choice to
+// the compiler.  The FP64 form asks for half the threads (its values take two registers).
+#ifndef DGK_THREADS_LIFT1
+#define DGK_THREADS_LIFT1 1728
+#endif
+#ifndef DGK_THREADS_LIFT2
+#define DGK_THREADS_LIFT2 1080
+#endif
+#ifndef DGK_THREADS_SURF
+#define DGK_THREADS_SURF 0
+#endif
+
 namespace dgk {
+
+__host__ __device__ constexpr int min_blocks(int threads_per_block, int threads_per_sm)
+{
+    return threads_per_sm / threads_per_block > 0 ? threads_per_sm / threads_per_block : 1;
+}
 
 // 1D operators in the bulk type (see Ops).
 template <typename R>
@@ -29,14 +49,13 @@ struct OpsR {
     R Lp[kMaxP], Lm[kMaxP], lp[kMaxP], lm[kMaxP];
 };
 
+// Per-problem data: geometry, walls and device arrays.  Kernel parameters for a single
+// problem; shared memory in the batched kernel.
 template <typename R>
-struct KArgs {
+struct KView {
     Geom g;
     GeomR<R> gr;
-    Phys ph;
-    PhysR<R> pr;
     WallsR<R> wr;
-    OpsR<R> op;
     double *U;           // [NV][ne][NP]
     double *G;           // [NV][ne][NP]
     R *Utv;              // [NV][ne][NP] volume part of U_t
@@ -44,8 +63,27 @@ struct KArgs {
     R *tr2;              // [2][ne][NF][NFP] traces of T and of d c / d x_normal
     R *fd;               // [NV+NV+1][ne][NF][NFP] one-sided face data (U, F, lambda)
     double *out;         // rhs output [NV][ne][NP], or nodal T [ne][NP]
-    const double *coef;  // device [A_0..A_4, B_0..B_4, dt]
+    const double *coef;  // device [A_0..A_4, B_0..B_4, dt] of this problem
     unsigned *status;
+};
+
+template <typename R>
+struct KArgs {
+    KView<R> v;
+    Phys ph;
+    PhysR<R> pr;
+    OpsR<R> op;
+};
+
+// What a kernel body sees: the problem's view plus the physics and the operators of
+// its degree (kernel parameters in both forms, so operator entries stay uniform
+// constant-bank operands).
+template <typename R>
+struct Ctx {
+    const KView<R> &v;
+    const Phys &ph;
+    const PhysR<R> &pr;
+    const OpsR<R> &op;
 };
 
 // ------------------------------------------------------------------ line helpers
@@ -123,19 +161,19 @@ __device__ __forceinline__ void check_state(unsigned *status, R rho, R T, double
 
 // Common per-thread prologue: local element, node, validity, element coordinates.
 // Neighbours are computed on demand (no per-thread array indexed at run time).
-template <int D, int N>
+template <int D, int N, int EB = 0>
 struct Slot {
-    using S = Shape<D, N>;
+    using S = Shape<D, N, EB>;
     int le, n;
     long long e;
     bool valid;
     int cx, cy, cz;
-    __device__ Slot(const Geom &g)
+    __device__ Slot(const Geom &g, long long blk)
     {
         le = threadIdx.x / S::NP;
         n = threadIdx.x % S::NP;
-        e = (long long)blockIdx.x * S::EPB + le;
-        valid = e < g.ne;
+        e = blk * S::EPB + le;
+        valid = (int)threadIdx.x < S::NT && e < g.ne;
         const unsigned ue = valid ? (unsigned)e : 0u, n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
         cx = (int)(ue % n0);
         cy = (int)((ue / n0) % n1);
@@ -165,25 +203,25 @@ struct Slot {
 // sDc[d][n] holds dc/dx_d; with write_tr2 the traces of dc/dx_d on the two faces normal
 // to d are written to tr2[1].
 
-template <int D, int N, typename R>
+template <int D, int N, typename R, int EB = 0>
 struct CLift {
-    using S = Shape<D, N>;
+    using S = Shape<D, N, EB>;
     static constexpr int smem_per_elem = S::NP + S::NF * S::NFP + D * S::NP + S::NP;  // c, c*, dc, T
 
-    __device__ static void run(const KArgs<R> &a, const Slot<D, N> &t, R *sC, R *sCs, R *sDc, double Ud[S::NV],
+    __device__ static void run(const Ctx<R> &a, const Slot<D, N, EB> &t, R *sC, R *sCs, R *sDc, double Ud[S::NV],
                                bool write_tr2)
     {
         constexpr int P = S::P, NP = S::NP, NF = S::NF, NFP = S::NFP, NV = S::NV;
-        const long long ne = a.g.ne;
+        const long long ne = a.v.g.ne;
         if (t.valid) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) Ud[v] = a.U[((long long)v * ne + t.e) * NP + t.n];
+            for (int v = 0; v < NV; ++v) Ud[v] = a.v.U[((long long)v * ne + t.e) * NP + t.n];
             sC[t.n] = to_bulk<R>(Ud[D + 2]);
             for (int q = t.n; q < NF * NFP; q += NP) {
                 const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
-                const R own = a.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
-                const long long b = t.nbr(a.g, f);
-                sCs[q] = b >= 0 ? R(0.5) * (own + a.tr1[fidx<NF, NFP>(ne, D + 1, b, 2 * dir + 1 - side, fp)]) : own;
+                const R own = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
+                const long long b = t.nbr(a.v.g, f);
+                sCs[q] = b >= 0 ? R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, D + 1, b, 2 * dir + 1 - side, fp)]) : own;
             }
         }
         __syncthreads();
@@ -193,13 +231,13 @@ struct CLift {
                 const int base = line_base<P>(line, dir), stride = line_stride<P>(dir);
                 R x[P], y[P];
                 load_line<P, R>(sC, base, stride, x);
-                lift_line<P, R>(a.op, x, sCs[(2 * dir) * NFP + line], sCs[(2 * dir + 1) * NFP + line], a.gr.inv2h[dir], y);
+                lift_line<P, R>(a.op, x, sCs[(2 * dir) * NFP + line], sCs[(2 * dir + 1) * NFP + line], a.v.gr.inv2h[dir], y);
                 store_line<P, R>(sDc + dir * NP, base, stride, y);
                 if (write_tr2) {
                     R tm, tp;
                     trace_pair<P, R>(a.op, y, tm, tp);
-                    a.tr2[fidx<NF, NFP>(ne, 1, t.e, 2 * dir, line)] = tm;
-                    a.tr2[fidx<NF, NFP>(ne, 1, t.e, 2 * dir + 1, line)] = tp;
+                    a.v.tr2[fidx<NF, NFP>(ne, 1, t.e, 2 * dir, line)] = tm;
+                    a.v.tr2[fidx<NF, NFP>(ne, 1, t.e, 2 * dir + 1, line)] = tp;
                 }
             }
         }
@@ -223,7 +261,7 @@ struct NodeState {
 };
 
 template <int D, typename R>
-__device__ __forceinline__ R node_temperature(const KArgs<R> &a, const double *Ud, const NodeState<D, R> &q,
+__device__ __forceinline__ R node_temperature(const Ctx<R> &a, const double *Ud, const NodeState<D, R> &q,
                                               const R *gc)
 {
     R msq = R(0), gc2 = R(0);
@@ -238,14 +276,13 @@ __device__ __forceinline__ R node_temperature(const KArgs<R> &a, const double *U
 
 // ------------------------------------------------------------------ kernel 1
 
-template <int D, int N, typename R>
-__global__ void __launch_bounds__(Shape<D, N>::NT) k_lift1(KArgs<R> a)
+template <int D, int N, typename R, int EB = 0>
+__device__ __forceinline__ void lift1_body(const Ctx<R> &a, long long blk, unsigned char *smraw)
 {
-    using S = Shape<D, N>;
-    using L = CLift<D, N, R>;
+    using S = Shape<D, N, EB>;
+    using L = CLift<D, N, R, EB>;
     constexpr int P = S::P, NP = S::NP, NFP = S::NFP, NF = S::NF, NV = S::NV;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const Slot<D, N> t(a.g);
+        const Slot<D, N, EB> t(a.v.g, blk);
     R *sC = reinterpret_cast<R *>(smraw) + (size_t)t.le * L::smem_per_elem;
     R *sCs = sC + NP, *sDc = sCs + NF * NFP, *sT = sDc + D * NP;
     double Ud[NV];
@@ -257,21 +294,29 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_lift1(KArgs<R> a)
         NodeState<D, R> q;
         q.load(Ud);
         const R T = node_temperature<D, R>(a, Ud, q, gc);
-        check_state<R>(a.status, q.rho, T, Ud[D + 1]);
+        check_state<R>(a.v.status, q.rho, T, Ud[D + 1]);
         sT[t.n] = T;
     }
     __syncthreads();
     if (t.valid) {
-        const long long ne = a.g.ne;
+        const long long ne = a.v.g.ne;
         for (int q = t.n; q < D * NFP; q += NP) {
             const int dir = q / NFP, line = q % NFP;
             R x[P], tm, tp;
             load_line<P, R>(sT, line_base<P>(line, dir), line_stride<P>(dir), x);
             trace_pair<P, R>(a.op, x, tm, tp);
-            a.tr2[fidx<NF, NFP>(ne, 0, t.e, 2 * dir, line)] = tm;
-            a.tr2[fidx<NF, NFP>(ne, 0, t.e, 2 * dir + 1, line)] = tp;
+            a.v.tr2[fidx<NF, NFP>(ne, 0, t.e, 2 * dir, line)] = tm;
+            a.v.tr2[fidx<NF, NFP>(ne, 0, t.e, 2 * dir + 1, line)] = tp;
         }
     }
+}
+
+template <int D, int N, typename R, int EB = 0>
+__global__ void __launch_bounds__(Shape<D, N, EB>::NT, min_blocks(Shape<D, N, EB>::NT, DGK_THREADS_LIFT1 / (int)(sizeof(R) / 4))) k_lift1(KArgs<R> args)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const Ctx<R> a{args.v, args.ph, args.pr, args.op};
+    lift1_body<D, N, R, EB>(a, blockIdx.x, smraw);
 }
 
 // ------------------------------------------------------------------ face flux
@@ -292,7 +337,7 @@ struct FaceRec {
 // pressure and signal speed, minus the wall viscous flux with u_wall = 0, zeta = 0 and
 // grad c . n from the contact angle), and the Rusanov signal speed |u_DIR| + s.
 template <int D, typename R, int DIR>
-__device__ __forceinline__ void face_flux(const KArgs<R> &a, int f, bool wall, const R *r, R *F, R &lam)
+__device__ __forceinline__ void face_flux(const Ctx<R> &a, int f, bool wall, const R *r, R *F, R &lam)
 {
     using FR = FaceRec<D>;
     const PhysR<R> &ph = a.pr;
@@ -337,7 +382,7 @@ __device__ __forceinline__ void face_flux(const KArgs<R> &a, int f, bool wall, c
         return;
     }
     const R nsign = (f & 1) ? R(1) : R(-1);
-    const R gn = a.wr.K[f] * (c - a.wr.rl[f]) * (c - a.wr.rv[f]);
+    const R gn = a.v.wr.K[f] * (c - a.v.wr.rl[f]) * (c - a.v.wr.rv[f]);
     R Fi[D + 3], Fg[D + 3], Ui[D + 3], Ug[D + 3];
     const R ui = u[DIR], ug = -u[DIR];
     Fi[0] = m[DIR];
@@ -372,11 +417,11 @@ __device__ __forceinline__ void face_flux(const KArgs<R> &a, int f, bool wall, c
 
 // Face record of face point (f, fp) with f normal to DIR, traced from the nodal fields
 // in shared memory along the line through fp (one end), then its face data.
-template <int D, int N, typename R, int DIR>
-__device__ __forceinline__ void face_point(const KArgs<R> &a, long long e, bool wall, int f, int fp, const R *sG,
+template <int D, int N, typename R, int DIR, int EB = 0>
+__device__ __forceinline__ void face_point(const Ctx<R> &a, long long e, bool wall, int f, int fp, const R *sG,
                                            const R *sGT, const R *sN)
 {
-    using S = Shape<D, N>;
+    using S = Shape<D, N, EB>;
     using FR = FaceRec<D>;
     constexpr int P = S::P, NP = S::NP, NL = S::NL, NV = S::NV, NQ = FR::NQ, NF = S::NF, NFP = S::NFP;
     const int base = line_base<P>(fp, DIR);
@@ -403,22 +448,22 @@ __device__ __forceinline__ void face_point(const KArgs<R> &a, long long e, bool 
     }
     R F[NV], lam;
     face_flux<D, R, DIR>(a, f, wall, r, F, lam);
-    const long long ne = a.g.ne;
+    const long long ne = a.v.g.ne;
     const long long st = ne * NF * NFP;
     const long long fo = (e * NF + f) * NFP + fp;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        a.fd[v * st + fo] = r[v];
-        a.fd[(NV + v) * st + fo] = F[v];
+        a.v.fd[v * st + fo] = r[v];
+        a.v.fd[(NV + v) * st + fo] = F[v];
     }
-    a.fd[(2 * NV) * st + fo] = lam;
+    a.v.fd[(2 * NV) * st + fo] = lam;
 }
 
 // ------------------------------------------------------------------ kernel 2
 
-template <int D, int N, typename R>
+template <int D, int N, typename R, int EB = 0>
 struct K2Smem {
-    using S = Shape<D, N>;
+    using S = Shape<D, N, EB>;
     static constexpr int G = D * S::NL * S::NP;  // pass-1 gradients sG[d][v][n]
     static constexpr int GT = D * S::NP;         // grad T
     static constexpr int X1 = S::NL * S::NP + S::NF * S::NL * S::NFP;  // prims, q*
@@ -430,17 +475,16 @@ struct K2Smem {
     static constexpr int per_elem = G + GT + X;
 };
 
-template <int D, int N, typename R>
-__global__ void __launch_bounds__(Shape<D, N>::NT) k_lift2vol(KArgs<R> a)
+template <int D, int N, typename R, int EB = 0>
+__device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, unsigned char *smraw)
 {
-    using S = Shape<D, N>;
-    using M = K2Smem<D, N, R>;
+    using S = Shape<D, N, EB>;
+    using M = K2Smem<D, N, R, EB>;
     constexpr int P = S::P, NP = S::NP, NFP = S::NFP, NF = S::NF, NL = S::NL, NV = S::NV;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const Slot<D, N> t(a.g);
+        const Slot<D, N, EB> t(a.v.g, blk);
     R *sG = reinterpret_cast<R *>(smraw) + (size_t)t.le * M::per_elem;
     R *sGT = sG + M::G, *sX = sGT + M::GT;
-    const long long ne = a.g.ne;
+    const long long ne = a.v.g.ne;
     const int n = t.n;
 
     // ---- pass 1: prims (rho, u, c) and central face values (one-sided rho, c and u* = 0 at walls)
@@ -449,7 +493,7 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_lift2vol(KArgs<R> a)
     NodeState<D, R> ns;
     if (t.valid) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) Ud[v] = a.U[((long long)v * ne + t.e) * NP + n];
+        for (int v = 0; v < NV; ++v) Ud[v] = a.v.U[((long long)v * ne + t.e) * NP + n];
         ns.load(Ud);
         sQ[n] = ns.rho;
 #pragma unroll
@@ -457,12 +501,12 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_lift2vol(KArgs<R> a)
         sQ[(D + 1) * NP + n] = ns.c;
         for (int q = n; q < NF * NFP; q += NP) {
             const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
-            const long long b = t.nbr(a.g, f);
+            const long long b = t.nbr(a.v.g, f);
 #pragma unroll
             for (int v = 0; v < NL; ++v) {
-                const R own = a.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)];
+                const R own = a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)];
                 R val;
-                if (b >= 0) val = R(0.5) * (own + a.tr1[fidx<NF, NFP>(ne, v, b, 2 * dir + 1 - side, fp)]);
+                if (b >= 0) val = R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, v, b, 2 * dir + 1 - side, fp)]);
                 else val = (v >= 1 && v <= D) ? R(0) : own;
                 sQs[(f * NL + v) * NFP + fp] = val;
             }
@@ -479,7 +523,7 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_lift2vol(KArgs<R> a)
                 R x[P], y[P];
                 load_line<P, R>(sQ + v * NP, base, stride, x);
                 lift_line<P, R>(a.op, x, sQs[((2 * dir) * NL + v) * NFP + line], sQs[((2 * dir + 1) * NL + v) * NFP + line],
-                                a.gr.inv2h[dir], y);
+                                a.v.gr.inv2h[dir], y);
                 store_line<P, R>(sG + (dir * NL + v) * NP, base, stride, y);
             }
         }
@@ -502,18 +546,18 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_lift2vol(KArgs<R> a)
         sT[n] = T;
         for (int q = n; q < NF * NFP; q += NP) {
             const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
-            const long long b = t.nbr(a.g, f);
-            const R ownT = a.tr2[fidx<NF, NFP>(ne, 0, t.e, f, fp)];
-            const R ownD = a.tr2[fidx<NF, NFP>(ne, 1, t.e, f, fp)];
+            const long long b = t.nbr(a.v.g, f);
+            const R ownT = a.v.tr2[fidx<NF, NFP>(ne, 0, t.e, f, fp)];
+            const R ownD = a.v.tr2[fidx<NF, NFP>(ne, 1, t.e, f, fp)];
             R vT, vD;
             if (b >= 0) {
                 const int fo = 2 * dir + 1 - side;
-                vT = R(0.5) * (ownT + a.tr2[fidx<NF, NFP>(ne, 0, b, fo, fp)]);
-                vD = R(0.5) * (ownD + a.tr2[fidx<NF, NFP>(ne, 1, b, fo, fp)]);
+                vT = R(0.5) * (ownT + a.v.tr2[fidx<NF, NFP>(ne, 0, b, fo, fp)]);
+                vD = R(0.5) * (ownD + a.v.tr2[fidx<NF, NFP>(ne, 1, b, fo, fp)]);
             } else {
-                const R cm = a.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
-                const R gn = a.wr.K[f] * (cm - a.wr.rl[f]) * (cm - a.wr.rv[f]);
-                vT = a.wr.Tw[f];
+                const R cm = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
+                const R gn = a.v.wr.K[f] * (cm - a.v.wr.rl[f]) * (cm - a.v.wr.rv[f]);
+                vT = a.v.wr.Tw[f];
                 vD = side ? gn : -gn;
             }
             sTs[q] = vT;
@@ -535,7 +579,7 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_lift2vol(KArgs<R> a)
             R *dst = isT ? sGT + dir * NP : sLp + dir * NP;
             R x[P], y[P];
             load_line<P, R>(src, base, stride, x);
-            lift_line<P, R>(a.op, x, qs[(2 * dir) * NFP + line], qs[(2 * dir + 1) * NFP + line], a.gr.inv2h[dir], y);
+            lift_line<P, R>(a.op, x, qs[(2 * dir) * NFP + line], qs[(2 * dir + 1) * NFP + line], a.v.gr.inv2h[dir], y);
             store_line<P, R>(dst, base, stride, y);
         }
     }
@@ -582,7 +626,7 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_lift2vol(KArgs<R> a)
                 const int base = line_base<P>(line, dir);
                 R x[P], y[P];
                 load_line<P, R>(sF + v * NP, base, stride, x);
-                dhat_line<P, R>(a.op, x, a.gr.inv2h[dir], y);
+                dhat_line<P, R>(a.op, x, a.v.gr.inv2h[dir], y);
                 if (dir > 0) {
 #pragma unroll
                     for (int l = 0; l < P; ++l) y[l] += sAcc[v * NP + base + l * stride];
@@ -595,7 +639,7 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_lift2vol(KArgs<R> a)
     R *sN = sX + M::X4;  // nodal U, div u, lap c (clear of sF, sAcc)
     if (t.valid) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) a.Utv[((long long)v * ne + t.e) * NP + n] = S_[v] - sAcc[v * NP + n];
+        for (int v = 0; v < NV; ++v) a.v.Utv[((long long)v * ne + t.e) * NP + n] = S_[v] - sAcc[v * NP + n];
         sN[n] = rho;
 #pragma unroll
         for (int k = 0; k < D; ++k) sN[(1 + k) * NP + n] = m[k];
@@ -614,29 +658,37 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_lift2vol(KArgs<R> a)
     if (t.valid) {
         for (int q = n; q < NF * NFP; q += NP) {
             const int f = q / NFP, fp = q % NFP, dir = f >> 1;
-            const bool wall = t.nbr(a.g, f) < 0;
-            if (dir == 0) face_point<D, N, R, 0>(a, t.e, wall, f, fp, sG, sGT, sN);
-            else if (D == 2 || dir == 1) face_point<D, N, R, 1>(a, t.e, wall, f, fp, sG, sGT, sN);
-            else face_point<D, N, R, (D == 3 ? 2 : 1)>(a, t.e, wall, f, fp, sG, sGT, sN);
+            const bool wall = t.nbr(a.v.g, f) < 0;
+            if (dir == 0) face_point<D, N, R, 0, EB>(a, t.e, wall, f, fp, sG, sGT, sN);
+            else if (D == 2 || dir == 1) face_point<D, N, R, 1, EB>(a, t.e, wall, f, fp, sG, sGT, sN);
+            else face_point<D, N, R, (D == 3 ? 2 : 1), EB>(a, t.e, wall, f, fp, sG, sGT, sN);
         }
     }
 }
 
+template <int D, int N, typename R, int EB = 0>
+__global__ void __launch_bounds__(Shape<D, N, EB>::NT, min_blocks(Shape<D, N, EB>::NT, DGK_THREADS_LIFT2 / (int)(sizeof(R) / 4))) k_lift2vol(KArgs<R> args)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const Ctx<R> a{args.v, args.ph, args.pr, args.op};
+    lift2vol_body<D, N, R, EB>(a, blockIdx.x, smraw);
+}
+
 // ------------------------------------------------------------------ kernel 3
 
-template <int D, int N, typename R>
+template <int D, int N, typename R, int EB = 0>
 struct K3Smem {
-    using S = Shape<D, N>;
+    using S = Shape<D, N, EB>;
     static constexpr int a1 = S::NF * S::NV * S::NFP;
     static constexpr int a2 = S::NL * S::NP;
     static constexpr int per_elem = a1 > a2 ? a1 : a2;
 };
 
 // New pass-1 traces of (rho, u, c) of the element's state (double U -> bulk type).
-template <int D, int N, typename R>
-__device__ __forceinline__ void write_traces(const KArgs<R> &a, const Slot<D, N> &t, R *sQ, const double *Ud)
+template <int D, int N, typename R, int EB = 0>
+__device__ __forceinline__ void write_traces(const Ctx<R> &a, const Slot<D, N, EB> &t, R *sQ, const double *Ud)
 {
-    using S = Shape<D, N>;
+    using S = Shape<D, N, EB>;
     constexpr int P = S::P, NP = S::NP, NFP = S::NFP, NF = S::NF, NL = S::NL;
     if (t.valid) {
         const R rho = to_bulk<R>(Ud[0]), irho = R(1) / rho;
@@ -647,30 +699,29 @@ __device__ __forceinline__ void write_traces(const KArgs<R> &a, const Slot<D, N>
     }
     __syncthreads();
     if (t.valid) {
-        const long long ne = a.g.ne;
+        const long long ne = a.v.g.ne;
         for (int q = t.n; q < D * NL * NFP; q += NP) {
             const int dir = q / (NL * NFP), v = (q / NFP) % NL, line = q % NFP;
             R x[P], tm, tp;
             load_line<P, R>(sQ + v * NP, line_base<P>(line, dir), line_stride<P>(dir), x);
             trace_pair<P, R>(a.op, x, tm, tp);
-            a.tr1[fidx<NF, NFP>(ne, v, t.e, 2 * dir, line)] = tm;
-            a.tr1[fidx<NF, NFP>(ne, v, t.e, 2 * dir + 1, line)] = tp;
+            a.v.tr1[fidx<NF, NFP>(ne, v, t.e, 2 * dir, line)] = tm;
+            a.v.tr1[fidx<NF, NFP>(ne, v, t.e, 2 * dir + 1, line)] = tp;
         }
     }
 }
 
-// mode 0: write U_t (double) to a.out; mode 1: RK stage `stage` with coefficients from
-// a.coef (G = A G + dt U_t; U = U + B G) and new traces.
-template <int D, int N, typename R>
-__global__ void __launch_bounds__(Shape<D, N>::NT) k_surf_rk(KArgs<R> a, int mode, int stage)
+// mode 0: write U_t (double) to a.v.out; mode 1: RK stage `stage` with coefficients from
+// a.v.coef (G = A G + dt U_t; U = U + B G) and new traces.
+template <int D, int N, typename R, int EB = 0>
+__device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, unsigned char *smraw, int mode, int stage)
 {
-    using S = Shape<D, N>;
-    using M = K3Smem<D, N, R>;
+    using S = Shape<D, N, EB>;
+    using M = K3Smem<D, N, R, EB>;
     constexpr int P = S::P, NP = S::NP, NFP = S::NFP, NF = S::NF, NV = S::NV;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const Slot<D, N> t(a.g);
+        const Slot<D, N, EB> t(a.v.g, blk);
     R *sFs = reinterpret_cast<R *>(smraw) + (size_t)t.le * M::per_elem;
-    const long long ne = a.g.ne;
+    const long long ne = a.v.g.ne;
     // issue the node loads first so that their latency overlaps the face phase
     R utv[NV];
     double u0[NV], g0[NV];
@@ -678,10 +729,10 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_surf_rk(KArgs<R> a, int mod
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const long long idx = ((long long)v * ne + t.e) * NP + t.n;
-            utv[v] = a.Utv[idx];
+            utv[v] = a.v.Utv[idx];
             if (mode != 0) {
-                u0[v] = a.U[idx];
-                g0[v] = a.G[idx];
+                u0[v] = a.v.U[idx];
+                g0[v] = a.v.G[idx];
             }
         }
     }
@@ -689,19 +740,19 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_surf_rk(KArgs<R> a, int mod
         const long long st = ne * NF * NFP;
         for (int q = t.n; q < NF * NFP; q += NP) {
             const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
-            const long long b = t.nbr(a.g, f);
+            const long long b = t.nbr(a.v.g, f);
             const long long oo = ((long long)t.e * NF + f) * NFP + fp;
             if (b < 0) {
 #pragma unroll
-                for (int v = 0; v < NV; ++v) sFs[(f * NV + v) * NFP + fp] = a.fd[(NV + v) * st + oo];
+                for (int v = 0; v < NV; ++v) sFs[(f * NV + v) * NFP + fp] = a.v.fd[(NV + v) * st + oo];
             } else {
                 const long long ob = ((long long)b * NF + (2 * dir + 1 - side)) * NFP + fp;
                 const long long iL = side ? oo : ob, iR = side ? ob : oo;
-                const R lam = fmax(a.fd[(2 * NV) * st + iL], a.fd[(2 * NV) * st + iR]);
+                const R lam = fmax(a.v.fd[(2 * NV) * st + iL], a.v.fd[(2 * NV) * st + iR]);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    const R FL = a.fd[(NV + v) * st + iL], FR = a.fd[(NV + v) * st + iR];
-                    const R UL = a.fd[v * st + iL], UR = a.fd[v * st + iR];
+                    const R FL = a.v.fd[(NV + v) * st + iL], FR = a.v.fd[(NV + v) * st + iR];
+                    const R UL = a.v.fd[v * st + iL], UR = a.v.fd[v * st + iR];
                     sFs[(f * NV + v) * NFP + fp] = R(0.5) * (FL + FR) - R(0.5) * lam * (UR - UL);
                 }
             }
@@ -721,8 +772,8 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_surf_rk(KArgs<R> a, int mod
 #pragma unroll
             for (int l = 0; l < P; ++l)
                 if (l == i) { vp = a.op.Lp[l]; vm = a.op.Lm[l]; }
-            Lp[d] = vp * a.gr.inv2h[d];
-            Lm[d] = vm * a.gr.inv2h[d];
+            Lp[d] = vp * a.v.gr.inv2h[d];
+            Lm[d] = vm * a.v.gr.inv2h[d];
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -736,7 +787,7 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_surf_rk(KArgs<R> a, int mod
     if (mode == 0) {
         if (t.valid) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) a.out[((long long)v * ne + t.e) * NP + t.n] = to_f64<R>(Ut[v]);
+            for (int v = 0; v < NV; ++v) a.v.out[((long long)v * ne + t.e) * NP + t.n] = to_f64<R>(Ut[v]);
         }
         return;
     }
@@ -744,7 +795,7 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_surf_rk(KArgs<R> a, int mod
     if (t.valid) {
         // FP64 accumulation: G = A G + dt U_t, U = U + B G (two FP64 FMAs per variable;
         // in the FP32-bulk form dt U_t is formed in float, as U_t itself is)
-        const double A = a.coef[stage], B = a.coef[5 + stage], dt = a.coef[10];
+        const double A = a.v.coef[stage], B = a.v.coef[5 + stage], dt = a.v.coef[10];
         const R dtR = to_bulk<R>(dt);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -753,45 +804,59 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_surf_rk(KArgs<R> a, int mod
             if constexpr (sizeof(R) == 8) gg = A * g0[v] + dt * Ut[v];
             else gg = fma(A, g0[v], to_f64<R>(dtR * Ut[v]));
             const double uu = fma(B, gg, u0[v]);
-            a.G[idx] = gg;
-            a.U[idx] = uu;
+            a.v.G[idx] = gg;
+            a.v.U[idx] = uu;
             Ud[v] = uu;
         }
     }
     __syncthreads();  // sFs dead; reuse as sQ
-    write_traces<D, N, R>(a, t, sFs, Ud);
+    write_traces<D, N, R, EB>(a, t, sFs, Ud);
+}
+
+template <int D, int N, typename R, int EB = 0>
+__global__ void __launch_bounds__(Shape<D, N, EB>::NT, min_blocks(Shape<D, N, EB>::NT, DGK_THREADS_SURF / (int)(sizeof(R) / 4))) k_surf_rk(KArgs<R> args, int mode, int stage)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const Ctx<R> a{args.v, args.ph, args.pr, args.op};
+    surf_rk_body<D, N, R, EB>(a, blockIdx.x, smraw, mode, stage);
 }
 
 // ------------------------------------------------------------------ set-up kernels
 
 // pass-1 traces of the current state
-template <int D, int N, typename R>
-__global__ void __launch_bounds__(Shape<D, N>::NT) k_traces(KArgs<R> a)
+template <int D, int N, typename R, int EB = 0>
+__device__ __forceinline__ void traces_body(const Ctx<R> &a, long long blk, unsigned char *smraw)
 {
-    using S = Shape<D, N>;
+    using S = Shape<D, N, EB>;
     constexpr int NP = S::NP, NV = S::NV;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const Slot<D, N> t(a.g);
+        const Slot<D, N, EB> t(a.v.g, blk);
     R *sQ = reinterpret_cast<R *>(smraw) + (size_t)t.le * (size_t)S::NL * NP;
     double Ud[NV];
     if (t.valid) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) Ud[v] = a.U[((long long)v * a.g.ne + t.e) * NP + t.n];
+        for (int v = 0; v < NV; ++v) Ud[v] = a.v.U[((long long)v * a.v.g.ne + t.e) * NP + t.n];
     }
-    write_traces<D, N, R>(a, t, sQ, Ud);
+    write_traces<D, N, R, EB>(a, t, sQ, Ud);
 }
 
-// mode 0: nodal temperature into a.out[ne][NP]; mode 1: set rho e from the temperature in
-// a.out (dgk_set_primitive): rho e = rho (R cv T - a rho) + |m|^2/(2 rho)
-// + alpha/2 (rho - c)^2 + gamma_K/2 |grad c|^2, grad c lifted from the current traces.
-template <int D, int N, typename R>
-__global__ void __launch_bounds__(Shape<D, N>::NT) k_node_T(KArgs<R> a, int mode)
+template <int D, int N, typename R, int EB = 0>
+__global__ void __launch_bounds__(Shape<D, N, EB>::NT) k_traces(KArgs<R> args)
 {
-    using S = Shape<D, N>;
-    using L = CLift<D, N, R>;
-    constexpr int NP = S::NP, NF = S::NF, NFP = S::NFP, NV = S::NV;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const Slot<D, N> t(a.g);
+    const Ctx<R> a{args.v, args.ph, args.pr, args.op};
+    traces_body<D, N, R, EB>(a, blockIdx.x, smraw);
+}
+
+// mode 0: nodal temperature into a.v.out[ne][NP]; mode 1: set rho e from the temperature in
+// a.v.out (dgk_set_primitive): rho e = rho (R cv T - a rho) + |m|^2/(2 rho)
+// + alpha/2 (rho - c)^2 + gamma_K/2 |grad c|^2, grad c lifted from the current traces.
+template <int D, int N, typename R, int EB = 0>
+__device__ __forceinline__ void node_T_body(const Ctx<R> &a, long long blk, unsigned char *smraw, int mode)
+{
+    using S = Shape<D, N, EB>;
+    using L = CLift<D, N, R, EB>;
+    constexpr int NP = S::NP, NF = S::NF, NFP = S::NFP, NV = S::NV;
+        const Slot<D, N, EB> t(a.v.g, blk);
     R *sC = reinterpret_cast<R *>(smraw) + (size_t)t.le * L::smem_per_elem;
     R *sCs = sC + NP, *sDc = sCs + NF * NFP;
     double Ud[NV];
@@ -804,10 +869,10 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_node_T(KArgs<R> a, int mode
     if (mode == 0) {
         NodeState<D, R> q;
         q.load(Ud);
-        a.out[idx] = to_f64<R>(node_temperature<D, R>(a, Ud, q, gc));
+        a.v.out[idx] = to_f64<R>(node_temperature<D, R>(a, Ud, q, gc));
         return;
     }
-    const double rho = Ud[0], T = a.out[idx];
+    const double rho = Ud[0], T = a.v.out[idx];
     double msq = 0.0, gc2 = 0.0;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -815,8 +880,16 @@ __global__ void __launch_bounds__(Shape<D, N>::NT) k_node_T(KArgs<R> a, int mode
         gc2 += (double)gc[k] * (double)gc[k];
     }
     const double dc = rho - Ud[D + 2];
-    a.U[((long long)(D + 1) * a.g.ne + t.e) * NP + t.n] =
+    a.v.U[((long long)(D + 1) * a.v.g.ne + t.e) * NP + t.n] =
         rho * (kRgas * a.ph.cv * T - kAvdw * rho) + 0.5 * msq / rho + 0.5 * a.ph.alpha * dc * dc + 0.5 * a.ph.gK * gc2;
+}
+
+template <int D, int N, typename R, int EB = 0>
+__global__ void __launch_bounds__(Shape<D, N, EB>::NT) k_node_T(KArgs<R> args, int mode)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const Ctx<R> a{args.v, args.ph, args.pr, args.op};
+    node_T_body<D, N, R, EB>(a, blockIdx.x, smraw, mode);
 }
 
 }  // namespace dgk

@@ -27,7 +27,7 @@ struct Launcher {
     static constexpr size_t sm_surf = (size_t)S::EPB * K3Smem<D, N, R>::per_elem * sizeof(R);
     static constexpr size_t sm_traces = (size_t)S::EPB * S::NL * S::NP * sizeof(R);
 
-    static unsigned blocks(const KArgs<R> &a) { return (unsigned)((a.g.ne + S::EPB - 1) / S::EPB); }
+    static unsigned blocks(const KArgs<R> &a) { return (unsigned)((a.v.g.ne + S::EPB - 1) / S::EPB); }
 
     static cudaError_t prepare()
     {
@@ -74,6 +74,24 @@ struct Launcher {
         return &t;
     }
 };
+
+// Arguments of the batched persistent stage kernel (dgk_batch.cu), FP32-bulk form.
+struct BatchLaunch {
+    const KView<float> *views;                         // [nprob]
+    const int *prob_N, *tile_prob, *tile_blk, *tile_len;
+    int ntiles;
+    Phys ph;
+    PhysR<float> pr;
+    OpsR<float> op[3];                                 // N = 3, 4, 5
+    unsigned *bar, *status;                            // barrier words, batch status
+    long long bar_limit;                               // barrier spin limit (cycles)
+};
+size_t batch_smem();
+size_t batch_args_bytes();
+cudaError_t batch_prepare(int *max_blocks_per_sm);
+cudaError_t batch_upload_args(const BatchLaunch &L, void *dev);
+cudaError_t batch_bind_args(const void *dev, cudaStream_t s);
+cudaError_t batch_stage_launch(int grid, int stage, cudaStream_t s);
 
 }  // namespace dgk
 

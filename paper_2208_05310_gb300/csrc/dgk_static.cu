@@ -70,12 +70,12 @@ template <typename R>
 int fill(dgk::KArgs<R> &a, const dgk_params &q, const dgk_box_mesh &m, const dgk::host::Operators1D &op, int D, long long ne)
 {
     std::memset(&a, 0, sizeof(a));
-    a.g.ne = ne;
+    a.v.g.ne = ne;
     for (int d = 0; d < 3; ++d) {
-        a.g.n[d] = d < D ? m.n[d] : 1;
-        a.g.periodic[d] = d < D ? m.periodic[d] : 1;
-        a.g.inv2h[d] = d < D ? 2.0 / ((m.hi[d] - m.lo[d]) / m.n[d]) : 0.0;
-        a.gr.inv2h[d] = (R)a.g.inv2h[d];
+        a.v.g.n[d] = d < D ? m.n[d] : 1;
+        a.v.g.periodic[d] = d < D ? m.periodic[d] : 1;
+        a.v.g.inv2h[d] = d < D ? 2.0 / ((m.hi[d] - m.lo[d]) / m.n[d]) : 0.0;
+        a.v.gr.inv2h[d] = (R)a.v.g.inv2h[d];
     }
     a.ph = dgk::Phys{q.model, q.gammaK, q.mu, q.kappa, q.cv, q.alpha, q.beta, 0.5 * q.alpha, 0.5 * q.gammaK,
                      1.0 / (dgk::kRgas * q.cv)};
@@ -100,10 +100,10 @@ int fill(dgk::KArgs<R> &a, const dgk_params &q, const dgk_box_mesh &m, const dgk
         if (!dgk::host::maxwell(m.wall[f].T_wall, rv, rl) || !dgk::host::sigma_vl(m.wall[f].T_wall, q.gammaK, sig))
             return fail_static(DGK_ERR_THERMO, "wall temperature has no saturation states (need 0 < T_wall < 1)");
         const double dr = rl - rv;
-        a.wr.K[f] = (R)(-6.0 * sig * std::cos(m.wall[f].theta_deg * M_PI / 180.0) / (q.gammaK * dr * dr * dr));
-        a.wr.rl[f] = (R)rl;
-        a.wr.rv[f] = (R)rv;
-        a.wr.Tw[f] = (R)m.wall[f].T_wall;
+        a.v.wr.K[f] = (R)(-6.0 * sig * std::cos(m.wall[f].theta_deg * M_PI / 180.0) / (q.gammaK * dr * dr * dr));
+        a.v.wr.rl[f] = (R)rl;
+        a.v.wr.rv[f] = (R)rv;
+        a.v.wr.Tw[f] = (R)m.wall[f].T_wall;
     }
     const int P = op.P;
     for (int i = 0; i < P; ++i) {
@@ -121,19 +121,19 @@ void place(dgk::KArgs<R> &a, unsigned char *base, const double *U, double *Ut, i
 {
     const int NV = D + 3, NL = D + 2, NF = 2 * D;
     size_t off = 0;
-    a.status = reinterpret_cast<unsigned *>(base + off);
+    a.v.status = reinterpret_cast<unsigned *>(base + off);
     off += 256;
-    a.Utv = reinterpret_cast<R *>(base + off);
+    a.v.Utv = reinterpret_cast<R *>(base + off);
     off += align256((size_t)NV * ne * NP * sizeof(R));
-    a.tr1 = reinterpret_cast<R *>(base + off);
+    a.v.tr1 = reinterpret_cast<R *>(base + off);
     off += align256((size_t)NL * ne * NF * NFP * sizeof(R));
-    a.tr2 = reinterpret_cast<R *>(base + off);
+    a.v.tr2 = reinterpret_cast<R *>(base + off);
     off += align256((size_t)2 * ne * NF * NFP * sizeof(R));
-    a.fd = reinterpret_cast<R *>(base + off);
-    a.U = const_cast<double *>(U);
-    a.G = nullptr;
-    a.out = Ut;
-    a.coef = nullptr;
+    a.v.fd = reinterpret_cast<R *>(base + off);
+    a.v.U = const_cast<double *>(U);
+    a.v.G = nullptr;
+    a.v.out = Ut;
+    a.v.coef = nullptr;
 }
 
 }  // namespace

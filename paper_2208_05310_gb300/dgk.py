@@ -46,7 +46,9 @@ EXPORTS = ("dgk_create", "dgk_destroy", "dgk_set_params", "dgk_mesh_box", "dgk_s
            "dgk_set_primitive", "dgk_upload_state", "dgk_download_state", "dgk_rhs", "dgk_rk_step", "dgk_run",
            "dgk_max_dt", "dgk_diagnostics", "dgk_status", "dgk_set_timing", "dgk_kernel_time", "dgk_maxwell",
            "dgk_sigma_vl", "dgk_interface_width", "dgk_status_string", "dgk_last_error", "dgk_check_conversions",
-           "dgk_rhs_static")
+           "dgk_rhs_static", "dgk_node_temperature_pressure", "dgk_batch_create", "dgk_batch_destroy",
+           "dgk_batch_problem", "dgk_batch_set_dt", "dgk_batch_run", "dgk_batch_autotune", "dgk_batch_status",
+           "dgk_batch_set_config")
 
 
 def lib():
@@ -74,6 +76,15 @@ def lib():
         "dgk_run": (i, [vp, i, d]),
         "dgk_max_dt": (i, [vp, d, d, dp]),
         "dgk_diagnostics": (i, [vp, dp]),
+        "dgk_node_temperature_pressure": (i, [vp, vp, vp, sz, i]),
+        "dgk_batch_create": (i, [C.POINTER(vp), i, vp, C.POINTER(DgkParams), i, C.POINTER(DgkBoxMesh)]),
+        "dgk_batch_destroy": (None, [vp]),
+        "dgk_batch_problem": (vp, [vp, i]),
+        "dgk_batch_set_dt": (i, [vp, dp]),
+        "dgk_batch_run": (i, [vp, i]),
+        "dgk_batch_autotune": (i, [vp, C.POINTER(i)]),
+        "dgk_batch_status": (i, [vp, C.POINTER(i)]),
+        "dgk_batch_set_config": (i, [vp, C.POINTER(i)]),
         "dgk_status": (i, [vp]),
         "dgk_set_timing": (i, [vp, i]),
         "dgk_kernel_time": (i, [vp, i, dp, C.POINTER(C.c_longlong)]),
@@ -263,6 +274,14 @@ class Context:
         _check(lib().dgk_diagnostics(self._h, out.ctypes.data_as(C.POINTER(C.c_double))), "dgk_diagnostics")
         return dict(zip(DIAG_NAMES, out))
 
+    def temperature_pressure(self):
+        """Nodal temperature and pressure, numpy arrays of shape (nelem, np)."""
+        T = np.zeros((self.nelem, self.np))
+        p = np.zeros((self.nelem, self.np))
+        _check(lib().dgk_node_temperature_pressure(self._h, T.ctypes.data, p.ctypes.data, T.size, 0),
+               "dgk_node_temperature_pressure")
+        return T, p
+
     def status(self):
         """Synchronise and raise if the device latched an error."""
         _check(lib().dgk_status(self._h), "dgk_status")
@@ -277,3 +296,76 @@ class Context:
         ms, cnt = C.c_double(), C.c_longlong()
         _check(lib().dgk_kernel_time(self._h, which, C.byref(ms), C.byref(cnt)), "dgk_kernel_time")
         return ms.value, cnt.value
+
+
+class _BatchMember(Context):
+    """A problem of a batch: the single-problem calls on a context owned by the batch."""
+
+    def __init__(self, handle, stream, dim, N):
+        self.device = None
+        self.stream = stream
+        self._h = C.c_void_p(handle)
+        ne, npn, nv = C.c_longlong(), C.c_int(), C.c_int()
+        _check(lib().dgk_sizes(self._h, C.byref(ne), C.byref(npn), C.byref(nv)), "dgk_sizes")
+        self.dim, self.nelem, self.np, self.nv = dim, ne.value, npn.value, nv.value
+        self.N = N
+
+    def close(self):
+        self._h = C.c_void_p()
+
+
+class Batch:
+    """An ensemble of independent 2D problems advanced by one persistent launch per RK
+    stage (FP32-bulk form).  meshes: list of dicts with keys dim, N, n, lo, hi,
+    periodic, walls (as for Context.mesh_box)."""
+
+    def __init__(self, meshes, device=0, stream=None, **params):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
+        p = make_params(precision="fp32bulk", **params)
+        arr = (DgkBoxMesh * len(meshes))()
+        for k, m in enumerate(meshes):
+            dim = m["dim"]
+            arr[k] = make_box_mesh(dim, m["N"], list(m["n"]) + [1] * (3 - dim), list(m["lo"]) + [0.0] * (3 - dim),
+                                   list(m["hi"]) + [1.0] * (3 - dim), list(m["periodic"]) + [1] * (3 - dim),
+                                   m.get("walls"))
+        self._h = C.c_void_p()
+        _check(lib().dgk_batch_create(C.byref(self._h), device, C.c_void_p(self.stream.cuda_stream), C.byref(p),
+                                      len(meshes), arr), "dgk_batch_create")
+        self.problems = [_BatchMember(lib().dgk_batch_problem(self._h, k), self.stream, m["dim"], m["N"])
+                         for k, m in enumerate(meshes)]
+
+    def close(self):
+        if self._h:
+            for q in self.problems:
+                q.close()
+            lib().dgk_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_dt(self, dt):
+        dt = np.ascontiguousarray(dt, dtype=np.float64)
+        _check(lib().dgk_batch_set_dt(self._h, dt.ctypes.data_as(C.POINTER(C.c_double))), "dgk_batch_set_dt")
+
+    def run(self, nsteps):
+        _check(lib().dgk_batch_run(self._h, int(nsteps)), "dgk_batch_run")
+
+    def autotune(self):
+        out = (C.c_int * 4)()
+        _check(lib().dgk_batch_autotune(self._h, out), "dgk_batch_autotune")
+        return dict(blocks_per_sm=out[0], k3=out[1], k4=out[2], k5=out[3])
+
+    def set_config(self, blocks_per_sm, k3, k4, k5):
+        cfg = (C.c_int * 4)(blocks_per_sm, k3, k4, k5)
+        _check(lib().dgk_batch_set_config(self._h, cfg), "dgk_batch_set_config")
+
+    def status(self):
+        """Synchronise; raise on the first error (barrier timeout, then any problem's)."""
+        per = (C.c_int * len(self.problems))()
+        _check(lib().dgk_batch_status(self._h, per), "dgk_batch_status")
+        return list(per)

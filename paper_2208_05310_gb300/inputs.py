@@ -102,6 +102,24 @@ def ensemble_specs(nprob, seed, n_range=(16, 96), N_choices=(3, 4, 5), T_range=(
     return specs
 
 
+def ensemble_mesh(spec):
+    """Mesh of one ensemble problem: [0,1]^2 on n x n elements of degree N, periodic in x,
+    isothermal no-slip walls at y = 0 and y = 1 at the problem's temperature and contact
+    angle (mesh dictionary with keys dim, N, n, lo, hi, periodic, walls)."""
+    w = (spec["T"], spec["theta"])
+    return dict(dim=2, N=spec["N"], n=[spec["n"], spec["n"]], lo=[0.0, 0.0], hi=[1.0, 1.0], periodic=[1, 0],
+                walls={2: w, 3: w})
+
+
+def ensemble_primitive(x, spec, rho_v, rho_l, width, noise_amp=1e-3):
+    """Initial state of one ensemble problem: a droplet (or a bubble) of the drawn radius
+    centred on the bottom wall, tanh interface between the saturation densities, seeded
+    density noise, at rest at the problem's temperature."""
+    noise = uniform_noise(x[0].shape, spec["seed"])
+    return droplet(x, [0.5, 0.0], spec["radius"], rho_v, rho_l, width, spec["T"], liquid_inside=spec["droplet"],
+                   noise=noise, noise_amp=noise_amp)
+
+
 def random_admissible(dim, nelem, np_, seed, rho_range=(0.3, 1.9), T_range=(0.8, 0.95), u_amp=0.05, c_amp=0.01):
     """Coordinate-free seeded state for exact-input tests: per-element density levels
     plus per-node variation, small velocities, temperatures in T_range and c = rho

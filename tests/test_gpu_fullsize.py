@@ -1,0 +1,81 @@
+"""Parity at full size: the confined-bridge workload the bench times (3D, N = 5,
+64x64x32 elements, 28.3 M nodes, same kernels and launch shapes), right-hand side
+sampled element by element against the oracle.
+
+The right-hand side of an element depends on the state of elements at most three
+elements away (pass-1 lifting -> temperature -> pass-2 lifting -> face data of the
+neighbours), and the initial energy on one more (the lifted grad c of set-up).  The
+oracle therefore evaluates the same input recipe on a 9x9x9-element sub-box centred on
+the sampled element (aligned with a wall when the element is within four elements of
+it, with an artificial wall or periodic wrap at the far side), and the centre element's
+right-hand side is exact.
+
+The check is on what a time step does with the right-hand side: per conserved variable
+over the sampled element's nodes, the difference of the increments dt*U_t (dt the
+oracle's stable step for the sub-box) relative to the element's state, with the floors
+of rel_l2.  FP64: 1e-12, the bar for conserved variables; FP32-bulk: the per-variable
+bounds of one step of the FP32-bulk parity tests.  (At rest, U_t is round-off in the
+quiescent liquid and vapour and in the z-momentum everywhere, so a ratio of U_t norms
+would compare round-off with round-off.)  The relative right-hand-side error is printed."""
+import numpy as np
+import pytest
+
+from cases import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+# interface (bridge radius 0.5 about x = y = 1) at mid-height and at both walls, liquid
+# core, vapour, vapour next to the bottom wall
+SAMPLES = [(47, 32, 16), (16, 32, 0), (32, 47, 31), (31, 32, 8), (5, 5, 16), (48, 48, 1)]
+
+
+def _sub_box(orc, wl, ix, iy, iz, W=9):
+    m = wl["mesh"]
+    h = [(m["hi"][d] - m["lo"][d]) / m["n"][d] for d in range(3)]
+    nz = m["n"][2]
+    x0, y0 = ix - W // 2, iy - W // 2
+    if iz <= W // 2:
+        z0, periodic_z, walls = 0, 0, {4: m["walls"][4], 5: (0.85, 90.0)}
+    elif iz >= nz - 1 - W // 2:
+        z0, periodic_z, walls = nz - W, 0, {4: (0.85, 90.0), 5: m["walls"][5]}
+    else:
+        z0, periodic_z, walls = iz - W // 2, 1, {}
+    lo = [m["lo"][0] + x0 * h[0], m["lo"][1] + y0 * h[1], m["lo"][2] + z0 * h[2]]
+    hi = [lo[0] + W * h[0], lo[1] + W * h[1], lo[2] + W * h[2]]
+    mesh = orc.make_mesh(3, m["N"], [W, W, W], lo, hi, [1, 1, periodic_z], walls)
+    local = (ix - x0) + W * ((iy - y0) + W * (iz - z0))
+    return orc.Oracle(mesh, orc.make_params(**wl["params"])), local
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32bulk"])
+def test_fullsize_sampled_rhs(orc, precision):
+    import bench
+    from paper_2208_05310_gb300 import dgk
+    wl = bench.workload_c5()
+    m = wl["mesh"]
+    g = dgk.Context()
+    g.set_params(rk=wl["rk"], precision=precision, **wl["params"])
+    g.mesh_box(3, m["N"], m["n"], m["lo"], m["hi"], m["periodic"], m["walls"])
+    rv, rl = dgk.maxwell(wl["T0"])
+    width = dgk.interface_width(wl["T0"], wl["params"]["cv"], wl["params"]["gammaK"])
+    g.set_primitive(bench.primitive_state(wl, g.node_coords(), rv, rl, width))
+    Ut = g.rhs()
+    g.close()
+    orv, orl = orc.maxwell(wl["T0"])
+    owidth = orc.interface_width(wl["T0"], wl["params"]["cv"], wl["params"]["gammaK"])
+    nx, ny = m["n"][0], m["n"][1]
+    for (ix, iy, iz) in SAMPLES:
+        o, local = _sub_box(orc, wl, ix, iy, iz)
+        Uo = o.set_primitive(bench.primitive_state(wl, o.node_coords(), orv, orl, owidth))
+        ref = o.rhs(Uo)[:, local, :]
+        dt = o.max_dt(Uo)
+        e = ix + nx * (iy + ny * iz)
+        got = Ut[:, e, :]
+        snorm = np.sqrt((Uo[:, local, :] ** 2).sum(axis=1))
+        den = np.maximum(snorm, 1e-3 * snorm.max())
+        err = dt * np.sqrt(((got - ref) ** 2).sum(axis=1)) / den
+        rhs_err = rel_l2(got[:, None, :], ref[:, None, :])
+        print(f"{precision} sample {(ix, iy, iz)}: increment error / state {np.array2string(err, precision=1)}, "
+              f"rhs relative {np.array2string(rhs_err, precision=1)}")
+        tol = np.full(6, 1e-12) if precision == "fp64" else np.array([1e-7, 3e-5, 3e-5, 3e-5, 2e-7, 5e-7])
+        assert np.all(err < tol), ((ix, iy, iz), err, tol)
