@@ -441,11 +441,15 @@ def batch_measure(wl, local_rank, steps, warmup, unbatched=True, e2e=False):
     peak, peak_kind = measured_peak()
     avg_launch_ms = ms / steps / stages
     achieved = alg / (avg_launch_ms / 1e3) / 1e9
+    launches = stages * steps * (1 if cfg["form"] == "persistent" else 3)
     out = dict(value=dof * stages * steps / (ms / 1e3), unit=UNIT, ms_per_step=ms / steps, steps=steps,
-               nodes=dof, problems=len(meshes), autotuned=cfg, autotune_s=t_tune, gpu_launches=stages * steps,
-               roofline=dict(bound="hbm", kernel="k_batch_stage", achieved=achieved, peak=peak, unit="GB/s",
-                             frac=achieved / peak, peak_kind=peak_kind, alg_bytes_per_launch=alg,
-                             avg_launch_ms=avg_launch_ms, traffic=None))
+               nodes=dof, problems=len(meshes), autotuned=cfg, autotune_s=t_tune, gpu_launches=launches,
+               roofline=dict(bound="hbm",
+                             kernel="k_batch_stage" if cfg["form"] == "persistent" else "k_batch_phase<0,1,2>",
+                             achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, peak_kind=peak_kind,
+                             alg_bytes_per_launch=alg, avg_launch_ms=avg_launch_ms, traffic=None,
+                             note="per RK stage: one persistent launch, or the three grouped phase launches; "
+                                  "time from the graph-replayed steps / stages"))
     if e2e:
         host_in = [torch.empty(q.shape(), dtype=torch.float64, pin_memory=True) for q in B.problems]
         host_out = [torch.empty(q.shape(), dtype=torch.float64, pin_memory=True) for q in B.problems]

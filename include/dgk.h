@@ -173,10 +173,11 @@ int dgk_check_conversions(const double *x, size_t n, int on_device, unsigned lon
 /* ---------------- batched ensembles ----------------
  *
  * Many independent 2D problems (degrees N = 3, 4, 5, any mesh sizes, walls and
- * temperatures; common physics parameters, FP32-bulk form) advanced together: every RK
- * stage is ONE persistent cooperative launch that runs the three phases of the stage for
- * all problems, separated by grid barriers (bounded spin; a timeout is reported as
- * DGK_ERR_TIMEOUT, never a hang), and one step is replayed as a captured CUDA graph.
+ * temperatures; common physics parameters, FP32-bulk form) advanced together, one step
+ * replayed as a captured CUDA graph.  Persistent form: every RK stage is ONE cooperative
+ * launch that runs the three phases of the stage for all problems, separated by grid
+ * barriers (bounded spin; a timeout is reported as DGK_ERR_TIMEOUT, never a hang).
+ * Grouped form: every phase is one launch over all problems.  The autotuner picks.
  * Each problem has its own time step.  The problems are ordinary contexts owned by the
  * batch: use dgk_batch_problem() with the single-problem calls (set-up, download,
  * diagnostics, max_dt).
@@ -196,16 +197,21 @@ int dgk_batch_set_dt(dgk_batch *b, const double *dt);
 /* nsteps RK steps of every problem: stages x one persistent launch per step, replayed
    from a captured graph.  Asynchronous. */
 int dgk_batch_run(dgk_batch *b, int nsteps);
-/* Autotuner: times one step for candidate work decompositions -- elements per tile for
-   each degree N (k_N element blocks of the degree's block shape) and resident blocks
-   per SM of the persistent grid -- and keeps the fastest.  Every candidate runs three
-   steps from the current states, which are restored afterwards; the status words are
-   cleared after tuning (tuning refuses to start, returning the error, if a problem
-   already reports one).  out (nullable) = {blocks_per_sm, k_3, k_4, k_5}. */
+/* Autotuner: times candidate forms and work decompositions -- the persistent form
+   (one cooperative launch per stage, phases separated by grid barriers) for each count
+   of resident blocks per SM, the grouped form (one launch per phase over the tiles of
+   all problems, one element block per CTA), and, if the persistent form wins, element
+   blocks per tile k_N for each degree N -- and keeps the fastest.  Every candidate runs three steps from the current states,
+   which are restored afterwards; the status words are cleared after tuning (tuning
+   refuses to start, returning the error, if a problem already reports one).
+   out (nullable, 7 ints) = {form, blocks_per_sm, k_3, k_4, k_5, microseconds per step of
+   the best persistent candidate, microseconds per step of the grouped form}. */
 int dgk_batch_autotune(dgk_batch *b, int *out);
-/* Set the work decomposition directly: cfg = {blocks_per_sm, k_3, k_4, k_5} (as returned
-   by dgk_batch_autotune; blocks_per_sm in 1..the occupancy limit, k_N >= 1).  Results do
-   not depend on it: every element's arithmetic is the same for any decomposition. */
+/* Set the form and decomposition directly: cfg = {form (0 persistent, 1 grouped),
+   blocks_per_sm (1..the occupancy limit of the persistent kernel), k_3, k_4, k_5 (>= 1;
+   element blocks per tile of the persistent form; the grouped form ignores them and
+   blocks_per_sm)}.
+   Results do not depend on it: every element's arithmetic is the same. */
 int dgk_batch_set_config(dgk_batch *b, const int *cfg);
 /* Synchronise; per_problem (nullable, nprob ints) receives each problem's status.
    Returns the first error: barrier timeout, then any problem's error. */

@@ -910,6 +910,7 @@ struct dgk_batch {
     int *d_probN = nullptr, *d_tiles = nullptr;
     unsigned *d_bar = nullptr;  // [0..1] barrier, [2] status
     void *d_args = nullptr;     // device copy of the kernel parameters
+    int form = 0;               // 0 persistent launch per stage, 1 grouped launches per phase
     int sms = 0, max_bps = 1, bps = 1;
     int k[3] = {1, 1, 1};
     size_t tiles_cap = 0;
@@ -924,26 +925,31 @@ void batch_drop_graph(dgk_batch *b)
     b->graph = nullptr;
 }
 
-// tile table: runs of k_N element blocks of one problem, problems interleaved
+// tile table: runs of k_N element blocks of one problem; sorted by degree (N = 3, 4, 5),
+// problems of one degree interleaved
 int batch_build_tiles(dgk_batch *b)
 {
     std::vector<int> tp, tb, tl;
-    std::vector<long long> next(b->probs.size(), 0), nblk(b->probs.size());
+    std::vector<long long> nblk(b->probs.size());
     for (size_t p = 0; p < b->probs.size(); ++p) nblk[p] = (b->probs[p]->ne + b->probs[p]->kt->elems_per_block - 1) /
                                                           b->probs[p]->kt->elems_per_block;
-    bool more = true;
-    while (more) {
-        more = false;
-        for (size_t p = 0; p < b->probs.size(); ++p) {
-            if (next[p] >= nblk[p]) continue;
-            const int kk = b->k[b->probN[p] - 3];
-            const long long len = std::min<long long>(kk, nblk[p] - next[p]);
-            tp.push_back((int)p);
-            tb.push_back((int)next[p]);
-            tl.push_back((int)len);
-            next[p] += len;
-            more = true;
+    for (int N = 3; N <= 5; ++N) {
+        std::vector<long long> next(b->probs.size(), 0);
+        bool more = true;
+        while (more) {
+            more = false;
+            for (size_t p = 0; p < b->probs.size(); ++p) {
+                if (b->probN[p] != N || next[p] >= nblk[p]) continue;
+                const int kk = b->form == 1 ? 1 : b->k[N - 3];  // grouped form: one element block per CTA
+                const long long len = std::min<long long>(kk, nblk[p] - next[p]);
+                tp.push_back((int)p);
+                tb.push_back((int)next[p]);
+                tl.push_back((int)len);
+                next[p] += len;
+                more = true;
+            }
         }
+        if (N < 5) b->L.tile_split[N - 3] = (int)tp.size();
     }
     const size_t nt = tp.size();
     if (nt > b->tiles_cap) {
@@ -973,7 +979,8 @@ int batch_launch_step(dgk_batch *b)
     cudaError_t e0 = dgk::batch_bind_args(b->d_args, b->stream);
     if (e0 != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("batch parameters: ") + cudaGetErrorString(e0));
     for (int s = 0; s < ns; ++s) {
-        cudaError_t err = dgk::batch_stage_launch(b->sms * b->bps, s, b->stream);
+        cudaError_t err = b->form == 0 ? dgk::batch_stage_launch(b->sms * b->bps, s, b->stream)
+                                       : dgk::batch_phase_launches(b->L.ntiles, s, b->stream);
         if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("batched stage launch: ") + cudaGetErrorString(err));
     }
     return DGK_OK;
@@ -1122,12 +1129,14 @@ int dgk_batch_run(dgk_batch *b, int nsteps)
 int dgk_batch_set_config(dgk_batch *b, const int *cfg)
 {
     if (!b || !cfg) return fail(DGK_ERR_ARG, "null argument");
-    if (cfg[0] < 1 || cfg[0] > b->max_bps) return fail(DGK_ERR_ARG, "blocks per SM out of range");
-    for (int i = 1; i < 4; ++i)
-        if (cfg[i] < 1) return fail(DGK_ERR_ARG, "elements per tile must be positive");
+    if (cfg[0] != 0 && cfg[0] != 1) return fail(DGK_ERR_ARG, "form must be 0 (persistent) or 1 (grouped)");
+    if (cfg[1] < 1 || cfg[1] > b->max_bps) return fail(DGK_ERR_ARG, "blocks per SM out of range");
+    for (int i = 2; i < 5; ++i)
+        if (cfg[i] < 1) return fail(DGK_ERR_ARG, "element blocks per tile must be positive");
     DGK_CUDA(cudaStreamSynchronize(b->stream));
-    b->bps = cfg[0];
-    for (int i = 0; i < 3; ++i) b->k[i] = cfg[i + 1];
+    b->form = cfg[0];
+    b->bps = cfg[1];
+    for (int i = 0; i < 3; ++i) b->k[i] = cfg[i + 2];
     return batch_build_tiles(b);
 }
 
@@ -1195,16 +1204,31 @@ int dgk_batch_autotune(dgk_batch *b, int *out)
         return DGK_OK;
     };
     float best = 1e30f;
-    // resident blocks per SM, then elements per tile for each degree (greedy)
-    int best_bps = b->bps;
+    // persistent form over resident blocks per SM, then the grouped form; then element
+    // blocks per tile for each degree in the faster form (greedy)
+    int best_bps = b->bps, best_form = b->form;
+    float best_form_ms[2] = {1e30f, 1e30f};
+    b->form = 0;
+    rc = batch_build_tiles(b);
     for (int bps = 1; bps <= b->max_bps && !rc; ++bps) {
         b->bps = bps;
         float ms = 0;
         rc = time_config(ms);
-        if (!rc && ms < best) { best = ms; best_bps = bps; }
+        if (!rc && ms < best) { best = ms; best_bps = bps; best_form = 0; }
+        if (!rc && ms < best_form_ms[0]) best_form_ms[0] = ms;
     }
     b->bps = best_bps;
-    for (int n = 0; n < 3 && !rc; ++n) {
+    if (!rc) {
+        b->form = 1;
+        float ms = 0;
+        if (!(rc = batch_build_tiles(b))) rc = time_config(ms);
+        if (!rc && ms < best) { best = ms; best_form = 1; }
+        if (!rc) best_form_ms[1] = ms;
+    }
+    b->form = best_form;
+    if (!rc) rc = batch_build_tiles(b);
+    // element blocks per tile: the persistent form only
+    for (int n = 0; n < 3 && !rc && b->form == 0; ++n) {
         bool used = false;
         for (int q : b->probN) used |= (q == n + 3);
         if (!used) continue;
@@ -1215,6 +1239,7 @@ int dgk_batch_autotune(dgk_batch *b, int *out)
             float ms = 0;
             if ((rc = time_config(ms))) break;
             if (ms < best) { best = ms; best_k = kk; }
+            if (ms < best_form_ms[0]) best_form_ms[0] = ms;
         }
         b->k[n] = best_k;
     }
@@ -1229,10 +1254,13 @@ int dgk_batch_autotune(dgk_batch *b, int *out)
         if (c->status) cudaMemset(c->status, 0, sizeof(unsigned));
     cudaMemset(b->d_bar + 2, 0, sizeof(unsigned));
     if (out) {
-        out[0] = b->bps;
-        out[1] = b->k[0];
-        out[2] = b->k[1];
-        out[3] = b->k[2];
+        out[0] = b->form;
+        out[1] = b->bps;
+        out[2] = b->k[0];
+        out[3] = b->k[1];
+        out[4] = b->k[2];
+        out[5] = (int)(500.0f * best_form_ms[0]);  // two timed steps -> microseconds per step
+        out[6] = (int)(500.0f * best_form_ms[1]);
     }
     return rc;
 }

@@ -12,7 +12,13 @@
 // Work items ("tiles") are runs of K consecutive element blocks of one problem; the
 // tile table is built on the host from the autotuned K per degree.  Each block copies
 // the tile's problem view (geometry, walls, array pointers) into shared memory; physics
-// constants and the operators of the three degrees stay kernel parameters.
+// constants and the operators of the three degrees live in constant memory.
+//
+// A second, grouped form runs each phase as an ordinary launch over all tiles (three
+// launches per stage, no grid barrier): one kernel holds the bodies of all three phases
+// and degrees, and its register allocation is that of the heaviest of the nine, which
+// caps the persistent form's occupancy; the grouped kernels each carry one phase.  The
+// autotuner times both forms.
 #include <cuda_runtime.h>
 
 #include "dgk_launch.cuh"
@@ -30,6 +36,7 @@ struct BatchArgs {
     const int *tile_blk;    // [ntiles] first element block of the tile
     const int *tile_len;    // [ntiles] element blocks in the tile
     int ntiles;
+    int tile_split[2];      // tiles sorted by degree: [0, s0) N = 3, [s0, s1) N = 4, [s1, ntiles) N = 5
     Phys ph;
     PhysR<R> pr;
     OpsR<R> op[3];          // N = 3, 4, 5
@@ -77,65 +84,118 @@ __constant__ BatchArgs<float> c_batch;
 
 // One element block of one problem for one phase, in a function of its own (not
 // inlined), so that the nine (degree, phase) bodies get separate register allocations.
-#ifndef DGK_BATCH_INLINE
-#define DGK_BATCH_BLOCK_ATTR __noinline__
-#else
-#define DGK_BATCH_BLOCK_ATTR __forceinline__
-#endif
-
+// One element block of one problem for one phase.
 template <int N, int PHASE>
-__device__ DGK_BATCH_BLOCK_ATTR void batch_block(long long blk, int stage)
+__device__ __forceinline__ void phase_block(const KView<float> &v, long long blk, unsigned char *sm, int stage)
 {
-    extern __shared__ __align__(128) unsigned char smraw[];
-    const KView<float> &v = *reinterpret_cast<const KView<float> *>(smraw);
     const Ctx<float> a{v, c_batch.ph, c_batch.pr, c_batch.op[N - 3]};
-    unsigned char *sm = smraw + kBatchViewBytes;
     if (PHASE == 0) lift1_body<2, N, float>(a, blk, sm);
     else if (PHASE == 1) lift2vol_body<2, N, float>(a, blk, sm);
     else surf_rk_body<2, N, float>(a, blk, sm, 1, stage);
 }
 
-template <int PHASE>
-__device__ __forceinline__ void batch_dispatch(int N, long long blk, int stage)
+// Persistent form.  The tiles are sorted by degree, and each block walks its grid-stride
+// sequence of tiles as three consecutive loops, one per degree, each with one inlined
+// body: a single loop around a branch over the three degrees' bodies leaves the
+// register allocator with the union of their live ranges across the back edge and
+// spills heavily, whereas three single-body loops allocate about like the bodies alone.
+template <int N, int PHASE>
+__device__ __forceinline__ int run_tiles(int tile, int end, int stage, KView<float> *sv, int *sh)
 {
-    if (N == 3) batch_block<3, PHASE>(blk, stage);
-    else if (N == 4) batch_block<4, PHASE>(blk, stage);
-    else batch_block<5, PHASE>(blk, stage);
+    const BatchArgs<float> &b = c_batch;
+    unsigned char *sm = reinterpret_cast<unsigned char *>(sv) + kBatchViewBytes;
+    for (; tile < end; tile += gridDim.x) {
+        const int p = b.tile_prob[tile];
+        const unsigned *src = reinterpret_cast<const unsigned *>(b.views + p);
+        unsigned *dst = reinterpret_cast<unsigned *>(sv);
+        for (int i = threadIdx.x; i < (int)(sizeof(KView<float>) / 4); i += blockDim.x) dst[i] = src[i];
+        if (threadIdx.x == 0) {
+            sh[0] = b.tile_blk[tile];
+            sh[1] = b.tile_len[tile];
+        }
+        __syncthreads();
+        const int blk0 = sh[0], len = sh[1];
+        for (int j = 0; j < len; ++j) {
+            phase_block<N, PHASE>(*sv, blk0 + j, sm, stage);
+            __syncthreads();
+        }
+    }
+    return tile;
+}
+
+template <int PHASE>
+__device__ __forceinline__ void run_phase(int stage, KView<float> *sv, int *sh)
+{
+    const BatchArgs<float> &b = c_batch;
+    int tile = blockIdx.x;
+    tile = run_tiles<3, PHASE>(tile, b.tile_split[0], stage, sv, sh);
+    tile = run_tiles<4, PHASE>(tile, b.tile_split[1], stage, sv, sh);
+    run_tiles<5, PHASE>(tile, b.ntiles, stage, sv, sh);
 }
 
 #ifndef DGK_BATCH_MIN_BLOCKS
-#define DGK_BATCH_MIN_BLOCKS 4  // resident blocks per SM the register allocation targets
+#define DGK_BATCH_MIN_BLOCKS 3  // resident blocks per SM the register allocation targets
 #endif
 
 __global__ void __launch_bounds__(kBatchThreads, DGK_BATCH_MIN_BLOCKS) k_batch_stage(int stage)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     KView<float> *sv = reinterpret_cast<KView<float> *>(smraw);
-    __shared__ int sN, sblk, slen;
+    __shared__ int sh[2];
     const BatchArgs<float> &b = c_batch;
-    for (int phase = 0; phase < 3; ++phase) {
-        for (int tile = blockIdx.x; tile < b.ntiles; tile += gridDim.x) {
-            const int p = b.tile_prob[tile];
-            const unsigned *src = reinterpret_cast<const unsigned *>(b.views + p);
-            unsigned *dst = reinterpret_cast<unsigned *>(sv);
-            for (int i = threadIdx.x; i < (int)(sizeof(KView<float>) / 4); i += blockDim.x) dst[i] = src[i];
-            if (threadIdx.x == 0) {
-                sN = b.prob_N[p];
-                sblk = b.tile_blk[tile];
-                slen = b.tile_len[tile];
-            }
-            __syncthreads();
-            const int N = sN, len = slen;
-            for (int j = 0; j < len; ++j) {
-                const long long blk = sblk + j;
-                if (phase == 0) batch_dispatch<0>(N, blk, stage);
-                else if (phase == 1) batch_dispatch<1>(N, blk, stage);
-                else batch_dispatch<2>(N, blk, stage);
-                __syncthreads();
-            }
-        }
-        if (phase < 2 && !grid_barrier(b.bar, gridDim.x, b.status, b.bar_limit)) return;
+    run_phase<0>(stage, sv, sh);
+    if (!grid_barrier(b.bar, gridDim.x, b.status, b.bar_limit)) return;
+    run_phase<1>(stage, sv, sh);
+    if (!grid_barrier(b.bar, gridDim.x, b.status, b.bar_limit)) return;
+    run_phase<2>(stage, sv, sh);
+}
+
+// Grouped form: one ordinary launch per phase over the element blocks of all problems
+// (one element block per CTA: the tile table is built with k_N = 1).  Each phase kernel
+// holds only that phase's three bodies, so its register allocation is that of the phase
+// (the budgets of the single-problem kernels), not of the union of all nine bodies; and
+// with no loop around the three-way branch the allocation fits those budgets without
+// spilling, which a loop over element blocks around the same branch does not.
+template <int PHASE>
+struct PhaseBudget;  // resident blocks of kBatchThreads per SM the allocation targets
+template <> struct PhaseBudget<0> { static constexpr int min_blocks = 6; };
+template <> struct PhaseBudget<1> { static constexpr int min_blocks = 4; };
+template <> struct PhaseBudget<2> { static constexpr int min_blocks = 3; };
+
+template <int PHASE>
+__global__ void __launch_bounds__(kBatchThreads, PhaseBudget<PHASE>::min_blocks) k_batch_phase(int stage)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    KView<float> *sv = reinterpret_cast<KView<float> *>(smraw);
+    __shared__ int sN, sblk;
+    const BatchArgs<float> &b = c_batch;
+    const int tile = blockIdx.x;
+    const int p = b.tile_prob[tile];
+    const unsigned *src = reinterpret_cast<const unsigned *>(b.views + p);
+    unsigned *dst = reinterpret_cast<unsigned *>(sv);
+    for (int i = threadIdx.x; i < (int)(sizeof(KView<float>) / 4); i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x == 0) {
+        sN = b.prob_N[p];
+        sblk = b.tile_blk[tile];
     }
+    __syncthreads();
+    const int N = sN;
+    unsigned char *sm = smraw + kBatchViewBytes;
+    if (N == 3) phase_block<3, PHASE>(*sv, sblk, sm, stage);
+    else if (N == 4) phase_block<4, PHASE>(*sv, sblk, sm, stage);
+    else phase_block<5, PHASE>(*sv, sblk, sm, stage);
+}
+
+template <typename R, int PHASE>
+constexpr size_t phase_smem_bytes()
+{
+    size_t m = 0;
+    const size_t c[3] = {
+        PHASE == 0 ? Launcher<2, 3, R>::sm_lift1 : PHASE == 1 ? Launcher<2, 3, R>::sm_lift2 : Launcher<2, 3, R>::sm_surf,
+        PHASE == 0 ? Launcher<2, 4, R>::sm_lift1 : PHASE == 1 ? Launcher<2, 4, R>::sm_lift2 : Launcher<2, 4, R>::sm_surf,
+        PHASE == 0 ? Launcher<2, 5, R>::sm_lift1 : PHASE == 1 ? Launcher<2, 5, R>::sm_lift2 : Launcher<2, 5, R>::sm_surf};
+    for (size_t x : c) m = x > m ? x : m;
+    return kBatchViewBytes + m;
 }
 
 // shared memory of one block: the view plus the largest phase of the three degrees
@@ -162,6 +222,15 @@ cudaError_t batch_prepare(int *max_blocks_per_sm)
     cudaError_t err = cudaFuncSetAttribute(k_batch_stage, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)batch_smem_bytes<float>());
     if (err) return err;
+    if ((err = cudaFuncSetAttribute(k_batch_phase<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)phase_smem_bytes<float, 0>())))
+        return err;
+    if ((err = cudaFuncSetAttribute(k_batch_phase<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)phase_smem_bytes<float, 1>())))
+        return err;
+    if ((err = cudaFuncSetAttribute(k_batch_phase<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)phase_smem_bytes<float, 2>())))
+        return err;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_batch_stage, kBatchThreads,
                                                          batch_smem_bytes<float>());
 }
@@ -178,6 +247,8 @@ cudaError_t batch_upload_args(const BatchLaunch &L, void *dev)
     b.tile_blk = L.tile_blk;
     b.tile_len = L.tile_len;
     b.ntiles = L.ntiles;
+    b.tile_split[0] = L.tile_split[0];
+    b.tile_split[1] = L.tile_split[1];
     b.ph = L.ph;
     b.pr = L.pr;
     for (int i = 0; i < 3; ++i) b.op[i] = L.op[i];
@@ -206,6 +277,14 @@ cudaError_t batch_stage_launch(int grid, int stage, cudaStream_t s)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_batch_stage, stage);
+}
+
+cudaError_t batch_phase_launches(int ntiles, int stage, cudaStream_t s)
+{
+    k_batch_phase<0><<<ntiles, kBatchThreads, phase_smem_bytes<float, 0>(), s>>>(stage);
+    k_batch_phase<1><<<ntiles, kBatchThreads, phase_smem_bytes<float, 1>(), s>>>(stage);
+    k_batch_phase<2><<<ntiles, kBatchThreads, phase_smem_bytes<float, 2>(), s>>>(stage);
+    return cudaGetLastError();
 }
 
 }  // namespace dgk

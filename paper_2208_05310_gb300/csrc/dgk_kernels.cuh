@@ -22,9 +22,11 @@
 
 // Resident threads per SM requested from the compiler for each stage kernel, as a
 // register budget (65536 / threads).  Measured on the 3D N = 5 FP32-bulk workload:
-// k_lift1 gains 8% at 1728 threads, k_lift2vol 4% at 1080; capping k_surf_rk's
-// registers slows it (its loads in flight need the registers).  0 leaves the choice to
-// the compiler.  The FP64 form asks for half the threads (its values take two registers).
+// k_lift1 gains 8% at 1728 threads, k_lift2vol 4% at 1080; k_surf_rk runs 27% faster
+// at 896 (72 registers, four 216-thread blocks per SM) than with the compiler's 92
+// registers (two blocks), and slower again at 1120, where it starts to spill.  0 leaves
+// the choice to the compiler.  The FP64 form asks for half the threads (its values take
+// two registers).
 #ifndef DGK_THREADS_LIFT1
 #define DGK_THREADS_LIFT1 1728
 #endif
@@ -32,7 +34,7 @@
 #define DGK_THREADS_LIFT2 1080
 #endif
 #ifndef DGK_THREADS_SURF
-#define DGK_THREADS_SURF 0
+#define DGK_THREADS_SURF 896
 #endif
 
 namespace dgk {

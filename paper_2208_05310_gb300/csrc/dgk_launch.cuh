@@ -80,6 +80,7 @@ struct BatchLaunch {
     const KView<float> *views;                         // [nprob]
     const int *prob_N, *tile_prob, *tile_blk, *tile_len;
     int ntiles;
+    int tile_split[2];                                 // tiles sorted by degree (see dgk_batch.cu)
     Phys ph;
     PhysR<float> pr;
     OpsR<float> op[3];                                 // N = 3, 4, 5
@@ -92,6 +93,7 @@ cudaError_t batch_prepare(int *max_blocks_per_sm);
 cudaError_t batch_upload_args(const BatchLaunch &L, void *dev);
 cudaError_t batch_bind_args(const void *dev, cudaStream_t s);
 cudaError_t batch_stage_launch(int grid, int stage, cudaStream_t s);
+cudaError_t batch_phase_launches(int ntiles, int stage, cudaStream_t s);
 
 }  // namespace dgk
 

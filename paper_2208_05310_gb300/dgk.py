@@ -356,12 +356,15 @@ class Batch:
         _check(lib().dgk_batch_run(self._h, int(nsteps)), "dgk_batch_run")
 
     def autotune(self):
-        out = (C.c_int * 4)()
+        """Time the persistent and grouped forms and the tile lengths; keep the fastest."""
+        out = (C.c_int * 7)()
         _check(lib().dgk_batch_autotune(self._h, out), "dgk_batch_autotune")
-        return dict(blocks_per_sm=out[0], k3=out[1], k4=out[2], k5=out[3])
+        return dict(form=("persistent", "grouped")[out[0]], blocks_per_sm=out[1], k3=out[2], k4=out[3], k5=out[4],
+                    persistent_ms=out[5] / 1e3, grouped_ms=out[6] / 1e3)
 
-    def set_config(self, blocks_per_sm, k3, k4, k5):
-        cfg = (C.c_int * 4)(blocks_per_sm, k3, k4, k5)
+    def set_config(self, form, blocks_per_sm, k3, k4, k5):
+        """form: "persistent" or "grouped"."""
+        cfg = (C.c_int * 5)(("persistent", "grouped").index(form), blocks_per_sm, k3, k4, k5)
         _check(lib().dgk_batch_set_config(self._h, cfg), "dgk_batch_set_config")
 
     def status(self):

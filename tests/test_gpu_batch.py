@@ -106,13 +106,14 @@ def test_batch_decomposition_independence_and_autotune():
     b, prims, dts = _batch(meshes, specs)
     U0 = [q.download_state() for q in b.problems]
     out = []
-    for cfg in [(1, 1, 1, 1), (1, 4, 2, 1), (2, 2, 4, 3)]:
+    for cfg in [("persistent", 1, 1, 1, 1), ("persistent", 1, 4, 2, 1), ("persistent", 2, 2, 4, 3),
+                ("grouped", 1, 1, 1, 1), ("grouped", 1, 3, 1, 2)]:
         for q, prim in zip(b.problems, prims):
             q.set_primitive(prim)
         try:
             b.set_config(*cfg)
         except Exception:
-            if cfg[0] == 1:
+            if cfg[1] == 1:
                 raise
             continue  # two blocks per SM above the occupancy limit
         b.run(3)
@@ -124,7 +125,8 @@ def test_batch_decomposition_independence_and_autotune():
     for q, prim in zip(b.problems, prims):
         q.set_primitive(prim)
     tuned = b.autotune()
-    assert tuned["blocks_per_sm"] >= 1 and min(tuned["k3"], tuned["k4"], tuned["k5"]) >= 1
+    assert tuned["form"] in ("persistent", "grouped") and tuned["blocks_per_sm"] >= 1
+    assert min(tuned["k3"], tuned["k4"], tuned["k5"]) >= 1
     for q, u in zip(b.problems, U0):  # the autotuner restores the states
         assert np.array_equal(q.download_state(), u)
     b.run(3)
