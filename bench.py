@@ -33,13 +33,17 @@ UNIT = "DOF-stage/s"
 
 # Algorithmic bytes per node and launch of each stage kernel: every array element the
 # kernel consumes or produces, once (R = bulk type size; 3D: NV = 6, NL = 5, one face
-# point per node for N = 5).
+# point per node for N = 5).  The lifting kernels read the state: in the FP64 form the
+# double state, in the FP32-bulk form its float shadow (NV values and the energy
+# balance), which the RK update writes beside the double state.
 def kernel_bytes_per_node(dim, N, rsize):
     nv, nl = dim + 3, dim + 2
     f = 2 * dim / (N + 1)  # face points per node (own faces)
-    lift1 = 8 * nv + rsize * nl * f + rsize * 2 * f
-    lift2 = 8 * nv + rsize * nl * f + rsize * 2 * f + rsize * nv + rsize * (2 * nv + 1) * f
-    surf = rsize * (2 * nv + 1) * f + rsize * nv + 8 * nv * 4 + rsize * nl * f
+    state = 8 * nv if rsize == 8 else rsize * (nv + 1)
+    shadow_w = 0 if rsize == 8 else rsize * (nv + 1)
+    lift1 = state + rsize * 1 * f + rsize * 2 * f                       # c traces in, T and dc/dn traces out
+    lift2 = state + rsize * nl * f + rsize * 2 * f + rsize * nv + rsize * (2 * nv + 1) * f
+    surf = rsize * (2 * nv + 1) * f + rsize * nv + 8 * nv * 4 + rsize * nl * f + shadow_w
     return {"k_lift1": lift1, "k_lift2vol": lift2, "k_surf_rk": surf}
 
 

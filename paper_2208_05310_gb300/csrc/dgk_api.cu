@@ -211,6 +211,7 @@ struct dgk_ctx {
     size_t rsize = 8;
     double *U = nullptr, *G = nullptr, *Tbuf = nullptr, *coef = nullptr, *rhsbuf = nullptr, *partial = nullptr;
     void *Utv = nullptr, *tr1 = nullptr, *tr2 = nullptr, *fd = nullptr;
+    void *Us = nullptr;  // FP32-bulk form: shadow of U in float plus the energy balance
     unsigned *status = nullptr;
     unsigned long long *redbuf = nullptr;
     double coef_h[11] = {0};
@@ -230,11 +231,12 @@ namespace {
 
 void free_buffers(dgk_ctx *c)
 {
-    void *ptrs[] = {c->U, c->G, c->Tbuf, c->coef, c->rhsbuf, c->partial, c->Utv, c->tr1, c->tr2, c->fd, c->status, c->redbuf};
+    void *ptrs[] = {c->U,  c->G,   c->Tbuf, c->coef, c->rhsbuf, c->partial, c->Utv,
+                    c->tr1, c->tr2, c->fd,   c->Us,   c->status, c->redbuf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     c->U = c->G = c->Tbuf = c->coef = c->rhsbuf = c->partial = nullptr;
-    c->Utv = c->tr1 = c->tr2 = c->fd = nullptr;
+    c->Utv = c->tr1 = c->tr2 = c->fd = c->Us = nullptr;
     c->status = nullptr;
     c->redbuf = nullptr;
     if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -253,6 +255,7 @@ void fill_args(dgk_ctx *c, dgk::KArgs<R> &a)
     a.v.U = c->U;
     a.v.G = c->G;
     a.v.Utv = (R *)c->Utv;
+    a.v.Us = sizeof(R) == 4 ? (R *)c->Us : nullptr;
     a.v.tr1 = (R *)c->tr1;
     a.v.tr2 = (R *)c->tr2;
     a.v.fd = (R *)c->fd;
@@ -564,6 +567,7 @@ int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m)
     DGK_CUDA(cudaMalloc(&c->tr1, (size_t)c->NL * nface * c->rsize));
     DGK_CUDA(cudaMalloc(&c->tr2, (size_t)2 * nface * c->rsize));
     DGK_CUDA(cudaMalloc(&c->fd, (size_t)(2 * c->NV + 1) * nface * c->rsize));
+    if (f32) DGK_CUDA(cudaMalloc(&c->Us, (size_t)(c->NV + 1) * ne * c->NP * sizeof(float)));
     DGK_CUDA(cudaMemsetAsync(c->U, 0, nstate * sizeof(double), c->stream));
     DGK_CUDA(cudaMemsetAsync(c->G, 0, nstate * sizeof(double), c->stream));
     DGK_CUDA(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));

@@ -204,22 +204,21 @@ __device__ __forceinline__ bool finite_bits(double x)
 // Temperature from the total energy, Eq. (totalenergyalpha), with the vdW internal
 // energy rho eps = rho R cv T - a rho^2:
 //   rho R cv T = rho e + a rho^2 - (|m|^2/(2 rho) + alpha/2 (rho-c)^2 + gamma_K/2 |grad c|^2).
-// FP64 form: all in double.  FP32-bulk form: rho e + a rho^2 in double from the FP64
-// state, the small kinetic / relaxation / capillary terms and the scaling by
-// 1/(rho R cv) in float.  irho = 1/rho and d = rho - c in the bulk type; msq = |m|^2,
-// gc2 = |grad c|^2.
-template <typename R>
-__device__ __forceinline__ R temperature(const Phys &ph, const PhysR<R> &pr, double rho, R irho, double E, R d,
-                                         R msq, R gc2)
+// FP64 form: all in double.  FP32-bulk form: bal = rho e + a rho^2 formed in double from
+// the FP64 state (the caller passes it rounded to float), the small kinetic / relaxation
+// / capillary terms and the scaling by 1/(rho R cv) in float.  irho = 1/rho, d = rho - c,
+// msq = |m|^2, gc2 = |grad c|^2.
+__device__ __forceinline__ double temperature_f64(const Phys &ph, double rho, double irho, double E, double d,
+                                                  double msq, double gc2)
 {
-    if constexpr (sizeof(R) == 8) {
-        double num = E + kAvdw * rho * rho - 0.5 * msq * irho - ph.half_alpha * d * d - ph.half_gK * gc2;
-        return num * irho * ph.inv_Rcv;
-    } else {
-        const float small = 0.5f * msq * irho + pr.half_alpha * d * d + pr.half_gK * gc2;
-        const float bal = d2f(fma(kAvdw * rho, rho, E));
-        return (bal - small) * irho * pr.inv_Rcv;
-    }
+    const double num = E + kAvdw * rho * rho - 0.5 * msq * irho - ph.half_alpha * d * d - ph.half_gK * gc2;
+    return num * irho * ph.inv_Rcv;
+}
+template <typename R>
+__device__ __forceinline__ R temperature_bulk(const PhysR<R> &pr, R bal, R irho, R d, R msq, R gc2)
+{
+    const R small = R(0.5) * msq * irho + pr.half_alpha * d * d + pr.half_gK * gc2;
+    return (bal - small) * irho * pr.inv_Rcv;
 }
 
 // Pressure in the convective flux, Eq. (pressure), plus alpha/2 rho^2 for model 2

@@ -60,6 +60,7 @@ struct KView {
     WallsR<R> wr;
     double *U;           // [NV][ne][NP]
     double *G;           // [NV][ne][NP]
+    R *Us;               // FP32-bulk form: [NV+1][ne][NP] shadow of U (see NodeState); FP64 form: null
     R *Utv;              // [NV][ne][NP] volume part of U_t
     R *tr1;              // [NL][ne][NF][NFP] pass-1 traces of (rho, u, c)
     R *tr2;              // [2][ne][NF][NFP] traces of T and of d c / d x_normal
@@ -153,10 +154,10 @@ __device__ __forceinline__ long long fidx(long long ne, int v, long long e, int 
 }
 
 template <typename R>
-__device__ __forceinline__ void check_state(unsigned *status, R rho, R T, double E)
+__device__ __forceinline__ void check_state(unsigned *status, R rho, R T, R E)
 {
     unsigned s = 0;
-    if (!isfinite(rho) || !isfinite(T) || !finite_bits(E)) s |= kStatNonFinite;
+    if (!isfinite(rho) || !isfinite(T) || !isfinite(E)) s |= kStatNonFinite;
     else if (!(rho > R(0) && rho < R(1.0 / kBvdw) && T > R(0))) s |= kStatDomain;
     if (s) atomicOr(status, s);
 }
@@ -210,15 +211,12 @@ struct CLift {
     using S = Shape<D, N, EB>;
     static constexpr int smem_per_elem = S::NP + S::NF * S::NFP + D * S::NP + S::NP;  // c, c*, dc, T
 
-    __device__ static void run(const Ctx<R> &a, const Slot<D, N, EB> &t, R *sC, R *sCs, R *sDc, double Ud[S::NV],
-                               bool write_tr2)
+    __device__ static void run(const Ctx<R> &a, const Slot<D, N, EB> &t, R c, R *sC, R *sCs, R *sDc, bool write_tr2)
     {
-        constexpr int P = S::P, NP = S::NP, NF = S::NF, NFP = S::NFP, NV = S::NV;
+        constexpr int P = S::P, NP = S::NP, NF = S::NF, NFP = S::NFP;
         const long long ne = a.v.g.ne;
         if (t.valid) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) Ud[v] = a.v.U[((long long)v * ne + t.e) * NP + t.n];
-            sC[t.n] = to_bulk<R>(Ud[D + 2]);
+            sC[t.n] = c;
             for (int q = t.n; q < NF * NFP; q += NP) {
                 const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
                 const R own = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
@@ -247,11 +245,21 @@ struct CLift {
     }
 };
 
-// Bulk-type copies of one node's conserved state.
+// One node's conserved state in the bulk type, plus (FP32-bulk form) the energy balance
+// bal = rho e + a rho^2 of the temperature recovery (Eq. totalenergyalpha), formed in
+// double from the FP64 state and then rounded: near the spinodal the two terms nearly
+// cancel, so the sum is taken before any rounding to float.
+//
+// The FP64 form reads the double state.  The FP32-bulk form reads the shadow Us, which
+// every writer of the FP64 state (the RK update, the trace kernel after set-up) fills
+// from it: U in float and bal -- the same roundings the kernels would otherwise apply
+// to the double state per node and per kernel, done once per stage.
 template <int D, typename R>
 struct NodeState {
+    static constexpr int NV = D + 3;
     R rho, irho, m[D], E, c;
-    __device__ __forceinline__ void load(const double *Ud)
+    R bal;  // FP32-bulk form only
+    __device__ __forceinline__ void from_double(const double *Ud)
     {
         rho = to_bulk<R>(Ud[0]);
         irho = R(1) / rho;
@@ -259,12 +267,45 @@ struct NodeState {
         for (int k = 0; k < D; ++k) m[k] = to_bulk<R>(Ud[1 + k]);
         E = to_bulk<R>(Ud[D + 1]);
         c = to_bulk<R>(Ud[D + 2]);
+        bal = sizeof(R) == 4 ? to_bulk<R>(fma(kAvdw * Ud[0], Ud[0], Ud[D + 1])) : R(0);
+    }
+    __device__ __forceinline__ void load(const KView<R> &v, long long e, int n, int np)
+    {
+        if constexpr (sizeof(R) == 8) {
+            double Ud[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) Ud[k] = v.U[((long long)k * v.g.ne + e) * np + n];
+            from_double(Ud);
+        } else {
+            R u[NV + 1];
+#pragma unroll
+            for (int k = 0; k <= NV; ++k) u[k] = v.Us[((long long)k * v.g.ne + e) * np + n];
+            rho = u[0];
+            irho = R(1) / rho;
+#pragma unroll
+            for (int k = 0; k < D; ++k) m[k] = u[1 + k];
+            E = u[D + 1];
+            c = u[D + 2];
+            bal = u[NV];
+        }
+    }
+    // FP32-bulk form: write the shadow of this state (built by from_double)
+    __device__ __forceinline__ void store_shadow(const KView<R> &v, long long e, int n, int np) const
+    {
+        if constexpr (sizeof(R) == 4) {
+            const long long st = v.g.ne * np, o = e * np + n;
+            v.Us[o] = rho;
+#pragma unroll
+            for (int k = 0; k < D; ++k) v.Us[(1 + k) * st + o] = m[k];
+            v.Us[(D + 1) * st + o] = E;
+            v.Us[(D + 2) * st + o] = c;
+            v.Us[NV * st + o] = bal;
+        }
     }
 };
 
 template <int D, typename R>
-__device__ __forceinline__ R node_temperature(const Ctx<R> &a, const double *Ud, const NodeState<D, R> &q,
-                                              const R *gc)
+__device__ __forceinline__ R node_temperature(const Ctx<R> &a, const NodeState<D, R> &q, const R *gc)
 {
     R msq = R(0), gc2 = R(0);
 #pragma unroll
@@ -272,8 +313,9 @@ __device__ __forceinline__ R node_temperature(const Ctx<R> &a, const double *Ud,
         msq += q.m[k] * q.m[k];
         gc2 += gc[k] * gc[k];
     }
-    const R d = sizeof(R) == 8 ? R(Ud[0] - Ud[D + 2]) : q.rho - q.c;
-    return temperature<R>(a.ph, a.pr, Ud[0], q.irho, Ud[D + 1], d, msq, gc2);
+    const R d = q.rho - q.c;
+    if constexpr (sizeof(R) == 8) return temperature_f64(a.ph, q.rho, q.irho, q.E, d, msq, gc2);
+    else return temperature_bulk(a.pr, q.bal, q.irho, d, msq, gc2);
 }
 
 // ------------------------------------------------------------------ kernel 1
@@ -287,16 +329,15 @@ __device__ __forceinline__ void lift1_body(const Ctx<R> &a, long long blk, unsig
         const Slot<D, N, EB> t(a.v.g, blk);
     R *sC = reinterpret_cast<R *>(smraw) + (size_t)t.le * L::smem_per_elem;
     R *sCs = sC + NP, *sDc = sCs + NF * NFP, *sT = sDc + D * NP;
-    double Ud[NV];
-    L::run(a, t, sC, sCs, sDc, Ud, true);
+    NodeState<D, R> q;
+    if (t.valid) q.load(a.v, t.e, t.n, NP);
+    L::run(a, t, q.c, sC, sCs, sDc, true);
     if (t.valid) {
         R gc[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) gc[d] = sDc[d * NP + t.n];
-        NodeState<D, R> q;
-        q.load(Ud);
-        const R T = node_temperature<D, R>(a, Ud, q, gc);
-        check_state<R>(a.v.status, q.rho, T, Ud[D + 1]);
+        const R T = node_temperature<D, R>(a, q, gc);
+        check_state<R>(a.v.status, q.rho, T, q.E);
         sT[t.n] = T;
     }
     __syncthreads();
@@ -491,12 +532,9 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
 
     // ---- pass 1: prims (rho, u, c) and central face values (one-sided rho, c and u* = 0 at walls)
     R *sQ = sX, *sQs = sX + NL * NP;
-    double Ud[NV];
     NodeState<D, R> ns;
     if (t.valid) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) Ud[v] = a.v.U[((long long)v * ne + t.e) * NP + n];
-        ns.load(Ud);
+        ns.load(a.v, t.e, n, NP);
         sQ[n] = ns.rho;
 #pragma unroll
         for (int k = 0; k < D; ++k) sQ[(1 + k) * NP + n] = ns.m[k] * ns.irho;
@@ -511,6 +549,31 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
                 if (b >= 0) val = R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, v, b, 2 * dir + 1 - side, fp)]);
                 else val = (v >= 1 && v <= D) ? R(0) : own;
                 sQs[(f * NL + v) * NFP + fp] = val;
+            }
+        }
+    }
+    // pass-2 central face values (T*, and dc/dx_dir* for the lap c lifting; at walls T_wall
+    // and the contact-angle gradient), loaded now so that their latency overlaps pass 1
+    constexpr int KF = (NF * NFP + NP - 1) / NP;  // face points per thread
+    R pT[KF], pD[KF];
+#pragma unroll
+    for (int j = 0; j < KF; ++j) {
+        const int q = n + j * NP;
+        pT[j] = pD[j] = R(0);
+        if (t.valid && q < NF * NFP) {
+            const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
+            const long long b = t.nbr(a.v.g, f);
+            const R ownT = a.v.tr2[fidx<NF, NFP>(ne, 0, t.e, f, fp)];
+            const R ownD = a.v.tr2[fidx<NF, NFP>(ne, 1, t.e, f, fp)];
+            if (b >= 0) {
+                const int fo = 2 * dir + 1 - side;
+                pT[j] = R(0.5) * (ownT + a.v.tr2[fidx<NF, NFP>(ne, 0, b, fo, fp)]);
+                pD[j] = R(0.5) * (ownD + a.v.tr2[fidx<NF, NFP>(ne, 1, b, fo, fp)]);
+            } else {
+                const R cm = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
+                const R gn = a.v.wr.K[f] * (cm - a.v.wr.rl[f]) * (cm - a.v.wr.rv[f]);
+                pT[j] = a.v.wr.Tw[f];
+                pD[j] = side ? gn : -gn;
             }
         }
     }
@@ -544,26 +607,15 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
         R gc[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) gc[d] = g[d][D + 1];
-        T = node_temperature<D, R>(a, Ud, ns, gc);
+        T = node_temperature<D, R>(a, ns, gc);
         sT[n] = T;
-        for (int q = n; q < NF * NFP; q += NP) {
-            const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
-            const long long b = t.nbr(a.v.g, f);
-            const R ownT = a.v.tr2[fidx<NF, NFP>(ne, 0, t.e, f, fp)];
-            const R ownD = a.v.tr2[fidx<NF, NFP>(ne, 1, t.e, f, fp)];
-            R vT, vD;
-            if (b >= 0) {
-                const int fo = 2 * dir + 1 - side;
-                vT = R(0.5) * (ownT + a.v.tr2[fidx<NF, NFP>(ne, 0, b, fo, fp)]);
-                vD = R(0.5) * (ownD + a.v.tr2[fidx<NF, NFP>(ne, 1, b, fo, fp)]);
-            } else {
-                const R cm = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
-                const R gn = a.v.wr.K[f] * (cm - a.v.wr.rl[f]) * (cm - a.v.wr.rv[f]);
-                vT = a.v.wr.Tw[f];
-                vD = side ? gn : -gn;
+#pragma unroll
+        for (int j = 0; j < KF; ++j) {
+            const int q = n + j * NP;
+            if (q < NF * NFP) {
+                sTs[q] = pT[j];
+                sDs[q] = pD[j];
             }
-            sTs[q] = vT;
-            sDs[q] = vD;
         }
     }
     __syncthreads();
@@ -686,18 +738,21 @@ struct K3Smem {
     static constexpr int per_elem = a1 > a2 ? a1 : a2;
 };
 
-// New pass-1 traces of (rho, u, c) of the element's state (double U -> bulk type).
+// New pass-1 traces of (rho, u, c) of the element's state (double U -> bulk type), and in
+// the FP32-bulk form the shadow of the state.
 template <int D, int N, typename R, int EB = 0>
 __device__ __forceinline__ void write_traces(const Ctx<R> &a, const Slot<D, N, EB> &t, R *sQ, const double *Ud)
 {
     using S = Shape<D, N, EB>;
     constexpr int P = S::P, NP = S::NP, NFP = S::NFP, NF = S::NF, NL = S::NL;
     if (t.valid) {
-        const R rho = to_bulk<R>(Ud[0]), irho = R(1) / rho;
-        sQ[t.n] = rho;
+        NodeState<D, R> q;
+        q.from_double(Ud);
+        q.store_shadow(a.v, t.e, t.n, NP);
+        sQ[t.n] = q.rho;
 #pragma unroll
-        for (int k = 0; k < D; ++k) sQ[(1 + k) * NP + t.n] = to_bulk<R>(Ud[1 + k]) * irho;
-        sQ[(D + 1) * NP + t.n] = to_bulk<R>(Ud[D + 2]);
+        for (int k = 0; k < D; ++k) sQ[(1 + k) * NP + t.n] = q.m[k] * q.irho;
+        sQ[(D + 1) * NP + t.n] = q.c;
     }
     __syncthreads();
     if (t.valid) {
@@ -862,16 +917,20 @@ __device__ __forceinline__ void node_T_body(const Ctx<R> &a, long long blk, unsi
     R *sC = reinterpret_cast<R *>(smraw) + (size_t)t.le * L::smem_per_elem;
     R *sCs = sC + NP, *sDc = sCs + NF * NFP;
     double Ud[NV];
-    L::run(a, t, sC, sCs, sDc, Ud, false);
+    NodeState<D, R> q;
+    if (t.valid) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Ud[v] = a.v.U[((long long)v * a.v.g.ne + t.e) * NP + t.n];
+        q.from_double(Ud);
+    }
+    L::run(a, t, q.c, sC, sCs, sDc, false);
     if (!t.valid) return;
     R gc[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) gc[d] = sDc[d * NP + t.n];
     const long long idx = t.e * NP + t.n;
     if (mode == 0) {
-        NodeState<D, R> q;
-        q.load(Ud);
-        a.v.out[idx] = to_f64<R>(node_temperature<D, R>(a, Ud, q, gc));
+        a.v.out[idx] = to_f64<R>(node_temperature<D, R>(a, q, gc));
         return;
     }
     const double rho = Ud[0], T = a.v.out[idx];

@@ -130,6 +130,8 @@ void place(dgk::KArgs<R> &a, unsigned char *base, const double *U, double *Ut, i
     a.v.tr2 = reinterpret_cast<R *>(base + off);
     off += align256((size_t)2 * ne * NF * NFP * sizeof(R));
     a.v.fd = reinterpret_cast<R *>(base + off);
+    off += align256((size_t)(2 * NV + 1) * ne * NF * NFP * sizeof(R));
+    a.v.Us = sizeof(R) == 4 ? reinterpret_cast<R *>(base + off) : nullptr;
     a.v.U = const_cast<double *>(U);
     a.v.G = nullptr;
     a.v.out = Ut;
@@ -159,7 +161,8 @@ extern "C" int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *m, const 
     const bool f32 = p->precision == DGK_PREC_FP32BULK;
     const size_t rs = f32 ? sizeof(float) : sizeof(double);
     const size_t need = 256 + align256((size_t)NV * ne * NP * rs) + align256((size_t)NL * ne * NF * NFP * rs) +
-                        align256((size_t)2 * ne * NF * NFP * rs) + align256((size_t)(2 * NV + 1) * ne * NF * NFP * rs);
+                        align256((size_t)2 * ne * NF * NFP * rs) + align256((size_t)(2 * NV + 1) * ne * NF * NFP * rs) +
+                        (f32 ? align256((size_t)(NV + 1) * ne * NP * rs) : 0);
     if (need > (size_t)DGK_STATIC_SCRATCH_BYTES)
         return fail_static(DGK_ERR_ARG, "mesh too large for the static scratch of dgk_rhs_static (DGK_STATIC_SCRATCH_BYTES)");
     int device = 0;
