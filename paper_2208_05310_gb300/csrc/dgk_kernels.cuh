@@ -374,24 +374,38 @@ struct FaceRec {
                          LAP = NV + 3 * D + 1, NQ = NV + 3 * D + 2;
 };
 
-// One-sided flux F(U-, grads-) in direction DIR (interior faces), or the complete wall
-// flux in +e_DIR (wall faces; Sec. 2.4, Eq. bc_nsk_alpha with gamma_1 = gamma_2 =
+// v[d] for a run-time direction d, by selection (no run-time index into a register array)
+template <int D, typename R>
+__device__ __forceinline__ R pick(int d, const R *v)
+{
+    R x = v[0];
+#pragma unroll
+    for (int k = 1; k < D; ++k) x = d == k ? v[k] : x;
+    return x;
+}
+
+// One-sided flux F(U-, grads-) in direction dir (interior faces), or the complete wall
+// flux in +e_dir (wall faces; Sec. 2.4, Eq. bc_nsk_alpha with gamma_1 = gamma_2 =
 // gamma_4 = 0: Rusanov against the mirrored ghost (rho, m - 2(m.n)n, rho e, c) with equal
 // pressure and signal speed, minus the wall viscous flux with u_wall = 0, zeta = 0 and
-// grad c . n from the contact angle), and the Rusanov signal speed |u_DIR| + s.
-template <int D, typename R, int DIR>
-__device__ __forceinline__ void face_flux(const Ctx<R> &a, int f, bool wall, const R *r, R *F, R &lam)
+// grad c . n from the contact angle), and the Rusanov signal speed |u_dir| + s.  The
+// direction is a run-time value: the normal components are selected, so that face
+// points of all directions share one instruction stream.
+template <int D, typename R>
+__device__ __forceinline__ void face_flux(const Ctx<R> &a, int f, int dir, bool wall, const R *r, R *F, R &lam)
 {
     using FR = FaceRec<D>;
     const PhysR<R> &ph = a.pr;
     const R rho = r[0], E = r[D + 1], c = r[D + 2], irho = R(1) / rho;
-    R m[D], u[D], msq = R(0), gc2 = R(0);
+    R m[D], u[D], gc[D], ddu[D], msq = R(0), gc2 = R(0);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         m[k] = r[1 + k];
         u[k] = m[k] * irho;
         msq += m[k] * m[k];
-        gc2 += r[FR::GC + k] * r[FR::GC + k];
+        gc[k] = r[FR::GC + k];
+        gc2 += gc[k] * gc[k];
+        ddu[k] = r[FR::DDU + k];
     }
     // temperature of the interpolated face state (bulk type: the face state itself is
     // an interpolation in the bulk type)
@@ -399,43 +413,47 @@ __device__ __forceinline__ void face_flux(const Ctx<R> &a, int f, bool wall, con
                  ph.half_gK * gc2) * irho * ph.inv_Rcv;
     const R iomb = R(1) / (R(1) - R(kBvdw) * rho);
     const R pf = flux_pressure<R>(ph, rho, T, iomb);
-    lam = fabs(u[DIR]) + signal_speed<R>(ph, rho, T, iomb);
+    const R un = pick<D, R>(dir, u), mn = pick<D, R>(dir, m), dnn = pick<D, R>(dir, ddu);
+    lam = fabs(un) + signal_speed<R>(ph, rho, T, iomb);
     const R divu = r[FR::DIV];
-    // viscous stress column tau_{k, DIR} = mu (du_k/dx_DIR + du_DIR/dx_k) - 2/3 mu div u delta
+    // viscous stress column tau_{k, dir} = mu (du_k/dx_dir + du_dir/dx_k) - 2/3 mu div u delta;
+    // du_dir/dx_k (k != dir) sits in slot k of the record's second block if k < dir, else k-1
     R tau[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        const R dudk = k == DIR ? r[FR::DDU + DIR] : r[FR::DUD + (k < DIR ? k : k - 1)];
-        tau[k] = ph.mu * (r[FR::DDU + k] + dudk);
-        if (k == DIR) tau[k] -= ph.two_thirds_mu * divu;
+        const R below = k < D - 1 ? r[FR::DUD + (k < D - 1 ? k : 0)] : R(0);
+        const R above = k > 0 ? r[FR::DUD + (k > 0 ? k - 1 : 0)] : R(0);
+        const R dud = k == dir ? dnn : (k < dir ? below : above);
+        tau[k] = ph.mu * (ddu[k] + dud) - (k == dir ? ph.two_thirds_mu * divu : R(0));
     }
-    const R gTd = r[FR::GT], gcd = r[FR::GC + DIR], lap = r[FR::LAP];
+    const R gTd = r[FR::GT], gcd = pick<D, R>(dir, gc), lap = r[FR::LAP];
     if (!wall) {
         R work = R(0);
-        F[0] = m[DIR];
+        F[0] = mn;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             work += tau[k] * u[k];
-            F[1 + k] = m[k] * u[DIR] - tau[k] + (k == DIR ? pf : R(0));
+            F[1 + k] = m[k] * un - tau[k] + (k == dir ? pf : R(0));
         }
         const R zeta = ph.beta * (ph.gK * lap + ph.alpha * (rho - c));
         const R je = ph.kap * gTd - ph.gK * c * gcd * divu + ph.gK * gcd * zeta;
-        F[D + 1] = (E + pf) * u[DIR] - (work + je);
-        F[D + 2] = c * u[DIR] - ph.gKbeta * gcd;
+        F[D + 1] = (E + pf) * un - (work + je);
+        F[D + 2] = c * un - ph.gKbeta * gcd;
         return;
     }
     const R nsign = (f & 1) ? R(1) : R(-1);
     const R gn = a.v.wr.K[f] * (c - a.v.wr.rl[f]) * (c - a.v.wr.rv[f]);
     R Fi[D + 3], Fg[D + 3], Ui[D + 3], Ug[D + 3];
-    const R ui = u[DIR], ug = -u[DIR];
-    Fi[0] = m[DIR];
-    Fg[0] = -m[DIR];
+    const R ui = un, ug = -un;
+    Fi[0] = mn;
+    Fg[0] = -mn;
     Ui[0] = Ug[0] = rho;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        const R mg = k == DIR ? -m[k] : m[k];
-        Fi[1 + k] = m[k] * ui + (k == DIR ? pf : R(0));
-        Fg[1 + k] = mg * ug + (k == DIR ? pf : R(0));
+        const R mg = k == dir ? -m[k] : m[k];
+        const R pk = k == dir ? pf : R(0);
+        Fi[1 + k] = m[k] * ui + pk;
+        Fg[1 + k] = mg * ug + pk;
         Ui[1 + k] = m[k];
         Ug[1 + k] = mg;
     }
@@ -458,48 +476,25 @@ __device__ __forceinline__ void face_flux(const Ctx<R> &a, int f, bool wall, con
     F[D + 2] -= nsign * ph.gKbeta * gn;
 }
 
-// Face record of face point (f, fp) with f normal to DIR, traced from the nodal fields
-// in shared memory along the line through fp (one end), then its face data.
-template <int D, int N, typename R, int DIR, int EB = 0>
-__device__ __forceinline__ void face_point(const Ctx<R> &a, long long e, bool wall, int f, int fp, const R *sG,
-                                           const R *sGT, const R *sN)
+// Nodal array holding record quantity k of the faces normal to dir (FaceRec order):
+// conserved U and div u, lap c in sN; lifted gradients in sG[d][v] (v = rho, u_1..u_D, c);
+// grad T in sGT.
+template <int D, int N, typename R, int EB = 0>
+__device__ __forceinline__ const R *face_source(int k, int dir, const R *sG, const R *sGT, const R *sN)
 {
     using S = Shape<D, N, EB>;
     using FR = FaceRec<D>;
-    constexpr int P = S::P, NP = S::NP, NL = S::NL, NV = S::NV, NQ = FR::NQ, NF = S::NF, NFP = S::NFP;
-    const int base = line_base<P>(fp, DIR);
-    constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? P : P * P);
-    const bool side = f & 1;
-    R L[P];
-#pragma unroll
-    for (int l = 0; l < P; ++l) L[l] = side ? a.op.lp[l] : a.op.lm[l];
-    R r[NQ];
-#pragma unroll
-    for (int k = 0; k < NQ; ++k) {
-        const R *src;
-        if (k < FR::DDU) src = sN + k * NP;
-        else if (k < FR::DUD) src = sG + (DIR * NL + 1 + (k - FR::DDU)) * NP;
-        else if (k < FR::DIV) src = sG + (((k - FR::DUD) < DIR ? (k - FR::DUD) : (k - FR::DUD) + 1) * NL + 1 + DIR) * NP;
-        else if (k == FR::DIV) src = sN + NV * NP;
-        else if (k == FR::GT) src = sGT + DIR * NP;
-        else if (k < FR::LAP) src = sG + ((k - FR::GC) * NL + D + 1) * NP;
-        else src = sN + (NV + 1) * NP;
-        R acc = R(0);
-#pragma unroll
-        for (int l = 0; l < P; ++l) acc += L[l] * src[base + l * stride];
-        r[k] = acc;
+    constexpr int NP = S::NP, NL = S::NL, NV = S::NV;
+    if (k < FR::DDU) return sN + k * NP;
+    if (k < FR::DUD) return sG + (dir * NL + 1 + (k - FR::DDU)) * NP;
+    if (k < FR::DIV) {
+        const int j = k - FR::DUD, kabs = j < dir ? j : j + 1;
+        return sG + (kabs * NL + 1 + dir) * NP;
     }
-    R F[NV], lam;
-    face_flux<D, R, DIR>(a, f, wall, r, F, lam);
-    const long long ne = a.v.g.ne;
-    const long long st = ne * NF * NFP;
-    const long long fo = (e * NF + f) * NFP + fp;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        a.v.fd[v * st + fo] = r[v];
-        a.v.fd[(NV + v) * st + fo] = F[v];
-    }
-    a.v.fd[(2 * NV) * st + fo] = lam;
+    if (k == FR::DIV) return sN + NV * NP;
+    if (k == FR::GT) return sGT + dir * NP;
+    if (k < FR::LAP) return sG + ((k - FR::GC) * NL + D + 1) * NP;
+    return sN + (NV + 1) * NP;
 }
 
 // ------------------------------------------------------------------ kernel 2
@@ -708,14 +703,38 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
     __syncthreads();
 
     // ---- face data: one face point per task, its record traced directly from the
-    //      nodal fields (interior: one-sided data; wall: the complete wall flux)
+    //      nodal fields (interior: one-sided data; wall: the complete wall flux).  The
+    //      direction is a run-time value (no divergence between the face points of
+    //      different directions in a warp); the line is walked from the face, so that
+    //      both sides use l_j(-1): on nodes symmetric about 0, l_j(+1) = l_{P-1-j}(-1).
     if (t.valid) {
+        using FR = FaceRec<D>;
+        constexpr int NQ = FR::NQ;
+        const long long st = ne * NF * NFP;
         for (int q = n; q < NF * NFP; q += NP) {
-            const int f = q / NFP, fp = q % NFP, dir = f >> 1;
+            const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
             const bool wall = t.nbr(a.v.g, f) < 0;
-            if (dir == 0) face_point<D, N, R, 0, EB>(a, t.e, wall, f, fp, sG, sGT, sN);
-            else if (D == 2 || dir == 1) face_point<D, N, R, 1, EB>(a, t.e, wall, f, fp, sG, sGT, sN);
-            else face_point<D, N, R, (D == 3 ? 2 : 1), EB>(a, t.e, wall, f, fp, sG, sGT, sN);
+            const int stride = line_stride<P>(dir);
+            const int first = line_base<P>(fp, dir) + (side ? (P - 1) * stride : 0);
+            const int step = side ? -stride : stride;
+            R r[NQ];
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) {
+                const R *src = face_source<D, N, R, EB>(k, dir, sG, sGT, sN);
+                R acc = R(0);
+#pragma unroll
+                for (int l = 0; l < P; ++l) acc += a.op.lm[l] * src[first + l * step];
+                r[k] = acc;
+            }
+            R F[NV], lam;
+            face_flux<D, R>(a, f, dir, wall, r, F, lam);
+            const long long fo = (t.e * NF + f) * NFP + fp;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                a.v.fd[v * st + fo] = r[v];
+                a.v.fd[(NV + v) * st + fo] = F[v];
+            }
+            a.v.fd[(2 * NV) * st + fo] = lam;
         }
     }
 }
