@@ -15,7 +15,8 @@
  *   Sec. 2.3  relaxation models 1 and 2, Eq. (navierstokeskorteweg_p), (..._palpha)
  *   Sec. 2.4  wall boundary conditions, Eq. (bc_nsk_alpha), (helmfreesurftot_derivative),
  *             (surftenscoef)
- *   Sec. 3.1  DGSEM on Legendre-Gauss nodes, Rusanov flux, BR1 lifting (twice for the
+ *   Sec. 3.1  DGSEM on Legendre-Gauss nodes, Rusanov and HLLC fluxes (Toro 2009, the
+ *             paper's reference for both; Sec. 4: HLLC for model 2), BR1 lifting (twice for the
  *             second derivative), point-wise non-conservative sources, low-storage RK
  *   Sec. 3.2  15-point Gauss quadrature for the surface tension integral
  *   Sec. 4    interface width L_i(T), initial tanh profiles
@@ -299,6 +300,8 @@ static int setup(const or_mesh *m, const or_params *p, ctx_t *c)
     if (m->dim != 2 && m->dim != 3) return -1;
     if (m->N < 1 || m->N + 1 > MAXP) return -1;
     if (p->model < 0 || p->model > 2) return -1;
+    if (p->flux != 0 && p->flux != 1) return -1;
+    if (p->flux == 1 && p->model != 2) return -1; /* HLLC: model 2 (its hyperbolic part) */
     c->d = m->dim; c->N = m->N; c->P = m->N + 1;
     c->np = ipow(c->P, c->d);
     c->nfp = ipow(c->P, c->d - 1);
@@ -470,6 +473,43 @@ static void conv_flux(const ctx_t *c, const double *U, double pr, int dir, doubl
     for (int k = 0; k < d; ++k) F[1 + k] = U[1 + k] * u + (k == dir ? pr : 0.0);
     F[d + 1] = (U[d + 1] + pr) * u;
     if (c->prm.model != 0) F[d + 2] = U[d + 2] * u;
+}
+
+/* HLLC flux of the convective part in +e_dir (Toro, Riemann Solvers and Numerical
+   Methods for Fluid Dynamics, 3rd ed., Sec. 10.4): wave-speed estimates
+   S_L = min(u_L - a_L, u_R - a_R), S_R = max(u_L + a_L, u_R + a_R); contact speed
+     S* = (p_R - p_L + rho_L u_L (S_L - u_L) - rho_R u_R (S_R - u_R))
+          / (rho_L (S_L - u_L) - rho_R (S_R - u_R));
+   star states U*_K = chi_K (1, S* e_dir + tangential u_K, E_K/rho_K + (S* - u_K)(S* +
+   p_K/(rho_K (S_K - u_K))), c_K/rho_K), chi_K = rho_K (S_K - u_K)/(S_K - S*), the order
+   parameter carried like a passive scalar; F = F_L, F_L + S_L (U*_L - U_L),
+   F_R + S_R (U*_R - U_R) or F_R by the sign pattern of S_L, S*, S_R.  p is the
+   model's convective pressure (model 2: p + alpha/2 rho^2) and a its sound speed
+   sqrt(cs^2 + alpha rho). */
+static void hllc_flux(const ctx_t *c, const double *UL, double pL, double aL, const double *UR, double pR,
+                      double aR, int dir, double *F)
+{
+    int d = c->d, nv = c->nv;
+    double rL = UL[0], rR = UR[0];
+    double uL = UL[1 + dir] / rL, uR = UR[1 + dir] / rR;
+    double SL = fmin(uL - aL, uR - aR), SR = fmax(uL + aL, uR + aR);
+    double FL[8], FR[8];
+    conv_flux(c, UL, pL, dir, FL);
+    conv_flux(c, UR, pR, dir, FR);
+    if (SL >= 0.0) { for (int v = 0; v < nv; ++v) F[v] = FL[v]; return; }
+    if (SR <= 0.0) { for (int v = 0; v < nv; ++v) F[v] = FR[v]; return; }
+    double Ss = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) / (rL * (SL - uL) - rR * (SR - uR));
+    const double *UK = Ss >= 0.0 ? UL : UR;
+    const double *FK = Ss >= 0.0 ? FL : FR;
+    double SK = Ss >= 0.0 ? SL : SR, pK = Ss >= 0.0 ? pL : pR;
+    double rK = UK[0], uK = UK[1 + dir] / rK;
+    double chi = rK * (SK - uK) / (SK - Ss);
+    double Us[8];
+    Us[0] = chi;
+    for (int k = 0; k < d; ++k) Us[1 + k] = chi * (k == dir ? Ss : UK[1 + k] / rK);
+    Us[d + 1] = chi * (UK[d + 1] / rK + (Ss - uK) * (Ss + pK / (rK * (SK - uK))));
+    Us[d + 2] = chi * UK[d + 2] / rK;
+    for (int v = 0; v < nv; ++v) F[v] = FK[v] + SK * (Us[v] - UK[v]);
 }
 
 /* Viscous flux F^V in direction dir.
@@ -733,11 +773,17 @@ static void wall_flux(const ctx_t *c, int f, const double *U, const double *g, c
     conv_flux(c, Ug, pr, dir, FR);
     double Fconv[8];
     /* flux in +e_dir computed as for an interior face with the ghost on the outside */
-    for (int v = 0; v < nv; ++v) {
-        double Fin = FL[v], Fout = FR[v], Uin = U[v], Uout = Ug[v];
-        double Fl = nsign > 0 ? Fin : Fout, Fr = nsign > 0 ? Fout : Fin;
-        double Ul = nsign > 0 ? Uin : Uout, Ur = nsign > 0 ? Uout : Uin;
-        Fconv[v] = 0.5 * (Fl + Fr) - 0.5 * lam * (Ur - Ul);
+    if (p->flux == 1) {
+        double a = sound_speed(c, U[0], T);
+        if (nsign > 0) hllc_flux(c, U, pr, a, Ug, pr, a, dir, Fconv);
+        else           hllc_flux(c, Ug, pr, a, U, pr, a, dir, Fconv);
+    } else {
+        for (int v = 0; v < nv; ++v) {
+            double Fin = FL[v], Fout = FR[v], Uin = U[v], Uout = Ug[v];
+            double Fl = nsign > 0 ? Fin : Fout, Fr = nsign > 0 ? Fout : Fin;
+            double Ul = nsign > 0 ? Uin : Uout, Ur = nsign > 0 ? Uout : Uin;
+            Fconv[v] = 0.5 * (Fl + Fr) - 0.5 * lam * (Ur - Ul);
+        }
     }
     /* viscous normal flux, outward */
     double rho = U[0], cm = U[d + 2];
@@ -876,11 +922,22 @@ static int rhs_core(const ctx_t *c, const double *U, double *Ut, double t, or_fo
                     const double *gL = s ? go : gn, *gR = s ? gn : go;
                     const double *tL = s ? gTo : gTn, *tR = s ? gTn : gTo;
                     double lL = s ? lapo : lapn, lR = s ? lapn : lapo;
-                    double FL[8], FR[8], laL, laR;
-                    point_flux(c, UL, gL, tL, lL, dir, FL, &laL);
-                    point_flux(c, UR, gR, tR, lR, dir, FR, &laR);
-                    double lam = laL > laR ? laL : laR;
-                    for (int v = 0; v < nv; ++v) Fstar[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (UR[v] - UL[v]);
+                    if (c->prm.flux == 1) {
+                        /* HLLC for the convective part, central BR1 flux for the viscous part */
+                        double TL = temperature(c, UL, gL), TR = temperature(c, UR, gR);
+                        double Fc[8], FvL[8], FvR[8];
+                        hllc_flux(c, UL, flux_pressure(c, UL[0], TL), sound_speed(c, UL[0], TL), UR,
+                                  flux_pressure(c, UR[0], TR), sound_speed(c, UR[0], TR), dir, Fc);
+                        visc_flux(c, UL, gL, tL, lL, dir, FvL);
+                        visc_flux(c, UR, gR, tR, lR, dir, FvR);
+                        for (int v = 0; v < nv; ++v) Fstar[v] = Fc[v] - 0.5 * (FvL[v] + FvR[v]);
+                    } else {
+                        double FL[8], FR[8], laL, laR;
+                        point_flux(c, UL, gL, tL, lL, dir, FL, &laL);
+                        point_flux(c, UR, gR, tR, lR, dir, FR, &laR);
+                        double lam = laL > laR ? laL : laR;
+                        for (int v = 0; v < nv; ++v) Fstar[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (UR[v] - UL[v]);
+                    }
                 } else {
                     double Fn[8];
                     wall_flux(c, f, Uo, go, gTo, Fn);
@@ -1152,6 +1209,50 @@ int or_diagnostics(const or_mesh *m, const or_params *p, const double *U, double
         }
     out[6] = sqrt(out[6]);
     free(T);
+    return 0;
+}
+
+/* point fluxes for the tests: a 1-element periodic context gives d, nv and the model */
+static int point_ctx(const or_params *p, int dim, ctx_t *c)
+{
+    or_mesh m;
+    memset(&m, 0, sizeof(m));
+    m.dim = dim;
+    m.N = 1;
+    for (int d = 0; d < 3; ++d) { m.n[d] = 1; m.hi[d] = 1.0; m.periodic[d] = 1; }
+    return setup(&m, p, c);
+}
+
+int or_conv_point(const or_params *p, int dim, int dir, const double *U, double T, double *F)
+{
+    ctx_t c;
+    if (point_ctx(p, dim, &c) || dir < 0 || dir >= dim) return -1;
+    conv_flux(&c, U, flux_pressure(&c, U[0], T), dir, F);
+    return 0;
+}
+
+int or_hllc_point(const or_params *p, int dim, int dir, const double *UL, double TL, const double *UR, double TR,
+                  double *F)
+{
+    ctx_t c;
+    if (point_ctx(p, dim, &c) || dir < 0 || dir >= dim || c.nv < dim + 3) return -1;
+    hllc_flux(&c, UL, flux_pressure(&c, UL[0], TL), sound_speed(&c, UL[0], TL), UR, flux_pressure(&c, UR[0], TR),
+              sound_speed(&c, UR[0], TR), dir, F);
+    return 0;
+}
+
+int or_rusanov_point(const or_params *p, int dim, int dir, const double *UL, double TL, const double *UR, double TR,
+                     double *F)
+{
+    ctx_t c;
+    if (point_ctx(p, dim, &c) || dir < 0 || dir >= dim) return -1;
+    double FL[8], FR[8];
+    conv_flux(&c, UL, flux_pressure(&c, UL[0], TL), dir, FL);
+    conv_flux(&c, UR, flux_pressure(&c, UR[0], TR), dir, FR);
+    double lL = fabs(UL[1 + dir] / UL[0]) + sound_speed(&c, UL[0], TL);
+    double lR = fabs(UR[1 + dir] / UR[0]) + sound_speed(&c, UR[0], TR);
+    double lam = lL > lR ? lL : lR;
+    for (int v = 0; v < c.nv; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (UR[v] - UL[v]);
     return 0;
 }
 

@@ -37,7 +37,18 @@ typedef struct {
 typedef struct {
     int model;          /* 0 original NSK (periodic boxes only), 1 relaxation model 1, 2 relaxation model 2 */
     double gammaK, mu, kappa, cv, alpha, beta;
+    int flux;           /* convective numerical flux: 0 Rusanov, 1 HLLC (model 2 only, Sec. 4) */
 } or_params;
+
+/* ---- point fluxes, for the tests of the numerical flux functions ----
+   Convective flux F^C(U) in +e_dir at temperature T, and the HLLC flux between the
+   states UL (at xi_dir = -) and UR (at xi_dir = +).  p: the model's convective pressure,
+   a: the signal speed of the Rusanov flux. */
+int or_conv_point(const or_params *p, int dim, int dir, const double *U, double T, double *F);
+int or_hllc_point(const or_params *p, int dim, int dir, const double *UL, double TL, const double *UR, double TR,
+                  double *F);
+int or_rusanov_point(const or_params *p, int dim, int dir, const double *UL, double TL, const double *UR, double TR,
+                     double *F);
 
 /* ---- thermodynamics (Sec. 2.1) ---- */
 double or_psi(double rho, double T, double cv);

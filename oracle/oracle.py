@@ -30,7 +30,7 @@ class OrMesh(C.Structure):
 class OrParams(C.Structure):
     _fields_ = [("model", C.c_int), ("gammaK", C.c_double), ("mu", C.c_double),
                 ("kappa", C.c_double), ("cv", C.c_double), ("alpha", C.c_double),
-                ("beta", C.c_double)]
+                ("beta", C.c_double), ("flux", C.c_int)]
 
 
 FORCING = C.CFUNCTYPE(None, C.c_int, C.POINTER(C.c_double), C.c_double, C.POINTER(C.c_double), C.c_void_p)
@@ -74,6 +74,9 @@ def lib():
         L.or_max_dt.argtypes = [mp, pp, dp, C.c_double, C.c_double, dp]
         L.or_diagnostics.argtypes = [mp, pp, dp, dp]
         L.or_num_threads.restype = C.c_int
+        L.or_conv_point.argtypes = [pp, C.c_int, C.c_int, dp, C.c_double, dp]
+        L.or_hllc_point.argtypes = [pp, C.c_int, C.c_int, dp, C.c_double, dp, C.c_double, dp]
+        L.or_rusanov_point.argtypes = [pp, C.c_int, C.c_int, dp, C.c_double, dp, C.c_double, dp]
         _lib = L
     return _lib
 
@@ -103,8 +106,30 @@ def make_mesh(dim, N, n, lo, hi, periodic, walls=None):
     return m
 
 
-def make_params(model=1, gammaK=1e-4, mu=0.01, kappa=1.0 / 150.0, cv=5.0, alpha=100.0, beta=100.0):
-    return OrParams(model, gammaK, mu, kappa, cv, alpha, beta)
+FLUX = {"rusanov": 0, "hllc": 1}
+
+
+def make_params(model=1, gammaK=1e-4, mu=0.01, kappa=1.0 / 150.0, cv=5.0, alpha=100.0, beta=100.0, flux="rusanov"):
+    return OrParams(model, gammaK, mu, kappa, cv, alpha, beta, FLUX[flux])
+
+
+def point_flux(kind, params, dim, direction, UL, TL, UR=None, TR=None):
+    """kind: "conv" (F^C(UL) at TL), "hllc" or "rusanov" (numerical flux between UL, UR)."""
+    import numpy as np
+    nv = dim + 3 if params.model != 0 else dim + 2
+    F = np.zeros(nv)
+    ul = np.ascontiguousarray(UL, dtype=np.float64)
+    dp = C.POINTER(C.c_double)
+    if kind == "conv":
+        rc = lib().or_conv_point(C.byref(params), dim, direction, ul.ctypes.data_as(dp), TL, F.ctypes.data_as(dp))
+    else:
+        ur = np.ascontiguousarray(UR, dtype=np.float64)
+        fn = lib().or_hllc_point if kind == "hllc" else lib().or_rusanov_point
+        rc = fn(C.byref(params), dim, direction, ul.ctypes.data_as(dp), TL, ur.ctypes.data_as(dp), TR,
+                F.ctypes.data_as(dp))
+    if rc:
+        raise ValueError(f"or_{kind}_point failed ({rc})")
+    return F
 
 
 # ---------------- thermodynamics ----------------
