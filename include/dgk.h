@@ -56,6 +56,9 @@ extern "C" {
                                 the nodal temperature recovery, the RK accumulation and the
                                 diagnostics in FP64 */
 
+#define DGK_FLUX_RUSANOV 0   /* Rusanov flux (the paper's flux for model 1) */
+#define DGK_FLUX_HLLC 1      /* HLLC flux (the paper's flux for model 2) */
+
 #define DGK_NDIAG 8 /* mass, momentum x/y/z, total energy, -int rho eta, ||rho-c||_2, max|u| */
 
 typedef struct dgk_ctx dgk_ctx;
@@ -72,6 +75,9 @@ typedef struct {
     double cv;       /* heat capacity ratio cv = c_v/R_gas */
     double alpha;    /* Korteweg relaxation parameter alpha > 0 (Sec. 2.3) */
     double beta;     /* order-parameter relaxation rate beta > 0 (Eq. orderparametersourcenskalpha) */
+    int flux;        /* convective numerical flux: DGK_FLUX_RUSANOV, or DGK_FLUX_HLLC (model 2 only; the
+                        paper's flux for model 2, Sec. 4; HLLC as in Toro 2009, Sec. 10.4, with the
+                        model-2 pressure p + alpha/2 rho^2 and sound speed sqrt(cs^2 + alpha rho)) */
 } dgk_params;
 
 /* One face of the box.  kind 0: none (the direction must be periodic); kind 1:
@@ -185,7 +191,8 @@ int dgk_check_conversions(const double *x, size_t n, int on_device, unsigned lon
  * start of every step: batches on different streams must not run at the same time.
  */
 typedef struct dgk_batch dgk_batch;
-/* p: common parameters (precision must be DGK_PREC_FP32BULK); meshes[nprob]: 2D box
+/* p: common parameters (precision must be DGK_PREC_FP32BULK, flux DGK_FLUX_RUSANOV);
+   meshes[nprob]: 2D box
    meshes with N in 3..5.  cuda_stream as for dgk_create (shared by all problems). */
 int dgk_batch_create(dgk_batch **out, int device, void *cuda_stream, const dgk_params *p, int nprob,
                      const dgk_box_mesh *meshes);

@@ -266,7 +266,8 @@ void fill_args(dgk_ctx *c, dgk::KArgs<R> &a)
 
 // constants in the bulk type, derived once on the host
 template <typename R>
-void fill_bulk(dgk::KArgs<R> &a, const dgk::Geom &g, const dgk::Phys &ph, const dgk::Walls &w, const dgk::Ops &o)
+void fill_bulk(dgk::KArgs<R> &a, const dgk::Geom &g, const dgk::Phys &ph, const dgk::Walls &w, const dgk::Ops &o,
+               int flux)
 {
     for (int i = 0; i < dgk::kMaxP * dgk::kMaxP; ++i) a.op.Dh[i] = (R)o.Dhat[i];
     for (int i = 0; i < dgk::kMaxP; ++i) {
@@ -291,6 +292,7 @@ void fill_bulk(dgk::KArgs<R> &a, const dgk::Geom &g, const dgk::Phys &ph, const 
     p.s_coef = (R)(dgk::kRgas * (1.0 + 1.0 / ph.cv));
     p.inv_Rcv = (R)(1.0 / (dgk::kRgas * ph.cv));
     p.half_alpha_p = ph.model == 2 ? (R)(0.5 * ph.alpha) : (R)0;
+    p.flux = flux;
     for (int f = 0; f < 6; ++f) {
         a.v.wr.K[f] = (R)w.K[f];
         a.v.wr.rl[f] = (R)w.rl[f];
@@ -340,8 +342,8 @@ int build_consts(dgk_ctx *c)
     }
     c->a64.v.g = c->a32.v.g = g;
     c->a64.ph = c->a32.ph = ph;
-    fill_bulk(c->a64, g, ph, w, o);
-    fill_bulk(c->a32, g, ph, w, o);
+    fill_bulk(c->a64, g, ph, w, o, c->prm.flux);
+    fill_bulk(c->a32, g, ph, w, o, c->prm.flux);
     return DGK_OK;
 }
 
@@ -507,6 +509,8 @@ int dgk_set_params(dgk_ctx *c, const dgk_params *p)
     if (p->precision != DGK_PREC_FP64 && p->precision != DGK_PREC_FP32BULK) return fail(DGK_ERR_ARG, "bad precision");
     if (!(p->gammaK > 0) || !(p->mu >= 0) || !(p->kappa >= 0) || !(p->cv > 0) || !(p->alpha >= 0) || !(p->beta >= 0))
         return fail(DGK_ERR_ARG, "parameters out of range");
+    if (p->flux != DGK_FLUX_RUSANOV && p->flux != DGK_FLUX_HLLC) return fail(DGK_ERR_ARG, "flux must be Rusanov or HLLC");
+    if (p->flux == DGK_FLUX_HLLC && p->model != 2) return fail(DGK_ERR_UNSUPPORTED, "the HLLC flux is for model 2");
     if (c->have_mesh && p->precision != c->prm.precision)
         return fail(DGK_ERR_STATE, "precision is fixed once the mesh is built");
     c->prm = *p;
@@ -566,7 +570,7 @@ int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m)
     DGK_CUDA(cudaMalloc(&c->Utv, nstate * c->rsize));
     DGK_CUDA(cudaMalloc(&c->tr1, (size_t)c->NL * nface * c->rsize));
     DGK_CUDA(cudaMalloc(&c->tr2, (size_t)2 * nface * c->rsize));
-    DGK_CUDA(cudaMalloc(&c->fd, (size_t)(2 * c->NV + 1) * nface * c->rsize));
+    DGK_CUDA(cudaMalloc(&c->fd, (size_t)(2 * c->NV + 3) * nface * c->rsize));
     if (f32) DGK_CUDA(cudaMalloc(&c->Us, (size_t)(c->NV + 1) * ne * c->NP * sizeof(float)));
     DGK_CUDA(cudaMemsetAsync(c->U, 0, nstate * sizeof(double), c->stream));
     DGK_CUDA(cudaMemsetAsync(c->G, 0, nstate * sizeof(double), c->stream));
@@ -1000,6 +1004,7 @@ int dgk_batch_create(dgk_batch **out, int device, void *cuda_stream, const dgk_p
     if (!out || !p || nprob < 1 || !meshes) return fail(DGK_ERR_ARG, "bad arguments");
     *out = nullptr;
     if (p->precision != DGK_PREC_FP32BULK) return fail(DGK_ERR_UNSUPPORTED, "batched ensembles run the FP32-bulk form");
+    if (p->flux != DGK_FLUX_RUSANOV) return fail(DGK_ERR_UNSUPPORTED, "batched ensembles use the Rusanov flux");
     for (int i = 0; i < nprob; ++i)
         if (meshes[i].dim != 2 || meshes[i].N < 3 || meshes[i].N > 5)
             return fail(DGK_ERR_UNSUPPORTED, "batched ensembles take 2D meshes with N = 3..5");

@@ -37,6 +37,7 @@ struct PhysR {
     R s_coef;   // R_gas (1 + 1/cv)
     R inv_Rcv;  // 1 / (R_gas cv)
     R half_alpha_p;  // alpha/2 in the model-2 pressure, 0 for model 1
+    int flux;        // convective numerical flux: 0 Rusanov, 1 HLLC (model 2)
 };
 
 // Per box face (-x,+x,-y,+y,-z,+z): isothermal no-slip wall with static contact angle.

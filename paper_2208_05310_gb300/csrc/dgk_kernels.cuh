@@ -8,8 +8,8 @@
 //   k_lift2vol   BR1 pass 1 of (rho, u, c) (recomputed, not stored), T, pass 2 (grad T,
 //                lap c), point fluxes and sources, volume integral with Dhat per
 //                direction -> U_t(vol); face traces -> one-sided face data (U-, F-, lambda-)
-//   k_surf_rk    Rusanov + central viscous flux per face point, surface lifting with
-//                l(+-1)/w, Jacobian 2/h, RK stage update in FP64, new pass-1 traces
+//   k_surf_rk    Rusanov (or HLLC) + central viscous flux per face point, surface lifting
+//                with l(+-1)/w, Jacobian 2/h, RK stage update in FP64, new pass-1 traces
 //
 // Thread layout: one thread per node for point-wise work (EPB elements per block).  The
 // tensor-product contractions are done line by line ("sum factorisation"): a thread
@@ -35,6 +35,14 @@
 #endif
 #ifndef DGK_THREADS_SURF
 #define DGK_THREADS_SURF 896
+#endif
+// k_surf_rk with the HLLC flux loads U and G after the face phase: its face phase needs
+// the registers that hold them otherwise (1.77 against 2.10 ms on the 3D N = 5 workload).
+#ifndef DGK_SURF_HLLC_LATE
+#define DGK_SURF_HLLC_LATE 1
+#endif
+#ifndef DGK_THREADS_SURF_HLLC
+#define DGK_THREADS_SURF_HLLC 896  // k_surf_rk with the HLLC flux
 #endif
 
 namespace dgk {
@@ -64,7 +72,8 @@ struct KView {
     R *Utv;              // [NV][ne][NP] volume part of U_t
     R *tr1;              // [NL][ne][NF][NFP] pass-1 traces of (rho, u, c)
     R *tr2;              // [2][ne][NF][NFP] traces of T and of d c / d x_normal
-    R *fd;               // [NV+NV+1][ne][NF][NFP] one-sided face data (U, F, lambda)
+    R *fd;               // [2NV+3][ne][NF][NFP] one-sided face data: U, F = F^C - F^V, lambda, and
+                         // for the HLLC flux the convective pressure and the sound speed
     double *out;         // rhs output [NV][ne][NP], or nodal T [ne][NP]
     const double *coef;  // device [A_0..A_4, B_0..B_4, dt] of this problem
     unsigned *status;
@@ -384,6 +393,96 @@ __device__ __forceinline__ R pick(int d, const R *v)
     return x;
 }
 
+// Convective flux F^C in +e_dir of the state U with convective pressure p and
+// irho = 1/rho (Eq. navierstokeskorteweg_palpha for model 2).
+template <int D, typename R>
+__device__ __forceinline__ void conv_flux(int dir, const R *U, R p, R irho, R *F)
+{
+    R m[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) m[k] = U[1 + k];
+    const R mn = pick<D, R>(dir, m), un = mn * irho;
+    F[0] = mn;
+#pragma unroll
+    for (int k = 0; k < D; ++k) F[1 + k] = m[k] * un + (k == dir ? p : R(0));
+    F[D + 1] = (U[D + 1] + p) * un;
+    F[D + 2] = U[D + 2] * un;
+}
+
+// HLLC flux in +e_dir between UL (the - side) and UR (the + side), with their convective
+// fluxes FL, FR, pressures, sound speeds and 1/rho (Toro 2009, Sec. 10.4): wave speeds
+// S_L = min(u_L - a_L, u_R - a_R), S_R = max(u_L + a_L, u_R + a_R); contact speed S* from
+// the pressures and momenta; star state of the side the contact leaves behind,
+// chi (1, S* e_dir + tangential u, E/rho + (S* - u)(S* + p/(rho (S - u))), c/rho) with
+// chi = rho (S - u)/(S - S*), the order parameter carried like a passive scalar.
+template <int D, typename R>
+__device__ __forceinline__ void hllc_flux(int dir, const R *UL, const R *FL, R pL, R aL, R irL, const R *UR,
+                                          const R *FR, R pR, R aR, R irR, R *F)
+{
+    constexpr int NV = D + 3;
+    R mL[D], mR[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        mL[k] = UL[1 + k];
+        mR[k] = UR[1 + k];
+    }
+    const R rL = UL[0], rR = UR[0];
+    const R uL = pick<D, R>(dir, mL) * irL, uR = pick<D, R>(dir, mR) * irR;
+    const R SL = fmin(uL - aL, uR - aR), SR = fmax(uL + aL, uR + aR);
+    if (SL >= R(0) || SR <= R(0)) {
+        const bool left = SL >= R(0);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = left ? FL[v] : FR[v];
+        return;
+    }
+    const R Ss = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) / (rL * (SL - uL) - rR * (SR - uR));
+    const bool left = Ss >= R(0);
+    R UK[NV], FK[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        UK[v] = left ? UL[v] : UR[v];
+        FK[v] = left ? FL[v] : FR[v];
+    }
+    const R SK = left ? SL : SR, pK = left ? pL : pR, rK = UK[0], irK = left ? irL : irR, uK = left ? uL : uR;
+    const R chi = rK * (SK - uK) / (SK - Ss);
+    R Us[NV];
+    Us[0] = chi;
+#pragma unroll
+    for (int k = 0; k < D; ++k) Us[1 + k] = chi * (k == dir ? Ss : UK[1 + k] * irK);
+    Us[D + 1] = chi * (UK[D + 1] * irK + (Ss - uK) * (Ss + pK * irK / (SK - uK)));
+    Us[D + 2] = chi * UK[D + 2] * irK;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = FK[v] + SK * (Us[v] - UK[v]);
+}
+
+// Numerical flux of one interior face point from the one-sided face data fd of its two
+// sides (indices iL on the - side, iR on the + side, array stride st): HLLC for the
+// convective part, central for the viscous part, F* = HLLC(F^C) - (F^V_L + F^V_R)/2 with
+// F^V = F^C - F.  Written to out[v * ostride].
+template <int D, typename R>
+__device__ __forceinline__ void hllc_face(const R *fd, long long st, long long iL, long long iR, int dir, R *out,
+                                       int ostride)
+{
+    constexpr int NV = D + 3;
+    R UL[NV], UR[NV], FcL[NV], FcR[NV], Fh[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        UL[v] = fd[v * st + iL];
+        UR[v] = fd[v * st + iR];
+    }
+    const R pL = fd[(2 * NV + 1) * st + iL], aL = fd[(2 * NV + 2) * st + iL];
+    const R pR = fd[(2 * NV + 1) * st + iR], aR = fd[(2 * NV + 2) * st + iR];
+    const R irL = R(1) / UL[0], irR = R(1) / UR[0];
+    conv_flux<D, R>(dir, UL, pL, irL, FcL);
+    conv_flux<D, R>(dir, UR, pR, irR, FcR);
+    hllc_flux<D, R>(dir, UL, FcL, pL, aL, irL, UR, FcR, pR, aR, irR, Fh);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const R FvL = FcL[v] - fd[(NV + v) * st + iL], FvR = FcR[v] - fd[(NV + v) * st + iR];
+        out[v * ostride] = Fh[v] - R(0.5) * (FvL + FvR);
+    }
+}
+
 // One-sided flux F(U-, grads-) in direction dir (interior faces), or the complete wall
 // flux in +e_dir (wall faces; Sec. 2.4, Eq. bc_nsk_alpha with gamma_1 = gamma_2 =
 // gamma_4 = 0: Rusanov against the mirrored ghost (rho, m - 2(m.n)n, rho e, c) with equal
@@ -392,7 +491,8 @@ __device__ __forceinline__ R pick(int d, const R *v)
 // direction is a run-time value: the normal components are selected, so that face
 // points of all directions share one instruction stream.
 template <int D, typename R>
-__device__ __forceinline__ void face_flux(const Ctx<R> &a, int f, int dir, bool wall, const R *r, R *F, R &lam)
+__device__ __forceinline__ void face_flux(const Ctx<R> &a, int f, int dir, bool wall, const R *r, R *F, R &lam, R &pf_out,
+                                          R &s_out)
 {
     using FR = FaceRec<D>;
     const PhysR<R> &ph = a.pr;
@@ -414,7 +514,10 @@ __device__ __forceinline__ void face_flux(const Ctx<R> &a, int f, int dir, bool 
     const R iomb = R(1) / (R(1) - R(kBvdw) * rho);
     const R pf = flux_pressure<R>(ph, rho, T, iomb);
     const R un = pick<D, R>(dir, u), mn = pick<D, R>(dir, m), dnn = pick<D, R>(dir, ddu);
-    lam = fabs(un) + signal_speed<R>(ph, rho, T, iomb);
+    const R sig = signal_speed<R>(ph, rho, T, iomb);
+    lam = fabs(un) + sig;
+    pf_out = pf;
+    s_out = sig;
     const R divu = r[FR::DIV];
     // viscous stress column tau_{k, dir} = mu (du_k/dx_dir + du_dir/dx_k) - 2/3 mu div u delta;
     // du_dir/dx_k (k != dir) sits in slot k of the record's second block if k < dir, else k-1
@@ -464,11 +567,17 @@ __device__ __forceinline__ void face_flux(const Ctx<R> &a, int f, int dir, bool 
     Ui[D + 1] = Ug[D + 1] = E;
     Ui[D + 2] = Ug[D + 2] = c;
     const bool plus = nsign > R(0);
+    if (ph.flux == 1) {
+        // HLLC against the ghost, same pressure and sound speed on both sides
+        if (plus) hllc_flux<D, R>(dir, Ui, Fi, pf, sig, irho, Ug, Fg, pf, sig, irho, F);
+        else hllc_flux<D, R>(dir, Ug, Fg, pf, sig, irho, Ui, Fi, pf, sig, irho, F);
+    } else {
 #pragma unroll
-    for (int v = 0; v < D + 3; ++v) {
-        const R FL = plus ? Fi[v] : Fg[v], FRr = plus ? Fg[v] : Fi[v];
-        const R UL = plus ? Ui[v] : Ug[v], UR = plus ? Ug[v] : Ui[v];
-        F[v] = R(0.5) * (FL + FRr) - R(0.5) * lam * (UR - UL);
+        for (int v = 0; v < D + 3; ++v) {
+            const R FL = plus ? Fi[v] : Fg[v], FRr = plus ? Fg[v] : Fi[v];
+            const R UL = plus ? Ui[v] : Ug[v], UR = plus ? Ug[v] : Ui[v];
+            F[v] = R(0.5) * (FL + FRr) - R(0.5) * lam * (UR - UL);
+        }
     }
 #pragma unroll
     for (int k = 0; k < D; ++k) F[1 + k] -= tau[k];
@@ -726,8 +835,8 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
                 for (int l = 0; l < P; ++l) acc += a.op.lm[l] * src[first + l * step];
                 r[k] = acc;
             }
-            R F[NV], lam;
-            face_flux<D, R>(a, f, dir, wall, r, F, lam);
+            R F[NV], lam, pf, sig;
+            face_flux<D, R>(a, f, dir, wall, r, F, lam, pf, sig);
             const long long fo = (t.e * NF + f) * NFP + fp;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -735,6 +844,10 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
                 a.v.fd[(NV + v) * st + fo] = F[v];
             }
             a.v.fd[(2 * NV) * st + fo] = lam;
+            if (a.pr.flux == 1) {
+                a.v.fd[(2 * NV + 1) * st + fo] = pf;
+                a.v.fd[(2 * NV + 2) * st + fo] = sig;
+            }
         }
     }
 }
@@ -789,12 +902,15 @@ __device__ __forceinline__ void write_traces(const Ctx<R> &a, const Slot<D, N, E
 
 // mode 0: write U_t (double) to a.v.out; mode 1: RK stage `stage` with coefficients from
 // a.v.coef (G = A G + dt U_t; U = U + B G) and new traces.
-template <int D, int N, typename R, int EB = 0>
+// FLUX: 0 Rusanov, 1 HLLC (a template parameter, so that each form keeps the register
+// allocation of its own flux).
+template <int D, int N, typename R, int EB = 0, int FLUX = 0>
 __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, unsigned char *smraw, int mode, int stage)
 {
     using S = Shape<D, N, EB>;
     using M = K3Smem<D, N, R, EB>;
     constexpr int P = S::P, NP = S::NP, NFP = S::NFP, NF = S::NF, NV = S::NV;
+    constexpr bool SURF_LATE = FLUX == 1 && DGK_SURF_HLLC_LATE;
         const Slot<D, N, EB> t(a.v.g, blk);
     R *sFs = reinterpret_cast<R *>(smraw) + (size_t)t.le * M::per_elem;
     const long long ne = a.v.g.ne;
@@ -806,7 +922,7 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
         for (int v = 0; v < NV; ++v) {
             const long long idx = ((long long)v * ne + t.e) * NP + t.n;
             utv[v] = a.v.Utv[idx];
-            if (mode != 0) {
+            if (mode != 0 && !SURF_LATE) {
                 u0[v] = a.v.U[idx];
                 g0[v] = a.v.G[idx];
             }
@@ -824,12 +940,16 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
             } else {
                 const long long ob = ((long long)b * NF + (2 * dir + 1 - side)) * NFP + fp;
                 const long long iL = side ? oo : ob, iR = side ? ob : oo;
-                const R lam = fmax(a.v.fd[(2 * NV) * st + iL], a.v.fd[(2 * NV) * st + iR]);
+                if (FLUX == 1) {
+                    hllc_face<D, R>(a.v.fd, st, iL, iR, dir, sFs + f * NV * NFP + fp, NFP);
+                } else {
+                    const R lam = fmax(a.v.fd[(2 * NV) * st + iL], a.v.fd[(2 * NV) * st + iR]);
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    const R FL = a.v.fd[(NV + v) * st + iL], FR = a.v.fd[(NV + v) * st + iR];
-                    const R UL = a.v.fd[v * st + iL], UR = a.v.fd[v * st + iR];
-                    sFs[(f * NV + v) * NFP + fp] = R(0.5) * (FL + FR) - R(0.5) * lam * (UR - UL);
+                    for (int v = 0; v < NV; ++v) {
+                        const R FL = a.v.fd[(NV + v) * st + iL], FR = a.v.fd[(NV + v) * st + iR];
+                        const R UL = a.v.fd[v * st + iL], UR = a.v.fd[v * st + iR];
+                        sFs[(f * NV + v) * NFP + fp] = R(0.5) * (FL + FR) - R(0.5) * lam * (UR - UL);
+                    }
                 }
             }
         }
@@ -867,6 +987,14 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
         }
         return;
     }
+    if (SURF_LATE && t.valid) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const long long idx = ((long long)v * ne + t.e) * NP + t.n;
+            u0[v] = a.v.U[idx];
+            g0[v] = a.v.G[idx];
+        }
+    }
     double Ud[NV];
     if (t.valid) {
         // FP64 accumulation: G = A G + dt U_t, U = U + B G (two FP64 FMAs per variable;
@@ -889,12 +1017,14 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
     write_traces<D, N, R, EB>(a, t, sFs, Ud);
 }
 
-template <int D, int N, typename R, int EB = 0>
-__global__ void __launch_bounds__(Shape<D, N, EB>::NT, min_blocks(Shape<D, N, EB>::NT, DGK_THREADS_SURF / (int)(sizeof(R) / 4))) k_surf_rk(KArgs<R> args, int mode, int stage)
+template <int D, int N, typename R, int EB = 0, int FLUX = 0>
+__global__ void __launch_bounds__(Shape<D, N, EB>::NT,
+                                  min_blocks(Shape<D, N, EB>::NT, (FLUX ? DGK_THREADS_SURF_HLLC : DGK_THREADS_SURF) / (int)(sizeof(R) / 4)))
+    k_surf_rk(KArgs<R> args, int mode, int stage)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const Ctx<R> a{args.v, args.ph, args.pr, args.op};
-    surf_rk_body<D, N, R, EB>(a, blockIdx.x, smraw, mode, stage);
+    surf_rk_body<D, N, R, EB, FLUX>(a, blockIdx.x, smraw, mode, stage);
 }
 
 // ------------------------------------------------------------------ set-up kernels

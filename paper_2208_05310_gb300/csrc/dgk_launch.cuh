@@ -35,6 +35,8 @@ struct Launcher {
         if ((err = cudaFuncSetAttribute(k_lift1<D, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_lift1))) return err;
         if ((err = cudaFuncSetAttribute(k_lift2vol<D, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_lift2))) return err;
         if ((err = cudaFuncSetAttribute(k_surf_rk<D, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_surf))) return err;
+        if ((err = cudaFuncSetAttribute(k_surf_rk<D, N, R, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_surf)))
+            return err;
         if ((err = cudaFuncSetAttribute(k_traces<D, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_traces))) return err;
         return cudaFuncSetAttribute(k_node_T<D, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_lift1);
     }
@@ -53,7 +55,8 @@ struct Launcher {
     static cudaError_t surf(const void *p, int mode, int stage, cudaStream_t s)
     {
         const KArgs<R> &a = *static_cast<const KArgs<R> *>(p);
-        k_surf_rk<D, N, R><<<blocks(a), S::NT, sm_surf, s>>>(a, mode, stage);
+        if (a.pr.flux == 1) k_surf_rk<D, N, R, 0, 1><<<blocks(a), S::NT, sm_surf, s>>>(a, mode, stage);
+        else k_surf_rk<D, N, R><<<blocks(a), S::NT, sm_surf, s>>>(a, mode, stage);
         return cudaGetLastError();
     }
     static cudaError_t traces(const void *p, cudaStream_t s)

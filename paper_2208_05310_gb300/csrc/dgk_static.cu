@@ -94,6 +94,7 @@ int fill(dgk::KArgs<R> &a, const dgk_params &q, const dgk_box_mesh &m, const dgk
     p.s_coef = (R)(dgk::kRgas * (1.0 + 1.0 / q.cv));
     p.inv_Rcv = (R)(1.0 / (dgk::kRgas * q.cv));
     p.half_alpha_p = q.model == 2 ? (R)(0.5 * q.alpha) : (R)0;
+    p.flux = q.flux;
     for (int f = 0; f < 2 * D; ++f) {
         if (m.periodic[f / 2]) continue;
         double rv, rl, sig;
@@ -130,7 +131,7 @@ void place(dgk::KArgs<R> &a, unsigned char *base, const double *U, double *Ut, i
     a.v.tr2 = reinterpret_cast<R *>(base + off);
     off += align256((size_t)2 * ne * NF * NFP * sizeof(R));
     a.v.fd = reinterpret_cast<R *>(base + off);
-    off += align256((size_t)(2 * NV + 1) * ne * NF * NFP * sizeof(R));
+    off += align256((size_t)(2 * NV + 3) * ne * NF * NFP * sizeof(R));
     a.v.Us = sizeof(R) == 4 ? reinterpret_cast<R *>(base + off) : nullptr;
     a.v.U = const_cast<double *>(U);
     a.v.G = nullptr;
@@ -145,6 +146,8 @@ extern "C" int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *m, const 
     if (!p || !m || !U || !Ut) return fail_static(DGK_ERR_ARG, "null argument");
     if (p->model != 1 && p->model != 2) return fail_static(DGK_ERR_UNSUPPORTED, "model must be 1 or 2");
     if (p->precision != DGK_PREC_FP64 && p->precision != DGK_PREC_FP32BULK) return fail_static(DGK_ERR_ARG, "bad precision");
+    if (p->flux != DGK_FLUX_RUSANOV && p->flux != DGK_FLUX_HLLC) return fail_static(DGK_ERR_ARG, "bad flux");
+    if (p->flux == DGK_FLUX_HLLC && p->model != 2) return fail_static(DGK_ERR_UNSUPPORTED, "the HLLC flux is for model 2");
     if (!(p->gammaK > 0) || !(p->mu >= 0) || !(p->kappa >= 0) || !(p->cv > 0) || !(p->alpha >= 0) || !(p->beta >= 0))
         return fail_static(DGK_ERR_ARG, "parameters out of range");
     if (m->dim != 2 && m->dim != 3) return fail_static(DGK_ERR_UNSUPPORTED, "dim must be 2 or 3");
@@ -161,7 +164,7 @@ extern "C" int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *m, const 
     const bool f32 = p->precision == DGK_PREC_FP32BULK;
     const size_t rs = f32 ? sizeof(float) : sizeof(double);
     const size_t need = 256 + align256((size_t)NV * ne * NP * rs) + align256((size_t)NL * ne * NF * NFP * rs) +
-                        align256((size_t)2 * ne * NF * NFP * rs) + align256((size_t)(2 * NV + 1) * ne * NF * NFP * rs) +
+                        align256((size_t)2 * ne * NF * NFP * rs) + align256((size_t)(2 * NV + 3) * ne * NF * NFP * rs) +
                         (f32 ? align256((size_t)(NV + 1) * ne * NP * rs) : 0);
     if (need > (size_t)DGK_STATIC_SCRATCH_BYTES)
         return fail_static(DGK_ERR_ARG, "mesh too large for the static scratch of dgk_rhs_static (DGK_STATIC_SCRATCH_BYTES)");

@@ -17,6 +17,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libdgk.so")
 
 DGK_PREC = {"fp64": 0, "fp32bulk": 1}
+DGK_FLUX = {"rusanov": 0, "hllc": 1}
 NDIAG = 8
 DIAG_NAMES = ("mass", "mom_x", "mom_y", "mom_z", "energy", "neg_entropy", "rho_minus_c_l2", "max_u")
 
@@ -26,7 +27,7 @@ _lib = None
 class DgkParams(C.Structure):
     _fields_ = [("model", C.c_int), ("rk", C.c_int), ("precision", C.c_int), ("gammaK", C.c_double),
                 ("mu", C.c_double), ("kappa", C.c_double), ("cv", C.c_double), ("alpha", C.c_double),
-                ("beta", C.c_double)]
+                ("beta", C.c_double), ("flux", C.c_int)]
 
 
 class DgkWall(C.Structure):
@@ -153,8 +154,8 @@ def check_conversions(x):
 
 
 def make_params(model=1, rk=4, precision="fp64", gammaK=1e-4, mu=0.01, kappa=1.0 / 150.0, cv=5.0, alpha=100.0,
-                beta=100.0):
-    return DgkParams(model, rk, DGK_PREC[precision], gammaK, mu, kappa, cv, alpha, beta)
+                beta=100.0, flux="rusanov"):
+    return DgkParams(model, rk, DGK_PREC[precision], gammaK, mu, kappa, cv, alpha, beta, DGK_FLUX[flux])
 
 
 def make_box_mesh(dim, N, n, lo, hi, periodic, walls=None):
@@ -210,8 +211,9 @@ class Context:
             pass
 
     def set_params(self, model=1, rk=4, precision="fp64", gammaK=1e-4, mu=0.01, kappa=1.0 / 150.0, cv=5.0,
-                   alpha=100.0, beta=100.0):
-        p = DgkParams(model, rk, DGK_PREC[precision], gammaK, mu, kappa, cv, alpha, beta)
+                   alpha=100.0, beta=100.0, flux="rusanov"):
+        """flux: "rusanov" or "hllc" (model 2)."""
+        p = make_params(model, rk, precision, gammaK, mu, kappa, cv, alpha, beta, flux)
         _check(lib().dgk_set_params(self._h, C.byref(p)), "dgk_set_params")
 
     def mesh_box(self, dim, N, n, lo, hi, periodic, walls=None):

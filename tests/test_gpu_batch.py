@@ -153,3 +153,10 @@ def test_batch_full_ensemble_sampled():
         err = rel_l2(b.problems[k].download_state(), ref)
         assert np.all(err < 1e-9), (k, meshes[k]["N"], meshes[k]["n"], err)
     b.close()
+
+
+def test_batch_refuses_hllc():
+    from paper_2208_05310_gb300 import dgk
+    _, meshes = ensemble(2, 3, (4, 6))
+    with pytest.raises(dgk.DgkError):
+        dgk.Batch(meshes, **dict(PAPER_PARAMS, model=2, flux="hllc"))

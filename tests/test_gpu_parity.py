@@ -56,6 +56,10 @@ CASES = {
     "3d_N4_periodic_m2": (mesh_spec(3, 4, [2, 1, 3]), dict(PAPER_PARAMS, model=2)),
     "3d_N5_walls": (mesh_spec(3, 5, [2, 2, 2], periodic=[1, 1, 0], walls={4: (0.95, 90.0), 5: (0.8, 90.0)}),
                     dict(PAPER_PARAMS)),
+    "2d_N4_walls_m2_hllc": (mesh_spec(2, 4, [3, 3], periodic=[1, 0], walls={2: (0.9, 30.0), 3: (0.85, 150.0)}),
+                            dict(PAPER_PARAMS, model=2, flux="hllc")),
+    "3d_N3_walls_m2_hllc": (mesh_spec(3, 3, [2, 2, 3], periodic=[1, 1, 0], walls={4: (0.85, 60.0), 5: (0.85, 90.0)}),
+                            dict(PAPER_PARAMS, model=2, flux="hllc")),
     "2d_single_element": (mesh_spec(2, 3, [1, 1]), dict(PAPER_PARAMS)),
     "3d_single_element_walls": (mesh_spec(3, 3, [1, 1, 1], periodic=[1, 1, 0],
                                           walls={4: (0.85, 45.0), 5: (0.85, 135.0)}), dict(PAPER_PARAMS)),
@@ -192,7 +196,8 @@ def tol32_step(dim):
     return np.array([1e-7] + [3e-5] * dim + [2e-7, 5e-7])
 
 
-@pytest.mark.parametrize("name", ["2d_N3_walls", "3d_N3_walls", "3d_N5_walls", "2d_N4_periodic_m2"])
+@pytest.mark.parametrize("name", ["2d_N3_walls", "3d_N3_walls", "3d_N5_walls", "2d_N4_periodic_m2", "2d_N4_walls_m2_hllc",
+                                  "3d_N3_walls_m2_hllc"])
 def test_fp32_bulk_against_oracle(orc, name):
     ms, ps = CASES[name]
     o, g, Uo = _state_pair(orc, ms, ps, precision="fp32bulk")
