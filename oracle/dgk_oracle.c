@@ -288,6 +288,7 @@ typedef struct {
     int periodic[3];
     int wall_kind[6];
     double wall_T[6], wall_rv[6], wall_rl[6], wall_sigma[6], wall_theta[6];
+    double wall_g[6][4]; /* kind 2: gamma_1..gamma_4 */
     double xi[MAXP], w[MAXP], Dhat[MAXP * MAXP], lm[MAXP], lp[MAXP];
     or_params prm;
 } ctx_t;
@@ -320,8 +321,14 @@ static int setup(const or_mesh *m, const or_params *p, ctx_t *c)
         for (int s = 0; s < 2; ++s) {
             int f = 2 * d + s;
             c->wall_kind[f] = m->periodic[d] ? 0 : m->wall_kind[f];
-            if (!m->periodic[d] && m->wall_kind[f] != 1) return -1;
-            if (c->wall_kind[f] == 1) {
+            if (!m->periodic[d] && m->wall_kind[f] != 1 && m->wall_kind[f] != 2) return -1;
+            if (c->wall_kind[f] == 2) {
+                for (int k = 0; k < 4; ++k) {
+                    if (!(m->wall_gamma[f][k] >= 0.0)) return -1;
+                    c->wall_g[f][k] = m->wall_gamma[f][k];
+                }
+            }
+            if (c->wall_kind[f] != 0) {
                 if (p->model == 0) return -1; /* original NSK: periodic boxes only */
                 c->wall_T[f] = m->wall_T[f];
                 c->wall_theta[f] = m->wall_theta_deg[f];
@@ -648,7 +655,11 @@ static void lift_pass1(const ctx_t *c, const double *q, const double *tr, double
                     for (int fp = 0; fp < nfp; ++fp) {
                         double own = tr[FIDX(v, e, f, fp, ne, nf, nfp)];
                         if (nb >= 0) qs[s][fp] = 0.5 * (own + tr[FIDX(v, nb, fo, fp, ne, nf, nfp)]);
-                        else qs[s][fp] = (v >= 1 && v <= d) ? 0.0 : own;
+                        else if (v >= 1 && v <= d)
+                            /* no-slip: u* = 0; Navier slip: no normal velocity, the
+                               tangential velocity of the fluid */
+                            qs[s][fp] = (c->wall_kind[f] == 2 && v != 1 + dir) ? own : 0.0;
+                        else qs[s][fp] = own;
                     }
                 }
                 lift_elem(c, q + IDX(v, e, 0, ne, np), dir, qs[0], qs[1], grad + IDX(dir * nl + v, e, 0, ne, np));
@@ -678,10 +689,12 @@ static void node_temperature(const ctx_t *c, const double *U, const double *grad
 }
 
 /* Contact-angle boundary value of the wall-normal gradient of the order parameter,
-   Eq. (bc_contactangle_alpha) with gamma_1 = 0: grad c . n = -(1/gamma_K) dpsi_wall/dc. */
-static double wall_gn(const ctx_t *c, int f, double cminus)
+   Eq. (bc_contactangle_alpha): grad c . n = (1/gamma_K) [gamma_1 div u- - dpsi_wall/dc]
+   (gamma_1 = 0 at kind-1 walls). */
+static double wall_gn(const ctx_t *c, int f, double cminus, double divu)
 {
-    return -or_wall_dpsi_dc(cminus, c->wall_rv[f], c->wall_rl[f], c->wall_sigma[f], c->wall_theta[f])
+    double g1 = c->wall_kind[f] == 2 ? c->wall_g[f][0] : 0.0;
+    return (g1 * divu - or_wall_dpsi_dc(cminus, c->wall_rv[f], c->wall_rl[f], c->wall_sigma[f], c->wall_theta[f]))
            / c->prm.gammaK;
 }
 
@@ -720,8 +733,17 @@ static void lift_pass2(const ctx_t *c, const double *T, const double *grad, cons
                         Ds[s][fp] = 0.5 * (dOwn + trD[((size_t)nb * nf + fo) * nfp + fp]);
                     } else {
                         double cm = trq[FIDX(vc, e, f, fp, ne, nf, nfp)];
-                        Ts[s][fp] = c->wall_T[f];
-                        Ds[s][fp] = (s ? 1.0 : -1.0) * wall_gn(c, f, cm);
+                        /* isothermal wall: T* = T_wall; heat-transfer wall (kind 2): the
+                           fluid's own trace, the wall heat flux enters the energy flux */
+                        Ts[s][fp] = c->wall_kind[f] == 2 ? tOwn : c->wall_T[f];
+                        double divu = 0.0;
+                        if (c->wall_kind[f] == 2)
+                            for (int k = 0; k < d; ++k) {
+                                double tk[MAXP * MAXP];
+                                trace_elem(c, grad + IDX(k * nl + 1 + k, e, 0, ne, np), dir, s, tk);
+                                divu += tk[fp];
+                            }
+                        Ds[s][fp] = (s ? 1.0 : -1.0) * wall_gn(c, f, cm, divu);
                     }
                 }
             }
@@ -749,8 +771,8 @@ static void point_flux(const ctx_t *c, const double *U, const double *g, const d
 }
 
 /* Numerical flux through a wall face in the outward normal direction n = nsign * e_dir
-   (Sec. 2.4, Eq. (bc_nsk_alpha), isothermal no-slip wall with static contact angle,
-   gamma_1 = gamma_2 = gamma_4 = 0):
+   (Sec. 2.4, Eq. (bc_nsk_alpha); kind 1: isothermal no-slip wall with static contact
+   angle, gamma_1 = gamma_2 = gamma_4 = 0; kind 2: generalized Navier slip, below):
    convective part: Rusanov flux against the mirrored ghost state (rho, m - 2(m.n)n, rho e, c)
    with the same pressure and signal speed;
    viscous part: tau(grad u-).n, energy kappa grad T-.n - gamma_K c- (grad c.n) div u-
@@ -789,16 +811,41 @@ static void wall_flux(const ctx_t *c, int f, const double *U, const double *g, c
     double rho = U[0], cm = U[d + 2];
     double divu = 0.0;
     for (int k = 0; k < d; ++k) divu += g[k * nl + 1 + k];
-    double gn = wall_gn(c, f, cm);
+    double gn = wall_gn(c, f, cm, divu);
     double Fv[8];
     Fv[0] = 0.0;
-    for (int k = 0; k < d; ++k) {
-        double tau = p->mu * (g[dir * nl + 1 + k] + g[k * nl + 1 + dir] - (k == dir ? 2.0 / 3.0 * divu : 0.0));
-        Fv[1 + k] = tau * nsign;
+    if (c->wall_kind[f] == 2) {
+        /* generalized Navier slip, Eq. (bc_nsk_alpha): the tangential traction is
+           gamma_1 div u grad_wall c - gamma_2 u_t (Eq. (bc_navierstokes_alpha)), the normal
+           traction that of the fluid; the wall moves with the fluid's tangential velocity,
+           so the traction does work t . u_t; heat flux kappa grad T . n =
+           -gamma_3 (1/T_wall - 1/T-) (Eq. (bc_energy_alpha)); zeta_c = -gamma_1 gamma_4 div u
+           (Eq. (bc_relaxation_alpha)); grad c . n with the gamma_1 term. */
+        double g1 = c->wall_g[f][0], g2 = c->wall_g[f][1], g3 = c->wall_g[f][2], g4 = c->wall_g[f][3];
+        double work = 0.0;
+        for (int k = 0; k < d; ++k) {
+            double uk = U[1 + k] / rho;
+            if (k == dir) {
+                double tnn = p->mu * (2.0 * g[dir * nl + 1 + dir] - 2.0 / 3.0 * divu);
+                Fv[1 + k] = tnn * nsign;
+            } else {
+                double tk = g1 * divu * g[k * nl + d + 1] - g2 * uk;
+                Fv[1 + k] = tk;
+                work += tk * uk;
+            }
+        }
+        double zeta = -g1 * g4 * divu;
+        double Tm = temperature(c, U, g);
+        Fv[d + 1] = work - g3 * (1.0 / c->wall_T[f] - 1.0 / Tm) - p->gammaK * cm * gn * divu + p->gammaK * gn * zeta;
+        Fv[d + 2] = p->gammaK * p->beta * gn;
+    } else {
+        for (int k = 0; k < d; ++k) {
+            double tau = p->mu * (g[dir * nl + 1 + k] + g[k * nl + 1 + dir] - (k == dir ? 2.0 / 3.0 * divu : 0.0));
+            Fv[1 + k] = tau * nsign;
+        }
+        Fv[d + 1] = p->kappa * gT[dir] * nsign - p->gammaK * cm * gn * divu;
+        Fv[d + 2] = p->gammaK * p->beta * gn;
     }
-    Fv[d + 1] = p->kappa * gT[dir] * nsign - p->gammaK * cm * gn * divu;
-    Fv[d + 2] = p->gammaK * p->beta * gn;
-    (void)rho;
     /* outward normal flux = nsign * Fconv - Fv */
     for (int v = 0; v < nv; ++v) Fn[v] = nsign * Fconv[v] - Fv[v];
 }
@@ -986,7 +1033,7 @@ int or_node_coords(const or_mesh *m, double *x)
 {
     or_params p = {1, 1e-4, 0.01, 1.0 / 150.0, 5.0, 100.0, 100.0};
     or_mesh mm = *m;
-    for (int f = 0; f < 6; ++f) if (mm.wall_kind[f] == 1) mm.wall_T[f] = 0.85;
+    for (int f = 0; f < 6; ++f) if (mm.wall_kind[f] != 0) mm.wall_T[f] = 0.85;
     ctx_t c;
     if (setup(&mm, &p, &c)) return -1;
     for (long e = 0; e < c.ne; ++e)

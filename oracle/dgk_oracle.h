@@ -28,10 +28,14 @@ typedef struct {
     double lo[3], hi[3];
     int periodic[3];
     /* faces of the box: -x, +x, -y, +y, -z, +z.  kind 0: no wall (direction must be
-       periodic); kind 1: isothermal no-slip wall with static contact angle. */
+       periodic); kind 1: isothermal no-slip wall with static contact angle; kind 2:
+       generalized Navier-slip wall, Eq. (bc_nsk_alpha), with the positive parameters
+       gamma_1 (contact-angle hysteresis), gamma_2 (slip friction), gamma_3 (heat
+       transfer; the wall temperature is wall_T) and gamma_4 (relaxation). */
     int wall_kind[6];
     double wall_T[6];
     double wall_theta_deg[6];
+    double wall_gamma[6][4];
 } or_mesh;
 
 typedef struct {

@@ -24,7 +24,7 @@ class OrMesh(C.Structure):
     _fields_ = [("dim", C.c_int), ("N", C.c_int), ("n", C.c_int * 3),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("periodic", C.c_int * 3),
                 ("wall_kind", C.c_int * 6), ("wall_T", C.c_double * 6),
-                ("wall_theta_deg", C.c_double * 6)]
+                ("wall_theta_deg", C.c_double * 6), ("wall_gamma", (C.c_double * 4) * 6)]
 
 
 class OrParams(C.Structure):
@@ -91,7 +91,9 @@ def _check(rc, what):
 
 
 def make_mesh(dim, N, n, lo, hi, periodic, walls=None):
-    """walls: dict face -> (T_wall, theta_deg) for faces 0..5 (-x,+x,-y,+y,-z,+z)."""
+    """walls: dict face -> (T_wall, theta_deg) for faces 0..5 (-x,+x,-y,+y,-z,+z): an
+    isothermal no-slip wall; or (T_wall, theta_deg, gamma_1, gamma_2, gamma_3, gamma_4): a
+    generalized Navier-slip wall (Eq. bc_nsk_alpha)."""
     m = OrMesh()
     m.dim, m.N = dim, N
     for d in range(3):
@@ -99,10 +101,12 @@ def make_mesh(dim, N, n, lo, hi, periodic, walls=None):
         m.lo[d] = float(lo[d]) if d < dim else 0.0
         m.hi[d] = float(hi[d]) if d < dim else 1.0
         m.periodic[d] = int(periodic[d]) if d < dim else 1
-    for f, (Tw, th) in (walls or {}).items():
-        m.wall_kind[f] = 1
-        m.wall_T[f] = Tw
-        m.wall_theta_deg[f] = th
+    for f, spec in (walls or {}).items():
+        m.wall_kind[f] = 1 if len(spec) == 2 else 2
+        m.wall_T[f] = spec[0]
+        m.wall_theta_deg[f] = spec[1]
+        for k, gk in enumerate(spec[2:6]):
+            m.wall_gamma[f][k] = gk
     return m
 
 
