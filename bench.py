@@ -36,14 +36,15 @@ UNIT = "DOF-stage/s"
 # point per node for N = 5).  The lifting kernels read the state: in the FP64 form the
 # double state, in the FP32-bulk form its float shadow (NV values and the energy
 # balance), which the RK update writes beside the double state.
-def kernel_bytes_per_node(dim, N, rsize):
+def kernel_bytes_per_node(dim, N, rsize, flux="rusanov"):
     nv, nl = dim + 3, dim + 2
     f = 2 * dim / (N + 1)  # face points per node (own faces)
+    nfd = 2 * nv + (3 if flux == "hllc" else 1)  # face data values (HLLC: + pressure, sound speed)
     state = 8 * nv if rsize == 8 else rsize * (nv + 1)
     shadow_w = 0 if rsize == 8 else rsize * (nv + 1)
     lift1 = state + rsize * 1 * f + rsize * 2 * f                       # c traces in, T and dc/dn traces out
-    lift2 = state + rsize * nl * f + rsize * 2 * f + rsize * nv + rsize * (2 * nv + 1) * f
-    surf = rsize * (2 * nv + 1) * f + rsize * nv + 8 * nv * 4 + rsize * nl * f + shadow_w
+    lift2 = state + rsize * nl * f + rsize * 2 * f + rsize * nv + rsize * nfd * f
+    surf = rsize * nfd * f + rsize * nv + 8 * nv * 4 + rsize * nl * f + shadow_w
     return {"k_lift1": lift1, "k_lift2vol": lift2, "k_surf_rk": surf}
 
 
@@ -335,7 +336,7 @@ def run_ours(args, wl, rank, world, local_rank):
     ctx.set_timing(False)
     ctx.status()
     rsize = 4 if args.precision == "fp32bulk" else 8
-    kb = kernel_bytes_per_node(m["dim"], m["N"], rsize)
+    kb = kernel_bytes_per_node(m["dim"], m["N"], rsize, wl["params"].get("flux", "rusanov"))
     total_k = sum(t for t, _ in ktimes.values())
     dom = max(ktimes, key=lambda k: ktimes[k][0])
     avg_ms = ktimes[dom][0] / max(ktimes[dom][1], 1)
@@ -577,6 +578,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--flux", default="rusanov", choices=["rusanov", "hllc"],
+                    help="hllc runs the workload with relaxation model 2 and the HLLC flux")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -584,6 +587,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     wl = WORKLOADS[args.workload]()
+    if args.flux == "hllc":
+        if "batch" in wl:
+            print(json.dumps({"error": "batched ensembles use the Rusanov flux"}))
+            return 2
+        wl["params"] = dict(wl["params"], model=2, flux="hllc")
+        wl["name"] += ", model 2 + HLLC"
     if args.impl == "reference":
         return run_reference(args, wl, rank, world)
     if world > 1:

@@ -83,11 +83,16 @@ typedef struct {
 /* One face of the box.  kind 0: none (the direction must be periodic); kind 1:
    isothermal no-slip wall at temperature T_wall with static contact angle theta_deg
    (Eq. bc_nsk_alpha with gamma_1 = gamma_2 = gamma_4 = 0; the saturation densities and
-   sigma_vl at T_wall are computed by the library, Eq. surftenscoef). */
+   sigma_vl at T_wall are computed by the library, Eq. surftenscoef); kind 2: generalized
+   Navier-slip wall, Eq. bc_nsk_alpha with the non-negative parameters gamma[0..3] =
+   gamma_1 (contact-angle hysteresis), gamma_2 (slip friction), gamma_3 (heat transfer
+   to the wall at T_wall) and gamma_4 (relaxation condition); the fluid slips along the
+   wall (no normal velocity). */
 typedef struct {
     int kind;
     double T_wall;
     double theta_deg;
+    double gamma[4];  /* kind 2 only */
 } dgk_wall;
 
 /* Cartesian box mesh of hexahedral (dim 3) or quadrilateral (dim 2) elements. */

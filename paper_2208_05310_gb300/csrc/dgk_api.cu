@@ -294,6 +294,12 @@ void fill_bulk(dgk::KArgs<R> &a, const dgk::Geom &g, const dgk::Phys &ph, const 
     p.half_alpha_p = ph.model == 2 ? (R)(0.5 * ph.alpha) : (R)0;
     p.flux = flux;
     for (int f = 0; f < 6; ++f) {
+        a.v.wr.kind[f] = w.kind[f];
+        a.v.wr.g1[f] = (R)w.g[f][0];
+        a.v.wr.g2[f] = (R)w.g[f][1];
+        a.v.wr.g3[f] = (R)w.g[f][2];
+        a.v.wr.g1gK[f] = (R)(w.g[f][0] / ph.gK);
+        a.v.wr.g1g4[f] = (R)(w.g[f][0] * w.g[f][3]);
         a.v.wr.K[f] = (R)w.K[f];
         a.v.wr.rl[f] = (R)w.rl[f];
         a.v.wr.rv[f] = (R)w.rv[f];
@@ -323,7 +329,8 @@ int build_consts(dgk_ctx *c)
         double rv, rl, sig;
         if (!dgk::host::maxwell(wf.T_wall, rv, rl) || !dgk::host::sigma_vl(wf.T_wall, c->prm.gammaK, sig))
             return fail(DGK_ERR_THERMO, "wall temperature has no saturation states (need 0 < T_wall < 1)");
-        w.kind[f] = 1;
+        w.kind[f] = wf.kind;
+        for (int k = 0; k < 4; ++k) w.g[f][k] = wf.kind == 2 ? wf.gamma[k] : 0.0;
         w.Tw[f] = wf.T_wall;
         w.rv[f] = rv;
         w.rl[f] = rl;
@@ -532,8 +539,14 @@ int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m)
         if (m->n[d] < 1 || !(m->hi[d] > m->lo[d])) return fail(DGK_ERR_ARG, "bad element count or extent");
         ne *= m->n[d];
         if (!m->periodic[d]) {
-            for (int s = 0; s < 2; ++s)
-                if (m->wall[2 * d + s].kind != 1) return fail(DGK_ERR_ARG, "non-periodic direction needs walls on both faces");
+            for (int s = 0; s < 2; ++s) {
+                const dgk_wall &w = m->wall[2 * d + s];
+                if (w.kind != 1 && w.kind != 2) return fail(DGK_ERR_ARG, "non-periodic direction needs walls on both faces");
+                if (w.kind == 2)
+                    for (int k = 0; k < 4; ++k)
+                        if (!(w.gamma[k] >= 0.0) || !std::isfinite(w.gamma[k]))
+                            return fail(DGK_ERR_ARG, "wall parameters gamma_1..gamma_4 must be finite and non-negative");
+            }
         }
     }
     DGK_CUDA(cudaSetDevice(c->device));

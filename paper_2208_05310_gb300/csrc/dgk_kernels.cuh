@@ -579,6 +579,29 @@ __device__ __forceinline__ void face_flux(const Ctx<R> &a, int f, int dir, bool 
             F[v] = R(0.5) * (FL + FRr) - R(0.5) * lam * (UR - UL);
         }
     }
+    if (a.v.wr.kind[f] == 2) {
+        // generalized Navier slip (Eq. bc_nsk_alpha): outward tangential traction
+        // gamma_1 div u (grad c)_k - gamma_2 u_k, normal traction of the fluid; work on the
+        // slipping fluid; heat flux -gamma_3 (1/T_wall - 1/T); zeta = -gamma_1 gamma_4 div u;
+        // grad c . n with the gamma_1 div u term.  F is the flux in +e_dir: outward
+        // quantities enter with nsign.
+        const R gnn = gn + a.v.wr.g1gK[f] * divu;
+        R work = R(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const R tk = a.v.wr.g1[f] * divu * gc[k] - a.v.wr.g2[f] * u[k];
+            if (k == dir) F[1 + k] -= tau[k];
+            else {
+                F[1 + k] -= nsign * tk;
+                work += tk * u[k];
+            }
+        }
+        const R zeta = -a.v.wr.g1g4[f] * divu;
+        const R qn = -a.v.wr.g3[f] * (R(1) / a.v.wr.Tw[f] - R(1) / T);
+        F[D + 1] -= nsign * (work + qn - ph.gK * c * gnn * divu + ph.gK * gnn * zeta);
+        F[D + 2] -= nsign * ph.gKbeta * gnn;
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < D; ++k) F[1 + k] -= tau[k];
     F[D + 1] -= ph.kap * gTd - nsign * ph.gK * c * gn * divu;
@@ -651,7 +674,8 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
                 const R own = a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)];
                 R val;
                 if (b >= 0) val = R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, v, b, 2 * dir + 1 - side, fp)]);
-                else val = (v >= 1 && v <= D) ? R(0) : own;
+                // walls: u* = 0 (no slip), or the fluid's tangential velocity (Navier slip)
+                else val = (v >= 1 && v <= D && (a.v.wr.kind[f] != 2 || v == 1 + dir)) ? R(0) : own;
                 sQs[(f * NL + v) * NFP + fp] = val;
             }
         }
@@ -674,9 +698,12 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
                 pT[j] = R(0.5) * (ownT + a.v.tr2[fidx<NF, NFP>(ne, 0, b, fo, fp)]);
                 pD[j] = R(0.5) * (ownD + a.v.tr2[fidx<NF, NFP>(ne, 1, b, fo, fp)]);
             } else {
+                // isothermal wall: T* = T_wall; Navier-slip wall: the fluid's trace (the
+                // wall heat flux enters the energy flux); contact-angle gradient (its
+                // gamma_1 div u part is added once div u is known, in the node phase)
                 const R cm = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
                 const R gn = a.v.wr.K[f] * (cm - a.v.wr.rl[f]) * (cm - a.v.wr.rv[f]);
-                pT[j] = a.v.wr.Tw[f];
+                pT[j] = a.v.wr.kind[f] == 2 ? ownT : a.v.wr.Tw[f];
                 pD[j] = side ? gn : -gn;
             }
         }
@@ -718,7 +745,21 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
             const int q = n + j * NP;
             if (q < NF * NFP) {
                 sTs[q] = pT[j];
-                sDs[q] = pD[j];
+                R dD = R(0);
+                const int f = q / NFP;
+                if (a.v.wr.kind[f] == 2 && a.v.wr.g1gK[f] != R(0) && t.nbr(a.v.g, f) < 0) {
+                    // Eq. bc_contactangle_alpha: + (gamma_1/gamma_K) div u- at the face point
+                    const int dir = f >> 1, fp = q % NFP;
+                    const int base = line_base<P>(fp, dir), stride = line_stride<P>(dir);
+                    R divu = R(0);
+#pragma unroll
+                    for (int k = 0; k < D; ++k)
+#pragma unroll
+                        for (int l = 0; l < P; ++l)
+                            divu += ((f & 1) ? a.op.lp[l] : a.op.lm[l]) * sG[(k * NL + 1 + k) * NP + base + l * stride];
+                    dD = ((f & 1) ? R(1) : R(-1)) * a.v.wr.g1gK[f] * divu;
+                }
+                sDs[q] = pD[j] + dD;
             }
         }
     }

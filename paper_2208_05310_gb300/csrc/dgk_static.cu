@@ -102,6 +102,15 @@ int fill(dgk::KArgs<R> &a, const dgk_params &q, const dgk_box_mesh &m, const dgk
             return fail_static(DGK_ERR_THERMO, "wall temperature has no saturation states (need 0 < T_wall < 1)");
         const double dr = rl - rv;
         a.v.wr.K[f] = (R)(-6.0 * sig * std::cos(m.wall[f].theta_deg * M_PI / 180.0) / (q.gammaK * dr * dr * dr));
+        const dgk_wall &wf = m.wall[f];
+        const double g1 = wf.kind == 2 ? wf.gamma[0] : 0.0, g2 = wf.kind == 2 ? wf.gamma[1] : 0.0;
+        const double g3 = wf.kind == 2 ? wf.gamma[2] : 0.0, g4 = wf.kind == 2 ? wf.gamma[3] : 0.0;
+        a.v.wr.kind[f] = wf.kind;
+        a.v.wr.g1[f] = (R)g1;
+        a.v.wr.g2[f] = (R)g2;
+        a.v.wr.g3[f] = (R)g3;
+        a.v.wr.g1gK[f] = (R)(g1 / q.gammaK);
+        a.v.wr.g1g4[f] = (R)(g1 * g4);
         a.v.wr.rl[f] = (R)rl;
         a.v.wr.rv[f] = (R)rv;
         a.v.wr.Tw[f] = (R)m.wall[f].T_wall;
@@ -157,8 +166,14 @@ extern "C" int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *m, const 
     long long ne = 1;
     for (int d = 0; d < D; ++d) {
         if (m->n[d] < 1 || !(m->hi[d] > m->lo[d])) return fail_static(DGK_ERR_ARG, "bad element count or extent");
-        if (!m->periodic[d] && (m->wall[2 * d].kind != 1 || m->wall[2 * d + 1].kind != 1))
-            return fail_static(DGK_ERR_ARG, "non-periodic direction needs walls on both faces");
+        for (int s = 0; s < 2 && !m->periodic[d]; ++s) {
+            const dgk_wall &w = m->wall[2 * d + s];
+            if (w.kind != 1 && w.kind != 2) return fail_static(DGK_ERR_ARG, "non-periodic direction needs walls on both faces");
+            if (w.kind == 2)
+                for (int k = 0; k < 4; ++k)
+                    if (!(w.gamma[k] >= 0.0) || !std::isfinite(w.gamma[k]))
+                        return fail_static(DGK_ERR_ARG, "wall parameters gamma_1..gamma_4 must be finite and non-negative");
+        }
         ne *= m->n[d];
     }
     const bool f32 = p->precision == DGK_PREC_FP32BULK;

@@ -31,7 +31,15 @@ class DgkParams(C.Structure):
 
 
 class DgkWall(C.Structure):
-    _fields_ = [("kind", C.c_int), ("T_wall", C.c_double), ("theta_deg", C.c_double)]
+    _fields_ = [("kind", C.c_int), ("T_wall", C.c_double), ("theta_deg", C.c_double), ("gamma", C.c_double * 4)]
+
+
+def _wall(spec):
+    """(T_wall, theta_deg): isothermal no-slip wall; (T_wall, theta_deg, gamma_1, gamma_2,
+    gamma_3, gamma_4): generalized Navier-slip wall."""
+    if len(spec) == 2:
+        return DgkWall(1, spec[0], spec[1])
+    return DgkWall(2, spec[0], spec[1], (C.c_double * 4)(*spec[2:6]))
 
 
 class DgkBoxMesh(C.Structure):
@@ -159,7 +167,8 @@ def make_params(model=1, rk=4, precision="fp64", gammaK=1e-4, mu=0.01, kappa=1.0
 
 
 def make_box_mesh(dim, N, n, lo, hi, periodic, walls=None):
-    """walls: {face: (T_wall, theta_deg)}, faces 0..5 = -x,+x,-y,+y,-z,+z."""
+    """walls: {face: (T_wall, theta_deg)} (no-slip) or {face: (T_wall, theta_deg, g1, g2, g3, g4)}
+    (Navier slip), faces 0..5 = -x,+x,-y,+y,-z,+z."""
     m = DgkBoxMesh()
     m.dim, m.N = dim, N
     for d in range(3):
@@ -167,8 +176,8 @@ def make_box_mesh(dim, N, n, lo, hi, periodic, walls=None):
         m.lo[d] = float(lo[d]) if d < dim else 0.0
         m.hi[d] = float(hi[d]) if d < dim else 1.0
         m.periodic[d] = int(periodic[d]) if d < dim else 1
-    for f, (Tw, th) in (walls or {}).items():
-        m.wall[f] = DgkWall(1, Tw, th)
+    for f, spec in (walls or {}).items():
+        m.wall[f] = _wall(spec)
     return m
 
 
@@ -217,7 +226,8 @@ class Context:
         _check(lib().dgk_set_params(self._h, C.byref(p)), "dgk_set_params")
 
     def mesh_box(self, dim, N, n, lo, hi, periodic, walls=None):
-        """walls: {face: (T_wall, theta_deg)}, faces 0..5 = -x,+x,-y,+y,-z,+z."""
+        """walls: {face: (T_wall, theta_deg)} (no-slip) or {face: (T_wall, theta_deg, g1, g2, g3, g4)}
+    (Navier slip), faces 0..5 = -x,+x,-y,+y,-z,+z."""
         m = DgkBoxMesh()
         m.dim, m.N = dim, N
         for d in range(3):
@@ -225,8 +235,8 @@ class Context:
             m.lo[d] = float(lo[d]) if d < dim else 0.0
             m.hi[d] = float(hi[d]) if d < dim else 1.0
             m.periodic[d] = int(periodic[d]) if d < dim else 1
-        for f, (Tw, th) in (walls or {}).items():
-            m.wall[f] = DgkWall(1, Tw, th)
+        for f, spec in (walls or {}).items():
+            m.wall[f] = _wall(spec)
         _check(lib().dgk_mesh_box(self._h, C.byref(m)), "dgk_mesh_box")
         ne, npn, nv = C.c_longlong(), C.c_int(), C.c_int()
         _check(lib().dgk_sizes(self._h, C.byref(ne), C.byref(npn), C.byref(nv)), "dgk_sizes")

@@ -4,7 +4,8 @@ mesh size, temperature and contact angle advanced by one persistent launch per R
 
 Checks: against the FP64 oracle within the FP32-bulk step tolerances; against the same
 problems run one by one through single contexts; independence of the work
-decomposition (bit-exact across tile lengths and grid sizes); the autotuner leaves the
+decomposition (bit-exact across tile lengths and grid sizes within a form, FP32
+rounding between the persistent and the grouped kernels); the autotuner leaves the
 states untouched; and at the full ensemble size (256 problems, 16x16 to 96x96 elements)
 sampled problems match single-context runs and mass is conserved."""
 import numpy as np
@@ -105,7 +106,7 @@ def test_batch_decomposition_independence_and_autotune():
     specs, meshes = ensemble(12, 17, (6, 24))
     b, prims, dts = _batch(meshes, specs)
     U0 = [q.download_state() for q in b.problems]
-    out = []
+    out = {}
     for cfg in [("persistent", 1, 1, 1, 1), ("persistent", 1, 4, 2, 1), ("persistent", 2, 2, 4, 3),
                 ("grouped", 1, 1, 1, 1), ("grouped", 1, 3, 1, 2)]:
         for q, prim in zip(b.problems, prims):
@@ -118,10 +119,16 @@ def test_batch_decomposition_independence_and_autotune():
             continue  # two blocks per SM above the occupancy limit
         b.run(3)
         b.status()
-        out.append([q.download_state() for q in b.problems])
-    for other in out[1:]:
-        for a, c in zip(out[0], other):
-            assert np.array_equal(a, c)
+        out.setdefault(cfg[0], []).append([q.download_state() for q in b.problems])
+    # within a form (one kernel): bit-exact for every decomposition
+    for form, runs in out.items():
+        for other in runs[1:]:
+            for a, c in zip(runs[0], other):
+                assert np.array_equal(a, c), form
+    # across the forms (separate kernels, whose compiled floating-point contraction may
+    # differ): to the FP32 rounding of U_t, seen through dt in the FP64 state
+    for a, c in zip(out["persistent"][0], out["grouped"][0]):
+        assert np.all(rel_l2(c, a) < 1e-9)
     for q, prim in zip(b.problems, prims):
         q.set_primitive(prim)
     tuned = b.autotune()
@@ -131,7 +138,7 @@ def test_batch_decomposition_independence_and_autotune():
         assert np.array_equal(q.download_state(), u)
     b.run(3)
     b.status()
-    for a, q in zip(out[0], b.problems):
+    for a, q in zip(out[tuned["form"]][0], b.problems):
         assert np.array_equal(a, q.download_state())
     b.close()
 

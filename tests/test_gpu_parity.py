@@ -60,6 +60,12 @@ CASES = {
                             dict(PAPER_PARAMS, model=2, flux="hllc")),
     "3d_N3_walls_m2_hllc": (mesh_spec(3, 3, [2, 2, 3], periodic=[1, 1, 0], walls={4: (0.85, 60.0), 5: (0.85, 90.0)}),
                             dict(PAPER_PARAMS, model=2, flux="hllc")),
+    "2d_N4_slip": (mesh_spec(2, 4, [3, 3], periodic=[1, 0], walls={2: (0.9, 30.0, 0.02, 0.1, 0.3, 0.5),
+                                                                   3: (0.85, 150.0, 0.01, 0.2, 0.1, 1.0)}),
+                   dict(PAPER_PARAMS)),
+    "3d_N3_slip_m2": (mesh_spec(3, 3, [2, 2, 3], periodic=[1, 1, 0], walls={4: (0.85, 60.0, 0.03, 0.05, 0.2, 0.3),
+                                                                            5: (0.8, 90.0, 0.0, 0.5, 1.0, 0.0)}),
+                      dict(PAPER_PARAMS, model=2)),
     "2d_single_element": (mesh_spec(2, 3, [1, 1]), dict(PAPER_PARAMS)),
     "3d_single_element_walls": (mesh_spec(3, 3, [1, 1, 1], periodic=[1, 1, 0],
                                           walls={4: (0.85, 45.0), 5: (0.85, 135.0)}), dict(PAPER_PARAMS)),
@@ -197,7 +203,7 @@ def tol32_step(dim):
 
 
 @pytest.mark.parametrize("name", ["2d_N3_walls", "3d_N3_walls", "3d_N5_walls", "2d_N4_periodic_m2", "2d_N4_walls_m2_hllc",
-                                  "3d_N3_walls_m2_hllc"])
+                                  "3d_N3_walls_m2_hllc", "2d_N4_slip", "3d_N3_slip_m2"])
 def test_fp32_bulk_against_oracle(orc, name):
     ms, ps = CASES[name]
     o, g, Uo = _state_pair(orc, ms, ps, precision="fp32bulk")
