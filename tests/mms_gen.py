@@ -25,8 +25,40 @@ def _fields_2d(x, y, t):
     return rho, [u, v], T, c
 
 
+def system_2d_nsk(prm):
+    """The original NSK system (Eq. navierstokeskorteweg, Korteweg stress Eq.
+    cauchystressnsk, energy flux Eq. energyfluxnsk): U = (rho, rho u, rho e) with
+    rho e = rho eps + rho |u|^2/2 + gamma_K/2 |grad rho|^2, no source."""
+    x, y, t = sp.symbols("x y t", real=True)
+    X = [x, y]
+    gK, mu, kap, cv = (sp.Float(prm[k]) for k in ("gammaK", "mu", "kappa", "cv"))
+    rho, vel, T, _ = _fields_2d(x, y, t)
+    grad = lambda f: [sp.diff(f, xi) for xi in X]  # noqa: E731
+    gr = grad(rho)
+    p = rho * R * T / (1 - B * rho) - A * rho ** 2
+    gr2 = gr[0] ** 2 + gr[1] ** 2
+    E = rho * (R * cv * T - A * rho) + sp.Rational(1, 2) * rho * (vel[0] ** 2 + vel[1] ** 2) + gK / 2 * gr2
+    U = [rho, rho * vel[0], rho * vel[1], E]
+    divu = sp.diff(vel[0], x) + sp.diff(vel[1], y)
+    du = [[sp.diff(vel[k], X[i]) for k in range(2)] for i in range(2)]
+    lap = sp.diff(rho, x, 2) + sp.diff(rho, y, 2)
+    gT = grad(T)
+    F = []
+    for i in range(2):
+        tau = [mu * (du[i][k] + du[k][i] - (sp.Rational(2, 3) * divu if k == i else 0))
+               + gK * ((sp.Rational(1, 2) * gr2 + rho * lap if k == i else 0) - gr[k] * gr[i]) for k in range(2)]
+        je = kap * gT[i] - gK * rho * gr[i] * divu
+        Fc = [rho * vel[i]] + [rho * vel[k] * vel[i] + (p if k == i else 0) for k in range(2)] + [(E + p) * vel[i]]
+        Fv = [0] + tau + [tau[0] * vel[0] + tau[1] * vel[1] + je]
+        F.append([fc - fv for fc, fv in zip(Fc, Fv)])
+    Q = [sp.diff(U[v], t) + sp.diff(F[0][v], x) + sp.diff(F[1][v], y) for v in range(4)]
+    return (x, y, t), U + [rho], Q + [sp.Integer(0)]
+
+
 def system_2d(prm):
     """Return (U, Q) expressions of the 2D manufactured solution for parameters prm."""
+    if prm["model"] == 0:
+        return system_2d_nsk(prm)
     x, y, t = sp.symbols("x y t", real=True)
     X = [x, y]
     gK, mu, kap, cv, al, be = (sp.Float(prm[k]) for k in ("gammaK", "mu", "kappa", "cv", "alpha", "beta"))
