@@ -66,7 +66,11 @@ typedef struct dgk_ctx dgk_ctx;
 /* Physical and numerical parameters.  Defaults of the paper (Sec. 4, table
    "fluidproperties"): gammaK 1e-4, mu 0.01, kappa 1/150, cv 5; alpha = beta = 100. */
 typedef struct {
-    int model;       /* 1: relaxation model 1 (Eq. navierstokeskorteweg_p); 2: model 2 (.._palpha) */
+    int model;       /* 1: relaxation model 1 (Eq. navierstokeskorteweg_p); 2: model 2 (.._palpha);
+                        0: the original NSK model (Eq. navierstokeskorteweg, Korteweg stress
+                        Eq. cauchystressnsk, energy flux Eq. energyfluxnsk; periodic boxes only).
+                        Model 0 keeps the state layout of the relaxation models: the c slot holds
+                        rho (set by dgk_set_primitive, kept equal by the kernels) */
     int rk;          /* 3: three-stage LSRK3, 4: five-stage LSRK4 (the paper's default, Sec. 3.1) */
     int precision;   /* DGK_PREC_FP64 or DGK_PREC_FP32BULK */
     double gammaK;   /* capillarity coefficient gamma_K > 0 (Eq. non-dimensionals) */

@@ -62,7 +62,8 @@ void rk_table(int rk, int &ns, double *A, double *B)
 }
 
 // primitive (rho, u, T, c) -> partial conserved state; T kept in Tbuf for the energy kernel
-__global__ void k_prim_partial(const double *prim, double *U, double *Tbuf, long long nn, int D)
+// (original NSK model: the c slot holds rho)
+__global__ void k_prim_partial(const double *prim, double *U, double *Tbuf, long long nn, int D, int model)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nn) return;
@@ -70,7 +71,7 @@ __global__ void k_prim_partial(const double *prim, double *U, double *Tbuf, long
     U[i] = rho;
     for (int k = 0; k < D; ++k) U[(1 + k) * nn + i] = rho * prim[(1 + k) * nn + i];
     U[(D + 1) * nn + i] = 0.0;
-    U[(D + 2) * nn + i] = prim[(D + 2) * nn + i];
+    U[(D + 2) * nn + i] = model == 0 ? rho : prim[(D + 2) * nn + i];
     Tbuf[i] = prim[(D + 1) * nn + i];
 }
 
@@ -93,11 +94,11 @@ __global__ void k_dt_reduce(const double *U, const double *T, long long ne, Node
     if (i < nn) {
         const double rho = U[i], t = T[i];
         double omb = 1.0 - dgk::kBvdw * rho;
-        double s2 = dgk::kRgas * t * (1.0 + 1.0 / ph.cv) / (omb * omb) - 2.0 * dgk::kAvdw * rho + ph.alpha * rho;
-        double s = s2 > 0.0 ? sqrt(s2) : 0.0;
+        double s2 = dgk::kRgas * t * (1.0 + 1.0 / ph.cv) / (omb * omb) - 2.0 * dgk::kAvdw * rho;
+        double s = ph.model == 0 ? sqrt(fabs(s2)) : (s2 + ph.alpha * rho > 0.0 ? sqrt(s2 + ph.alpha * rho) : 0.0);
         for (int k = 0; k < ni.D; ++k) lam += (fabs(U[(1 + k) * nn + i] / rho) + s) / ni.h[k];
         nu = fmax(4.0 * ph.mu / (3.0 * rho), ph.kap / (rho * dgk::kRgas * ph.cv));
-        nu = fmax(nu, ph.gK * ph.beta);
+        if (ph.model != 0) nu = fmax(nu, ph.gK * ph.beta);
         if (!isfinite(lam)) lam = INFINITY;
     }
     sl[threadIdx.x] = lam;
@@ -508,10 +509,19 @@ void dgk_destroy(dgk_ctx *c)
     delete c;
 }
 
+static bool has_walls(const dgk_box_mesh &m)
+{
+    for (int d = 0; d < m.dim; ++d)
+        if (!m.periodic[d]) return true;
+    return false;
+}
+
 int dgk_set_params(dgk_ctx *c, const dgk_params *p)
 {
     if (!c || !p) return fail(DGK_ERR_ARG, "null argument");
-    if (p->model != 1 && p->model != 2) return fail(DGK_ERR_UNSUPPORTED, "model must be 1 or 2");
+    if (p->model < 0 || p->model > 2) return fail(DGK_ERR_UNSUPPORTED, "model must be 0, 1 or 2");
+    if (p->model == 0 && c->have_mesh && has_walls(c->mesh))
+        return fail(DGK_ERR_UNSUPPORTED, "the original NSK model runs on periodic boxes");
     if (p->rk != 3 && p->rk != 4) return fail(DGK_ERR_ARG, "rk must be 3 or 4");
     if (p->precision != DGK_PREC_FP64 && p->precision != DGK_PREC_FP32BULK) return fail(DGK_ERR_ARG, "bad precision");
     if (!(p->gammaK > 0) || !(p->mu >= 0) || !(p->kappa >= 0) || !(p->cv > 0) || !(p->alpha >= 0) || !(p->beta >= 0))
@@ -549,6 +559,7 @@ int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m)
             }
         }
     }
+    if (c->prm.model == 0 && has_walls(*m)) return fail(DGK_ERR_UNSUPPORTED, "the original NSK model runs on periodic boxes");
     DGK_CUDA(cudaSetDevice(c->device));
     cudaStreamSynchronize(c->stream);
     free_buffers(c);
@@ -643,7 +654,7 @@ int dgk_set_primitive(dgk_ctx *c, const double *prim, size_t count, int on_devic
     rc = copy_in(c, c->G, prim, count, on_device);
     if (rc) return rc;
     const long long nn = c->ne * c->NP;
-    k_prim_partial<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->G, c->U, c->Tbuf, nn, c->D);
+    k_prim_partial<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->G, c->U, c->Tbuf, nn, c->D, c->prm.model);
     DGK_CUDA(cudaGetLastError());
     cudaError_t err = c->kt->traces(c->args(), c->stream);
     if (err != cudaSuccess) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
@@ -776,7 +787,7 @@ int dgk_max_dt(dgk_ctx *c, double cfl, double dfl, double *dt)
     const double k1 = 2.0 * c->N + 1.0;
     double r = cfl / (k1 * lam);
     if (nu > 0) r = std::fmin(r, dfl / (k1 * k1 * nu * ih2));
-    if (c->prm.alpha * c->prm.beta > 0) r = std::fmin(r, 2.0 / (c->prm.alpha * c->prm.beta));
+    if (c->prm.model != 0 && c->prm.alpha * c->prm.beta > 0) r = std::fmin(r, 2.0 / (c->prm.alpha * c->prm.beta));
     if (!std::isfinite(r) || !(r > 0)) return fail(DGK_ERR_NONFINITE, "non-finite time step (state invalid)");
     *dt = r;
     return DGK_OK;

@@ -235,9 +235,11 @@ __device__ __forceinline__ R flux_pressure(const PhysR<R> &pr, R rho, R T, R iom
 
 // Signal speed sqrt(c_s^2 + alpha rho) with the vdW isentropic
 // c_s^2 = R T (1 + 1/cv)/(1 - b rho)^2 - 2 a rho (Eq. speedofsound, Sec. 2.3).
+// Original NSK (model 0): sqrt(|c_s^2|).
 template <typename R>
 __device__ __forceinline__ R signal_speed(const PhysR<R> &pr, R rho, R T, R iomb)
 {
+    if (pr.model == 0) return sqrt(fabs(pr.s_coef * T * iomb * iomb - R(2.0 * kAvdw) * rho));
     R s2 = pr.s_coef * T * iomb * iomb + (pr.alpha - R(2.0 * kAvdw)) * rho;
     return s2 > R(0) ? sqrt(s2) : R(0);
 }
@@ -271,6 +273,27 @@ __device__ __forceinline__ void flux_dir(const PhysR<R> &ph, int dir, R rho, con
         F[1 + k] = m[k] * ud - tau;
         if (k == dir) F[1 + k] += ph_;
     }
+    if (ph.model == 0) {
+        // original NSK (Eq. navierstokeskorteweg): Korteweg stress gamma_K [(|grad rho|^2/2
+        // + rho lap rho) I - grad rho (x) grad rho] (Eq. cauchystressnsk) and energy flux
+        // kappa grad T - gamma_K rho grad rho div u (Eq. energyfluxnsk).  The c slot holds
+        // rho: gc = grad rho, lap = lap rho; its flux is the mass flux, so c stays rho.
+        R gr2 = R(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) gr2 += gc[k] * gc[k];
+        R kwork = R(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            R tk = -ph.gK * gc[k] * gc[dir];
+            if (k == dir) tk += ph.gK * (R(0.5) * gr2 + rho * lap);
+            F[1 + k] -= tk;
+            kwork += tk * u[k];
+        }
+        const R je = ph.kap * gT[dir] - ph.gK * rho * gc[dir] * divu;
+        F[D + 1] = (E + ph_) * ud - (work + kwork + je);
+        F[D + 2] = F[0];
+        return;
+    }
     R zeta = ph.beta * (ph.gK * lap + ph.alpha * (rho - c));
     R je = ph.kap * gT[dir] - ph.gK * c * gc[dir] * divu + ph.gK * gc[dir] * zeta;
     F[D + 1] = (E + ph_) * ud - (work + je);
@@ -283,6 +306,11 @@ __device__ __forceinline__ void flux_dir(const PhysR<R> &ph, int dir, R rho, con
 template <int D, typename R>
 __device__ __forceinline__ void source_terms(const PhysR<R> &ph, R rho, const R *u, R c, const R g[D][D + 2], R *S)
 {
+    if (ph.model == 0) {  // the original NSK system has no source
+#pragma unroll
+        for (int v = 0; v < D + 3; ++v) S[v] = R(0);
+        return;
+    }
     const R al = ph.alpha;
     R divu = R(0), gc2 = R(0), ccdu = R(0), work = R(0);
 #pragma unroll
@@ -304,61 +332,6 @@ __device__ __forceinline__ void source_terms(const PhysR<R> &ph, R rho, const R 
     R pw = ph.model == 1 ? R(0.5) * al * (c * c - rho * rho) : R(0.5) * al * c * c;
     S[D + 1] = work + pw * divu + ph.gK * (R(0.5) * gc2 * divu - ccdu);
     S[D + 2] = ph.alphabeta * (rho - c);
-}
-
-// Numerical flux in +e_dir through a wall face whose outward normal is nsign*e_dir
-// (Sec. 2.4, Eq. bc_nsk_alpha, gamma_1 = gamma_2 = gamma_4 = 0): Rusanov flux against
-// the mirrored ghost (rho, m - 2(m.n)n, rho e, c) with equal pressure and signal speed,
-// minus the wall viscous flux (tau(grad u).n, kappa grad T.n - gamma_K c gn div u,
-// gamma_K beta gn) with gn = grad c . n from the contact angle; u_wall = 0, zeta = 0.
-template <int D, typename R>
-__device__ __forceinline__ void wall_flux(const PhysR<R> &ph, int dir, R nsign, R rho, R irho, const R *m, R E, R c,
-                                          R ph_, R lam, const R du[D][D], const R *gT, R gn, R *F)
-{
-    R u[D], mg[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) { u[k] = m[k] * irho; mg[k] = m[k]; }
-    mg[dir] = -m[dir];
-    // convective fluxes of the interior and the ghost state in +e_dir
-    R Fi[D + 3], Fg[D + 3];
-    R ui = u[dir], ug = -u[dir];
-    Fi[0] = m[dir];
-    Fg[0] = mg[dir];
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        Fi[1 + k] = m[k] * ui + (k == dir ? ph_ : R(0));
-        Fg[1 + k] = mg[k] * ug + (k == dir ? ph_ : R(0));
-    }
-    Fi[D + 1] = (E + ph_) * ui;
-    Fg[D + 1] = (E + ph_) * ug;
-    Fi[D + 2] = c * ui;
-    Fg[D + 2] = c * ug;
-    R Ui[D + 3], Ug[D + 3];
-    Ui[0] = Ug[0] = rho;
-#pragma unroll
-    for (int k = 0; k < D; ++k) { Ui[1 + k] = m[k]; Ug[1 + k] = mg[k]; }
-    Ui[D + 1] = Ug[D + 1] = E;
-    Ui[D + 2] = Ug[D + 2] = c;
-    const bool plus = nsign > R(0);
-#pragma unroll
-    for (int v = 0; v < D + 3; ++v) {
-        R FL = plus ? Fi[v] : Fg[v], FR = plus ? Fg[v] : Fi[v];
-        R UL = plus ? Ui[v] : Ug[v], UR = plus ? Ug[v] : Ui[v];
-        F[v] = R(0.5) * (FL + FR) - R(0.5) * lam * (UR - UL);
-    }
-    // viscous normal flux (outward), subtracted as nsign * Fv in +e_dir
-    R divu = R(0);
-#pragma unroll
-    for (int k = 0; k < D; ++k) divu += du[k][k];
-    const R mu = ph.mu;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        R tau = mu * (du[dir][k] + du[k][dir]);
-        if (k == dir) tau -= ph.two_thirds_mu * divu;
-        F[1 + k] -= tau;  // nsign * (tau * nsign)
-    }
-    F[D + 1] -= ph.kap * gT[dir] - nsign * ph.gK * c * gn * divu;
-    F[D + 2] -= nsign * ph.gKbeta * gn;
 }
 
 }  // namespace dgk

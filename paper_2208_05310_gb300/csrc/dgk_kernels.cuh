@@ -530,6 +530,26 @@ __device__ __forceinline__ void face_flux(const Ctx<R> &a, int f, int dir, bool 
         tau[k] = ph.mu * (ddu[k] + dud) - (k == dir ? ph.two_thirds_mu * divu : R(0));
     }
     const R gTd = r[FR::GT], gcd = pick<D, R>(dir, gc), lap = r[FR::LAP];
+    if (!wall && ph.model == 0) {
+        // original NSK: viscous plus Korteweg stress, NSK energy flux; the c slot (= rho)
+        // carries the mass flux (see flux_dir)
+        R gr2 = R(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) gr2 += gc[k] * gc[k];
+        R work = R(0);
+        F[0] = mn;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            R tk = tau[k] - ph.gK * gc[k] * gcd;
+            if (k == dir) tk += ph.gK * (R(0.5) * gr2 + rho * lap);
+            work += tk * u[k];
+            F[1 + k] = m[k] * un - tk + (k == dir ? pf : R(0));
+        }
+        const R je = ph.kap * gTd - ph.gK * rho * gcd * divu;
+        F[D + 1] = (E + pf) * un - (work + je);
+        F[D + 2] = mn;
+        return;
+    }
     if (!wall) {
         R work = R(0);
         F[0] = mn;

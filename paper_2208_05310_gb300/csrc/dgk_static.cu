@@ -153,7 +153,9 @@ void place(dgk::KArgs<R> &a, unsigned char *base, const double *U, double *Ut, i
 extern "C" int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *m, const double *U, double *Ut, void *cuda_stream)
 {
     if (!p || !m || !U || !Ut) return fail_static(DGK_ERR_ARG, "null argument");
-    if (p->model != 1 && p->model != 2) return fail_static(DGK_ERR_UNSUPPORTED, "model must be 1 or 2");
+    if (p->model < 0 || p->model > 2) return fail_static(DGK_ERR_UNSUPPORTED, "model must be 0, 1 or 2");
+    for (int d = 0; d < m->dim && p->model == 0; ++d)
+        if (!m->periodic[d]) return fail_static(DGK_ERR_UNSUPPORTED, "the original NSK model runs on periodic boxes");
     if (p->precision != DGK_PREC_FP64 && p->precision != DGK_PREC_FP32BULK) return fail_static(DGK_ERR_ARG, "bad precision");
     if (p->flux != DGK_FLUX_RUSANOV && p->flux != DGK_FLUX_HLLC) return fail_static(DGK_ERR_ARG, "bad flux");
     if (p->flux == DGK_FLUX_HLLC && p->model != 2) return fail_static(DGK_ERR_UNSUPPORTED, "the HLLC flux is for model 2");

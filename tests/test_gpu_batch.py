@@ -16,6 +16,13 @@ from cases import PAPER_PARAMS, oracle_objects, rel_l2
 pytestmark = pytest.mark.gpu
 
 
+# batch kernels against single-problem kernels (and the two batch forms): the same
+# arithmetic in separate kernels, whose compiled floating-point contraction may differ;
+# FP32 rounding of U_t seen through dt in the FP64 state (momentum normalised by its own
+# small norm)
+SAME_FORM_TOL = np.array([1e-9, 1e-6, 1e-6, 1e-9, 1e-9])
+
+
 def tol32_step():
     return np.array([1e-7, 3e-5, 3e-5, 2e-7, 5e-7])  # rho, rho u, rho v, E, c (after 10 steps)
 
@@ -98,7 +105,7 @@ def test_batch_matches_single_contexts():
     for q, ms, prim, dt in zip(b.problems, meshes, prims, dts):
         ref = _single(ms, prim, dt, 5)
         err = rel_l2(q.download_state(), ref)
-        assert np.all(err < 1e-9), (ms["N"], ms["n"], err)
+        assert np.all(err < SAME_FORM_TOL), (ms["N"], ms["n"], err)
     b.close()
 
 
@@ -128,7 +135,7 @@ def test_batch_decomposition_independence_and_autotune():
     # across the forms (separate kernels, whose compiled floating-point contraction may
     # differ): to the FP32 rounding of U_t, seen through dt in the FP64 state
     for a, c in zip(out["persistent"][0], out["grouped"][0]):
-        assert np.all(rel_l2(c, a) < 1e-9)
+        assert np.all(rel_l2(c, a) < SAME_FORM_TOL)
     for q, prim in zip(b.problems, prims):
         q.set_primitive(prim)
     tuned = b.autotune()
@@ -158,7 +165,7 @@ def test_batch_full_ensemble_sampled():
     for k in sorted({0, 255, int(np.argmax(sizes)), int(np.argmin(sizes))}):
         ref = _single(meshes[k], prims[k], dts[k], 20)
         err = rel_l2(b.problems[k].download_state(), ref)
-        assert np.all(err < 1e-9), (k, meshes[k]["N"], meshes[k]["n"], err)
+        assert np.all(err < SAME_FORM_TOL), (k, meshes[k]["N"], meshes[k]["n"], err)
     b.close()
 
 
