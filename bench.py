@@ -123,6 +123,22 @@ def ncu_traffic(kernel, workload):
         return None
 
 
+def replica_max(v, dist=None, device="cuda"):
+    """Max of a per-rank time over all ranks (replicas run independent problems; the
+    slowest rank sets the whole job's time).  dist: torch.distributed or None."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank, world, ms_max):
+    """Whole-job rate: the units all ranks processed over the max-over-ranks time."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -297,11 +313,7 @@ def run_ours(args, wl, rank, world, local_rank):
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(v, dist)
 
     ctx = make_ctx(args.precision)
     dof = ctx.nelem * ctx.np
@@ -323,7 +335,7 @@ def run_ours(args, wl, rank, world, local_rank):
     ms = e0.elapsed_time(e1)
     ctx.status()
     ms_max = max_over_ranks(ms)
-    value = dof * stages * args.steps * world / (ms_max / 1e3)
+    value = replica_rate(dof * stages * args.steps, world, ms_max)
 
     # --- pass B: the same steps kernel by kernel with per-kernel CUDA events
     ctx.set_timing(True)
@@ -516,17 +528,13 @@ def run_batch(args, wl, rank, world, local_rank):
         dist.barrier()
     with ClockSampler(local_rank) as clk:
         r = batch_measure(wl, local_rank, args.steps, args.warmup, unbatched=not args.no_fp64, e2e=not args.no_e2e)
-    ms = r["ms_per_step"] * args.steps
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replica_max(r["ms_per_step"] * args.steps, dist)
     stages = 5 if wl["rk"] == 4 else 3
     if rank == 0:
         e2e = r.pop("e2e", None)
         if e2e is not None:
             e2e = dict(e2e, value=e2e["value"] * world)
-        line = dict(metric=METRIC, value=r["nodes"] * stages * args.steps * world / (ms / 1e3), unit=UNIT,
+        line = dict(metric=METRIC, value=replica_rate(r["nodes"] * stages * args.steps, world, ms), unit=UNIT,
                     n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms / args.steps,
                     higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32/f64", data="synthetic",
                     config=dict(workload=wl["name"], dof=r["nodes"], problems=r["problems"], stages_per_step=stages,
