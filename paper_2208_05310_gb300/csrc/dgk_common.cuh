@@ -120,31 +120,6 @@ __device__ __forceinline__ int line_stride(int d)
     return d == 0 ? 1 : (d == 1 ? P : P * P);
 }
 
-// neighbours of element e across its 2D faces (f = 2*dir + side); -1 at a wall
-template <int D>
-__device__ __forceinline__ void neighbours(const Geom &g, long long e, long long nb[6])
-{
-    const unsigned ue = (unsigned)e, n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
-    int c[3];
-    c[0] = (int)(ue % n0);
-    c[1] = (int)((ue / n0) % n1);
-    c[2] = D == 3 ? (int)(ue / (n0 * n1)) : 0;
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            int cc[3] = {c[0], c[1], c[2]};
-            cc[d] += s ? 1 : -1;
-            long long r;
-            if (cc[d] < 0 || cc[d] >= g.n[d]) {
-                if (!g.periodic[d]) { nb[2 * d + s] = -1; continue; }
-                cc[d] = (cc[d] + g.n[d]) % g.n[d];
-            }
-            r = cc[0] + (long long)g.n[0] * (cc[1] + (long long)g.n[1] * cc[2]);
-            nb[2 * d + s] = r;
-        }
-    }
-}
 
 // ------------------------------------------------------------------ conversions
 //
@@ -197,11 +172,6 @@ __device__ __forceinline__ double to_f64(R x)
     else return f2d(x);
 }
 
-// finiteness of a double from its exponent field (no FP64 instruction)
-__device__ __forceinline__ bool finite_bits(double x)
-{
-    return ((((unsigned long long)__double_as_longlong(x)) >> 52) & 0x7ffull) != 0x7ffull;
-}
 
 // ------------------------------------------------------------------ thermodynamics
 
