@@ -361,7 +361,9 @@ def run_ours(args, wl, rank, world, local_rank):
                     avg_launch_ms=avg_ms,
                     share={k: ktimes[k][0] / total_k for k in ktimes},
                     step_bytes_alg=(8 * (m["dim"] + 3) * 4) * dof * stages,
-                    step_frac_alg=(8 * (m["dim"] + 3) * 4) * dof * stages / (ms / args.steps / 1e3) / 1e9 / peak)
+                    step_frac_alg=(8 * (m["dim"] + 3) * 4) * dof * stages / (ms / args.steps / 1e3) / 1e9 / peak,
+                    step_bytes_dataflow=sum(kb.values()) * dof * stages,
+                    step_frac_dataflow=sum(kb.values()) * dof * stages / (ms / args.steps / 1e3) / 1e9 / peak)
     del ctx
     torch.cuda.synchronize()
 
