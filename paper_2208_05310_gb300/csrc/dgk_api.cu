@@ -319,6 +319,8 @@ int build_consts(dgk_ctx *c)
         g.periodic[d] = d < c->D ? m.periodic[d] : 1;
         g.inv2h[d] = d < c->D ? 2.0 / ((m.hi[d] - m.lo[d]) / m.n[d]) : 0.0;
     }
+    g.div0.init((unsigned)g.n[0]);
+    g.div1.init((unsigned)g.n[1]);
     const dgk_params &q = c->prm;
     dgk::Phys ph{q.model, q.gammaK, q.mu, q.kappa, q.cv, q.alpha, q.beta,
                  0.5 * q.alpha, 0.5 * q.gammaK, 1.0 / (dgk::kRgas * q.cv)};
@@ -548,6 +550,7 @@ int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m)
     for (int d = 0; d < m->dim; ++d) {
         if (m->n[d] < 1 || !(m->hi[d] > m->lo[d])) return fail(DGK_ERR_ARG, "bad element count or extent");
         ne *= m->n[d];
+        if (ne >= (1LL << 32)) return fail(DGK_ERR_ARG, "more than 2^32 - 1 elements");
         if (!m->periodic[d]) {
             for (int s = 0; s < 2; ++s) {
                 const dgk_wall &w = m->wall[2 * d + s];

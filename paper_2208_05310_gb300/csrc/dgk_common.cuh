@@ -50,11 +50,35 @@ struct Walls {
     double g[6][4];  // kind 2 (generalized Navier slip): gamma_1..gamma_4
 };
 
+// Division of 32-bit unsigned integers by an invariant divisor d >= 1 with a multiply-high
+// and two shifts (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, Sec. 4): l = ceil(log2 d), m = floor(2^32 (2^l - d)/d) + 1,
+// then x / d = (t + ((x - t) >> s1)) >> s2 with t = mulhi(m, x), s1 = min(l, 1),
+// s2 = max(l - 1, 0).  Valid for every 32-bit x and every d < 2^31.
+struct FastDiv {
+    unsigned m;
+    int s1, s2;
+    __host__ void init(unsigned d)
+    {
+        int l = 0;
+        while ((1ull << l) < (unsigned long long)d) ++l;
+        m = (unsigned)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+        s1 = l < 1 ? l : 1;
+        s2 = l > 1 ? l - 1 : 0;
+    }
+    __device__ __forceinline__ unsigned div(unsigned x) const
+    {
+        const unsigned t = __umulhi(m, x);
+        return (t + ((x - t) >> s1)) >> s2;
+    }
+};
+
 struct Geom {
     int n[3];
     int periodic[3];
     double inv2h[3];  // 2 / h_d: d/dx = (2/h) d/dxi on the affine element
     long long ne;
+    FastDiv div0, div1;  // by n[0], by n[1] (element index -> Cartesian coordinates)
 };
 
 template <typename R>

@@ -187,9 +187,10 @@ struct Slot {
         e = blk * S::EPB + le;
         valid = (int)threadIdx.x < S::NT && e < g.ne;
         const unsigned ue = valid ? (unsigned)e : 0u, n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
-        cx = (int)(ue % n0);
-        cy = (int)((ue / n0) % n1);
-        cz = D == 3 ? (int)(ue / (n0 * n1)) : 0;
+        const unsigned q0 = g.div0.div(ue), q1 = g.div1.div(q0);
+        cx = (int)(ue - q0 * n0);
+        cy = (int)(q0 - q1 * n1);
+        cz = D == 3 ? (int)q1 : 0;
     }
     // neighbour across face f = 2*dir + side, or -1 at a wall
     __device__ __forceinline__ long long nbr(const Geom &g, int f) const

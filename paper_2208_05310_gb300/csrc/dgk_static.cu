@@ -77,6 +77,8 @@ int fill(dgk::KArgs<R> &a, const dgk_params &q, const dgk_box_mesh &m, const dgk
         a.v.g.inv2h[d] = d < D ? 2.0 / ((m.hi[d] - m.lo[d]) / m.n[d]) : 0.0;
         a.v.gr.inv2h[d] = (R)a.v.g.inv2h[d];
     }
+    a.v.g.div0.init((unsigned)a.v.g.n[0]);
+    a.v.g.div1.init((unsigned)a.v.g.n[1]);
     a.ph = dgk::Phys{q.model, q.gammaK, q.mu, q.kappa, q.cv, q.alpha, q.beta, 0.5 * q.alpha, 0.5 * q.gammaK,
                      1.0 / (dgk::kRgas * q.cv)};
     dgk::PhysR<R> &p = a.pr;
