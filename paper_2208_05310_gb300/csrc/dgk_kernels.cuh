@@ -660,7 +660,9 @@ struct K2Smem {
     static constexpr int X1 = S::NL * S::NP + S::NF * S::NL * S::NFP;  // prims, q*
     static constexpr int X2 = S::NP + 2 * S::NF * S::NFP + D * S::NP;  // T, T*, Dc*, lap parts
     static constexpr int X4 = 2 * S::NV * S::NP;                       // volume: F, acc
-    static constexpr int X3 = X4 + (S::NV + 2) * S::NP;                // nodal U/div/lap after acc
+    static constexpr int SR = S::NF * FaceRec<D>::NQ * S::NFP;         // traced face records
+    static constexpr int XN = X4 > SR ? X4 : SR;                       // nodal U/div/lap (sN) offset
+    static constexpr int X3 = XN + (S::NV + 2) * S::NP;
     static constexpr int XA = X1 > X2 ? X1 : X2;
     static constexpr int X = XA > X3 ? XA : X3;
     static constexpr int per_elem = G + GT + X;
@@ -856,7 +858,7 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
         }
         __syncthreads();
     }
-    R *sN = sX + M::X4;  // nodal U, div u, lap c (clear of sF, sAcc)
+    R *sN = sX + M::XN;  // nodal U, div u, lap c (clear of sF, sAcc and the traced records)
     if (t.valid) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) a.v.Utv[((long long)v * ne + t.e) * NP + n] = S_[v] - sAcc[v * NP + n];
@@ -873,30 +875,44 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
     }
     __syncthreads();
 
-    // ---- face data: one face point per task, its record traced directly from the
-    //      nodal fields (interior: one-sided data; wall: the complete wall flux).  The
-    //      direction is a run-time value (no divergence between the face points of
-    //      different directions in a warp); the line is walked from the face, so that
-    //      both sides use l_j(-1): on nodes symmetric about 0, l_j(+1) = l_{P-1-j}(-1).
+    // ---- face records: one task per line of one direction traces every record quantity
+    //      (FaceRec order) to both ends of the line, into sR[f][k][fp] (the line's values
+    //      are loaded once for the two faces)
+    using FR = FaceRec<D>;
+    constexpr int NQ = FR::NQ;
+    R *sR = sX;  // clear of sN; sF and sAcc are dead
     if (t.valid) {
-        using FR = FaceRec<D>;
-        constexpr int NQ = FR::NQ;
-        const long long st = ne * NF * NFP;
-        for (int q = n; q < NF * NFP; q += NP) {
-            const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
-            const bool wall = t.nbr(a.v.g, f) < 0;
-            const int stride = line_stride<P>(dir);
-            const int first = line_base<P>(fp, dir) + (side ? (P - 1) * stride : 0);
-            const int step = side ? -stride : stride;
-            R r[NQ];
+        for (int q = n; q < D * NFP; q += NP) {
+            const int dir = q / NFP, line = q % NFP;
+            const int base = line_base<P>(line, dir), stride = line_stride<P>(dir);
 #pragma unroll
             for (int k = 0; k < NQ; ++k) {
                 const R *src = face_source<D, N, R, EB>(k, dir, sG, sGT, sN);
-                R acc = R(0);
+                R am = R(0), ap = R(0);
 #pragma unroll
-                for (int l = 0; l < P; ++l) acc += a.op.lm[l] * src[first + l * step];
-                r[k] = acc;
+                for (int l = 0; l < P; ++l) {
+                    const R x = src[base + l * stride];
+                    am += a.op.lm[l] * x;
+                    ap += a.op.lp[l] * x;
+                }
+                sR[((2 * dir) * NQ + k) * NFP + line] = am;
+                sR[((2 * dir + 1) * NQ + k) * NFP + line] = ap;
             }
+        }
+    }
+    __syncthreads();
+
+    // ---- face data: one face point per task (interior: one-sided data; wall: the
+    //      complete wall flux).  The direction is a run-time value: all face points of
+    //      an element share one instruction stream.
+    if (t.valid) {
+        const long long st = ne * NF * NFP;
+        for (int q = n; q < NF * NFP; q += NP) {
+            const int f = q / NFP, fp = q % NFP, dir = f >> 1;
+            const bool wall = t.nbr(a.v.g, f) < 0;
+            R r[NQ];
+#pragma unroll
+            for (int k = 0; k < NQ; ++k) r[k] = sR[(f * NQ + k) * NFP + fp];
             R F[NV], lam, pf, sig;
             face_flux<D, R>(a, f, dir, wall, r, F, lam, pf, sig);
             const long long fo = (t.e * NF + f) * NFP + fp;
