@@ -395,6 +395,11 @@ def run_ours(args, wl, rank, world, local_rank):
     batched = None
     if not args.no_batch:
         batched = batch_measure(WORKLOADS["c4"](), local_rank, max(3, args.steps // 2), 3, unbatched=True)
+        if world > 1:  # one ensemble per rank: whole-job rate over the slowest rank
+            bms = replica_max(batched["ms_per_step"] * batched["steps"], dist)
+            stg = 5 if WORKLOADS["c4"]()["rk"] == 4 else 3
+            batched = dict(batched, value=replica_rate(batched["nodes"] * stg * batched["steps"], world, bms),
+                           ms_per_step=bms / batched["steps"], scope=f"{world} replicas")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
