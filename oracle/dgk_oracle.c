@@ -39,6 +39,7 @@ static const double AV = 3.0;
 static const double BV = 1.0 / 3.0;
 
 #define MAXP 10
+#define MAXG 9 /* geometry points per direction of a curved element */
 
 /* ======================================================================== */
 /* Thermodynamics, Sec. 2.1                                                 */
@@ -290,8 +291,18 @@ typedef struct {
     double wall_T[6], wall_rv[6], wall_rl[6], wall_sigma[6], wall_theta[6];
     double wall_g[6][4]; /* kind 2: gamma_1..gamma_4 */
     double xi[MAXP], w[MAXP], Dhat[MAXP * MAXP], lm[MAXP], lp[MAXP];
+    double Dm[MAXP * MAXP]; /* D_il = l_l'(xi_i) */
     or_params prm;
+    /* curved elements (Sec. 3.1: curvilinear hexahedra with metric terms) */
+    int curved, ngeo;
+    const double *xgeo; /* [d][e][(ngeo+1)^d], the caller's */
+    double *Ja;         /* [e][n][dir][k]: J a^dir_k (contravariant basis times J) at the nodes */
+    double *Jn;         /* [e][n]: Jacobian J at the nodes */
+    double *Jf;         /* [e][f][fp][k]: J a^dir_k at the face points, f = 2 dir + side */
+    double *xn;         /* [e][n][k]: node coordinates */
 } ctx_t;
+
+static int setup_curved(ctx_t *c);
 
 static int ipow(int a, int b) { int r = 1; while (b-- > 0) r *= a; return r; }
 
@@ -338,14 +349,31 @@ static int setup(const or_mesh *m, const or_params *p, ctx_t *c)
         }
     }
     or_gauss_legendre(c->P, c->xi, c->w);
-    double D[MAXP * MAXP];
+    double *D = c->Dm;
     or_dmatrix(c->N, c->xi, D);
     for (int i = 0; i < c->P; ++i)
         for (int j = 0; j < c->P; ++j)
             c->Dhat[i * c->P + j] = -(c->w[j] / c->w[i]) * D[j * c->P + i];
     or_lagrange_at(c->N, c->xi, -1.0, c->lm);
     or_lagrange_at(c->N, c->xi, 1.0, c->lp);
+    if (m->xgeo) {
+        c->ngeo = m->ngeo;
+        c->xgeo = m->xgeo;
+        if (m->ngeo < 1 || m->ngeo > MAXG - 1) return -1;
+        if (c->d == 2 ? m->ngeo > c->N : 2 * m->ngeo > c->N) return -1;
+        if (p->flux != 0) return -1;
+        for (int f = 0; f < 2 * c->d; ++f)
+            if (c->wall_kind[f] == 2) return -1;
+        c->curved = 1;
+        return setup_curved(c);
+    }
     return 0;
+}
+
+static void teardown(ctx_t *c)
+{
+    free(c->Ja); free(c->Jn); free(c->Jf); free(c->xn);
+    c->Ja = c->Jn = c->Jf = c->xn = NULL;
 }
 
 /* coordinate of node n along direction d */
@@ -392,6 +420,139 @@ static long neighbour(const ctx_t *c, long e, int d, int s)
     }
     return co[0] + c->n[0] * (co[1] + (long)c->n[1] * co[2]);
 }
+
+/* ======================================================================== */
+/* Curved elements: geometry and metric terms (Sec. 3.1)                     */
+/* ======================================================================== */
+
+/* Derivative of the Lagrange basis of the points t_0..t_n at x:
+   l_j'(x) = sum_{m != j} 1/(t_j - t_m) prod_{k != j, m} (x - t_k)/(t_j - t_k). */
+static void lagrange_deriv_at(int n, const double *t, double x, double *dl)
+{
+    for (int j = 0; j <= n; ++j) {
+        double s = 0.0;
+        for (int m = 0; m <= n; ++m) {
+            if (m == j) continue;
+            double prod = 1.0 / (t[j] - t[m]);
+            for (int k = 0; k <= n; ++k)
+                if (k != j && k != m) prod *= (x - t[k]) / (t[j] - t[k]);
+            s += prod;
+        }
+        dl[j] = s;
+    }
+}
+
+/* Position X and derivatives dX[j][k] = d X_k / d xi_j of element e's map at the
+   reference point xi (interpolation of the caller's equispaced geometry points). */
+static void geo_eval(const ctx_t *c, long e, const double *xi, double *X, double dX[3][3])
+{
+    int G = c->ngeo + 1, d = c->d, ng = ipow(G, d);
+    double t[MAXG], l[3][MAXG], dl[3][MAXG];
+    for (int a = 0; a < G; ++a) t[a] = -1.0 + 2.0 * a / c->ngeo;
+    for (int j = 0; j < d; ++j) {
+        or_lagrange_at(c->ngeo, t, xi[j], l[j]);
+        lagrange_deriv_at(c->ngeo, t, xi[j], dl[j]);
+    }
+    for (int k = 0; k < 3; ++k) {
+        X[k] = 0.0;
+        for (int j = 0; j < 3; ++j) dX[j][k] = 0.0;
+    }
+    for (int g = 0; g < ng; ++g) {
+        int a[3] = {g % G, (g / G) % G, g / (G * G)};
+        for (int k = 0; k < d; ++k) {
+            double x = c->xgeo[((size_t)k * c->ne + e) * ng + g];
+            double wv = 1.0;
+            for (int j = 0; j < d; ++j) wv *= l[j][a[j]];
+            X[k] += wv * x;
+            for (int j = 0; j < d; ++j) {
+                double wd = 1.0;
+                for (int jj = 0; jj < d; ++jj) wd *= (jj == j) ? dl[jj][a[jj]] : l[jj][a[jj]];
+                dX[j][k] += wd * x;
+            }
+        }
+    }
+}
+
+/* Metric terms of the map at one point: J a^i = dX/dxi_{i+1} x dX/dxi_{i+2} (cyclic;
+   in 2D J a^1 = (y_eta, -x_eta), J a^2 = (-y_xi, x_xi)), returned in Ja[i][k], and the
+   Jacobian J = dX/dxi_1 . (J a^1).  For a map of degree ngeo these are polynomials of
+   degree <= 2 ngeo (3D) or ngeo (2D) per direction, so with 2 ngeo <= N (ngeo <= N) they
+   satisfy the discrete metric identities sum_i D (J a^i) = 0 exactly. */
+static double cofactor(int d, double dX[3][3], double Ja[3][3])
+{
+    if (d == 2) {
+        Ja[0][0] = dX[1][1];
+        Ja[0][1] = -dX[1][0];
+        Ja[1][0] = -dX[0][1];
+        Ja[1][1] = dX[0][0];
+        return dX[0][0] * dX[1][1] - dX[1][0] * dX[0][1];
+    }
+    for (int i = 0; i < 3; ++i) {
+        const double *a = dX[(i + 1) % 3], *b = dX[(i + 2) % 3];
+        Ja[i][0] = a[1] * b[2] - a[2] * b[1];
+        Ja[i][1] = a[2] * b[0] - a[0] * b[2];
+        Ja[i][2] = a[0] * b[1] - a[1] * b[0];
+    }
+    return dX[0][0] * Ja[0][0] + dX[0][1] * Ja[0][1] + dX[0][2] * Ja[0][2];
+}
+
+/* Node coordinates, J a^dir at the nodes and at the face points, J at the nodes.  A face
+   shared by two elements takes the face metric of the element on its minus side (the
+   element whose plus face it is), so that both elements see one normal and one surface
+   element (conservation). */
+static int setup_curved(ctx_t *c)
+{
+    long ne = c->ne;
+    int np = c->np, d = c->d, nf = 2 * d, nfp = c->nfp;
+    c->Ja = (double *)malloc(sizeof(double) * ne * np * 9);
+    c->Jn = (double *)malloc(sizeof(double) * ne * np);
+    c->Jf = (double *)malloc(sizeof(double) * ne * nf * nfp * 3);
+    c->xn = (double *)malloc(sizeof(double) * ne * np * 3);
+    if (!c->Ja || !c->Jn || !c->Jf || !c->xn) { teardown(c); return -2; }
+    int bad = 0;
+    for (long e = 0; e < ne; ++e) {
+        for (int n = 0; n < np; ++n) {
+            double xi[3] = {0, 0, 0}, X[3], dX[3][3], Ja[3][3];
+            for (int k = 0; k < d; ++k) xi[k] = c->xi[ncoord(c, n, k)];
+            geo_eval(c, e, xi, X, dX);
+            double J = cofactor(d, dX, Ja);
+            if (!(J > 0.0)) bad = 1;
+            c->Jn[(size_t)e * np + n] = J;
+            for (int i = 0; i < 3; ++i) {
+                c->xn[((size_t)e * np + n) * 3 + i] = X[i];
+                for (int k = 0; k < 3; ++k) c->Ja[(((size_t)e * np + n) * 3 + i) * 3 + k] = Ja[i][k];
+            }
+        }
+        for (int f = 0; f < nf; ++f) {
+            int dir = f / 2, s = f % 2;
+            if (s == 0 && neighbour(c, e, dir, 0) >= 0) continue;
+            for (int fp = 0; fp < nfp; ++fp) {
+                int n0 = fp_to_node(c, fp, dir, 0);
+                double xi[3] = {0, 0, 0}, X[3], dX[3][3], Ja[3][3];
+                for (int k = 0; k < d; ++k) xi[k] = c->xi[ncoord(c, n0, k)];
+                xi[dir] = s ? 1.0 : -1.0;
+                geo_eval(c, e, xi, X, dX);
+                cofactor(d, dX, Ja);
+                for (int k = 0; k < 3; ++k) c->Jf[(((size_t)e * nf + f) * nfp + fp) * 3 + k] = Ja[dir][k];
+            }
+        }
+    }
+    for (long e = 0; e < ne; ++e)
+        for (int dir = 0; dir < d; ++dir) {
+            long nb = neighbour(c, e, dir, 0);
+            if (nb < 0) continue;
+            for (int fp = 0; fp < nfp; ++fp)
+                for (int k = 0; k < 3; ++k)
+                    c->Jf[(((size_t)e * nf + 2 * dir) * nfp + fp) * 3 + k] =
+                        c->Jf[(((size_t)nb * nf + 2 * dir + 1) * nfp + fp) * 3 + k];
+        }
+    if (bad) { teardown(c); return -3; }
+    return 0;
+}
+
+#define JA(c, e, n, i, k) ((c)->Ja[((((size_t)(e)) * (c)->np + (n)) * 3 + (i)) * 3 + (k)])
+#define JN(c, e, n) ((c)->Jn[((size_t)(e)) * (c)->np + (n)])
+#define JF(c, e, f, fp, k) ((c)->Jf[((((size_t)(e)) * 2 * (c)->d + (f)) * (c)->nfp + (fp)) * 3 + (k)])
 
 /* trace of a nodal field of one element on face (d, s): sum_l l_l(+-1) f_l along lines */
 static void trace_elem(const ctx_t *c, const double *f, int d, int s, double *out)
@@ -873,6 +1034,10 @@ static void work_free(work_t *w)
 
 static void node_coord(const ctx_t *c, long e, int n, double *x)
 {
+    if (c->curved) {
+        for (int d = 0; d < c->d; ++d) x[d] = c->xn[((size_t)e * c->np + n) * 3 + d];
+        return;
+    }
     long co[3];
     co[0] = e % c->n[0];
     co[1] = (e / c->n[0]) % c->n[1];
@@ -1018,6 +1183,321 @@ static int rhs_core(const ctx_t *c, const double *U, double *Ut, double t, or_fo
 }
 
 /* ======================================================================== */
+/* Right-hand side on curved elements (Sec. 3.1 with metric terms)           */
+/* ======================================================================== */
+
+/* BR1 gradient of one nodal field f of element e, strong (chain-rule) form: with
+   D_il = l_l'(xi_i), f- the trace of f on a face and f* its face value,
+     J d f/d x_k = sum_dir [ J a^dir_k (sum_l D_il f_l)
+                             + l_i(+1)/w_i (f*_+ - f-_+) (J a^dir_k)_+
+                             - l_i(-1)/w_i (f*_- - f-_-) (J a^dir_k)_- ],
+   where _+ and _- are the face points of the line through node i along dir.  On an
+   affine element this is the weak form of lift_elem (Gauss collocation sums by parts
+   exactly).  fs[f * nfp + fp] holds f* on face f; out[k * np + n] = d f / d x_k. */
+static void grad_curved(const ctx_t *c, long e, const double *f, const double *fs, double *out)
+{
+    int P = c->P, d = c->d, np = c->np, nfp = c->nfp;
+    for (int n = 0; n < np; ++n) {
+        double acc[3] = {0, 0, 0};
+        for (int dir = 0; dir < d; ++dir) {
+            int i = ncoord(c, n, dir), fp = node_to_fp(c, n, dir);
+            double df = 0.0, tm = 0.0, tp = 0.0;
+            for (int l = 0; l < P; ++l) {
+                double x = f[fp_to_node(c, fp, dir, l)];
+                df += c->Dm[i * P + l] * x;
+                tm += c->lm[l] * x;
+                tp += c->lp[l] * x;
+            }
+            double jp = c->lp[i] / c->w[i] * (fs[(2 * dir + 1) * nfp + fp] - tp);
+            double jm = c->lm[i] / c->w[i] * (fs[(2 * dir) * nfp + fp] - tm);
+            for (int k = 0; k < d; ++k)
+                acc[k] += JA(c, e, n, dir, k) * df + jp * JF(c, e, 2 * dir + 1, fp, k) - jm * JF(c, e, 2 * dir, fp, k);
+        }
+        for (int k = 0; k < d; ++k) out[k * np + n] = acc[k] / JN(c, e, n);
+    }
+}
+
+/* Outward unit normal and surface element of face point fp of face f of element e */
+static double face_normal(const ctx_t *c, long e, int f, int fp, double *nh)
+{
+    double s2 = 0.0;
+    for (int k = 0; k < c->d; ++k) s2 += JF(c, e, f, fp, k) * JF(c, e, f, fp, k);
+    double sa = sqrt(s2), sg = (f % 2) ? 1.0 : -1.0;
+    for (int k = 0; k < 3; ++k) nh[k] = k < c->d ? sg * JF(c, e, f, fp, k) / sa : 0.0;
+    return sa;
+}
+
+/* BR1 pass 1 on curved elements: face values as in lift_pass1 (central; at a no-slip
+   wall rho* = rho-, u* = 0, c* = c-), gradients by grad_curved. */
+static void lift_pass1_c(const ctx_t *c, const double *q, const double *tr, double *grad)
+{
+    long ne = c->ne;
+    int np = c->np, nf = 2 * c->d, nfp = c->nfp, nl = c->nl, d = c->d;
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < ne; ++e) {
+        double fs[6 * MAXP * MAXP], out[3 * MAXP * MAXP * MAXP];
+        for (int v = 0; v < nl; ++v) {
+            for (int f = 0; f < nf; ++f) {
+                int dir = f / 2, s = f % 2, fo = 2 * dir + (1 - s);
+                long nb = neighbour(c, e, dir, s);
+                for (int fp = 0; fp < nfp; ++fp) {
+                    double own = tr[FIDX(v, e, f, fp, ne, nf, nfp)];
+                    if (nb >= 0) fs[f * nfp + fp] = 0.5 * (own + tr[FIDX(v, nb, fo, fp, ne, nf, nfp)]);
+                    else fs[f * nfp + fp] = (v >= 1 && v <= d) ? 0.0 : own;
+                }
+            }
+            grad_curved(c, e, q + IDX(v, e, 0, ne, np), fs, out);
+            for (int k = 0; k < d; ++k)
+                for (int n = 0; n < np; ++n) grad[IDX(k * nl + v, e, n, ne, np)] = out[k * np + n];
+        }
+    }
+}
+
+/* BR1 pass 2 on curved elements: grad T (T* central, T_wall at walls) and
+   lap c = sum_k [BR1 gradient of the lifted d c/d x_k]_k, whose face values are the
+   central means of the interpolated d c/d x_k; at a wall the interpolated gradient with
+   its normal component replaced by the contact-angle value,
+   g* = g- + (g_n - g-.n) n (only g*.n enters the lifting). */
+static void lift_pass2_c(const ctx_t *c, const double *T, const double *grad, const double *trq,
+                         double *gT, double *lap)
+{
+    long ne = c->ne;
+    int np = c->np, nf = 2 * c->d, nfp = c->nfp, nl = c->nl, d = c->d;
+    int vc = (c->prm.model == 0) ? 0 : d + 1;
+    /* traces: trT[e][f][fp], trG[k][e][f][fp] */
+    double *trT = (double *)malloc(sizeof(double) * ne * nf * nfp);
+    double *trG = (double *)malloc(sizeof(double) * d * ne * nf * nfp);
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < ne; ++e)
+        for (int f = 0; f < nf; ++f) {
+            int dir = f / 2, s = f % 2;
+            trace_elem(c, T + (size_t)e * np, dir, s, trT + ((size_t)e * nf + f) * nfp);
+            for (int k = 0; k < d; ++k)
+                trace_elem(c, grad + IDX(k * nl + vc, e, 0, ne, np), dir, s, trG + FIDX(k, e, f, 0, ne, nf, nfp));
+        }
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < ne; ++e) {
+        double Ts[6 * MAXP * MAXP], Gs[3][6 * MAXP * MAXP], out[3 * MAXP * MAXP * MAXP];
+        for (int f = 0; f < nf; ++f) {
+            int dir = f / 2, s = f % 2, fo = 2 * dir + (1 - s);
+            long nb = neighbour(c, e, dir, s);
+            for (int fp = 0; fp < nfp; ++fp) {
+                double tOwn = trT[((size_t)e * nf + f) * nfp + fp];
+                if (nb >= 0) {
+                    Ts[f * nfp + fp] = 0.5 * (tOwn + trT[((size_t)nb * nf + fo) * nfp + fp]);
+                    for (int k = 0; k < d; ++k)
+                        Gs[k][f * nfp + fp] = 0.5 * (trG[FIDX(k, e, f, fp, ne, nf, nfp)] +
+                                                     trG[FIDX(k, nb, fo, fp, ne, nf, nfp)]);
+                } else {
+                    double nh[3], gm[3] = {0, 0, 0}, gmn = 0.0;
+                    face_normal(c, e, f, fp, nh);
+                    for (int k = 0; k < d; ++k) {
+                        gm[k] = trG[FIDX(k, e, f, fp, ne, nf, nfp)];
+                        gmn += gm[k] * nh[k];
+                    }
+                    double gn = wall_gn(c, f, trq[FIDX(vc, e, f, fp, ne, nf, nfp)], 0.0);
+                    Ts[f * nfp + fp] = c->wall_T[f];
+                    for (int k = 0; k < d; ++k) Gs[k][f * nfp + fp] = gm[k] + (gn - gmn) * nh[k];
+                }
+            }
+        }
+        grad_curved(c, e, T + (size_t)e * np, Ts, out);
+        for (int k = 0; k < d; ++k)
+            for (int n = 0; n < np; ++n) gT[IDX(k, e, n, ne, np)] = out[k * np + n];
+        for (int n = 0; n < np; ++n) lap[(size_t)e * np + n] = 0.0;
+        for (int k = 0; k < d; ++k) {
+            grad_curved(c, e, grad + IDX(k * nl + vc, e, 0, ne, np), Gs[k], out);
+            for (int n = 0; n < np; ++n) lap[(size_t)e * np + n] += out[k * np + n];
+        }
+    }
+    free(trT);
+    free(trG);
+}
+
+/* F . a = sum_k a_k F_k of the full flux F = F^C - F^V along the vector a, from the
+   Cartesian point fluxes; lam = |u.a| + s |a| (the Rusanov signal speed along a). */
+static void flux_along(const ctx_t *c, const double *U, const double *g, const double *gT, double lap,
+                       const double *a, double *Fa, double *lam)
+{
+    int d = c->d, nv = c->nv;
+    double F[8], l, un = 0.0, an = 0.0;
+    for (int v = 0; v < nv; ++v) Fa[v] = 0.0;
+    for (int k = 0; k < d; ++k) {
+        point_flux(c, U, g, gT, lap, k, F, &l);
+        for (int v = 0; v < nv; ++v) Fa[v] += a[k] * F[v];
+        un += a[k] * U[1 + k] / U[0];
+        an += a[k] * a[k];
+    }
+    *lam = fabs(un) + sound_speed(c, U[0], temperature(c, U, g)) * sqrt(an);
+}
+
+/* Outward normal flux through a no-slip contact-angle wall with unit outward normal nh,
+   per unit area (wall_flux for a general normal): Rusanov against the ghost
+   (rho, m - 2(m.n)n, rho e, c) with equal pressure and signal speed, minus the viscous
+   flux tau(grad u-).n, kappa grad T-.n - gamma_K c- g_n div u-, gamma_K beta g_n. */
+static void wall_flux_c(const ctx_t *c, int f, const double *U, const double *g, const double *gT,
+                        const double *nh, double *Fn)
+{
+    const or_params *p = &c->prm;
+    int d = c->d, nl = c->nl, nv = c->nv;
+    double T = temperature(c, U, g);
+    double pr = flux_pressure(c, U[0], T);
+    double a = sound_speed(c, U[0], T);
+    double mn = 0.0;
+    for (int k = 0; k < d; ++k) mn += U[1 + k] * nh[k];
+    double lam = fabs(mn / U[0]) + a;
+    double Ug[8], Fi[8], Fg[8], F[8];
+    for (int v = 0; v < nv; ++v) { Ug[v] = U[v]; Fi[v] = Fg[v] = 0.0; }
+    for (int k = 0; k < d; ++k) Ug[1 + k] = U[1 + k] - 2.0 * mn * nh[k];
+    for (int k = 0; k < d; ++k) {
+        conv_flux(c, U, pr, k, F);
+        for (int v = 0; v < nv; ++v) Fi[v] += nh[k] * F[v];
+        conv_flux(c, Ug, pr, k, F);
+        for (int v = 0; v < nv; ++v) Fg[v] += nh[k] * F[v];
+    }
+    double divu = 0.0;
+    for (int k = 0; k < d; ++k) divu += g[k * nl + 1 + k];
+    double cm = U[d + 2];
+    double gn = wall_gn(c, f, cm, divu);
+    double Fv[8];
+    Fv[0] = 0.0;
+    for (int k = 0; k < d; ++k) {
+        double t = 0.0;
+        for (int j = 0; j < d; ++j)
+            t += p->mu * (g[j * nl + 1 + k] + g[k * nl + 1 + j] - (k == j ? 2.0 / 3.0 * divu : 0.0)) * nh[j];
+        Fv[1 + k] = t;
+    }
+    double gTn = 0.0;
+    for (int k = 0; k < d; ++k) gTn += gT[k] * nh[k];
+    Fv[d + 1] = p->kappa * gTn - p->gammaK * cm * gn * divu;
+    Fv[d + 2] = p->gammaK * p->beta * gn;
+    for (int v = 0; v < nv; ++v) Fn[v] = 0.5 * (Fi[v] + Fg[v]) - 0.5 * lam * (Ug[v] - U[v]) - Fv[v];
+}
+
+/* rhs_core on curved elements: the same stages with the metric terms,
+   U_t,i = S_i - (1/J_i) sum_dir [ sum_l Dhat_il (F . J a^dir)_l
+                                   + l_i(+1)/w_i F~*_+ - l_i(-1)/w_i F~*_- ],
+   with F~* the numerical flux along the face metric J a^dir (oriented along +xi_dir):
+   Rusanov F~* = (F_L.Ja + F_R.Ja)/2 - max(lam_L, lam_R)/2 (U_R - U_L), lam = |u.Ja| + s|Ja|
+   (L on the minus side of the face), and at a wall |Ja| times the outward wall flux. */
+static int rhs_core_c(const ctx_t *c, const double *U, double *Ut, double t, or_forcing_fn forcing, void *user)
+{
+    long ne = c->ne;
+    int np = c->np, nf = 2 * c->d, nfp = c->nfp, nl = c->nl, nv = c->nv, d = c->d, P = c->P;
+    work_t w;
+    if (work_alloc(c, &w)) { work_free(&w); return -2; }
+    primitives(c, U, w.q);
+    traces(c, w.q, nl, w.trq);
+    lift_pass1_c(c, w.q, w.trq, w.grad);
+    node_temperature(c, U, w.grad, w.T);
+    lift_pass2_c(c, w.T, w.grad, w.trq, w.gT, w.lap);
+
+    int nq = nv + d * nl + d + 1;
+    double *trall = (double *)malloc(sizeof(double) * (size_t)nq * ne * nf * nfp);
+    if (!trall) { work_free(&w); return -2; }
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < ne; ++e)
+        for (int f = 0; f < nf; ++f) {
+            int dir = f / 2, s = f % 2;
+            for (int v = 0; v < nv; ++v)
+                trace_elem(c, U + IDX(v, e, 0, ne, np), dir, s, trall + FIDX(v, e, f, 0, ne, nf, nfp));
+            for (int k = 0; k < d * nl; ++k)
+                trace_elem(c, w.grad + IDX(k, e, 0, ne, np), dir, s, trall + FIDX(nv + k, e, f, 0, ne, nf, nfp));
+            for (int k = 0; k < d; ++k)
+                trace_elem(c, w.gT + IDX(k, e, 0, ne, np), dir, s, trall + FIDX(nv + d * nl + k, e, f, 0, ne, nf, nfp));
+            trace_elem(c, w.lap + (size_t)e * np, dir, s, trall + FIDX(nv + d * nl + d, e, f, 0, ne, nf, nfp));
+        }
+
+    /* volume integral of the contravariant fluxes and point-wise sources */
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < ne; ++e) {
+        double (*F)[MAXP * MAXP * MAXP][8] = malloc(sizeof(double) * 3 * MAXP * MAXP * MAXP * 8);
+        double Ul[8], g[24], gT[3], S[8];
+        for (int n = 0; n < np; ++n) {
+            for (int v = 0; v < nv; ++v) Ul[v] = U[IDX(v, e, n, ne, np)];
+            gather_grad(c, w.grad, e, n, g);
+            for (int k = 0; k < d; ++k) gT[k] = w.gT[IDX(k, e, n, ne, np)];
+            double lap = w.lap[(size_t)e * np + n];
+            for (int dir = 0; dir < d; ++dir) {
+                double a[3], lam;
+                for (int k = 0; k < 3; ++k) a[k] = JA(c, e, n, dir, k);
+                flux_along(c, Ul, g, gT, lap, a, F[dir][n], &lam);
+            }
+            source(c, Ul, g, S);
+            for (int v = 0; v < nv; ++v) Ut[IDX(v, e, n, ne, np)] = S[v];
+        }
+        for (int n = 0; n < np; ++n)
+            for (int dir = 0; dir < d; ++dir) {
+                int i = ncoord(c, n, dir), fp = node_to_fp(c, n, dir);
+                for (int v = 0; v < nv; ++v) {
+                    double acc = 0.0;
+                    for (int l = 0; l < P; ++l) acc += c->Dhat[i * P + l] * F[dir][fp_to_node(c, fp, dir, l)][v];
+                    Ut[IDX(v, e, n, ne, np)] -= acc / JN(c, e, n);
+                }
+            }
+        free(F);
+    }
+
+    /* surface integral */
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < ne; ++e) {
+        for (int f = 0; f < nf; ++f) {
+            int dir = f / 2, s = f % 2, fo = 2 * dir + (1 - s);
+            long nb = neighbour(c, e, dir, s);
+            for (int fp = 0; fp < nfp; ++fp) {
+                double Uo[8], go[24], gTo[3], lapo, Fstar[8], a[3];
+                for (int k = 0; k < 3; ++k) a[k] = JF(c, e, f, fp, k);
+                for (int v = 0; v < nv; ++v) Uo[v] = trall[FIDX(v, e, f, fp, ne, nf, nfp)];
+                for (int k = 0; k < d * nl; ++k) go[k] = trall[FIDX(nv + k, e, f, fp, ne, nf, nfp)];
+                for (int k = 0; k < d; ++k) gTo[k] = trall[FIDX(nv + d * nl + k, e, f, fp, ne, nf, nfp)];
+                lapo = trall[FIDX(nv + d * nl + d, e, f, fp, ne, nf, nfp)];
+                if (nb >= 0) {
+                    double Un[8], gn[24], gTn[3], lapn;
+                    for (int v = 0; v < nv; ++v) Un[v] = trall[FIDX(v, nb, fo, fp, ne, nf, nfp)];
+                    for (int k = 0; k < d * nl; ++k) gn[k] = trall[FIDX(nv + k, nb, fo, fp, ne, nf, nfp)];
+                    for (int k = 0; k < d; ++k) gTn[k] = trall[FIDX(nv + d * nl + k, nb, fo, fp, ne, nf, nfp)];
+                    lapn = trall[FIDX(nv + d * nl + d, nb, fo, fp, ne, nf, nfp)];
+                    const double *UL = s ? Uo : Un, *UR = s ? Un : Uo;
+                    const double *gL = s ? go : gn, *gR = s ? gn : go;
+                    const double *tL = s ? gTo : gTn, *tR = s ? gTn : gTo;
+                    double lL = s ? lapo : lapn, lR = s ? lapn : lapo;
+                    double FL[8], FR[8], laL, laR;
+                    flux_along(c, UL, gL, tL, lL, a, FL, &laL);
+                    flux_along(c, UR, gR, tR, lR, a, FR, &laR);
+                    double lam = laL > laR ? laL : laR;
+                    for (int v = 0; v < nv; ++v) Fstar[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (UR[v] - UL[v]);
+                } else {
+                    double nh[3], Fn[8];
+                    double sa = face_normal(c, e, f, fp, nh);
+                    wall_flux_c(c, f, Uo, go, gTo, nh, Fn);
+                    double nsign = s ? 1.0 : -1.0;
+                    for (int v = 0; v < nv; ++v) Fstar[v] = nsign * sa * Fn[v];
+                }
+                for (int l = 0; l < P; ++l) {
+                    int n = fp_to_node(c, fp, dir, l);
+                    double coef = s ? c->lp[l] / c->w[l] : -c->lm[l] / c->w[l];
+                    for (int v = 0; v < nv; ++v) Ut[IDX(v, e, n, ne, np)] -= coef * Fstar[v] / JN(c, e, n);
+                }
+            }
+        }
+    }
+
+    if (forcing) {
+#pragma omp parallel for schedule(static)
+        for (long e = 0; e < ne; ++e)
+            for (int n = 0; n < np; ++n) {
+                double x[3] = {0, 0, 0}, q[8];
+                node_coord(c, e, n, x);
+                forcing(d, x, t, q, user);
+                for (int v = 0; v < nv; ++v) Ut[IDX(v, e, n, ne, np)] += q[v];
+            }
+    }
+    free(trall);
+    work_free(&w);
+    return 0;
+}
+
+/* ======================================================================== */
 /* Public entry points                                                       */
 /* ======================================================================== */
 
@@ -1026,12 +1506,13 @@ int or_sizes(const or_mesh *m, const or_params *p, long *nelem, int *np, int *nv
     ctx_t c;
     if (setup(m, p, &c)) return -1;
     *nelem = c.ne; *np = c.np; *nv = c.nv;
+    teardown(&c);
     return 0;
 }
 
 int or_node_coords(const or_mesh *m, double *x)
 {
-    or_params p = {1, 1e-4, 0.01, 1.0 / 150.0, 5.0, 100.0, 100.0};
+    or_params p = {1, 1e-4, 0.01, 1.0 / 150.0, 5.0, 100.0, 100.0, 0};
     or_mesh mm = *m;
     for (int f = 0; f < 6; ++f) if (mm.wall_kind[f] != 0) mm.wall_T[f] = 0.85;
     ctx_t c;
@@ -1042,6 +1523,7 @@ int or_node_coords(const or_mesh *m, double *x)
             node_coord(&c, e, n, xx);
             for (int d = 0; d < c.d; ++d) x[IDX(d, e, n, c.ne, c.np)] = xx[d];
         }
+    teardown(&c);
     return 0;
 }
 
@@ -1063,10 +1545,11 @@ int or_set_primitive(const or_mesh *m, const or_params *p, const double *prim, d
             if (p->model != 0) U[IDX(d + 2, e, n, ne, np)] = prim[IDX(d + 2, e, n, ne, np)];
         }
     work_t w;
-    if (work_alloc(&c, &w)) { work_free(&w); return -2; }
+    if (work_alloc(&c, &w)) { work_free(&w); teardown(&c); return -2; }
     primitives(&c, U, w.q);
     traces(&c, w.q, c.nl, w.trq);
-    lift_pass1(&c, w.q, w.trq, w.grad);
+    if (c.curved) lift_pass1_c(&c, w.q, w.trq, w.grad);
+    else lift_pass1(&c, w.q, w.trq, w.grad);
     int vc = (p->model == 0) ? 0 : d + 1;
     for (long e = 0; e < ne; ++e)
         for (int n = 0; n < np; ++n) {
@@ -1086,6 +1569,7 @@ int or_set_primitive(const or_mesh *m, const or_params *p, const double *prim, d
             U[IDX(d + 1, e, n, ne, np)] = E;
         }
     work_free(&w);
+    teardown(&c);
     (void)nv;
     return 0;
 }
@@ -1095,12 +1579,14 @@ int or_temperature(const or_mesh *m, const or_params *p, const double *U, double
     ctx_t c;
     if (setup(m, p, &c)) return -1;
     work_t w;
-    if (work_alloc(&c, &w)) { work_free(&w); return -2; }
+    if (work_alloc(&c, &w)) { work_free(&w); teardown(&c); return -2; }
     primitives(&c, U, w.q);
     traces(&c, w.q, c.nl, w.trq);
-    lift_pass1(&c, w.q, w.trq, w.grad);
+    if (c.curved) lift_pass1_c(&c, w.q, w.trq, w.grad);
+    else lift_pass1(&c, w.q, w.trq, w.grad);
     node_temperature(&c, U, w.grad, T);
     work_free(&w);
+    teardown(&c);
     return 0;
 }
 
@@ -1114,7 +1600,9 @@ int or_rhs_forced(const or_mesh *m, const or_params *p, const double *U, double 
 {
     ctx_t c;
     if (setup(m, p, &c)) return -1;
-    return rhs_core(&c, U, Ut, t, f, user);
+    int rc = c.curved ? rhs_core_c(&c, U, Ut, t, f, user) : rhs_core(&c, U, Ut, t, f, user);
+    teardown(&c);
+    return rc;
 }
 
 /* Low-storage Runge-Kutta coefficients (Sec. 3.1; Kennedy & Carpenter):
@@ -1153,16 +1641,17 @@ int or_run(const or_mesh *m, const or_params *p, double *U, int nsteps, double d
     if (setup(m, p, &c)) return -1;
     int ns;
     double A[5], B[5], cs[5];
-    if (or_rk_coeffs(rk, &ns, A, B, cs)) return -1;
+    if (or_rk_coeffs(rk, &ns, A, B, cs)) { teardown(&c); return -1; }
     size_t n = (size_t)c.nv * c.ne * c.np;
     double *G = (double *)calloc(n, sizeof(double));
     double *Ut = (double *)malloc(n * sizeof(double));
-    if (!G || !Ut) { free(G); free(Ut); return -2; }
+    if (!G || !Ut) { free(G); free(Ut); teardown(&c); return -2; }
     double t = t0;
     int rc = 0;
     for (int step = 0; step < nsteps && !rc; ++step) {
         for (int s = 0; s < ns; ++s) {
-            rc = rhs_core(&c, U, Ut, t + cs[s] * dt, f, user);
+            rc = c.curved ? rhs_core_c(&c, U, Ut, t + cs[s] * dt, f, user)
+                          : rhs_core(&c, U, Ut, t + cs[s] * dt, f, user);
             if (rc) break;
             for (size_t i = 0; i < n; ++i) {
                 G[i] = A[s] * G[i] + dt * Ut[i];
@@ -1173,6 +1662,7 @@ int or_run(const or_mesh *m, const or_params *p, double *U, int nsteps, double d
     }
     free(G);
     free(Ut);
+    teardown(&c);
     return rc;
 }
 
@@ -1181,7 +1671,11 @@ int or_run(const or_mesh *m, const or_params *p, double *U, int nsteps, double d
    direction sums of Sec. 3.1's explicit scheme:
    dt_c = CFL / ((2N+1) max_nodes sum_d (|u_d| + s)/h_d)
    dt_v = DFL / ((2N+1)^2 nu_max sum_d 1/h_d^2),  nu = max(4 mu/(3 rho), kappa/(rho R cv), gamma_K beta)
-   dt_s = 2 / (alpha beta). */
+   dt_s = 2 / (alpha beta).
+   On curved elements the spacing along xi_dir at a node is h_dir = 2 J / |J a^dir| and the
+   velocity along it u.(J a^dir)/|J a^dir|: the sums are taken per node,
+   sum_dir (|u.J a^dir| + s |J a^dir|) / (2J) and sum_dir (|J a^dir| / (2J))^2 (both reduce
+   to the box's). */
 int or_max_dt(const or_mesh *m, const or_params *p, const double *U, double cfl, double dfl, double *dt)
 {
     ctx_t c;
@@ -1189,15 +1683,29 @@ int or_max_dt(const or_mesh *m, const or_params *p, const double *U, double cfl,
     long ne = c.ne;
     int np = c.np, d = c.d;
     double *T = (double *)malloc(sizeof(double) * ne * np);
-    if (!T) return -2;
+    if (!T) { teardown(&c); return -2; }
     or_temperature(m, p, U, T);
-    double lmax = 0.0, numax = 0.0;
+    double lmax = 0.0, numax = 0.0, ih2 = 0.0;
     for (long e = 0; e < ne; ++e)
         for (int n = 0; n < np; ++n) {
             double rho = U[IDX(0, e, n, ne, np)];
             double s = sound_speed(&c, rho, T[(size_t)e * np + n]);
             double lam = 0.0;
-            for (int k = 0; k < d; ++k) lam += (fabs(U[IDX(1 + k, e, n, ne, np)] / rho) + s) / c.h[k];
+            if (c.curved) {
+                double J2 = 2.0 * JN(&c, e, n), h2 = 0.0;
+                for (int dir = 0; dir < d; ++dir) {
+                    double un = 0.0, a2 = 0.0;
+                    for (int k = 0; k < d; ++k) {
+                        un += U[IDX(1 + k, e, n, ne, np)] / rho * JA(&c, e, n, dir, k);
+                        a2 += JA(&c, e, n, dir, k) * JA(&c, e, n, dir, k);
+                    }
+                    lam += (fabs(un) + s * sqrt(a2)) / J2;
+                    h2 += a2 / (J2 * J2);
+                }
+                if (h2 > ih2) ih2 = h2;
+            } else {
+                for (int k = 0; k < d; ++k) lam += (fabs(U[IDX(1 + k, e, n, ne, np)] / rho) + s) / c.h[k];
+            }
             if (lam > lmax) lmax = lam;
             double nu = 4.0 * p->mu / (3.0 * rho);
             double nk = p->kappa / (rho * RV * p->cv);
@@ -1206,8 +1714,9 @@ int or_max_dt(const or_mesh *m, const or_params *p, const double *U, double cfl,
             if (nu > numax) numax = nu;
         }
     free(T);
-    double ih2 = 0.0;
-    for (int k = 0; k < d; ++k) ih2 += 1.0 / (c.h[k] * c.h[k]);
+    if (!c.curved)
+        for (int k = 0; k < d; ++k) ih2 += 1.0 / (c.h[k] * c.h[k]);
+    teardown(&c);
     double k1 = 2.0 * c.N + 1.0;
     double dtc = cfl / (k1 * lmax);
     double dtv = numax > 0.0 ? dfl / (k1 * k1 * numax * ih2) : 1e300;
@@ -1229,14 +1738,14 @@ int or_diagnostics(const or_mesh *m, const or_params *p, const double *U, double
     long ne = c.ne;
     int np = c.np, d = c.d;
     double *T = (double *)malloc(sizeof(double) * ne * np);
-    if (!T) return -2;
+    if (!T) { teardown(&c); return -2; }
     or_temperature(m, p, U, T);
     double J = 1.0;
     for (int k = 0; k < d; ++k) J *= 0.5 * c.h[k];
     for (int k = 0; k < OR_NDIAG; ++k) out[k] = 0.0;
     for (long e = 0; e < ne; ++e)
         for (int n = 0; n < np; ++n) {
-            double W = J;
+            double W = c.curved ? JN(&c, e, n) : J;
             for (int k = 0; k < d; ++k) W *= c.w[ncoord(&c, n, k)];
             double rho = U[IDX(0, e, n, ne, np)];
             out[0] += W * rho;
@@ -1256,6 +1765,28 @@ int or_diagnostics(const or_mesh *m, const or_params *p, const double *U, double
         }
     out[6] = sqrt(out[6]);
     free(T);
+    teardown(&c);
+    return 0;
+}
+
+/* Quadrature weight of every node, W[e][n] = J w_i w_j (w_k): the collocated Gauss
+   quadrature of the diagnostics (J = prod h/2 on the straight box). */
+int or_node_weights(const or_mesh *m, double *W)
+{
+    or_params p = {1, 1e-4, 0.01, 1.0 / 150.0, 5.0, 100.0, 100.0, 0};
+    or_mesh mm = *m;
+    for (int f = 0; f < 6; ++f) if (mm.wall_kind[f] != 0) mm.wall_T[f] = 0.85;
+    ctx_t c;
+    if (setup(&mm, &p, &c)) return -1;
+    double J = 1.0;
+    for (int k = 0; k < c.d; ++k) J *= 0.5 * c.h[k];
+    for (long e = 0; e < c.ne; ++e)
+        for (int n = 0; n < c.np; ++n) {
+            double w = c.curved ? JN(&c, e, n) : J;
+            for (int k = 0; k < c.d; ++k) w *= c.w[ncoord(&c, n, k)];
+            W[(size_t)e * c.np + n] = w;
+        }
+    teardown(&c);
     return 0;
 }
 

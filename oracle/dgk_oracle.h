@@ -36,6 +36,16 @@ typedef struct {
     double wall_T[6];
     double wall_theta_deg[6];
     double wall_gamma[6][4];
+    /* Curved elements (optional; xgeo = NULL: the straight box lo..hi).  Element e maps
+       the reference cube [-1,1]^dim by the polynomial of degree ngeo per direction that
+       interpolates xgeo[k][e][g] (coordinate k) at the equispaced points
+       t_a = -1 + 2a/ngeo, g = a + (ngeo+1)(b + (ngeo+1)c).  The element connectivity is
+       the box's (n, periodic, walls); neighbouring elements must share their face
+       points.  Requires ngeo <= N (2D) or 2 ngeo <= N (3D), so that the metric terms
+       are polynomials the scheme differentiates exactly; walls of kind 1 and the
+       Rusanov flux only. */
+    int ngeo;
+    const double *xgeo;
 } or_mesh;
 
 typedef struct {
@@ -77,6 +87,7 @@ void or_dmatrix(int N, const double *xi, double *D);
 /* ---- discretisation ---- */
 int  or_sizes(const or_mesh *m, const or_params *p, long *nelem, int *np, int *nv);
 int  or_node_coords(const or_mesh *m, double *x);
+int  or_node_weights(const or_mesh *m, double *W); /* J times the Gauss weights, [e][n] */
 int  or_set_primitive(const or_mesh *m, const or_params *p, const double *prim, double *U);
 int  or_temperature(const or_mesh *m, const or_params *p, const double *U, double *T);
 typedef void (*or_forcing_fn)(int dim, const double *x, double t, double *q, void *user);

@@ -24,7 +24,8 @@ class OrMesh(C.Structure):
     _fields_ = [("dim", C.c_int), ("N", C.c_int), ("n", C.c_int * 3),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("periodic", C.c_int * 3),
                 ("wall_kind", C.c_int * 6), ("wall_T", C.c_double * 6),
-                ("wall_theta_deg", C.c_double * 6), ("wall_gamma", (C.c_double * 4) * 6)]
+                ("wall_theta_deg", C.c_double * 6), ("wall_gamma", (C.c_double * 4) * 6),
+                ("ngeo", C.c_int), ("xgeo", C.POINTER(C.c_double))]
 
 
 class OrParams(C.Structure):
@@ -65,6 +66,7 @@ def lib():
         mp, pp = C.POINTER(OrMesh), C.POINTER(OrParams)
         L.or_sizes.argtypes = [mp, pp, C.POINTER(C.c_long), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.or_node_coords.argtypes = [mp, dp]
+        L.or_node_weights.argtypes = [mp, dp]
         L.or_set_primitive.argtypes = [mp, pp, dp, dp]
         L.or_temperature.argtypes = [mp, pp, dp, dp]
         L.or_rhs.argtypes = [mp, pp, dp, dp]
@@ -90,11 +92,20 @@ def _check(rc, what):
         raise RuntimeError(f"oracle {what} failed with status {rc}")
 
 
-def make_mesh(dim, N, n, lo, hi, periodic, walls=None):
+def make_mesh(dim, N, n, lo, hi, periodic, walls=None, geometry=None):
     """walls: dict face -> (T_wall, theta_deg) for faces 0..5 (-x,+x,-y,+y,-z,+z): an
     isothermal no-slip wall; or (T_wall, theta_deg, gamma_1, gamma_2, gamma_3, gamma_4): a
-    generalized Navier-slip wall (Eq. bc_nsk_alpha)."""
+    generalized Navier-slip wall (Eq. bc_nsk_alpha).
+    geometry: None (the straight box) or (ngeo, xgeo), xgeo[dim][nelem][(ngeo+1)^dim] the
+    element maps at equispaced points (see dgk_oracle.h); the array is kept alive by the
+    returned mesh."""
     m = OrMesh()
+    if geometry is not None:
+        ngeo, xgeo = geometry
+        xgeo = np.ascontiguousarray(xgeo, dtype=np.float64)
+        m.ngeo = int(ngeo)
+        m.xgeo = _dp(xgeo)
+        m._xgeo_keep = xgeo
     m.dim, m.N = dim, N
     for d in range(3):
         m.n[d] = int(n[d]) if d < dim else 1
@@ -219,6 +230,11 @@ class Oracle:
         x = np.zeros((self.dim, self.nelem, self.np))
         _check(lib().or_node_coords(C.byref(self.mesh), _dp(x)), "node_coords")
         return x
+
+    def node_weights(self):
+        W = np.zeros((self.nelem, self.np))
+        _check(lib().or_node_weights(C.byref(self.mesh), _dp(W)), "node_weights")
+        return W
 
     def set_primitive(self, prim):
         prim = np.ascontiguousarray(prim, dtype=np.float64)

@@ -134,3 +134,44 @@ def random_admissible(dim, nelem, np_, seed, rho_range=(0.3, 1.9), T_range=(0.8,
     prim[dim + 1] = rng.uniform(*T_range, size=(nelem, np_))
     prim[dim + 2] = rho * (1.0 + c_amp * rng.uniform(-1, 1, size=(nelem, np_)))
     return prim
+
+
+def box_geometry(dim, n, lo, hi, ngeo, amp=0.0, rotation=None):
+    """Element maps of a box mesh for the curved-element interface: xgeo[k][e][g], the
+    coordinate k of element e = ix + nx (iy + ny iz) at its equispaced points
+    g = a + (ngeo+1)(b + (ngeo+1)c), t_a = -1 + 2a/ngeo.
+
+    The straight box point x is moved to
+        x_k + amp L_k sin(2 pi (x_j - lo_j) / L_j),   j = k+1 cyclic,
+    a map that is periodic in every direction (the faces of a periodic direction stay
+    translates of one another) and bends the faces of the others; then multiplied by the
+    orthogonal matrix `rotation` if given.  Points shared by neighbouring elements are
+    computed from one integer index, so they coincide bit for bit.  The element maps are
+    the degree-ngeo interpolants of this map (amp = 0, no rotation: the box itself)."""
+    G = ngeo + 1
+    n = [int(v) for v in n[:dim]]
+    L = [float(hi[k]) - float(lo[k]) for k in range(dim)]
+    ne = int(np.prod(n))
+    a = np.arange(G)
+    # global point index per direction, per element and local point
+    idx = [None] * dim
+    for k in range(dim):
+        idx[k] = (np.arange(n[k])[:, None] * ngeo + a[None, :])  # [n_k][G]
+    # element coordinates
+    e = np.arange(ne)
+    ec = [e % n[0], (e // n[0]) % n[1]] + ([e // (n[0] * n[1])] if dim == 3 else [])
+    g = np.arange(G ** dim)
+    gc = [g % G, (g // G) % G] + ([g // (G * G)] if dim == 3 else [])
+    x = np.empty((dim, ne, G ** dim))
+    for k in range(dim):
+        gi = idx[k][ec[k][:, None], gc[k][None, :]]
+        x[k] = float(lo[k]) + L[k] * (gi / float(n[k] * ngeo))
+    y = x.copy()
+    if amp:
+        for k in range(dim):
+            j = (k + 1) % dim
+            y[k] = x[k] + amp * L[k] * np.sin(2.0 * np.pi * (x[j] - float(lo[j])) / L[j])
+    if rotation is not None:
+        R = np.asarray(rotation, dtype=np.float64)
+        y = np.einsum("kj,jeg->keg", R, y)
+    return y

@@ -9,17 +9,30 @@ from paper_2208_05310_gb300 import inputs
 PAPER_PARAMS = dict(model=1, gammaK=1e-4, mu=0.01, kappa=1.0 / 150.0, cv=5.0, alpha=100.0, beta=100.0)
 
 
-def mesh_spec(dim, N, n, lo=None, hi=None, periodic=None, walls=None):
+def mesh_spec(dim, N, n, lo=None, hi=None, periodic=None, walls=None, geometry=None):
+    """geometry: None (straight box) or dict(ngeo=, amp=, rotation=) for curved elements
+    (inputs.box_geometry)."""
     lo = lo or [0.0] * dim
     hi = hi or [1.0] * dim
     periodic = periodic if periodic is not None else [1] * dim
-    return dict(dim=dim, N=N, n=list(n), lo=list(lo), hi=list(hi), periodic=list(periodic), walls=dict(walls or {}))
+    return dict(dim=dim, N=N, n=list(n), lo=list(lo), hi=list(hi), periodic=list(periodic), walls=dict(walls or {}),
+                geometry=geometry)
+
+
+def geometry_array(mspec):
+    """(ngeo, xgeo) of a curved mesh specification, or None."""
+    g = mspec.get("geometry")
+    if g is None:
+        return None
+    x = inputs.box_geometry(mspec["dim"], mspec["n"], mspec["lo"], mspec["hi"], g["ngeo"], amp=g.get("amp", 0.0),
+                            rotation=g.get("rotation"))
+    return g["ngeo"], x
 
 
 def oracle_objects(orc, mspec, pspec):
     m = orc.make_mesh(mspec["dim"], mspec["N"], mspec["n"] + [1] * (3 - mspec["dim"]),
                       mspec["lo"] + [0.0] * (3 - mspec["dim"]), mspec["hi"] + [1.0] * (3 - mspec["dim"]),
-                      mspec["periodic"] + [1] * (3 - mspec["dim"]), mspec["walls"])
+                      mspec["periodic"] + [1] * (3 - mspec["dim"]), mspec["walls"], geometry=geometry_array(mspec))
     p = orc.make_params(**pspec)
     return orc.Oracle(m, p)
 

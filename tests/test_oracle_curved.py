@@ -1,0 +1,189 @@
+"""Pins of the oracle's curved-element path (Sec. 3.1 on curvilinear hexahedra: metric
+terms, strong-form BR1 with the chain rule, contravariant volume fluxes, numerical
+fluxes along the face metric).  None of these compares the path with itself:
+
+* an affine map of the box reproduces the straight-box discretisation (its weak-form
+  lifting and diagonal metrics are pinned by the other oracle tests);
+* a rotated box gives the rotated right-hand side (mass, energy, c unchanged, momentum
+  rotated): this catches transposed metric terms and wrong normals, also at walls;
+* a uniform state is preserved on curved elements (discrete metric identities and one
+  face metric for both elements), also at rest against bent walls at 90 degrees;
+* mass (and, without sources, momentum) is conserved on a periodic curved mesh;
+* a manufactured solution converges at the design order on a curved mesh.
+"""
+import numpy as np
+import pytest
+
+import mms_gen
+from cases import PAPER_PARAMS, mesh_spec, oracle_objects, rel_l2
+from paper_2208_05310_gb300 import inputs
+
+WALLS2 = {2: (0.85, 60.0), 3: (0.8, 120.0)}
+WALLS3 = {4: (0.85, 60.0), 5: (0.8, 120.0)}
+# beta = 1 keeps the relaxation bound 2/(alpha beta) from deciding max_dt
+DT_PARAMS = dict(PAPER_PARAMS, beta=1.0)
+
+
+def _rot2(th):
+    return np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+
+
+def _rot3(axis, th):
+    a = np.asarray(axis, dtype=float)
+    a = a / np.linalg.norm(a)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + np.sin(th) * K + (1 - np.cos(th)) * K @ K
+
+
+BOX_CASES = {
+    "2d_N3_walls": mesh_spec(2, 3, [4, 3], periodic=[1, 0], walls=WALLS2),
+    "2d_N4_periodic": mesh_spec(2, 4, [3, 3]),
+    "3d_N3_walls": mesh_spec(3, 3, [2, 3, 2], periodic=[1, 1, 0], walls=WALLS3),
+}
+
+
+@pytest.mark.parametrize("name", sorted(BOX_CASES))
+def test_affine_map_equals_box(orc, name):
+    ms = BOX_CASES[name]
+    mc = dict(ms, geometry=dict(ngeo=1))
+    ob, oc = oracle_objects(orc, ms, DT_PARAMS), oracle_objects(orc, mc, DT_PARAMS)
+    assert np.abs(oc.node_coords() - ob.node_coords()).max() < 1e-15
+    assert np.allclose(oc.node_weights(), ob.node_weights(), rtol=1e-14, atol=0)
+    prim = inputs.random_admissible(ms["dim"], ob.nelem, ob.np, 7)
+    Ub, Uc = ob.set_primitive(prim), oc.set_primitive(prim)
+    assert np.all(rel_l2(Uc, Ub) < 1e-14)
+    err = rel_l2(oc.rhs(Uc), ob.rhs(Ub))
+    assert np.all(err < 1e-12), err
+    assert abs(oc.max_dt(Uc) - ob.max_dt(Ub)) < 1e-13 * ob.max_dt(Ub)
+    db, dc = ob.diagnostics(Ub), oc.diagnostics(Uc)
+    for k in db:
+        assert abs(dc[k] - db[k]) <= 1e-13 * max(1.0, abs(db[k])), k
+
+
+ROT_CASES = {
+    "2d_periodic": (mesh_spec(2, 4, [4, 3]), _rot2(0.4)),
+    "2d_walls": (mesh_spec(2, 3, [4, 3], periodic=[1, 0], walls=WALLS2), _rot2(-1.1)),
+    "3d_periodic": (mesh_spec(3, 3, [2, 2, 3]), _rot3([1.0, 2.0, 0.5], 0.7)),
+    "3d_walls": (mesh_spec(3, 3, [3, 2, 2], periodic=[1, 1, 0], walls=WALLS3), _rot3([-0.3, 1.0, 0.8], 2.0)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ROT_CASES))
+def test_rotated_box_rotates_the_rhs(orc, name):
+    ms, R = ROT_CASES[name]
+    d = ms["dim"]
+    mr = dict(ms, geometry=dict(ngeo=1, rotation=R))
+    ob, orr = oracle_objects(orc, ms, DT_PARAMS), oracle_objects(orc, mr, DT_PARAMS)
+    assert np.abs(orr.node_coords() - np.einsum("kj,jen->ken", R, ob.node_coords())).max() < 1e-14
+    prim = inputs.random_admissible(d, ob.nelem, ob.np, 3)
+    pr = prim.copy()
+    pr[1:1 + d] = np.einsum("kj,jen->ken", R, prim[1:1 + d])
+    Ub, Ur = ob.set_primitive(prim), orr.set_primitive(pr)
+    Rb = ob.rhs(Ub)
+    exp = Rb.copy()
+    exp[1:1 + d] = np.einsum("kj,jen->ken", R, Rb[1:1 + d])
+    err = rel_l2(orr.rhs(Ur), exp)
+    assert np.all(err < 1e-12), err
+    assert abs(orr.max_dt(Ur) - ob.max_dt(Ub)) < 1e-12 * ob.max_dt(Ub)
+
+
+FREE_CASES = [(2, 4, 2, [4, 3]), (2, 3, 3, [3, 3]), (3, 4, 2, [2, 3, 2]), (3, 3, 1, [3, 2, 2])]
+
+
+@pytest.mark.parametrize("dim,N,ngeo,n", FREE_CASES)
+def test_free_stream_on_curved_elements(orc, dim, N, ngeo, n):
+    ms = mesh_spec(dim, N, n, geometry=dict(ngeo=ngeo, amp=0.05))
+    o = oracle_objects(orc, ms, PAPER_PARAMS)
+    prim = np.zeros((dim + 3, o.nelem, o.np))
+    prim[0] = 0.6
+    prim[1:1 + dim] = np.array([0.3, -0.2, 0.1][:dim])[:, None, None]
+    prim[dim + 1] = 0.95
+    prim[dim + 2] = 0.6
+    Ut = o.rhs(o.set_primitive(prim))
+    # the flux differences are O(p |J a| / J) ~ 1e1 here
+    assert np.abs(Ut).max() < 1e-10, np.abs(Ut).max(axis=(1, 2))
+
+
+@pytest.mark.parametrize("dim,N,ngeo,n", [(2, 4, 2, [4, 3]), (3, 4, 2, [2, 2, 3])])
+def test_rest_against_bent_walls(orc, dim, N, ngeo, n):
+    """Uniform fluid at rest at the wall temperature, contact angle 90 degrees: the walls
+    (bent by the map) exert the pressure only, which the curved volume terms balance."""
+    walls = {2 * (dim - 1): (0.9, 90.0), 2 * (dim - 1) + 1: (0.9, 90.0)}
+    per = [1] * (dim - 1) + [0]
+    ms = mesh_spec(dim, N, n, periodic=per, walls=walls, geometry=dict(ngeo=ngeo, amp=0.05))
+    o = oracle_objects(orc, ms, PAPER_PARAMS)
+    prim = np.zeros((dim + 3, o.nelem, o.np))
+    prim[0] = 1.7
+    prim[dim + 1] = 0.9
+    prim[dim + 2] = 1.7
+    Ut = o.rhs(o.set_primitive(prim))
+    assert np.abs(Ut).max() < 1e-10, np.abs(Ut).max(axis=(1, 2))
+
+
+@pytest.mark.parametrize("dim,N,ngeo,n", [(2, 4, 2, [4, 3]), (3, 4, 2, [2, 3, 2])])
+def test_conservation_on_curved_elements(orc, dim, N, ngeo, n):
+    ms = mesh_spec(dim, N, n, geometry=dict(ngeo=ngeo, amp=0.05))
+    o = oracle_objects(orc, ms, PAPER_PARAMS)
+    W = o.node_weights()
+    prim = inputs.random_admissible(dim, o.nelem, o.np, 5)
+    Ut = o.rhs(o.set_primitive(prim))
+    assert abs((W * Ut[0]).sum()) < 1e-13 * (W * np.abs(Ut[0])).sum()
+    # without the non-conservative sources (alpha = 0) momentum is conserved too
+    o0 = oracle_objects(orc, ms, dict(PAPER_PARAMS, alpha=0.0))
+    Ut = o0.rhs(o0.set_primitive(prim))
+    for v in range(1 + dim):
+        assert abs((W * Ut[v]).sum()) < 1e-12 * (W * np.abs(Ut[v])).sum(), v
+
+
+MMS = dict(gammaK=0.01, mu=0.01, kappa=0.02, cv=5.0, alpha=10.0, beta=10.0)
+
+
+def _mms_error(orc, lib, fo, prm, N, n, geometry, dt, tend):
+    ms = mesh_spec(2, N, [n, n], geometry=geometry)
+    o = oracle_objects(orc, ms, prm)
+    x = o.node_coords()
+    nsteps = int(round(tend / dt))
+    U = o.run(mms_gen.exact_state(lib, x, 0.0), nsteps, dt, rk=4, forcing=fo)
+    Ue = mms_gen.exact_state(lib, x, nsteps * dt)
+    return np.sqrt(((U - Ue) ** 2).mean(axis=(1, 2)))
+
+
+@pytest.mark.parametrize("model,N,dt", [(1, 3, 2e-4), (2, 4, 5e-5)])
+def test_mms_convergence_on_curved_mesh(orc, model, N, dt):
+    """The periodic map tiles the same periodic square, so the manufactured solution of
+    the straight-box pins applies unchanged.  Curved elements converge at the design
+    order (N+1, with a pre-asymptotic margin) and stay within a factor 10 of the
+    straight box's error."""
+    prm = dict(MMS, model=model)
+    lib, _, fo = mms_gen.build(prm)
+    geo = dict(ngeo=2, amp=0.04)
+    e8 = _mms_error(orc, lib, fo, prm, N, 8, geo, dt, 0.02)
+    e16 = _mms_error(orc, lib, fo, prm, N, 16, geo, dt, 0.02)
+    eoc = np.log2(e8 / e16)
+    assert np.all(eoc > N + 0.3), eoc
+    box16 = _mms_error(orc, lib, fo, prm, N, 16, None, dt, 0.02)
+    assert np.all(e16 < 10.0 * box16), e16 / box16
+
+
+def test_curved_input_checks(orc):
+    p = orc.make_params(**PAPER_PARAMS)
+
+    def sizes(ms):
+        m = orc.make_mesh(ms["dim"], ms["N"], ms["n"] + [1] * (3 - ms["dim"]), ms["lo"] + [0.0] * (3 - ms["dim"]),
+                          ms["hi"] + [1.0] * (3 - ms["dim"]), ms["periodic"] + [1] * (3 - ms["dim"]), ms["walls"],
+                          geometry=(ms["geometry"]["ngeo"],
+                                    inputs.box_geometry(ms["dim"], ms["n"], ms["lo"], ms["hi"], ms["geometry"]["ngeo"],
+                                                        rotation=ms["geometry"].get("rotation"))))
+        import ctypes as C
+        ne, np_, nv = C.c_long(), C.c_int(), C.c_int()
+        return orc.lib().or_sizes(C.byref(m), C.byref(p), C.byref(ne), C.byref(np_), C.byref(nv))
+
+    assert sizes(mesh_spec(3, 4, [2, 2, 2], geometry=dict(ngeo=2))) == 0
+    assert sizes(mesh_spec(3, 3, [2, 2, 2], geometry=dict(ngeo=2))) != 0    # 2 ngeo > N in 3D
+    assert sizes(mesh_spec(2, 3, [2, 2], geometry=dict(ngeo=4))) != 0       # ngeo > N in 2D
+    # a reflection inverts the elements (J < 0)
+    assert sizes(mesh_spec(2, 3, [2, 2], geometry=dict(ngeo=1, rotation=np.diag([1.0, -1.0])))) != 0
+    slip = {2: (0.85, 90.0, 0.0, 0.1, 0.0, 0.0), 3: (0.85, 90.0)}
+    assert sizes(mesh_spec(2, 3, [2, 2], periodic=[1, 0], walls=slip, geometry=dict(ngeo=1))) != 0
+    with pytest.raises(RuntimeError):
+        oracle_objects(orc, mesh_spec(2, 3, [2, 2], geometry=dict(ngeo=1)), dict(PAPER_PARAMS, model=2, flux="hllc"))
