@@ -122,6 +122,25 @@ int dgk_set_params(dgk_ctx *ctx, const dgk_params *p);
 /* Build the box mesh: 1D operators on N+1 Legendre-Gauss nodes (Sec. 3.1), wall
    constants, and device buffers for the state, the RK register and the face traces. */
 int dgk_mesh_box(dgk_ctx *ctx, const dgk_box_mesh *mesh);
+/* Build a mesh of curved elements with the box's connectivity (Sec. 3.1: curvilinear
+   elements described by their metric terms).  mesh gives dim, N, the element counts,
+   periodic directions and walls (lo/hi are ignored); xgeo (host, caller-owned, read
+   during the call) holds the element maps: coordinate k of element e
+   (e = ix + nx (iy + ny iz)) at the equispaced reference points t_a = -1 + 2a/ngeo,
+   xgeo[(k * nelem + e) * (ngeo+1)^dim + g], g = a + (ngeo+1)(b + (ngeo+1)c).  Each element
+   is the tensor-product polynomial of degree ngeo through its points; neighbouring
+   elements must share the points of their common face (periodic directions: up to the
+   period's translation).  The library computes the metric terms J a^i (cofactors of
+   dX/dxi) and 1/J at the nodes and face points; with ngeo <= N (2D) or 2 ngeo <= N (3D)
+   they are polynomials the scheme differentiates exactly, so a uniform flow is
+   preserved.  Liftings use the strong BR1 form with the chain rule, the volume integral
+   the contravariant fluxes F . J a^i, the faces the numerical flux along the face metric
+   (one per face point, shared by both elements).  Restrictions: the Rusanov flux, walls
+   of kind 1 only.  Errors: DGK_ERR_UNSUPPORTED for these, DGK_ERR_ARG for an element map
+   with J <= 0 at a node; otherwise as dgk_mesh_box.  Memory: the metric terms add
+   (dim^2 + 1) values per node in the bulk type and in double, and dim values per face
+   point. */
+int dgk_mesh_curved(dgk_ctx *ctx, const dgk_box_mesh *mesh, int ngeo, const double *xgeo);
 /* Problem sizes: elements, nodes per element (N+1)^dim, conserved variables dim+3. */
 int dgk_sizes(const dgk_ctx *ctx, long long *nelem, int *nodes_per_elem, int *nvar);
 /* Node coordinates x[d][e][n] (dim x nelem x np doubles). */

@@ -15,12 +15,17 @@
 
 #include "dgk.h"
 #include "dgk_host_math.h"
+#include "dgk_curved.cuh"
 #include "dgk_launch.cuh"
 
 const dgk::KernelTable *dgk_table_2d_f64(int N);
 const dgk::KernelTable *dgk_table_2d_f32(int N);
 const dgk::KernelTable *dgk_table_3d_f64(int N);
 const dgk::KernelTable *dgk_table_3d_f32(int N);
+const dgk::CurvedTable *dgk_ctable_2d_f64(int N);
+const dgk::CurvedTable *dgk_ctable_2d_f32(int N);
+const dgk::CurvedTable *dgk_ctable_3d_f64(int N);
+const dgk::CurvedTable *dgk_ctable_3d_f32(int N);
 
 
 namespace {
@@ -80,6 +85,7 @@ struct NodeInfo {
     double h[3];
     double J;
     double w[dgk::kMaxP];
+    const double *met;  // curved elements: [D*D+1][ne][NP] J a^i_k and 1/J in double; box: null
 };
 
 // Largest stable dt contribution per node, reduced with atomicMax on the bit pattern
@@ -117,6 +123,56 @@ __global__ void k_dt_reduce(const double *U, const double *T, long long ne, Node
     }
 }
 
+// k_dt_reduce on curved elements: the spacing along xi_dir at a node is h_dir = 2J/|J a^dir|
+// and the velocity along it u.J a^dir/|J a^dir|, so the node's convective sum is
+// sum_dir (|u.J a^dir| + s |J a^dir|)/(2J) and its diffusive factor
+// sum_dir (|J a^dir|/(2J))^2 (reduced into ih2_max).
+__global__ void k_dt_reduce_c(const double *U, const double *T, long long ne, NodeInfo ni, dgk::Phys ph,
+                              unsigned long long *lam_max, unsigned long long *nu_max, unsigned long long *ih2_max)
+{
+    __shared__ double sl[256], sn[256], sh[256];
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nn = ne * ni.NP;
+    double lam = 0.0, nu = 0.0, ih2 = 0.0;
+    if (i < nn) {
+        const double rho = U[i], t = T[i];
+        double omb = 1.0 - dgk::kBvdw * rho;
+        double s2 = dgk::kRgas * t * (1.0 + 1.0 / ph.cv) / (omb * omb) - 2.0 * dgk::kAvdw * rho;
+        double s = ph.model == 0 ? sqrt(fabs(s2)) : (s2 + ph.alpha * rho > 0.0 ? sqrt(s2 + ph.alpha * rho) : 0.0);
+        const double half_iJ = 0.5 * ni.met[(long long)(ni.D * ni.D) * nn + i];
+        for (int d = 0; d < ni.D; ++d) {
+            double un = 0.0, a2 = 0.0;
+            for (int k = 0; k < ni.D; ++k) {
+                const double a = ni.met[(long long)(d * ni.D + k) * nn + i];
+                un += U[(1 + k) * nn + i] / rho * a;
+                a2 += a * a;
+            }
+            lam += (fabs(un) + s * sqrt(a2)) * half_iJ;
+            ih2 += a2 * half_iJ * half_iJ;
+        }
+        nu = fmax(4.0 * ph.mu / (3.0 * rho), ph.kap / (rho * dgk::kRgas * ph.cv));
+        if (ph.model != 0) nu = fmax(nu, ph.gK * ph.beta);
+        if (!isfinite(lam)) lam = INFINITY;
+    }
+    sl[threadIdx.x] = lam;
+    sn[threadIdx.x] = nu;
+    sh[threadIdx.x] = ih2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sl[threadIdx.x] = fmax(sl[threadIdx.x], sl[threadIdx.x + o]);
+            sn[threadIdx.x] = fmax(sn[threadIdx.x], sn[threadIdx.x + o]);
+            sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicMax(lam_max, (unsigned long long)__double_as_longlong(sl[0]));
+        atomicMax(nu_max, (unsigned long long)__double_as_longlong(sn[0]));
+        atomicMax(ih2_max, (unsigned long long)__double_as_longlong(sh[0]));
+    }
+}
+
 // Per-block partial sums of the integral diagnostics (fixed tree order; the host sums
 // the blocks in index order, so the result is deterministic).
 __global__ void k_diag_partial(const double *U, const double *T, long long ne, NodeInfo ni, dgk::Phys ph,
@@ -128,7 +184,7 @@ __global__ void k_diag_partial(const double *U, const double *T, long long ne, N
     double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (i < nn) {
         const int n = (int)(i % ni.NP);
-        double W = ni.J;
+        double W = ni.met ? 1.0 / ni.met[(long long)(ni.D * ni.D) * nn + i] : ni.J;
         int r = n;
         for (int k = 0; k < ni.D; ++k) { W *= ni.w[r % ni.P]; r /= ni.P; }
         const double rho = U[i], t = T[i];
@@ -213,6 +269,14 @@ struct dgk_ctx {
     double *U = nullptr, *G = nullptr, *Tbuf = nullptr, *coef = nullptr, *rhsbuf = nullptr, *partial = nullptr;
     void *Utv = nullptr, *tr1 = nullptr, *tr2 = nullptr, *fd = nullptr;
     void *Us = nullptr;  // FP32-bulk form: shadow of U in float plus the energy balance
+    // curved elements (dgk_mesh_curved): metric terms in the bulk type for the kernels
+    // (met, fmet) and in double for the time step and the diagnostics (metd; the same
+    // buffer as met in the FP64 form); host copy of the node coordinates
+    bool curved = false;
+    const dgk::CurvedTable *ct = nullptr;
+    void *met = nullptr, *fmet = nullptr;
+    double *metd = nullptr;
+    std::vector<double> xnodes;
     unsigned *status = nullptr;
     unsigned long long *redbuf = nullptr;
     double coef_h[11] = {0};
@@ -232,12 +296,18 @@ namespace {
 
 void free_buffers(dgk_ctx *c)
 {
+    if (c->metd && (void *)c->metd != c->met) cudaFree(c->metd);
     void *ptrs[] = {c->U,  c->G,   c->Tbuf, c->coef, c->rhsbuf, c->partial, c->Utv,
-                    c->tr1, c->tr2, c->fd,   c->Us,   c->status, c->redbuf};
+                    c->tr1, c->tr2, c->fd,   c->Us,   c->status, c->redbuf, c->met, c->fmet};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     c->U = c->G = c->Tbuf = c->coef = c->rhsbuf = c->partial = nullptr;
     c->Utv = c->tr1 = c->tr2 = c->fd = c->Us = nullptr;
+    c->met = c->fmet = nullptr;
+    c->metd = nullptr;
+    c->curved = false;
+    c->ct = nullptr;
+    c->xnodes.clear();
     c->status = nullptr;
     c->redbuf = nullptr;
     if (c->graph) cudaGraphExecDestroy(c->graph);
@@ -260,6 +330,8 @@ void fill_args(dgk_ctx *c, dgk::KArgs<R> &a)
     a.v.tr1 = (R *)c->tr1;
     a.v.tr2 = (R *)c->tr2;
     a.v.fd = (R *)c->fd;
+    a.v.met = (const R *)c->met;
+    a.v.fmet = (const R *)c->fmet;
     a.v.out = c->Tbuf;
     a.v.coef = c->coef;
     a.v.status = c->status;
@@ -270,7 +342,10 @@ template <typename R>
 void fill_bulk(dgk::KArgs<R> &a, const dgk::Geom &g, const dgk::Phys &ph, const dgk::Walls &w, const dgk::Ops &o,
                int flux)
 {
-    for (int i = 0; i < dgk::kMaxP * dgk::kMaxP; ++i) a.op.Dh[i] = (R)o.Dhat[i];
+    for (int i = 0; i < dgk::kMaxP * dgk::kMaxP; ++i) {
+        a.op.Dh[i] = (R)o.Dhat[i];
+        a.op.Dm[i] = (R)o.Dm[i];
+    }
     for (int i = 0; i < dgk::kMaxP; ++i) {
         a.op.Lp[i] = (R)o.Lp[i];
         a.op.Lm[i] = (R)o.Lm[i];
@@ -343,7 +418,10 @@ int build_consts(dgk_ctx *c)
     dgk::Ops o{};
     const int P = c->P;
     for (int i = 0; i < P; ++i) {
-        for (int j = 0; j < P; ++j) o.Dhat[i * P + j] = c->op1.Dhat[i * P + j];
+        for (int j = 0; j < P; ++j) {
+            o.Dhat[i * P + j] = c->op1.Dhat[i * P + j];
+            o.Dm[i * P + j] = c->op1.D[i * P + j];
+        }
         o.Lp[i] = c->op1.lp[i] / c->op1.w[i];
         o.Lm[i] = c->op1.lm[i] / c->op1.w[i];
         o.lp[i] = c->op1.lp[i];
@@ -391,6 +469,24 @@ int event_pair(dgk_ctx *c, int cls, cudaEvent_t &a, cudaEvent_t &b)
     return DGK_OK;
 }
 
+// stage and set-up kernels of the mesh kind (box or curved elements)
+cudaError_t run_lift1(const dgk_ctx *c, const void *a)
+{
+    return c->curved ? c->ct->lift1(a, c->stream) : c->kt->lift1(a, c->stream);
+}
+cudaError_t run_lift2vol(const dgk_ctx *c, const void *a)
+{
+    return c->curved ? c->ct->lift2vol(a, c->stream) : c->kt->lift2vol(a, c->stream);
+}
+cudaError_t run_surf(const dgk_ctx *c, const void *a, int mode, int stage)
+{
+    return c->curved ? c->ct->surf(a, mode, stage, c->stream) : c->kt->surf(a, mode, stage, c->stream);
+}
+cudaError_t run_nodeT(const dgk_ctx *c, int mode)
+{
+    return c->curved ? c->ct->nodeT(c->args(), mode, c->stream) : c->kt->nodeT(c->args(), mode, c->stream);
+}
+
 // one full RK step, kernel by kernel (optionally bracketed by timing events)
 int launch_step(dgk_ctx *c, bool timed)
 {
@@ -403,9 +499,7 @@ int launch_step(dgk_ctx *c, bool timed)
                 if (rc) return rc;
                 DGK_CUDA(cudaEventRecord(e0, c->stream));
             }
-            cudaError_t err = k == 0 ? c->kt->lift1(a, c->stream)
-                              : k == 1 ? c->kt->lift2vol(a, c->stream)
-                                       : c->kt->surf(a, 1, s, c->stream);
+            cudaError_t err = k == 0 ? run_lift1(c, a) : k == 1 ? run_lift2vol(c, a) : run_surf(c, a, 1, s);
             if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("stage kernel launch: ") + cudaGetErrorString(err));
             if (timed) DGK_CUDA(cudaEventRecord(e1, c->stream));
         }
@@ -449,6 +543,7 @@ NodeInfo node_info(const dgk_ctx *c)
         ni.J *= 0.5 * ni.h[d];
     }
     for (int i = 0; i < c->P; ++i) ni.w[i] = c->op1.w[i];
+    ni.met = c->curved ? c->metd : nullptr;
     return ni;
 }
 
@@ -530,6 +625,8 @@ int dgk_set_params(dgk_ctx *c, const dgk_params *p)
         return fail(DGK_ERR_ARG, "parameters out of range");
     if (p->flux != DGK_FLUX_RUSANOV && p->flux != DGK_FLUX_HLLC) return fail(DGK_ERR_ARG, "flux must be Rusanov or HLLC");
     if (p->flux == DGK_FLUX_HLLC && p->model != 2) return fail(DGK_ERR_UNSUPPORTED, "the HLLC flux is for model 2");
+    if (c->have_mesh && c->curved && p->flux != DGK_FLUX_RUSANOV)
+        return fail(DGK_ERR_UNSUPPORTED, "curved elements use the Rusanov flux");
     if (c->have_mesh && p->precision != c->prm.precision)
         return fail(DGK_ERR_STATE, "precision is fixed once the mesh is built");
     c->prm = *p;
@@ -593,7 +690,7 @@ int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m)
     DGK_CUDA(cudaMalloc(&c->Tbuf, (size_t)ne * c->NP * sizeof(double)));
     DGK_CUDA(cudaMalloc(&c->coef, 16 * sizeof(double)));
     DGK_CUDA(cudaMalloc(&c->status, sizeof(unsigned)));
-    DGK_CUDA(cudaMalloc(&c->redbuf, 2 * sizeof(unsigned long long)));
+    DGK_CUDA(cudaMalloc(&c->redbuf, 3 * sizeof(unsigned long long)));
     DGK_CUDA(cudaMalloc(&c->Utv, nstate * c->rsize));
     DGK_CUDA(cudaMalloc(&c->tr1, (size_t)c->NL * nface * c->rsize));
     DGK_CUDA(cudaMalloc(&c->tr2, (size_t)2 * nface * c->rsize));
@@ -608,6 +705,57 @@ int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m)
     c->coef_valid = false;
     c->have_mesh = true;
     DGK_CUDA(cudaStreamSynchronize(c->stream));
+    return DGK_OK;
+}
+
+int dgk_mesh_curved(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const double *xgeo)
+{
+    if (!c || !m || !xgeo) return fail(DGK_ERR_ARG, "null argument");
+    if (!c->have_params) return fail(DGK_ERR_STATE, "set params before the mesh");
+    if (m->dim != 2 && m->dim != 3) return fail(DGK_ERR_UNSUPPORTED, "dim must be 2 or 3");
+    if (ngeo < 1 || (m->dim == 2 ? ngeo > m->N : 2 * ngeo > m->N))
+        return fail(DGK_ERR_UNSUPPORTED, "curved elements need 1 <= ngeo <= N (2D) or 1 <= 2 ngeo <= N (3D)");
+    if (c->prm.flux != DGK_FLUX_RUSANOV) return fail(DGK_ERR_UNSUPPORTED, "curved elements use the Rusanov flux");
+    for (int f = 0; f < 2 * m->dim; ++f)
+        if (!m->periodic[f / 2] && m->wall[f].kind == 2)
+            return fail(DGK_ERR_UNSUPPORTED, "curved elements take walls of kind 1 (no-slip contact angle)");
+    int rc = dgk_mesh_box(c, m);  // validates the rest and allocates the stage buffers
+    if (rc) return rc;
+    c->have_mesh = false;
+    int n[3], per[3];
+    for (int d = 0; d < 3; ++d) {
+        n[d] = d < c->D ? m->n[d] : 1;
+        per[d] = d < c->D ? m->periodic[d] : 1;
+    }
+    dgk::host::CurvedGeometry geo;
+    std::string err;
+    if (!dgk::host::curved_geometry(c->D, c->op1, ngeo, n, per, c->ne, xgeo, geo, err)) return fail(DGK_ERR_ARG, err);
+    const bool f32 = c->prm.precision == DGK_PREC_FP32BULK;
+    c->ct = c->D == 2 ? (f32 ? dgk_ctable_2d_f32(c->N) : dgk_ctable_2d_f64(c->N))
+                      : (f32 ? dgk_ctable_3d_f32(c->N) : dgk_ctable_3d_f64(c->N));
+    if (!c->ct) return fail(DGK_ERR_UNSUPPORTED, "no curved-element kernels for this (dim, N, precision)");
+    DGK_CUDA(c->ct->prepare());
+    DGK_CUDA(cudaMalloc(&c->metd, geo.met.size() * sizeof(double)));
+    DGK_CUDA(cudaMemcpy(c->metd, geo.met.data(), geo.met.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (f32) {
+        std::vector<float> h(geo.met.begin(), geo.met.end());
+        DGK_CUDA(cudaMalloc(&c->met, h.size() * sizeof(float)));
+        DGK_CUDA(cudaMemcpy(c->met, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+        std::vector<float> hf(geo.fmet.begin(), geo.fmet.end());
+        DGK_CUDA(cudaMalloc(&c->fmet, hf.size() * sizeof(float)));
+        DGK_CUDA(cudaMemcpy(c->fmet, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+        c->met = c->metd;
+        DGK_CUDA(cudaMalloc(&c->fmet, geo.fmet.size() * sizeof(double)));
+        DGK_CUDA(cudaMemcpy(c->fmet, geo.fmet.data(), geo.fmet.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    c->xnodes = std::move(geo.x);
+    c->curved = true;
+    fill_args(c, c->a64);
+    fill_args(c, c->a32);
+    drop_graph(c);
+    c->coef_valid = false;
+    c->have_mesh = true;
     return DGK_OK;
 }
 
@@ -628,16 +776,20 @@ int dgk_node_coords(dgk_ctx *c, double *x, int on_device)
     if (!x) return fail(DGK_ERR_ARG, "null output");
     const size_t nn = (size_t)c->ne * c->NP;
     std::vector<double> h((size_t)c->D * nn);
-    for (long long e = 0; e < c->ne; ++e) {
-        long long co[3] = {e % c->mesh.n[0], (e / c->mesh.n[0]) % c->mesh.n[1],
-                           c->D == 3 ? e / ((long long)c->mesh.n[0] * c->mesh.n[1]) : 0};
-        for (int n = 0; n < c->NP; ++n) {
-            int r = n;
-            for (int d = 0; d < c->D; ++d) {
-                const int i = r % c->P;
-                r /= c->P;
-                const double hd = (c->mesh.hi[d] - c->mesh.lo[d]) / c->mesh.n[d];
-                h[(size_t)d * nn + (size_t)e * c->NP + n] = c->mesh.lo[d] + hd * (co[d] + 0.5 * (c->op1.xi[i] + 1.0));
+    if (c->curved) {
+        h = c->xnodes;
+    } else {
+        for (long long e = 0; e < c->ne; ++e) {
+            long long co[3] = {e % c->mesh.n[0], (e / c->mesh.n[0]) % c->mesh.n[1],
+                               c->D == 3 ? e / ((long long)c->mesh.n[0] * c->mesh.n[1]) : 0};
+            for (int n = 0; n < c->NP; ++n) {
+                int r = n;
+                for (int d = 0; d < c->D; ++d) {
+                    const int i = r % c->P;
+                    r /= c->P;
+                    const double hd = (c->mesh.hi[d] - c->mesh.lo[d]) / c->mesh.n[d];
+                    h[(size_t)d * nn + (size_t)e * c->NP + n] = c->mesh.lo[d] + hd * (co[d] + 0.5 * (c->op1.xi[i] + 1.0));
+                }
             }
         }
     }
@@ -661,7 +813,7 @@ int dgk_set_primitive(dgk_ctx *c, const double *prim, size_t count, int on_devic
     DGK_CUDA(cudaGetLastError());
     cudaError_t err = c->kt->traces(c->args(), c->stream);
     if (err != cudaSuccess) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
-    err = c->kt->nodeT(c->args(), 1, c->stream);
+    err = run_nodeT(c, 1);
     if (err != cudaSuccess) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
     rc = after_state_change(c);
     if (rc) return rc;
@@ -705,16 +857,16 @@ int dgk_rhs(dgk_ctx *c, double *Ut, size_t count, int on_device)
     }
     cudaError_t err;
     const void *a = c->args();
-    if ((err = c->kt->lift1(a, c->stream))) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
-    if ((err = c->kt->lift2vol(a, c->stream))) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
+    if ((err = run_lift1(c, a))) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
+    if ((err = run_lift2vol(c, a))) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
     if (c->prm.precision == DGK_PREC_FP32BULK) {
         dgk::KArgs<float> b = c->a32;
         b.v.out = dst;
-        err = c->kt->surf(&b, 0, 0, c->stream);
+        err = run_surf(c, &b, 0, 0);
     } else {
         dgk::KArgs<double> b = c->a64;
         b.v.out = dst;
-        err = c->kt->surf(&b, 0, 0, c->stream);
+        err = run_surf(c, &b, 0, 0);
     }
     if (err) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
     if (!on_device) {
@@ -768,24 +920,31 @@ int dgk_max_dt(dgk_ctx *c, double cfl, double dfl, double *dt)
     int rc = ready(c);
     if (rc) return rc;
     if (!dt || !(cfl > 0) || !(dfl > 0)) return fail(DGK_ERR_ARG, "bad arguments");
-    cudaError_t err = c->kt->nodeT(c->args(), 0, c->stream);
+    cudaError_t err = run_nodeT(c, 0);
     if (err) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
-    DGK_CUDA(cudaMemsetAsync(c->redbuf, 0, 2 * sizeof(unsigned long long), c->stream));
+    DGK_CUDA(cudaMemsetAsync(c->redbuf, 0, 3 * sizeof(unsigned long long), c->stream));
     const long long nn = c->ne * c->NP;
     dgk::Phys ph = c->a64.ph;
-    k_dt_reduce<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->U, c->Tbuf, c->ne, node_info(c), ph, c->redbuf,
-                                                                     c->redbuf + 1);
+    if (c->curved)
+        k_dt_reduce_c<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->U, c->Tbuf, c->ne, node_info(c), ph, c->redbuf,
+                                                                           c->redbuf + 1, c->redbuf + 2);
+    else
+        k_dt_reduce<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->U, c->Tbuf, c->ne, node_info(c), ph, c->redbuf,
+                                                                         c->redbuf + 1);
     DGK_CUDA(cudaGetLastError());
-    unsigned long long hv[2];
+    unsigned long long hv[3];
     DGK_CUDA(cudaMemcpyAsync(hv, c->redbuf, sizeof(hv), cudaMemcpyDeviceToHost, c->stream));
     DGK_CUDA(cudaStreamSynchronize(c->stream));
-    double lam, nu;
+    double lam, nu, ih2 = 0.0;
     std::memcpy(&lam, &hv[0], 8);
     std::memcpy(&nu, &hv[1], 8);
-    double ih2 = 0.0;
-    for (int d = 0; d < c->D; ++d) {
-        double h = (c->mesh.hi[d] - c->mesh.lo[d]) / c->mesh.n[d];
-        ih2 += 1.0 / (h * h);
+    if (c->curved) {
+        std::memcpy(&ih2, &hv[2], 8);
+    } else {
+        for (int d = 0; d < c->D; ++d) {
+            double h = (c->mesh.hi[d] - c->mesh.lo[d]) / c->mesh.n[d];
+            ih2 += 1.0 / (h * h);
+        }
     }
     const double k1 = 2.0 * c->N + 1.0;
     double r = cfl / (k1 * lam);
@@ -801,7 +960,7 @@ int dgk_diagnostics(dgk_ctx *c, double *out)
     int rc = ready(c);
     if (rc) return rc;
     if (!out) return fail(DGK_ERR_ARG, "null output");
-    cudaError_t err = c->kt->nodeT(c->args(), 0, c->stream);
+    cudaError_t err = run_nodeT(c, 0);
     if (err) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
     const long long nn = c->ne * c->NP;
     const unsigned nb = (unsigned)((nn + 255) / 256);
@@ -826,7 +985,7 @@ int dgk_node_temperature_pressure(dgk_ctx *c, double *T, double *p, size_t count
     if (rc) return rc;
     const size_t nn = (size_t)c->ne * c->NP;
     if (count != nn || (!T && !p)) return fail(DGK_ERR_ARG, "output arrays must hold nelem*np doubles");
-    cudaError_t err = c->kt->nodeT(c->args(), 0, c->stream);
+    cudaError_t err = run_nodeT(c, 0);
     if (err) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (T) DGK_CUDA(cudaMemcpyAsync(T, c->Tbuf, nn * sizeof(double), kind, c->stream));

@@ -1,0 +1,4 @@
+// Instantiation of the 2D curved-element stage kernels in the float bulk type for N = 2..5.
+#include "dgk_curved.cuh"
+
+DGK_DEFINE_CURVED_TABLE(dgk_ctable_2d_f32, 2, float)

@@ -98,6 +98,7 @@ struct WallsR {
 //   w = quadrature weights.
 struct Ops {
     double Dhat[kMaxP * kMaxP];
+    double Dm[kMaxP * kMaxP];  // D_ij = l_j'(xi_i)
     double Lp[kMaxP], Lm[kMaxP], lp[kMaxP], lm[kMaxP], w[kMaxP];
 };
 

@@ -1,6 +1,9 @@
 // dgk_host_math.h -- host-side set-up math of libdgk (operators, saturation states).
 #pragma once
 
+#include <string>
+#include <vector>
+
 namespace dgk {
 namespace host {
 
@@ -16,6 +19,15 @@ bool dg_operators(int N, Operators1D &op);
 double pressure(double rho, double T);
 bool maxwell(double T, double &rho_v, double &rho_l);
 bool sigma_vl(double T, double gammaK, double &sigma);
+
+// Curved elements (dgk_geom.cpp): node coordinates x [D][ne][NP], metric terms
+// met [D*D+1][ne][NP] (plane i*D + k: J a^i_k; plane D*D: 1/J) and face metrics
+// fmet [D][ne][NF][NFP] (J a^dir_k at the points of face f = 2 dir + side).
+struct CurvedGeometry {
+    std::vector<double> met, fmet, x;
+};
+bool curved_geometry(int D, const Operators1D &op, int ngeo, const int n[3], const int periodic[3], long long ne,
+                     const double *xgeo, CurvedGeometry &out, std::string &err);
 
 }  // namespace host
 }  // namespace dgk

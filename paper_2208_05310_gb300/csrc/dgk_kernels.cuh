@@ -56,6 +56,7 @@ __host__ __device__ constexpr int min_blocks(int threads_per_block, int threads_
 template <typename R>
 struct OpsR {
     R Dh[kMaxP * kMaxP];
+    R Dm[kMaxP * kMaxP];  // D_ij = l_j'(xi_i) (strong form, curved elements)
     R Lp[kMaxP], Lm[kMaxP], lp[kMaxP], lm[kMaxP];
 };
 
@@ -74,6 +75,8 @@ struct KView {
     R *tr2;              // [2][ne][NF][NFP] traces of T and of d c / d x_normal
     R *fd;               // [2NV+3][ne][NF][NFP] one-sided face data: U, F = F^C - F^V, lambda, and
                          // for the HLLC flux the convective pressure and the sound speed
+    const R *met;        // curved elements: [D*D+1][ne][NP] J a^dir_k (plane dir*D + k) and 1/J; box: null
+    const R *fmet;       // curved elements: [D][ne][NF][NFP] J a^dir_k at the face points; box: null
     double *out;         // rhs output [NV][ne][NP], or nodal T [ne][NP]
     const double *coef;  // device [A_0..A_4, B_0..B_4, dt] of this problem
     unsigned *status;
@@ -981,8 +984,10 @@ __device__ __forceinline__ void write_traces(const Ctx<R> &a, const Slot<D, N, E
 // mode 0: write U_t (double) to a.v.out; mode 1: RK stage `stage` with coefficients from
 // a.v.coef (G = A G + dt U_t; U = U + B G) and new traces.
 // FLUX: 0 Rusanov, 1 HLLC (a template parameter, so that each form keeps the register
-// allocation of its own flux).
-template <int D, int N, typename R, int EB = 0, int FLUX = 0>
+// allocation of its own flux).  GEO 1: curved elements, whose face data are already
+// scaled by the surface element; the surface term takes 1/J of the node (a.v.met) in
+// place of 2/h.
+template <int D, int N, typename R, int EB = 0, int FLUX = 0, int GEO = 0>
 __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, unsigned char *smraw, int mode, int stage)
 {
     using S = Shape<D, N, EB>;
@@ -1036,8 +1041,10 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
     R Ut[NV];
     if (t.valid) {
         // (2/h) l_i(+-1)/w_i of this node's index in each direction, selected into registers
+        // (curved elements: (1/J) l_i(+-1)/w_i)
         R Lp[D], Lm[D];
         int fpd[D];
+        const R iJ = GEO ? a.v.met[((long long)(D * D) * ne + t.e) * NP + t.n] : R(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const int i = ncoord<P>(t.n, d);
@@ -1046,8 +1053,8 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
 #pragma unroll
             for (int l = 0; l < P; ++l)
                 if (l == i) { vp = a.op.Lp[l]; vm = a.op.Lm[l]; }
-            Lp[d] = vp * a.v.gr.inv2h[d];
-            Lm[d] = vm * a.v.gr.inv2h[d];
+            Lp[d] = vp * (GEO ? iJ : a.v.gr.inv2h[d]);
+            Lm[d] = vm * (GEO ? iJ : a.v.gr.inv2h[d]);
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -1095,14 +1102,14 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
     write_traces<D, N, R, EB>(a, t, sFs, Ud);
 }
 
-template <int D, int N, typename R, int EB = 0, int FLUX = 0>
+template <int D, int N, typename R, int EB = 0, int FLUX = 0, int GEO = 0>
 __global__ void __launch_bounds__(Shape<D, N, EB>::NT,
                                   min_blocks(Shape<D, N, EB>::NT, (FLUX ? DGK_THREADS_SURF_HLLC : DGK_THREADS_SURF) / (int)(sizeof(R) / 4)))
     k_surf_rk(KArgs<R> args, int mode, int stage)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const Ctx<R> a{args.v, args.ph, args.pr, args.op};
-    surf_rk_body<D, N, R, EB, FLUX>(a, blockIdx.x, smraw, mode, stage);
+    surf_rk_body<D, N, R, EB, FLUX, GEO>(a, blockIdx.x, smraw, mode, stage);
 }
 
 // ------------------------------------------------------------------ set-up kernels

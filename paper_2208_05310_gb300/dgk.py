@@ -51,7 +51,7 @@ class DgkError(RuntimeError):
     pass
 
 
-EXPORTS = ("dgk_create", "dgk_destroy", "dgk_set_params", "dgk_mesh_box", "dgk_sizes", "dgk_node_coords",
+EXPORTS = ("dgk_create", "dgk_destroy", "dgk_set_params", "dgk_mesh_box", "dgk_mesh_curved", "dgk_sizes", "dgk_node_coords",
            "dgk_set_primitive", "dgk_upload_state", "dgk_download_state", "dgk_rhs", "dgk_rk_step", "dgk_run",
            "dgk_max_dt", "dgk_diagnostics", "dgk_status", "dgk_set_timing", "dgk_kernel_time", "dgk_maxwell",
            "dgk_sigma_vl", "dgk_interface_width", "dgk_status_string", "dgk_last_error", "dgk_check_conversions",
@@ -75,6 +75,7 @@ def lib():
         "dgk_destroy": (None, [vp]),
         "dgk_set_params": (i, [vp, C.POINTER(DgkParams)]),
         "dgk_mesh_box": (i, [vp, C.POINTER(DgkBoxMesh)]),
+        "dgk_mesh_curved": (i, [vp, C.POINTER(DgkBoxMesh), i, dp]),
         "dgk_sizes": (i, [vp, C.POINTER(C.c_longlong), C.POINTER(i), C.POINTER(i)]),
         "dgk_node_coords": (i, [vp, vp, i]),
         "dgk_set_primitive": (i, [vp, vp, sz, i]),
@@ -228,16 +229,21 @@ class Context:
     def mesh_box(self, dim, N, n, lo, hi, periodic, walls=None):
         """walls: {face: (T_wall, theta_deg)} (no-slip) or {face: (T_wall, theta_deg, g1, g2, g3, g4)}
     (Navier slip), faces 0..5 = -x,+x,-y,+y,-z,+z."""
-        m = DgkBoxMesh()
-        m.dim, m.N = dim, N
-        for d in range(3):
-            m.n[d] = int(n[d]) if d < dim else 1
-            m.lo[d] = float(lo[d]) if d < dim else 0.0
-            m.hi[d] = float(hi[d]) if d < dim else 1.0
-            m.periodic[d] = int(periodic[d]) if d < dim else 1
-        for f, spec in (walls or {}).items():
-            m.wall[f] = _wall(spec)
+        m = make_box_mesh(dim, N, n, lo, hi, periodic, walls)
         _check(lib().dgk_mesh_box(self._h, C.byref(m)), "dgk_mesh_box")
+        self._sizes(dim)
+
+    def mesh_curved(self, dim, N, n, periodic, walls, ngeo, xgeo):
+        """Curved elements with the box's connectivity (dgk_mesh_curved): xgeo is a float64
+        array [dim][nelem][(ngeo+1)^dim] of the element maps at equispaced reference
+        points; walls as for mesh_box (kind 1 only)."""
+        m = make_box_mesh(dim, N, n, [0.0] * 3, [1.0] * 3, periodic, walls)
+        x = np.ascontiguousarray(xgeo, dtype=np.float64)
+        _check(lib().dgk_mesh_curved(self._h, C.byref(m), int(ngeo), x.ctypes.data_as(C.POINTER(C.c_double))),
+               "dgk_mesh_curved")
+        self._sizes(dim)
+
+    def _sizes(self, dim):
         ne, npn, nv = C.c_longlong(), C.c_int(), C.c_int()
         _check(lib().dgk_sizes(self._h, C.byref(ne), C.byref(npn), C.byref(nv)), "dgk_sizes")
         self.dim, self.nelem, self.np, self.nv = dim, ne.value, npn.value, nv.value

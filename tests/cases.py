@@ -110,6 +110,11 @@ def dgk_context(mspec, pspec, precision="fp64", rk=4):
     ctx = dgk.Context()
     ctx.set_params(rk=rk, precision=precision, **pspec)
     dim = mspec["dim"]
+    geo = geometry_array(mspec)
+    if geo is not None:
+        ctx.mesh_curved(dim, mspec["N"], mspec["n"] + [1] * (3 - dim), mspec["periodic"] + [1] * (3 - dim),
+                        mspec["walls"], geo[0], geo[1])
+        return ctx
     ctx.mesh_box(dim, mspec["N"], mspec["n"] + [1] * (3 - dim), mspec["lo"] + [0.0] * (3 - dim),
                  mspec["hi"] + [1.0] * (3 - dim), mspec["periodic"] + [1] * (3 - dim), mspec["walls"])
     return ctx
