@@ -36,7 +36,10 @@ UNIT = "DOF-stage/s"
 # point per node for N = 5).  The lifting kernels read the state: in the FP64 form the
 # double state, in the FP32-bulk form its float shadow (NV values and the energy
 # balance), which the RK update writes beside the double state.
-def kernel_bytes_per_node(dim, N, rsize, flux="rusanov"):
+def kernel_bytes_per_node(dim, N, rsize, flux="rusanov", curved=False):
+    """curved: the curved-element kernels read in addition the metric terms (dim^2 + 1
+    values per node: J a^i and 1/J) and the face metrics (dim values per face point) in
+    the lifting kernels, and 1/J in k_surf_rk."""
     nv, nl = dim + 3, dim + 2
     f = 2 * dim / (N + 1)  # face points per node (own faces)
     nfd = 2 * nv + (3 if flux == "hllc" else 1)  # face data values (HLLC: + pressure, sound speed)
@@ -45,7 +48,18 @@ def kernel_bytes_per_node(dim, N, rsize, flux="rusanov"):
     lift1 = state + rsize * 1 * f + rsize * 2 * f                       # c traces in, T and dc/dn traces out
     lift2 = state + rsize * nl * f + rsize * 2 * f + rsize * nv + rsize * nfd * f
     surf = rsize * nfd * f + rsize * nv + 8 * nv * 4 + rsize * nl * f + shadow_w
+    if curved:
+        geo = rsize * (dim * dim + 1) + rsize * dim * f
+        return {"k_lift1c": lift1 + geo, "k_lift2volc": lift2 + geo, "k_surf_rk": surf + rsize}
     return {"k_lift1": lift1, "k_lift2vol": lift2, "k_surf_rk": surf}
+
+
+def geometry_of(m, geo):
+    """(ngeo, element maps) of a curved variant of mesh m (inputs.box_geometry), or None."""
+    if not geo:
+        return None
+    from paper_2208_05310_gb300 import inputs
+    return geo["ngeo"], inputs.box_geometry(m["dim"], m["n"], m["lo"], m["hi"], geo["ngeo"], amp=geo["amp"])
 
 
 def workload_c5(scale=1):
@@ -207,8 +221,9 @@ def oracle_rate(wl, seconds_target=15.0, steps=None, sub=(6, 6, None)):
     h = [(m["hi"][d] - m["lo"][d]) / m["n"][d] for d in range(dim)]
     nsub = [sub[d] if sub[d] else m["n"][d] for d in range(dim)]
     hi = [m["lo"][d] + nsub[d] * h[d] for d in range(dim)]
+    geo = geometry_of(dict(m, n=nsub, hi=hi), wl.get("geometry"))
     mesh = orc.make_mesh(dim, m["N"], nsub + [1] * (3 - dim), m["lo"] + [0.0] * (3 - dim), hi + [1.0] * (3 - dim),
-                         m["periodic"] + [1] * (3 - dim), m["walls"])
+                         m["periodic"] + [1] * (3 - dim), m["walls"], geometry=geo)
     o = orc.Oracle(mesh, orc.make_params(**wl["params"]))
     rv, rl = orc.maxwell(wl["T0"])
     width = orc.interface_width(wl["T0"], 5.0, wl["params"]["gammaK"])
@@ -300,8 +315,12 @@ def run_ours(args, wl, rank, world, local_rank):
         ctx = dgk.Context(device=local_rank)
         ctx.set_params(rk=wl["rk"], precision=precision, **wl["params"])
         dim = m["dim"]
-        ctx.mesh_box(dim, m["N"], m["n"] + [1] * (3 - dim), m["lo"] + [0.0] * (3 - dim), m["hi"] + [1.0] * (3 - dim),
-                     m["periodic"] + [1] * (3 - dim), m["walls"])
+        geo = geometry_of(m, wl.get("geometry"))
+        if geo:
+            ctx.mesh_curved(dim, m["N"], m["n"] + [1] * (3 - dim), m["periodic"] + [1] * (3 - dim), m["walls"], *geo)
+        else:
+            ctx.mesh_box(dim, m["N"], m["n"] + [1] * (3 - dim), m["lo"] + [0.0] * (3 - dim),
+                         m["hi"] + [1.0] * (3 - dim), m["periodic"] + [1] * (3 - dim), m["walls"])
         rv, rl = dgk.maxwell(wl["T0"])
         width = dgk.interface_width(wl["T0"], wl["params"]["cv"], wl["params"]["gammaK"])
         ctx.set_primitive(primitive_state(wl, ctx.node_coords(), rv, rl, width))
@@ -343,20 +362,21 @@ def run_ours(args, wl, rank, world, local_rank):
     barrier()
     ctx.run(args.steps, dt)
     ktimes = {}
-    for k, name in enumerate(("k_lift1", "k_lift2vol", "k_surf_rk")):
+    curved = bool(wl.get("geometry"))
+    for k, name in enumerate(("k_lift1c", "k_lift2volc", "k_surf_rk") if curved else ("k_lift1", "k_lift2vol", "k_surf_rk")):
         tot, cnt = ctx.kernel_time(k)
         ktimes[name] = (tot, cnt)
     ctx.set_timing(False)
     ctx.status()
     rsize = 4 if args.precision == "fp32bulk" else 8
-    kb = kernel_bytes_per_node(m["dim"], m["N"], rsize, wl["params"].get("flux", "rusanov"))
+    kb = kernel_bytes_per_node(m["dim"], m["N"], rsize, wl["params"].get("flux", "rusanov"), curved=curved)
     total_k = sum(t for t, _ in ktimes.values())
     dom = max(ktimes, key=lambda k: ktimes[k][0])
     avg_ms = ktimes[dom][0] / max(ktimes[dom][1], 1)
     alg_bytes = kb[dom] * dof
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
-    traffic = ncu_traffic(dom, args.workload + ("_fp32" if rsize == 4 else "_fp64"))
+    traffic = ncu_traffic(dom, args.workload + ("curved" if curved else "") + ("_fp32" if rsize == 4 else "_fp64"))
     roofline = dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=traffic,
                     kernel=dom, peak_kind=peak_kind, alg_bytes_per_launch=alg_bytes,
                     avg_launch_ms=avg_ms,
@@ -600,6 +620,9 @@ def main():
                     help="0: the original NSK model (the workload's walls become periodic)")
     ap.add_argument("--walls", default="noslip", choices=["noslip", "slip"],
                     help="slip: generalized Navier-slip walls (gamma_1..4 = 1e-5, 0.1, 0.05, 1)")
+    ap.add_argument("--mesh", default="box", choices=["box", "curved"],
+                    help="curved: the workload's box mapped to curved elements (degree-2 element maps of "
+                         "x_k + 0.02 L_k sin(2 pi x_{k+1}/L_{k+1}); the walls are bent)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -625,6 +648,12 @@ def main():
         # explicit step diverge on this mesh, in the oracle as well
         wl["mesh"] = dict(wl["mesh"], walls={f: (Tw, th, 1e-5, 0.1, 0.05, 1.0) for f, (Tw, th) in wl["mesh"]["walls"].items()})
         wl["name"] += ", Navier-slip walls"
+    if args.mesh == "curved":
+        if "batch" in wl or args.flux == "hllc" or args.walls != "noslip":
+            print(json.dumps({"error": "curved elements: single problems, Rusanov flux, no-slip walls"}))
+            return 2
+        wl["geometry"] = dict(ngeo=2, amp=0.02)
+        wl["name"] += ", curved elements (degree-2 maps, walls bent by 2% of the height)"
     if args.impl == "reference":
         return run_reference(args, wl, rank, world)
     if world > 1:

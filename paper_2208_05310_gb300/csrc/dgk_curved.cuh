@@ -21,7 +21,26 @@
 
 #include "dgk_kernels.cuh"
 
+// Resident threads per SM requested for the curved lifting kernels, as a register budget
+// (65536 / threads); 0 leaves the choice to the compiler.  The FP64 form asks for half.
+#ifndef DGK_THREADS_LIFT1C
+#define DGK_THREADS_LIFT1C 1728
+#endif
+#ifndef DGK_THREADS_LIFT2C
+#define DGK_THREADS_LIFT2C 864
+#endif
+// 1: ask for the largest shared-memory carveout for k_lift2volc (its blocks hold 43 KB
+// in the 3D N = 5 FP32-bulk form)
+#ifndef DGK_CURVED_CARVEOUT
+#define DGK_CURVED_CARVEOUT 1
+#endif
+
 namespace dgk {
+
+__host__ __device__ constexpr int curved_min_blocks(int threads_per_block, int threads_per_sm)
+{
+    return threads_per_sm > 0 ? min_blocks(threads_per_block, threads_per_sm) : 1;
+}
 
 // Face record of a curved face point:
 //   U (NV) | d u_k/d x_j at DU + j D + k (D*D) | grad T (D) | grad c (D) | lap c
@@ -344,7 +363,8 @@ __device__ __forceinline__ void lift1c_body(const Ctx<R> &a, long long blk, unsi
 }
 
 template <int D, int N, typename R>
-__global__ void __launch_bounds__(Shape<D, N>::NT) k_lift1c(KArgs<R> args)
+__global__ void __launch_bounds__(Shape<D, N>::NT, curved_min_blocks(Shape<D, N>::NT, DGK_THREADS_LIFT1C / (int)(sizeof(R) / 4)))
+    k_lift1c(KArgs<R> args)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const Ctx<R> a{args.v, args.ph, args.pr, args.op};
@@ -727,7 +747,8 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
 }
 
 template <int D, int N, typename R>
-__global__ void __launch_bounds__(Shape<D, N>::NT) k_lift2volc(KArgs<R> args)
+__global__ void __launch_bounds__(Shape<D, N>::NT, curved_min_blocks(Shape<D, N>::NT, DGK_THREADS_LIFT2C / (int)(sizeof(R) / 4)))
+    k_lift2volc(KArgs<R> args)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const Ctx<R> a{args.v, args.ph, args.pr, args.op};
@@ -758,6 +779,10 @@ struct CurvedLauncher {
         cudaError_t err;
         if ((err = cudaFuncSetAttribute(k_lift1c<D, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_lift1))) return err;
         if ((err = cudaFuncSetAttribute(k_lift2volc<D, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_lift2)))
+            return err;
+        if (DGK_CURVED_CARVEOUT &&
+            (err = cudaFuncSetAttribute(k_lift2volc<D, N, R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared)))
             return err;
         if ((err = cudaFuncSetAttribute(k_surf_rk<D, N, R, 0, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_surf)))
             return err;

@@ -1000,7 +1000,9 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
     // issue the node loads first so that their latency overlaps the face phase
     R utv[NV];
     double u0[NV], g0[NV];
+    R iJ = R(0);  // curved elements: 1/J of the node
     if (t.valid) {
+        if (GEO) iJ = a.v.met[((long long)(D * D) * ne + t.e) * NP + t.n];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const long long idx = ((long long)v * ne + t.e) * NP + t.n;
@@ -1044,7 +1046,6 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
         // (curved elements: (1/J) l_i(+-1)/w_i)
         R Lp[D], Lm[D];
         int fpd[D];
-        const R iJ = GEO ? a.v.met[((long long)(D * D) * ne + t.e) * NP + t.n] : R(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             const int i = ncoord<P>(t.n, d);
