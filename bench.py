@@ -108,10 +108,12 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def kernel_sources_sha():
+def kernel_sources_sha(curved=False):
+    """Hash of the sources of the stage kernels (with the curved-element kernels for a
+    curved workload): a committed ncu summary counts only while it matches."""
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2208_05310_gb300", "csrc")
-    for fn in ("dgk_common.cuh", "dgk_kernels.cuh"):
+    for fn in ("dgk_common.cuh", "dgk_kernels.cuh") + (("dgk_curved.cuh",) if curved else ()):
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -129,7 +131,7 @@ def ncu_traffic(kernel, workload):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha1") != kernel_sources_sha():
+    if vals.get("kernel_source_sha1") != kernel_sources_sha(curved="curved" in workload):
         return None
     try:
         return float(vals["dram_bytes_per_launch_full"])
