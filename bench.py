@@ -54,6 +54,11 @@ def kernel_bytes_per_node(dim, N, rsize, flux="rusanov", curved=False):
     return {"k_lift1": lift1, "k_lift2vol": lift2, "k_surf_rk": surf}
 
 
+# element maps of the curved variant of a workload (`--mesh curved`): degree 2, walls
+# bent by 2% of the domain height
+CURVED_GEOMETRY = dict(ngeo=2, amp=0.02)
+
+
 def geometry_of(m, geo):
     """(ngeo, element maps) of a curved variant of mesh m (inputs.box_geometry), or None."""
     if not geo:
@@ -654,7 +659,7 @@ def main():
         if "batch" in wl or args.flux == "hllc" or args.walls != "noslip":
             print(json.dumps({"error": "curved elements: single problems, Rusanov flux, no-slip walls"}))
             return 2
-        wl["geometry"] = dict(ngeo=2, amp=0.02)
+        wl["geometry"] = dict(CURVED_GEOMETRY)
         wl["name"] += ", curved elements (degree-2 maps, walls bent by 2% of the height)"
     if args.impl == "reference":
         return run_reference(args, wl, rank, world)
