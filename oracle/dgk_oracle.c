@@ -296,6 +296,7 @@ typedef struct {
     /* curved elements (Sec. 3.1: curvilinear hexahedra with metric terms) */
     int curved, ngeo;
     const double *xgeo; /* [d][e][(ngeo+1)^d], the caller's */
+    const int *conn;    /* unstructured connectivity [e][2d][3], the caller's, or NULL */
     double *Ja;         /* [e][n][dir][k]: J a^dir_k (contravariant basis times J) at the nodes */
     double *Jn;         /* [e][n]: Jacobian J at the nodes */
     double *Jf;         /* [e][f][fp][k]: J a^dir_k at the face points, f = 2 dir + side */
@@ -356,9 +357,11 @@ static int setup(const or_mesh *m, const or_params *p, ctx_t *c)
             c->Dhat[i * c->P + j] = -(c->w[j] / c->w[i]) * D[j * c->P + i];
     or_lagrange_at(c->N, c->xi, -1.0, c->lm);
     or_lagrange_at(c->N, c->xi, 1.0, c->lp);
+    if (m->conn && !m->xgeo) return -1;
     if (m->xgeo) {
         c->ngeo = m->ngeo;
         c->xgeo = m->xgeo;
+        c->conn = m->conn;
         if (m->ngeo < 1 || m->ngeo > MAXG - 1) return -1;
         if (c->d == 2 ? m->ngeo > c->N : 2 * m->ngeo > c->N) return -1;
         if (p->flux != 0) return -1;
@@ -409,6 +412,10 @@ static int fp_to_node(const ctx_t *c, int fp, int d, int l)
 /* neighbour of element e across face (d, s) (s = 0: minus side, 1: plus side); -1 at a wall */
 static long neighbour(const ctx_t *c, long e, int d, int s)
 {
+    if (c->conn) {
+        long v = c->conn[((size_t)e * 2 * c->d + 2 * d + s) * 3];
+        return v >= 0 ? v : -1;
+    }
     long co[3];
     co[0] = e % c->n[0];
     co[1] = (e / c->n[0]) % c->n[1];
@@ -419,6 +426,32 @@ static long neighbour(const ctx_t *c, long e, int d, int s)
         co[d] = (co[d] + c->n[d]) % c->n[d];
     }
     return co[0] + c->n[0] * (co[1] + (long)c->n[1] * co[2]);
+}
+
+/* The neighbour's face facing face f of element e (box: the opposite face). */
+static int nb_face(const ctx_t *c, long e, int f)
+{
+    if (c->conn) return c->conn[((size_t)e * 2 * c->d + f) * 3 + 1];
+    return 2 * (f / 2) + 1 - f % 2;
+}
+
+/* The neighbour's face point matching face point fp of face f of element e (box: fp). */
+static int nb_fp(const ctx_t *c, long e, int f, int fp)
+{
+    if (!c->conn) return fp;
+    int o = c->conn[((size_t)e * 2 * c->d + f) * 3 + 2], N = c->N;
+    int a = fp % c->P, b = fp / c->P;
+    int u = (o & 1) ? b : a, v = (o & 1) ? a : b;
+    if (o & 2) u = N - u;
+    if (o & 4) v = N - v;
+    return u + c->P * v;
+}
+
+/* Wall table entry of face f of element e (box: f itself). */
+static int wall_of(const ctx_t *c, long e, int f)
+{
+    if (c->conn) return -1 - c->conn[((size_t)e * 2 * c->d + f) * 3];
+    return f;
 }
 
 /* ======================================================================== */
@@ -525,7 +558,7 @@ static int setup_curved(ctx_t *c)
         }
         for (int f = 0; f < nf; ++f) {
             int dir = f / 2, s = f % 2;
-            if (s == 0 && neighbour(c, e, dir, 0) >= 0) continue;
+            if (!c->conn && s == 0 && neighbour(c, e, dir, 0) >= 0) continue;
             for (int fp = 0; fp < nfp; ++fp) {
                 int n0 = fp_to_node(c, fp, dir, 0);
                 double xi[3] = {0, 0, 0}, X[3], dX[3][3], Ja[3][3];
@@ -537,15 +570,33 @@ static int setup_curved(ctx_t *c)
             }
         }
     }
-    for (long e = 0; e < ne; ++e)
-        for (int dir = 0; dir < d; ++dir) {
-            long nb = neighbour(c, e, dir, 0);
-            if (nb < 0) continue;
-            for (int fp = 0; fp < nfp; ++fp)
-                for (int k = 0; k < 3; ++k)
-                    c->Jf[(((size_t)e * nf + 2 * dir) * nfp + fp) * 3 + k] =
-                        c->Jf[(((size_t)nb * nf + 2 * dir + 1) * nfp + fp) * 3 + k];
-        }
+    if (c->conn) {
+        /* unstructured: a shared face takes the metric of the element with the smaller
+           index (of the smaller face for an element facing itself), in the other
+           element's frame: the outward normals are opposite, J a^dir = nsign * outward */
+        for (long e = 0; e < ne; ++e)
+            for (int f = 0; f < nf; ++f) {
+                long nb = neighbour(c, e, f / 2, f % 2);
+                int fo = nb_face(c, e, f);
+                if (nb < 0 || nb < e || (nb == e && fo < f)) continue;
+                double sg = -((f % 2) ? 1.0 : -1.0) * ((fo % 2) ? 1.0 : -1.0);
+                for (int fp = 0; fp < nfp; ++fp) {
+                    int fq = nb_fp(c, e, f, fp);
+                    for (int k = 0; k < 3; ++k)
+                        c->Jf[(((size_t)nb * nf + fo) * nfp + fq) * 3 + k] = sg * c->Jf[(((size_t)e * nf + f) * nfp + fp) * 3 + k];
+                }
+            }
+    } else {
+        for (long e = 0; e < ne; ++e)
+            for (int dir = 0; dir < d; ++dir) {
+                long nb = neighbour(c, e, dir, 0);
+                if (nb < 0) continue;
+                for (int fp = 0; fp < nfp; ++fp)
+                    for (int k = 0; k < 3; ++k)
+                        c->Jf[(((size_t)e * nf + 2 * dir) * nfp + fp) * 3 + k] =
+                            c->Jf[(((size_t)nb * nf + 2 * dir + 1) * nfp + fp) * 3 + k];
+            }
+    }
     if (bad) { teardown(c); return -3; }
     return 0;
 }
@@ -1238,11 +1289,11 @@ static void lift_pass1_c(const ctx_t *c, const double *q, const double *tr, doub
         double fs[6 * MAXP * MAXP], out[3 * MAXP * MAXP * MAXP];
         for (int v = 0; v < nl; ++v) {
             for (int f = 0; f < nf; ++f) {
-                int dir = f / 2, s = f % 2, fo = 2 * dir + (1 - s);
+                int dir = f / 2, s = f % 2, fo = nb_face(c, e, f);
                 long nb = neighbour(c, e, dir, s);
                 for (int fp = 0; fp < nfp; ++fp) {
                     double own = tr[FIDX(v, e, f, fp, ne, nf, nfp)];
-                    if (nb >= 0) fs[f * nfp + fp] = 0.5 * (own + tr[FIDX(v, nb, fo, fp, ne, nf, nfp)]);
+                    if (nb >= 0) fs[f * nfp + fp] = 0.5 * (own + tr[FIDX(v, nb, fo, nb_fp(c, e, f, fp), ne, nf, nfp)]);
                     else fs[f * nfp + fp] = (v >= 1 && v <= d) ? 0.0 : own;
                 }
             }
@@ -1279,15 +1330,16 @@ static void lift_pass2_c(const ctx_t *c, const double *T, const double *grad, co
     for (long e = 0; e < ne; ++e) {
         double Ts[6 * MAXP * MAXP], Gs[3][6 * MAXP * MAXP], out[3 * MAXP * MAXP * MAXP];
         for (int f = 0; f < nf; ++f) {
-            int dir = f / 2, s = f % 2, fo = 2 * dir + (1 - s);
+            int dir = f / 2, s = f % 2, fo = nb_face(c, e, f);
             long nb = neighbour(c, e, dir, s);
             for (int fp = 0; fp < nfp; ++fp) {
                 double tOwn = trT[((size_t)e * nf + f) * nfp + fp];
+                int fq = nb_fp(c, e, f, fp);
                 if (nb >= 0) {
-                    Ts[f * nfp + fp] = 0.5 * (tOwn + trT[((size_t)nb * nf + fo) * nfp + fp]);
+                    Ts[f * nfp + fp] = 0.5 * (tOwn + trT[((size_t)nb * nf + fo) * nfp + fq]);
                     for (int k = 0; k < d; ++k)
                         Gs[k][f * nfp + fp] = 0.5 * (trG[FIDX(k, e, f, fp, ne, nf, nfp)] +
-                                                     trG[FIDX(k, nb, fo, fp, ne, nf, nfp)]);
+                                                     trG[FIDX(k, nb, fo, fq, ne, nf, nfp)]);
                 } else {
                     double nh[3], gm[3] = {0, 0, 0}, gmn = 0.0;
                     face_normal(c, e, f, fp, nh);
@@ -1295,8 +1347,9 @@ static void lift_pass2_c(const ctx_t *c, const double *T, const double *grad, co
                         gm[k] = trG[FIDX(k, e, f, fp, ne, nf, nfp)];
                         gmn += gm[k] * nh[k];
                     }
-                    double gn = wall_gn(c, f, trq[FIDX(vc, e, f, fp, ne, nf, nfp)], 0.0);
-                    Ts[f * nfp + fp] = c->wall_T[f];
+                    int w = wall_of(c, e, f);
+                    double gn = wall_gn(c, w, trq[FIDX(vc, e, f, fp, ne, nf, nfp)], 0.0);
+                    Ts[f * nfp + fp] = c->wall_T[w];
                     for (int k = 0; k < d; ++k) Gs[k][f * nfp + fp] = gm[k] + (gn - gmn) * nh[k];
                 }
             }
@@ -1442,10 +1495,11 @@ static int rhs_core_c(const ctx_t *c, const double *U, double *Ut, double t, or_
 #pragma omp parallel for schedule(static)
     for (long e = 0; e < ne; ++e) {
         for (int f = 0; f < nf; ++f) {
-            int dir = f / 2, s = f % 2, fo = 2 * dir + (1 - s);
+            int dir = f / 2, s = f % 2, fo = nb_face(c, e, f);
             long nb = neighbour(c, e, dir, s);
             for (int fp = 0; fp < nfp; ++fp) {
                 double Uo[8], go[24], gTo[3], lapo, Fstar[8], a[3];
+                int fq = nb_fp(c, e, f, fp);
                 for (int k = 0; k < 3; ++k) a[k] = JF(c, e, f, fp, k);
                 for (int v = 0; v < nv; ++v) Uo[v] = trall[FIDX(v, e, f, fp, ne, nf, nfp)];
                 for (int k = 0; k < d * nl; ++k) go[k] = trall[FIDX(nv + k, e, f, fp, ne, nf, nfp)];
@@ -1453,10 +1507,10 @@ static int rhs_core_c(const ctx_t *c, const double *U, double *Ut, double t, or_
                 lapo = trall[FIDX(nv + d * nl + d, e, f, fp, ne, nf, nfp)];
                 if (nb >= 0) {
                     double Un[8], gn[24], gTn[3], lapn;
-                    for (int v = 0; v < nv; ++v) Un[v] = trall[FIDX(v, nb, fo, fp, ne, nf, nfp)];
-                    for (int k = 0; k < d * nl; ++k) gn[k] = trall[FIDX(nv + k, nb, fo, fp, ne, nf, nfp)];
-                    for (int k = 0; k < d; ++k) gTn[k] = trall[FIDX(nv + d * nl + k, nb, fo, fp, ne, nf, nfp)];
-                    lapn = trall[FIDX(nv + d * nl + d, nb, fo, fp, ne, nf, nfp)];
+                    for (int v = 0; v < nv; ++v) Un[v] = trall[FIDX(v, nb, fo, fq, ne, nf, nfp)];
+                    for (int k = 0; k < d * nl; ++k) gn[k] = trall[FIDX(nv + k, nb, fo, fq, ne, nf, nfp)];
+                    for (int k = 0; k < d; ++k) gTn[k] = trall[FIDX(nv + d * nl + k, nb, fo, fq, ne, nf, nfp)];
+                    lapn = trall[FIDX(nv + d * nl + d, nb, fo, fq, ne, nf, nfp)];
                     const double *UL = s ? Uo : Un, *UR = s ? Un : Uo;
                     const double *gL = s ? go : gn, *gR = s ? gn : go;
                     const double *tL = s ? gTo : gTn, *tR = s ? gTn : gTo;
@@ -1469,7 +1523,7 @@ static int rhs_core_c(const ctx_t *c, const double *U, double *Ut, double t, or_
                 } else {
                     double nh[3], Fn[8];
                     double sa = face_normal(c, e, f, fp, nh);
-                    wall_flux_c(c, f, Uo, go, gTo, nh, Fn);
+                    wall_flux_c(c, wall_of(c, e, f), Uo, go, gTo, nh, Fn);
                     double nsign = s ? 1.0 : -1.0;
                     for (int v = 0; v < nv; ++v) Fstar[v] = nsign * sa * Fn[v];
                 }

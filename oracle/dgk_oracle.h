@@ -46,6 +46,15 @@ typedef struct {
        Rusanov flux only. */
     int ngeo;
     const double *xgeo;
+    /* Unstructured connectivity (optional, with xgeo; NULL: the box's).  For face
+       f = 2 dir + side of element e, conn[(e * 2dim + f) * 3 + 0..2] = (neighbour element,
+       the neighbour's face, orientation), or (-1 - w, 0, 0) for a face on wall w of the
+       wall table above.  Orientation o maps the face point (a, b) of e's face (tangential
+       indices in increasing direction order, a fastest) to the neighbour's face point
+       (a', b'): (u, v) = o & 1 ? (b, a) : (a, b); a' = o & 2 ? N - u : u;
+       b' = o & 4 ? N - v : v (2D: one index, bit 1 only).  Elements may have any
+       orientation-preserving local frame. */
+    const int *conn;
 } or_mesh;
 
 typedef struct {

@@ -175,3 +175,154 @@ def box_geometry(dim, n, lo, hi, ngeo, amp=0.0, rotation=None):
         R = np.asarray(rotation, dtype=np.float64)
         y = np.einsum("kj,jeg->keg", R, y)
     return y
+
+
+def box_connectivity(dim, n, periodic):
+    """The box's element connectivity in the unstructured format: conn[e][f] =
+    (neighbour, its face, orientation 0), or (-1 - f, 0, 0) on the wall of box face f."""
+    n = [int(v) for v in n[:dim]]
+    ne = int(np.prod(n))
+    conn = np.zeros((ne, 2 * dim, 3), dtype=np.int32)
+    stride = [1, n[0], n[0] * (n[1] if dim > 1 else 1)]
+    for e in range(ne):
+        co = [e % n[0], (e // n[0]) % n[1]] + ([e // (n[0] * n[1])] if dim == 3 else [])
+        for d in range(dim):
+            for s in range(2):
+                f = 2 * d + s
+                c = co[d] + (1 if s else -1)
+                if c < 0 or c >= n[d]:
+                    if not periodic[d]:
+                        conn[e, f] = (-1 - f, 0, 0)
+                        continue
+                    c %= n[d]
+                conn[e, f] = (e + (c - co[d]) * stride[d], 2 * d + 1 - s, 0)
+    return conn
+
+
+def _frames(dim, ne, rng):
+    """Random orientation-preserving changes of the reference frame, one per element:
+    new axis a is old axis perm[a] with sign sgn[a] (xi_perm[a] = sgn[a] eta_a)."""
+    import itertools
+    frames = []
+    for p in itertools.permutations(range(dim)):
+        inv = sum(1 for i in range(dim) for j in range(i + 1, dim) if p[i] > p[j])
+        for sg in itertools.product((1, -1), repeat=dim):
+            if (-1) ** inv * int(np.prod(sg)) == 1:
+                frames.append((p, sg))
+    pick = rng.integers(0, len(frames), ne)
+    return [frames[i] for i in pick]
+
+
+def _old_index(dim, K, frame, idx):
+    """Old tensor indices (along old axes) of the new tensor index vector idx."""
+    p, sg = frame
+    old = [0] * dim
+    for a in range(dim):
+        old[p[a]] = idx[a] if sg[a] > 0 else K - 1 - idx[a]
+    return old
+
+
+def reoriented_mesh(dim, N, n, periodic, ngeo, xgeo, seed):
+    """The same physical mesh as the box mesh (n, periodic) with element maps xgeo, with
+    the elements renumbered at random and each given a random orientation-preserving
+    local frame.  Returns (xgeo', conn', node_index): node_index[e'][n'] is the flat
+    index e * NP + n of the same node in the box numbering, so that a nodal array A of
+    the box mesh is A[..., node_index] on the new one (the physical components of vectors
+    are unchanged)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = [int(v) for v in n[:dim]]
+    ne = int(np.prod(n))
+    P, G = N + 1, ngeo + 1
+    NP, NG = P ** dim, G ** dim
+    order = rng.permutation(ne)          # new element k is old element order[k]
+    new_of = np.empty(ne, dtype=np.int64)
+    new_of[order] = np.arange(ne)
+    frames = _frames(dim, ne, rng)       # frame of new element k
+    box = box_connectivity(dim, n, periodic)
+
+    def flat(idx, K):
+        return sum(idx[a] * K ** a for a in range(dim))
+
+    def unflat(v, K):
+        return [(v // K ** a) % K for a in range(dim)]
+
+    xnew = np.empty((dim, ne, NG))
+    node_index = np.empty((ne, NP), dtype=np.int64)
+    for k in range(ne):
+        e, fr = order[k], frames[k]
+        for g in range(NG):
+            xnew[:, k, g] = xgeo[:, e, flat(_old_index(dim, G, fr, unflat(g, G)), G)]
+        for q in range(NP):
+            node_index[k, q] = e * NP + flat(_old_index(dim, P, fr, unflat(q, P)), P)
+
+    def new_face(fr, d_old, s_old):
+        p, sg = fr
+        a = p.index(d_old)
+        return 2 * a + (s_old if sg[a] > 0 else 1 - s_old)
+
+    def face_old_tangential(fr, f, t):
+        """old tensor indices of the new face point with tangential indices t (new axes
+        other than the face's, increasing)"""
+        a_n = f // 2
+        idx, j = [0] * dim, 0
+        for a in range(dim):
+            if a == a_n:
+                idx[a] = (P - 1) * (f % 2)
+            else:
+                idx[a] = t[j]
+                j += 1
+        return _old_index(dim, P, fr, idx)
+
+    conn = np.zeros((ne, 2 * dim, 3), dtype=np.int32)
+    nt = P ** (dim - 1)
+    for k in range(ne):
+        e, fr = order[k], frames[k]
+        for f in range(2 * dim):
+            # the old face this new face is
+            a = f // 2
+            d_old, sg = fr[0][a], fr[1][a]
+            s_old = (f % 2) if sg > 0 else 1 - (f % 2)
+            nb_old, fo_old, _ = box[e, 2 * d_old + s_old]
+            if nb_old < 0:
+                conn[k, f] = (nb_old, 0, 0)
+                continue
+            k2 = new_of[nb_old]
+            fr2 = frames[k2]
+            f2 = new_face(fr2, fo_old // 2, fo_old % 2)
+            # where each face point of (k, f) lands on (k2, f2): the structured faces
+            # match by the old tangential indices
+            want = []
+            for tp in range(nt):
+                t = [tp % P, tp // P][:dim - 1]
+                old = face_old_tangential(fr, f, t)
+                old_t = [old[b] for b in range(dim) if b != d_old]
+                # find the tangential indices on (k2, f2) with the same old tangential indices
+                hit = None
+                for tq in range(nt):
+                    t2 = [tq % P, tq // P][:dim - 1]
+                    old2 = face_old_tangential(fr2, f2, t2)
+                    if [old2[b] for b in range(dim) if b != d_old] == old_t:
+                        hit = tq
+                        break
+                want.append(hit)
+            o_found = None
+            for o in range(8 if dim == 3 else 3):
+                if dim == 2 and o & 5:
+                    continue
+                ok = True
+                for tp in range(nt):
+                    aa, bb = tp % P, tp // P
+                    u, v = (bb, aa) if o & 1 else (aa, bb)
+                    if o & 2:
+                        u = P - 1 - u
+                    if o & 4:
+                        v = P - 1 - v
+                    if u + P * v != want[tp]:
+                        ok = False
+                        break
+                if ok:
+                    o_found = o
+                    break
+            assert o_found is not None
+            conn[k, f] = (k2, f2, o_found)
+    return xnew, conn, node_index

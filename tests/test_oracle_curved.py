@@ -187,3 +187,55 @@ def test_curved_input_checks(orc):
     assert sizes(mesh_spec(2, 3, [2, 2], periodic=[1, 0], walls=slip, geometry=dict(ngeo=1))) != 0
     with pytest.raises(RuntimeError):
         oracle_objects(orc, mesh_spec(2, 3, [2, 2], geometry=dict(ngeo=1)), dict(PAPER_PARAMS, model=2, flux="hllc"))
+
+
+UNSTRUCTURED_CASES = {
+    "2d_walls": (mesh_spec(2, 3, [4, 3], periodic=[1, 0], walls=WALLS2, geometry=dict(ngeo=2, amp=0.05)), 3),
+    "3d_walls": (mesh_spec(3, 3, [2, 3, 2], periodic=[1, 1, 0], walls=WALLS3, geometry=dict(ngeo=1, amp=0.05)), 4),
+    "3d_periodic": (mesh_spec(3, 4, [2, 2, 3], geometry=dict(ngeo=2, amp=0.04)), 5),
+}
+
+
+def _unstructured(orc, ms, seed, params):
+    from cases import geometry_array
+    d = ms["dim"]
+    ngeo, xg = geometry_array(ms)
+    xn, conn, ni = inputs.reoriented_mesh(d, ms["N"], ms["n"], ms["periodic"], ngeo, xg, seed)
+    m = orc.make_mesh(d, ms["N"], ms["n"] + [1] * (3 - d), [0.0] * 3, [1.0] * 3, ms["periodic"] + [1] * (3 - d),
+                      ms["walls"], geometry=(ngeo, xn), conn=conn)
+    return orc.Oracle(m, orc.make_params(**params)), conn, ni
+
+
+@pytest.mark.parametrize("name", sorted(UNSTRUCTURED_CASES))
+def test_renumbered_reoriented_mesh(orc, name):
+    """The same physical mesh with its elements renumbered and each element in a random
+    orientation-preserving local frame, connected through the unstructured tables
+    (neighbour, its face, face-point orientation): node coordinates, state, right-hand
+    side, max_dt and diagnostics equal those of the structured mesh (permuted)."""
+    ms, seed = UNSTRUCTURED_CASES[name]
+    d = ms["dim"]
+    o1 = oracle_objects(orc, ms, DT_PARAMS)
+    o2, conn, ni = _unstructured(orc, ms, seed, DT_PARAMS)
+    assert np.abs(o2.node_coords() - o1.node_coords().reshape(d, -1)[:, ni]).max() < 1e-14
+    prim = inputs.random_admissible(d, o1.nelem, o1.np, 5)
+    U1 = o1.set_primitive(prim)
+    U2 = o2.set_primitive(prim.reshape(prim.shape[0], -1)[:, ni])
+    perm = lambda A: A.reshape(A.shape[0], -1)[:, ni]
+    assert np.all(rel_l2(U2, perm(U1)) < 1e-14)
+    err = rel_l2(o2.rhs(U2), perm(o1.rhs(U1)))
+    assert np.all(err < 1e-12), err
+    assert abs(o2.max_dt(U2) / o1.max_dt(U1) - 1) < 1e-13
+    d1, d2 = o1.diagnostics(U1), o2.diagnostics(U2)
+    for k in d1:
+        assert abs(d2[k] - d1[k]) <= 1e-13 * max(1.0, abs(d1[k])), k
+    # the orientations matter: a wrong one on one interior face changes the result
+    bad = conn.copy()
+    e, f = next((e, f) for e in range(bad.shape[0]) for f in range(bad.shape[1]) if bad[e, f, 0] >= 0)
+    bad[e, f, 2] ^= 2
+    from cases import geometry_array
+    ngeo, _ = geometry_array(ms)
+    xn = inputs.reoriented_mesh(d, ms["N"], ms["n"], ms["periodic"], ngeo, geometry_array(ms)[1], seed)[0]
+    m3 = orc.make_mesh(d, ms["N"], ms["n"] + [1] * (3 - d), [0.0] * 3, [1.0] * 3, ms["periodic"] + [1] * (3 - d),
+                       ms["walls"], geometry=(ngeo, xn), conn=bad)
+    o3 = orc.Oracle(m3, orc.make_params(**DT_PARAMS))
+    assert np.any(rel_l2(o3.rhs(o3.set_primitive(prim.reshape(prim.shape[0], -1)[:, ni])), perm(o1.rhs(U1))) > 1e-6)
