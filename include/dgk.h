@@ -141,6 +141,22 @@ int dgk_mesh_box(dgk_ctx *ctx, const dgk_box_mesh *mesh);
    (dim^2 + 1) values per node in the bulk type and in double, and dim values per face
    point. */
 int dgk_mesh_curved(dgk_ctx *ctx, const dgk_box_mesh *mesh, int ngeo, const double *xgeo);
+/* Curved elements with unstructured connectivity (Sec. 3.1: the method on general
+   hexahedral meshes): as dgk_mesh_curved, with the element neighbours given by tables
+   instead of the box's index arithmetic.  mesh gives dim, N, the element count
+   (n[0] n[1] n[2]) and the wall table (wall[w] for the faces that name wall w; those
+   walls' directions must be non-periodic, kind 1); lo/hi and the element layout are
+   ignored.  conn (host, caller-owned, read during the call): for face f = 2 dir + side of
+   element e (in the element's own reference frame), conn[(e * 2dim + f) * 3 + 0..2] =
+   (neighbour element, the neighbour's face, orientation), or (-1 - w, 0, 0) on wall w.
+   Orientation o maps the face point (a, b) of e's face (tangential indices in increasing
+   direction order, a fastest) to the neighbour's (a', b'): (u, v) = o & 1 ? (b, a) : (a, b);
+   a' = o & 2 ? N - u : u; b' = o & 4 ? N - v : v (2D: o = 0 or 2).  Every element may have
+   its own orientation-preserving frame.  The tables must be symmetric (the neighbour's
+   entry names e and f back) and match the element maps (the two elements' face metrics
+   agree to 1e-6 relative); otherwise DGK_ERR_ARG.  Fewer than 2^31 elements.  Memory:
+   3 ints per element face on the device. */
+int dgk_mesh_unstructured(dgk_ctx *ctx, const dgk_box_mesh *mesh, int ngeo, const double *xgeo, const int *conn);
 /* Problem sizes: elements, nodes per element (N+1)^dim, conserved variables dim+3. */
 int dgk_sizes(const dgk_ctx *ctx, long long *nelem, int *nodes_per_elem, int *nvar);
 /* Node coordinates x[d][e][n] (dim x nelem x np doubles). */

@@ -276,6 +276,7 @@ struct dgk_ctx {
     const dgk::CurvedTable *ct = nullptr;
     void *met = nullptr, *fmet = nullptr;
     double *metd = nullptr;
+    int *conn = nullptr;  // unstructured connectivity on the device, or null
     std::vector<double> xnodes;
     unsigned *status = nullptr;
     unsigned long long *redbuf = nullptr;
@@ -298,13 +299,14 @@ void free_buffers(dgk_ctx *c)
 {
     if (c->metd && (void *)c->metd != c->met) cudaFree(c->metd);
     void *ptrs[] = {c->U,  c->G,   c->Tbuf, c->coef, c->rhsbuf, c->partial, c->Utv,
-                    c->tr1, c->tr2, c->fd,   c->Us,   c->status, c->redbuf, c->met, c->fmet};
+                    c->tr1, c->tr2, c->fd,   c->Us,   c->status, c->redbuf, c->met, c->fmet, c->conn};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     c->U = c->G = c->Tbuf = c->coef = c->rhsbuf = c->partial = nullptr;
     c->Utv = c->tr1 = c->tr2 = c->fd = c->Us = nullptr;
     c->met = c->fmet = nullptr;
     c->metd = nullptr;
+    c->conn = nullptr;
     c->curved = false;
     c->ct = nullptr;
     c->xnodes.clear();
@@ -332,6 +334,7 @@ void fill_args(dgk_ctx *c, dgk::KArgs<R> &a)
     a.v.fd = (R *)c->fd;
     a.v.met = (const R *)c->met;
     a.v.fmet = (const R *)c->fmet;
+    a.v.conn = c->conn;
     a.v.out = c->Tbuf;
     a.v.coef = c->coef;
     a.v.status = c->status;
@@ -708,7 +711,7 @@ int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m)
     return DGK_OK;
 }
 
-int dgk_mesh_curved(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const double *xgeo)
+static int mesh_curved_impl(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const double *xgeo, const int *conn)
 {
     if (!c || !m || !xgeo) return fail(DGK_ERR_ARG, "null argument");
     if (!c->have_params) return fail(DGK_ERR_STATE, "set params before the mesh");
@@ -719,6 +722,28 @@ int dgk_mesh_curved(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const double *x
     for (int f = 0; f < 2 * m->dim; ++f)
         if (!m->periodic[f / 2] && m->wall[f].kind == 2)
             return fail(DGK_ERR_UNSUPPORTED, "curved elements take walls of kind 1 (no-slip contact angle)");
+    if (conn) {
+        // the tables: neighbours in range and pointing back, orientations of the
+        // dimension, walls of the box's wall table (kind 1)
+        long long ne = 1;
+        for (int d = 0; d < m->dim; ++d) ne *= m->n[d];
+        if (ne >= (1LL << 31)) return fail(DGK_ERR_ARG, "unstructured meshes take fewer than 2^31 elements");
+        const int NF = 2 * m->dim;
+        for (long long e = 0; e < ne; ++e)
+            for (int f = 0; f < NF; ++f) {
+                const int *t = conn + (e * NF + f) * 3;
+                if (t[0] < 0) {
+                    const int w = -1 - t[0];
+                    if (w >= NF || m->periodic[w / 2] || m->wall[w].kind != 1)
+                        return fail(DGK_ERR_ARG, "a boundary face names no kind-1 wall of the wall table");
+                    continue;
+                }
+                const bool o_ok = m->dim == 3 ? (t[2] >= 0 && t[2] < 8) : (t[2] == 0 || t[2] == 2);
+                if (t[0] >= ne || t[1] < 0 || t[1] >= NF || !o_ok) return fail(DGK_ERR_ARG, "connectivity entry out of range");
+                const int *back = conn + ((long long)t[0] * NF + t[1]) * 3;
+                if (back[0] != e || back[1] != f) return fail(DGK_ERR_ARG, "connectivity is not symmetric");
+            }
+    }
     int rc = dgk_mesh_box(c, m);  // validates the rest and allocates the stage buffers
     if (rc) return rc;
     c->have_mesh = false;
@@ -729,7 +754,12 @@ int dgk_mesh_curved(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const double *x
     }
     dgk::host::CurvedGeometry geo;
     std::string err;
-    if (!dgk::host::curved_geometry(c->D, c->op1, ngeo, n, per, c->ne, xgeo, geo, err)) return fail(DGK_ERR_ARG, err);
+    if (!dgk::host::curved_geometry(c->D, c->op1, ngeo, n, per, c->ne, xgeo, conn, geo, err)) return fail(DGK_ERR_ARG, err);
+    if (conn) {
+        const size_t nc = (size_t)c->ne * c->NF * 3;
+        DGK_CUDA(cudaMalloc(&c->conn, nc * sizeof(int)));
+        DGK_CUDA(cudaMemcpy(c->conn, conn, nc * sizeof(int), cudaMemcpyHostToDevice));
+    }
     const bool f32 = c->prm.precision == DGK_PREC_FP32BULK;
     c->ct = c->D == 2 ? (f32 ? dgk_ctable_2d_f32(c->N) : dgk_ctable_2d_f64(c->N))
                       : (f32 ? dgk_ctable_3d_f32(c->N) : dgk_ctable_3d_f64(c->N));
@@ -757,6 +787,17 @@ int dgk_mesh_curved(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const double *x
     c->coef_valid = false;
     c->have_mesh = true;
     return DGK_OK;
+}
+
+int dgk_mesh_curved(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const double *xgeo)
+{
+    return mesh_curved_impl(c, m, ngeo, xgeo, nullptr);
+}
+
+int dgk_mesh_unstructured(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const double *xgeo, const int *conn)
+{
+    if (!conn) return fail(DGK_ERR_ARG, "null connectivity");
+    return mesh_curved_impl(c, m, ngeo, xgeo, conn);
 }
 
 int dgk_sizes(const dgk_ctx *c, long long *nelem, int *np, int *nv)

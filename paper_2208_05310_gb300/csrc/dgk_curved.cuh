@@ -123,14 +123,14 @@ __device__ __forceinline__ void flux_vec(const PhysR<R> &ph, const R *a, R rho, 
 }
 
 // Face data of one curved face point from its record r, along the face metric a
-// (oriented along +xi_dir).  Interior: the one-sided flux F . a and the scaled signal
+// (oriented along +xi_dir; w: the wall-table entry of a wall face).  Interior: the one-sided flux F . a and the scaled signal
 // speed |u.a| + s |a|.  Wall (side: 0 minus, 1 plus face): the complete flux along a,
 // |a| nsign F_n with F_n the outward wall flux per unit area for the outward unit normal
 // n = nsign a/|a|: Rusanov against the ghost (rho, m - 2(m.n)n, rho e, c) with equal
 // pressure and signal speed, minus the viscous flux tau(grad u-).n,
 // kappa grad T-.n - gamma_K c- g_n div u-, gamma_K beta g_n (contact-angle g_n).
 template <int D, typename R>
-__device__ __forceinline__ void face_flux_c(const Ctx<R> &a, int f, bool wall, const R *r, const R *av, R *F, R &lam)
+__device__ __forceinline__ void face_flux_c(const Ctx<R> &a, int f, int w, bool wall, const R *r, const R *av, R *F, R &lam)
 {
     using FR = FaceRecC<D>;
     const PhysR<R> &ph = a.pr;
@@ -195,7 +195,7 @@ __device__ __forceinline__ void face_flux_c(const Ctx<R> &a, int f, bool wall, c
         divu += du[k][k];
         gTn += gT[k] * nh[k];
     }
-    const R gn = a.v.wr.K[f] * (c - a.v.wr.rl[f]) * (c - a.v.wr.rv[f]);
+    const R gn = a.v.wr.K[w] * (c - a.v.wr.rl[w]) * (c - a.v.wr.rv[w]);
     R Fv[D + 3];
     Fv[0] = R(0);
 #pragma unroll
@@ -211,6 +211,26 @@ __device__ __forceinline__ void face_flux_c(const Ctx<R> &a, int f, bool wall, c
 #pragma unroll
     for (int v = 0; v < D + 3; ++v)
         F[v] = scale * (R(0.5) * (Fi[v] + Fg[v]) - R(0.5) * lam * (Ug[v] - Ui[v]) - Fv[v]);
+}
+
+// Neighbour across face f of the slot's element: the element index (negative at a wall),
+// the neighbour's facing face fo, the face-point orientation o and the wall-table entry
+// w of a wall face.  Unstructured tables (v.conn) or the box's connectivity.
+template <int D, int N, typename R>
+__device__ __forceinline__ long long face_nbr(const KView<R> &v, const Slot<D, N> &t, int f, int &fo, int &o, int &w)
+{
+    if (v.conn) {
+        const int *c = v.conn + (t.e * (2 * D) + f) * 3;
+        const int nb = c[0];
+        fo = c[1];
+        o = c[2];
+        w = nb < 0 ? -1 - nb : f;
+        return nb;
+    }
+    fo = 2 * (f >> 1) + 1 - (f & 1);
+    o = 0;
+    w = f;
+    return t.nbr(v.g, f);
 }
 
 // Metric plane p of node n of element e (p = dir*D + k: J a^dir_k; p = D*D: 1/J).
@@ -274,10 +294,11 @@ struct CLiftC {
         if (t.valid) {
             sC[t.n] = c;
             for (int q = t.n; q < NF * NFP; q += NP) {
-                const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
+                const int f = q / NFP, fp = q % NFP;
                 const R own = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
-                const long long b = t.nbr(a.v.g, f);
-                sCs[q] = b >= 0 ? R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, D + 1, b, 2 * dir + 1 - side, fp)]) : own;
+                int fo, o, w;
+                const long long b = face_nbr<D, N, R>(a.v, t, f, fo, o, w);
+                sCs[q] = b >= 0 ? R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, D + 1, b, fo, map_fp<S::P>(o, fp))]) : own;
             }
             stage_face_metrics<D, N, R>(a, t, sJf);
         }
@@ -479,13 +500,15 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
         for (int k = 0; k < D; ++k) sQ[(1 + k) * NP + n] = ns.m[k] * ns.irho;
         sQ[(D + 1) * NP + n] = ns.c;
         for (int q = n; q < NF * NFP; q += NP) {
-            const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
-            const long long b = t.nbr(a.v.g, f);
+            const int f = q / NFP, fp = q % NFP;
+            int fo, o, w;
+            const long long b = face_nbr<D, N, R>(a.v, t, f, fo, o, w);
+            const int fq = map_fp<P>(o, fp);
 #pragma unroll
             for (int v = 0; v < NL; ++v) {
                 const R own = a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)];
                 R val;
-                if (b >= 0) val = R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, v, b, 2 * dir + 1 - side, fp)]);
+                if (b >= 0) val = R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, v, b, fo, fq)]);
                 else val = (v >= 1 && v <= D) ? R(0) : own;
                 sQs[(f * NL + v) * NFP + fp] = val;
             }
@@ -501,24 +524,26 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
         const int q = n + j * NP;
         pT[j] = pD[j] = R(0);
         if (t.valid && q < NF * NFP) {
-            const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
-            const long long b = t.nbr(a.v.g, f);
+            const int f = q / NFP, fp = q % NFP, side = f & 1;
+            int fo, o, w;
+            const long long b = face_nbr<D, N, R>(a.v, t, f, fo, o, w);
             const R ownT = a.v.tr2[fidx<NF, NFP>(ne, 0, t.e, f, fp)];
             const R ownD = a.v.tr2[fidx<NF, NFP>(ne, 1, t.e, f, fp)];
             if (b >= 0) {
-                const int fo = 2 * dir + 1 - side;
-                pT[j] = R(0.5) * (ownT + a.v.tr2[fidx<NF, NFP>(ne, 0, b, fo, fp)]);
-                pD[j] = R(0.5) * (ownD + a.v.tr2[fidx<NF, NFP>(ne, 1, b, fo, fp)]);
+                const int fq = map_fp<P>(o, fp);
+                pT[j] = R(0.5) * (ownT + a.v.tr2[fidx<NF, NFP>(ne, 0, b, fo, fq)]);
+                // the neighbour traced grad c . J a along its own face orientation
+                pD[j] = R(0.5) * (ownD + R(facing_sign(f, fo)) * a.v.tr2[fidx<NF, NFP>(ne, 1, b, fo, fq)]);
             } else {
                 const R cm = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
-                const R gn = a.v.wr.K[f] * (cm - a.v.wr.rl[f]) * (cm - a.v.wr.rv[f]);
+                const R gn = a.v.wr.K[w] * (cm - a.v.wr.rl[w]) * (cm - a.v.wr.rv[w]);
                 R a2 = R(0);
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
                     const R x = a.v.fmet[fidx<NF, NFP>(ne, k, t.e, f, fp)];
                     a2 += x * x;
                 }
-                pT[j] = a.v.wr.Tw[f];
+                pT[j] = a.v.wr.Tw[w];
                 pD[j] = (side ? R(1) : R(-1)) * sqrt(a2) * gn;
             }
         }
@@ -727,14 +752,15 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
         const long long st = ne * NF * NFP;
         for (int q = n; q < NF * NFP; q += NP) {
             const int f = q / NFP, fp = q % NFP;
-            const bool wall = t.nbr(a.v.g, f) < 0;
+            int f_nb, o_nb, w;
+            const bool wall = face_nbr<D, N, R>(a.v, t, f, f_nb, o_nb, w) < 0;
             R r[NQ], av[D];
 #pragma unroll
             for (int k = 0; k < NQ; ++k) r[k] = sR[(f * NQ + k) * NFP + fp];
 #pragma unroll
             for (int k = 0; k < D; ++k) av[k] = sJf[(k * NF + f) * NFP + fp];
             R F[NV], lam;
-            face_flux_c<D, R>(a, f, wall, r, av, F, lam);
+            face_flux_c<D, R>(a, f, w, wall, r, av, F, lam);
             const long long fo = (t.e * NF + f) * NFP + fp;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {

@@ -12,6 +12,9 @@
 // discrete metric identities hold and a uniform state is preserved.  The face metric of
 // a face shared by two elements is computed once, from the element on the face's minus
 // side, and used by both (one normal and surface element per face point: conservation).
+// With unstructured connectivity tables the face's owner is the element with the smaller
+// index, and the tables are checked against the element maps (the other element's own
+// face metric must agree with the owner's after the face-point orientation).
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -107,7 +110,7 @@ double cofactors(int D, const double J[3][3], double Ja[3][3])
 }  // namespace
 
 bool curved_geometry(int D, const Operators1D &op, int ngeo, const int n[3], const int periodic[3], long long ne,
-                     const double *xgeo, CurvedGeometry &out, std::string &err)
+                     const double *xgeo, const int *conn, CurvedGeometry &out, std::string &err)
 {
     const int P = op.P, G = ngeo + 1;
     const int NP = D == 2 ? P * P : P * P * P, NFP = D == 2 ? P : P * P, NF = 2 * D;
@@ -178,6 +181,42 @@ bool curved_geometry(int D, const Operators1D &op, int ngeo, const int n[3], con
                 for (int k = 0; k < D; ++k) out.fmet[(((size_t)k * ne + e) * NF + f) * NFP + p] = Ja[dir][k];
             }
         }
+    }
+    if (conn) {
+        // unstructured: a shared face takes the metric of the element with the smaller
+        // index (of the smaller face for an element facing itself), mapped to the other
+        // element's face points and frame (opposite outward normals: J a^dir = nsign *
+        // outward).  The other element's own metric must agree: a check that the tables
+        // match the element maps.
+        for (long long e = 0; e < ne; ++e)
+            for (int f = 0; f < NF; ++f) {
+                const int *c = conn + (e * NF + f) * 3;
+                const long long nb = c[0];
+                const int fo = c[1], o = c[2];
+                if (nb < 0 || nb < e || (nb == e && fo < f)) continue;
+                const double sg = ((f ^ fo) & 1) ? 1.0 : -1.0;
+                for (int p = 0; p < NFP; ++p) {
+                    const int a = p % P, b = p / P;
+                    int u = (o & 1) ? b : a, v = (o & 1) ? a : b;
+                    if (o & 2) u = P - 1 - u;
+                    if (o & 4) v = P - 1 - v;
+                    const int q = u + P * v;
+                    double diff = 0.0, mag = 0.0;
+                    for (int k = 0; k < D; ++k) {
+                        const double own = out.fmet[(((size_t)k * ne + e) * NF + f) * NFP + p];
+                        double &dst = out.fmet[(((size_t)k * ne + nb) * NF + fo) * NFP + q];
+                        diff += (dst - sg * own) * (dst - sg * own);
+                        mag += own * own;
+                        dst = sg * own;
+                    }
+                    if (diff > 1e-12 * mag) {
+                        err = "the connectivity does not match the element maps (element " + std::to_string(e) + ", face " +
+                              std::to_string(f) + ")";
+                        return false;
+                    }
+                }
+            }
+        return true;
     }
     // minus faces with a neighbour take the neighbour's plus-face metric
     const long long stride[3] = {1, n[0], (long long)n[0] * n[1]};

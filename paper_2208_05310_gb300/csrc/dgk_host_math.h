@@ -26,8 +26,10 @@ bool sigma_vl(double T, double gammaK, double &sigma);
 struct CurvedGeometry {
     std::vector<double> met, fmet, x;
 };
+// conn: unstructured connectivity [ne][NF][3] (neighbour or -1 - wall, its face, face-point
+// orientation) or null for the box's; the tables are checked against the element maps.
 bool curved_geometry(int D, const Operators1D &op, int ngeo, const int n[3], const int periodic[3], long long ne,
-                     const double *xgeo, CurvedGeometry &out, std::string &err);
+                     const double *xgeo, const int *conn, CurvedGeometry &out, std::string &err);
 
 }  // namespace host
 }  // namespace dgk

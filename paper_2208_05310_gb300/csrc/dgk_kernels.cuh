@@ -77,6 +77,8 @@ struct KView {
                          // for the HLLC flux the convective pressure and the sound speed
     const R *met;        // curved elements: [D*D+1][ne][NP] J a^dir_k (plane dir*D + k) and 1/J; box: null
     const R *fmet;       // curved elements: [D][ne][NF][NFP] J a^dir_k at the face points; box: null
+    const int *conn;     // unstructured connectivity [ne][NF][3] (neighbour or -1 - wall, its face,
+                         // face-point orientation); null: the box's
     double *out;         // rhs output [NV][ne][NP], or nodal T [ne][NP]
     const double *coef;  // device [A_0..A_4, B_0..B_4, dt] of this problem
     unsigned *status;
@@ -164,6 +166,22 @@ __device__ __forceinline__ long long fidx(long long ne, int v, long long e, int 
 {
     return (((long long)v * ne + e) * NF + f) * NFP + fp;
 }
+
+// The neighbour's face point matching face point fp under orientation o: (u, v) = o & 1 ?
+// (b, a) : (a, b) of fp = a + P b; u and v reversed by bits 1 and 2.
+template <int P>
+__device__ __forceinline__ int map_fp(int o, int fp)
+{
+    const int a = fp % P, b = fp / P;
+    int u = (o & 1) ? b : a, v = (o & 1) ? a : b;
+    if (o & 2) u = P - 1 - u;
+    if (o & 4) v = P - 1 - v;
+    return u + P * v;
+}
+
+// Sign between the face-metric orientations of two facing faces (J a^dir along +xi_dir
+// of each element): +1 when one is a plus and the other a minus face, else -1.
+__device__ __forceinline__ int facing_sign(int f, int fo) { return ((f ^ fo) & 1) ? 1 : -1; }
 
 template <typename R>
 __device__ __forceinline__ void check_state(unsigned *status, R rho, R T, R E)
@@ -1017,21 +1035,34 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
         const long long st = ne * NF * NFP;
         for (int q = t.n; q < NF * NFP; q += NP) {
             const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
-            const long long b = t.nbr(a.v.g, f);
+            // curved elements may come with unstructured connectivity (neighbour, its
+            // face, face-point orientation); the neighbour's one-sided flux is along its
+            // own face metric, of the sign facing_sign relative to this element's
+            long long b;
+            int fo = 2 * dir + 1 - side, fq = fp;
+            if (GEO && a.v.conn) {
+                const int *cn = a.v.conn + (t.e * NF + f) * 3;
+                b = cn[0] < 0 ? -1 : cn[0];
+                fo = cn[1];
+                fq = map_fp<P>(cn[2], fp);
+            } else {
+                b = t.nbr(a.v.g, f);
+            }
             const long long oo = ((long long)t.e * NF + f) * NFP + fp;
             if (b < 0) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) sFs[(f * NV + v) * NFP + fp] = a.v.fd[(NV + v) * st + oo];
             } else {
-                const long long ob = ((long long)b * NF + (2 * dir + 1 - side)) * NFP + fp;
+                const long long ob = ((long long)b * NF + fo) * NFP + fq;
                 const long long iL = side ? oo : ob, iR = side ? ob : oo;
+                const R sL = GEO && !side ? R(facing_sign(f, fo)) : R(1), sR = GEO && side ? R(facing_sign(f, fo)) : R(1);
                 if (FLUX == 1) {
                     hllc_face<D, R>(a.v.fd, st, iL, iR, dir, sFs + f * NV * NFP + fp, NFP);
                 } else {
                     const R lam = fmax(a.v.fd[(2 * NV) * st + iL], a.v.fd[(2 * NV) * st + iR]);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        const R FL = a.v.fd[(NV + v) * st + iL], FR = a.v.fd[(NV + v) * st + iR];
+                        const R FL = sL * a.v.fd[(NV + v) * st + iL], FR = sR * a.v.fd[(NV + v) * st + iR];
                         const R UL = a.v.fd[v * st + iL], UR = a.v.fd[v * st + iR];
                         sFs[(f * NV + v) * NFP + fp] = R(0.5) * (FL + FR) - R(0.5) * lam * (UR - UL);
                     }

@@ -146,6 +146,9 @@ void place(dgk::KArgs<R> &a, unsigned char *base, const double *U, double *Ut, i
     a.v.Us = sizeof(R) == 4 ? reinterpret_cast<R *>(base + off) : nullptr;
     a.v.U = const_cast<double *>(U);
     a.v.G = nullptr;
+    a.v.met = nullptr;  // box meshes: no metric terms, no connectivity tables
+    a.v.fmet = nullptr;
+    a.v.conn = nullptr;
     a.v.out = Ut;
     a.v.coef = nullptr;
 }

@@ -51,7 +51,7 @@ class DgkError(RuntimeError):
     pass
 
 
-EXPORTS = ("dgk_create", "dgk_destroy", "dgk_set_params", "dgk_mesh_box", "dgk_mesh_curved", "dgk_sizes", "dgk_node_coords",
+EXPORTS = ("dgk_create", "dgk_destroy", "dgk_set_params", "dgk_mesh_box", "dgk_mesh_curved", "dgk_mesh_unstructured", "dgk_sizes", "dgk_node_coords",
            "dgk_set_primitive", "dgk_upload_state", "dgk_download_state", "dgk_rhs", "dgk_rk_step", "dgk_run",
            "dgk_max_dt", "dgk_diagnostics", "dgk_status", "dgk_set_timing", "dgk_kernel_time", "dgk_maxwell",
            "dgk_sigma_vl", "dgk_interface_width", "dgk_status_string", "dgk_last_error", "dgk_check_conversions",
@@ -76,6 +76,7 @@ def lib():
         "dgk_set_params": (i, [vp, C.POINTER(DgkParams)]),
         "dgk_mesh_box": (i, [vp, C.POINTER(DgkBoxMesh)]),
         "dgk_mesh_curved": (i, [vp, C.POINTER(DgkBoxMesh), i, dp]),
+        "dgk_mesh_unstructured": (i, [vp, C.POINTER(DgkBoxMesh), i, dp, C.POINTER(C.c_int)]),
         "dgk_sizes": (i, [vp, C.POINTER(C.c_longlong), C.POINTER(i), C.POINTER(i)]),
         "dgk_node_coords": (i, [vp, vp, i]),
         "dgk_set_primitive": (i, [vp, vp, sz, i]),
@@ -241,6 +242,17 @@ class Context:
         x = np.ascontiguousarray(xgeo, dtype=np.float64)
         _check(lib().dgk_mesh_curved(self._h, C.byref(m), int(ngeo), x.ctypes.data_as(C.POINTER(C.c_double))),
                "dgk_mesh_curved")
+        self._sizes(dim)
+
+    def mesh_unstructured(self, dim, N, n, periodic, walls, ngeo, xgeo, conn):
+        """Curved elements with unstructured connectivity (dgk_mesh_unstructured): conn is
+        an int array [nelem][2 dim][3]; n gives the element count as a product and, with
+        periodic, which entries of the wall table (walls) exist."""
+        m = make_box_mesh(dim, N, n, [0.0] * 3, [1.0] * 3, periodic, walls)
+        x = np.ascontiguousarray(xgeo, dtype=np.float64)
+        cn = np.ascontiguousarray(conn, dtype=np.int32)
+        _check(lib().dgk_mesh_unstructured(self._h, C.byref(m), int(ngeo), x.ctypes.data_as(C.POINTER(C.c_double)),
+                                           cn.ctypes.data_as(C.POINTER(C.c_int))), "dgk_mesh_unstructured")
         self._sizes(dim)
 
     def _sizes(self, dim):

@@ -29,10 +29,25 @@ def geometry_array(mspec):
     return g["ngeo"], x
 
 
+def unstructured_arrays(mspec):
+    """(ngeo, xgeo, conn, node_index) of a specification whose geometry asks for
+    "reorient": seed (the same mesh renumbered, elements in random local frames, with
+    unstructured connectivity; inputs.reoriented_mesh), or None."""
+    g = mspec.get("geometry")
+    if g is None or g.get("reorient") is None:
+        return None
+    ngeo, x = geometry_array(mspec)
+    xn, conn, ni = inputs.reoriented_mesh(mspec["dim"], mspec["N"], mspec["n"], mspec["periodic"], ngeo, x,
+                                          g["reorient"])
+    return ngeo, xn, conn, ni
+
+
 def oracle_objects(orc, mspec, pspec):
+    un = unstructured_arrays(mspec)
+    geo, conn = (geometry_array(mspec), None) if un is None else ((un[0], un[1]), un[2])
     m = orc.make_mesh(mspec["dim"], mspec["N"], mspec["n"] + [1] * (3 - mspec["dim"]),
                       mspec["lo"] + [0.0] * (3 - mspec["dim"]), mspec["hi"] + [1.0] * (3 - mspec["dim"]),
-                      mspec["periodic"] + [1] * (3 - mspec["dim"]), mspec["walls"], geometry=geometry_array(mspec))
+                      mspec["periodic"] + [1] * (3 - mspec["dim"]), mspec["walls"], geometry=geo, conn=conn)
     p = orc.make_params(**pspec)
     return orc.Oracle(m, p)
 
@@ -110,6 +125,11 @@ def dgk_context(mspec, pspec, precision="fp64", rk=4):
     ctx = dgk.Context()
     ctx.set_params(rk=rk, precision=precision, **pspec)
     dim = mspec["dim"]
+    un = unstructured_arrays(mspec)
+    if un is not None:
+        ctx.mesh_unstructured(dim, mspec["N"], mspec["n"] + [1] * (3 - dim), mspec["periodic"] + [1] * (3 - dim),
+                              mspec["walls"], un[0], un[1], un[2])
+        return ctx
     geo = geometry_array(mspec)
     if geo is not None:
         ctx.mesh_curved(dim, mspec["N"], mspec["n"] + [1] * (3 - dim), mspec["periodic"] + [1] * (3 - dim),

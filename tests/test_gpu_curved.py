@@ -42,6 +42,18 @@ CASES = {
                                  geometry=dict(ngeo=2, amp=0.04)), dict(PAPER_PARAMS)),
     "2d_N3_g2_nsk": (mesh_spec(2, 3, [4, 4], geometry=dict(ngeo=2, amp=0.05)), dict(PAPER_PARAMS, model=0)),
     "3d_N3_g1_nsk": (mesh_spec(3, 3, [2, 2, 2], geometry=dict(ngeo=1, amp=0.05)), dict(PAPER_PARAMS, model=0)),
+    # unstructured connectivity: the same meshes renumbered, every element in a random
+    # orientation-preserving local frame, connected through the tables
+    "2d_N3_g3_walls_m2_unstr": (mesh_spec(2, 3, [4, 3], periodic=[1, 0], walls=W2,
+                                          geometry=dict(ngeo=3, amp=0.04, reorient=3)), dict(PAPER_PARAMS, model=2)),
+    "3d_N3_g1_walls_unstr": (mesh_spec(3, 3, [2, 2, 3], periodic=[1, 1, 0], walls=W3,
+                                       geometry=dict(ngeo=1, amp=0.05, reorient=4)), dict(PAPER_PARAMS)),
+    "3d_N4_g2_periodic_unstr": (mesh_spec(3, 4, [2, 2, 2], geometry=dict(ngeo=2, amp=0.05, reorient=5)),
+                                dict(PAPER_PARAMS)),
+    "3d_N5_g2_walls_unstr": (mesh_spec(3, 5, [2, 2, 2], periodic=[1, 1, 0], walls={4: (0.95, 90.0), 5: (0.8, 90.0)},
+                                       geometry=dict(ngeo=2, amp=0.04, reorient=6)), dict(PAPER_PARAMS)),
+    "3d_N3_g1_nsk_unstr": (mesh_spec(3, 3, [2, 2, 2], geometry=dict(ngeo=1, amp=0.05, reorient=7)),
+                           dict(PAPER_PARAMS, model=0)),
 }
 
 
@@ -95,7 +107,8 @@ def test_curved_one_step_fp64(orc, name):
     assert np.all(err < TOL64), err
 
 
-@pytest.mark.parametrize("name", ["2d_N3_g3_walls_m2", "3d_N3_g1_walls", "3d_N5_g2_walls", "2d_N3_g2_nsk"])
+@pytest.mark.parametrize("name", ["2d_N3_g3_walls_m2", "3d_N3_g1_walls", "3d_N5_g2_walls", "2d_N3_g2_nsk",
+                                  "3d_N5_g2_walls_unstr", "2d_N3_g3_walls_m2_unstr"])
 def test_curved_ten_steps_fp64(orc, name):
     ms, ps = CASES[name]
     o, g, Uo = _pair(orc, ms, ps, exact=False)
@@ -137,7 +150,7 @@ def test_curved_free_stream(precision, tol):
 CURVED32 = 2.0
 
 
-@pytest.mark.parametrize("name", ["2d_N3_g3_walls_m2", "3d_N3_g1_walls", "3d_N5_g2_walls"])
+@pytest.mark.parametrize("name", ["2d_N3_g3_walls_m2", "3d_N3_g1_walls", "3d_N5_g2_walls", "3d_N3_g1_walls_unstr"])
 def test_curved_fp32_bulk_against_oracle(orc, name):
     ms, ps = CASES[name]
     o, g, Uo = _pair(orc, ms, ps, precision="fp32bulk", exact=False)
@@ -165,3 +178,52 @@ def test_curved_refusals():
     slip = {2: (0.85, 90.0, 0.0, 0.1, 0.0, 0.0), 3: (0.85, 90.0)}
     with pytest.raises(dgk.DgkError):  # Navier-slip walls
         dgk_context(mesh_spec(2, 3, [2, 2], periodic=[1, 0], walls=slip, geometry=dict(ngeo=1)), PAPER_PARAMS)
+
+
+def test_unstructured_equals_structured_on_the_gpu(orc):
+    """The library on the renumbered, reoriented mesh against the library on the
+    structured curved mesh, permuted: the same discretisation (FP64, 1e-12)."""
+    from cases import unstructured_arrays
+    ms = mesh_spec(3, 4, [2, 3, 2], periodic=[1, 1, 0], walls=W3, geometry=dict(ngeo=2, amp=0.05))
+    mu = dict(ms, geometry=dict(ms["geometry"], reorient=11))
+    ni = unstructured_arrays(mu)[3]
+    gs, gu = dgk_context(ms, PAPER_PARAMS), dgk_context(mu, PAPER_PARAMS)
+    prim = inputs.random_admissible(3, gs.nelem, gs.np, 9)
+    gs.set_primitive(prim)
+    gu.set_primitive(np.ascontiguousarray(prim.reshape(prim.shape[0], -1)[:, ni]))
+    perm = lambda A: A.reshape(A.shape[0], -1)[:, ni]
+    assert np.all(rel_l2(gu.rhs(), perm(gs.rhs())) < TOL64)
+    dt = 0.5 * gs.max_dt()
+    assert abs(gu.max_dt() / gs.max_dt() - 1) < 1e-12
+    gs.run(3, dt)
+    gu.run(3, dt)
+    gs.status()
+    gu.status()
+    assert np.all(rel_l2(gu.download_state(), perm(gs.download_state())) < TOL64)
+
+
+def test_unstructured_refusals():
+    from cases import unstructured_arrays
+    from paper_2208_05310_gb300 import dgk
+    ms = mesh_spec(2, 3, [3, 3], periodic=[1, 0], walls=W2, geometry=dict(ngeo=2, amp=0.05, reorient=2))
+    ngeo, x, conn, _ = unstructured_arrays(ms)
+
+    def build(cn):
+        g = dgk.Context()
+        g.set_params(**PAPER_PARAMS)
+        g.mesh_unstructured(2, 3, [3, 3], [1, 0], W2, ngeo, x, cn)
+
+    build(conn)  # the valid tables
+    e, f = next((e, f) for e in range(conn.shape[0]) for f in range(conn.shape[1]) if conn[e, f, 0] >= 0)
+    bad = conn.copy()
+    bad[e, f, 2] ^= 2  # an orientation that does not match the element maps
+    with pytest.raises(dgk.DgkError):
+        build(bad)
+    bad = conn.copy()
+    bad[e, f, 1] = (bad[e, f, 1] + 1) % 4  # not symmetric
+    with pytest.raises(dgk.DgkError):
+        build(bad)
+    bad = conn.copy()
+    bad[e, f] = (-1, 0, 0)  # a wall on the periodic direction x (wall table entry 0)
+    with pytest.raises(dgk.DgkError):
+        build(bad)
