@@ -59,6 +59,17 @@ def kernel_bytes_per_node(dim, N, rsize, flux="rusanov", curved=False):
 CURVED_GEOMETRY = dict(ngeo=2, amp=0.02)
 
 
+def mesh_arrays(m, wl):
+    """(ngeo, element maps, connectivity tables or None) of a workload's curved or
+    unstructured variant, or None for the box."""
+    geo = geometry_of(m, wl.get("geometry"))
+    if geo is None or wl.get("reorient") is None:
+        return None if geo is None else (geo[0], geo[1], None)
+    from paper_2208_05310_gb300 import inputs
+    xn, conn = inputs.reoriented_frames(m["dim"], m["N"], m["n"], m["periodic"], geo[0], geo[1], wl["reorient"])
+    return geo[0], xn, conn
+
+
 def geometry_of(m, geo):
     """(ngeo, element maps) of a curved variant of mesh m (inputs.box_geometry), or None."""
     if not geo:
@@ -136,7 +147,7 @@ def ncu_traffic(kernel, workload):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha1") != kernel_sources_sha(curved="curved" in workload):
+    if vals.get("kernel_source_sha1") != kernel_sources_sha(curved="curved" in workload or "unstructured" in workload):
         return None
     try:
         return float(vals["dram_bytes_per_launch_full"])
@@ -228,9 +239,10 @@ def oracle_rate(wl, seconds_target=15.0, steps=None, sub=(6, 6, None)):
     h = [(m["hi"][d] - m["lo"][d]) / m["n"][d] for d in range(dim)]
     nsub = [sub[d] if sub[d] else m["n"][d] for d in range(dim)]
     hi = [m["lo"][d] + nsub[d] * h[d] for d in range(dim)]
-    geo = geometry_of(dict(m, n=nsub, hi=hi), wl.get("geometry"))
+    arrs = mesh_arrays(dict(m, n=nsub, hi=hi), wl)
     mesh = orc.make_mesh(dim, m["N"], nsub + [1] * (3 - dim), m["lo"] + [0.0] * (3 - dim), hi + [1.0] * (3 - dim),
-                         m["periodic"] + [1] * (3 - dim), m["walls"], geometry=geo)
+                         m["periodic"] + [1] * (3 - dim), m["walls"], geometry=arrs[:2] if arrs else None,
+                         conn=arrs[2] if arrs else None)
     o = orc.Oracle(mesh, orc.make_params(**wl["params"]))
     rv, rl = orc.maxwell(wl["T0"])
     width = orc.interface_width(wl["T0"], 5.0, wl["params"]["gammaK"])
@@ -322,9 +334,13 @@ def run_ours(args, wl, rank, world, local_rank):
         ctx = dgk.Context(device=local_rank)
         ctx.set_params(rk=wl["rk"], precision=precision, **wl["params"])
         dim = m["dim"]
-        geo = geometry_of(m, wl.get("geometry"))
-        if geo:
-            ctx.mesh_curved(dim, m["N"], m["n"] + [1] * (3 - dim), m["periodic"] + [1] * (3 - dim), m["walls"], *geo)
+        arrs = mesh_arrays(m, wl)
+        if arrs and arrs[2] is not None:
+            ctx.mesh_unstructured(dim, m["N"], m["n"] + [1] * (3 - dim), m["periodic"] + [1] * (3 - dim), m["walls"],
+                                  *arrs)
+        elif arrs:
+            ctx.mesh_curved(dim, m["N"], m["n"] + [1] * (3 - dim), m["periodic"] + [1] * (3 - dim), m["walls"],
+                            arrs[0], arrs[1])
         else:
             ctx.mesh_box(dim, m["N"], m["n"] + [1] * (3 - dim), m["lo"] + [0.0] * (3 - dim),
                          m["hi"] + [1.0] * (3 - dim), m["periodic"] + [1] * (3 - dim), m["walls"])
@@ -383,7 +399,8 @@ def run_ours(args, wl, rank, world, local_rank):
     alg_bytes = kb[dom] * dof
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
-    traffic = ncu_traffic(dom, args.workload + ("curved" if curved else "") + ("_fp32" if rsize == 4 else "_fp64"))
+    kind = "" if not curved else ("unstructured" if wl.get("reorient") is not None else "curved")
+    traffic = ncu_traffic(dom, args.workload + kind + ("_fp32" if rsize == 4 else "_fp64"))
     roofline = dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=traffic,
                     kernel=dom, peak_kind=peak_kind, alg_bytes_per_launch=alg_bytes,
                     avg_launch_ms=avg_ms,
@@ -627,9 +644,10 @@ def main():
                     help="0: the original NSK model (the workload's walls become periodic)")
     ap.add_argument("--walls", default="noslip", choices=["noslip", "slip"],
                     help="slip: generalized Navier-slip walls (gamma_1..4 = 1e-5, 0.1, 0.05, 1)")
-    ap.add_argument("--mesh", default="box", choices=["box", "curved"],
+    ap.add_argument("--mesh", default="box", choices=["box", "curved", "unstructured"],
                     help="curved: the workload's box mapped to curved elements (degree-2 element maps of "
-                         "x_k + 0.02 L_k sin(2 pi x_{k+1}/L_{k+1}); the walls are bent)")
+                         "x_k + 0.02 L_k sin(2 pi x_{k+1}/L_{k+1}); the walls are bent); unstructured: the same "
+                         "curved mesh with every element in a random local frame, connected through tables")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -655,12 +673,15 @@ def main():
         # explicit step diverge on this mesh, in the oracle as well
         wl["mesh"] = dict(wl["mesh"], walls={f: (Tw, th, 1e-5, 0.1, 0.05, 1.0) for f, (Tw, th) in wl["mesh"]["walls"].items()})
         wl["name"] += ", Navier-slip walls"
-    if args.mesh == "curved":
+    if args.mesh in ("curved", "unstructured"):
         if "batch" in wl or args.flux == "hllc" or args.walls != "noslip":
             print(json.dumps({"error": "curved elements: single problems, Rusanov flux, no-slip walls"}))
             return 2
         wl["geometry"] = dict(CURVED_GEOMETRY)
         wl["name"] += ", curved elements (degree-2 maps, walls bent by 2% of the height)"
+        if args.mesh == "unstructured":
+            wl["reorient"] = 2208
+            wl["name"] += ", unstructured connectivity (every element in a random local frame)"
     if args.impl == "reference":
         return run_reference(args, wl, rank, world)
     if world > 1:

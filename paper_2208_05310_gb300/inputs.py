@@ -326,3 +326,77 @@ def reoriented_mesh(dim, N, n, periodic, ngeo, xgeo, seed):
             assert o_found is not None
             conn[k, f] = (k2, f2, o_found)
     return xnew, conn, node_index
+
+
+def reoriented_frames(dim, N, n, periodic, ngeo, xgeo, seed):
+    """reoriented_mesh without the renumbering, vectorised for large meshes: every element
+    keeps its index and gets a random orientation-preserving local frame; the face-point
+    orientations follow from the two frames (a tangential axis of one element is the same
+    box axis as one of the neighbour's, with the product of the two frame signs deciding
+    the reversal).  Returns (xgeo', conn')."""
+    import itertools
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = [int(v) for v in n[:dim]]
+    ne = int(np.prod(n))
+    P, G = N + 1, ngeo + 1
+    frames = []
+    for p in itertools.permutations(range(dim)):
+        inv = sum(1 for i in range(dim) for j in range(i + 1, dim) if p[i] > p[j])
+        for sg in itertools.product((1, -1), repeat=dim):
+            if (-1) ** inv * int(np.prod(sg)) == 1:
+                frames.append((p, sg))
+    fid = rng.integers(0, len(frames), ne)
+    perm = np.array([frames[i][0] for i in fid])    # [ne][dim]: new axis a is box axis perm[a]
+    sgn = np.array([frames[i][1] for i in fid])     # sign of that correspondence
+    # element maps in the new frames
+    NG = G ** dim
+    gidx = np.arange(NG)
+    newidx = np.stack([(gidx // G ** a) % G for a in range(dim)])  # [dim][NG]
+    xnew = np.empty_like(xgeo)
+    for t, (p, sg) in enumerate(frames):
+        sel = np.nonzero(fid == t)[0]
+        if sel.size == 0:
+            continue
+        old = np.zeros(NG, dtype=np.int64)
+        for a in range(dim):
+            ia = newidx[a] if sg[a] > 0 else G - 1 - newidx[a]
+            old += ia * G ** p[a]
+        xnew[:, sel, :] = xgeo[:, sel][:, :, old]
+    box = box_connectivity(dim, n, periodic)
+    conn = np.zeros((ne, 2 * dim, 3), dtype=np.int32)
+    e = np.arange(ne)
+    for a in range(dim):
+        for s in range(2):
+            f = 2 * a + s
+            d_old = perm[:, a]
+            s_old = np.where(sgn[:, a] > 0, s, 1 - s)
+            bx = box[e, 2 * d_old + s_old]                  # [ne][3] in the box frames
+            wall = bx[:, 0] < 0
+            nb = np.where(wall, 0, bx[:, 0])
+            # the neighbour's new face: its new axis a2 with perm[nb][a2] == d_old
+            a2 = np.argmax(perm[nb] == d_old[:, None], axis=1)
+            so_old = bx[:, 1] % 2
+            s2 = np.where(sgn[nb, a2] > 0, so_old, 1 - so_old)
+            f2 = 2 * a2 + s2
+            # tangential axes, increasing new-axis order
+            tang = [b for b in range(dim) if b != a]
+            o = np.zeros(ne, dtype=np.int32)
+            if dim == 2:
+                t0 = tang[0]
+                t0n = np.where(a2 == 0, 1, 0)
+                flip = sgn[e, t0] * sgn[nb, t0n] < 0
+                o = np.where(flip, 2, 0)
+            else:
+                tn = np.array([[b for b in range(3) if b != x] for x in range(3)])[a2]  # [ne][2]
+                t0, t1 = tang
+                swap = perm[nb, tn[:, 0]] == perm[e, t1]
+                # u' runs along the neighbour's first tangential axis: from u (no swap) or v
+                src_u = np.where(swap, t1, t0)
+                src_v = np.where(swap, t0, t1)
+                flip_u = sgn[e, src_u] * sgn[nb, tn[:, 0]] < 0
+                flip_v = sgn[e, src_v] * sgn[nb, tn[:, 1]] < 0
+                o = swap.astype(np.int32) | (flip_u.astype(np.int32) << 1) | (flip_v.astype(np.int32) << 2)
+            conn[:, f, 0] = np.where(wall, bx[:, 0], nb)
+            conn[:, f, 1] = np.where(wall, 0, f2)
+            conn[:, f, 2] = np.where(wall, 0, o)
+    return xnew, conn

@@ -239,3 +239,24 @@ def test_renumbered_reoriented_mesh(orc, name):
                        ms["walls"], geometry=(ngeo, xn), conn=bad)
     o3 = orc.Oracle(m3, orc.make_params(**DT_PARAMS))
     assert np.any(rel_l2(o3.rhs(o3.set_primitive(prim.reshape(prim.shape[0], -1)[:, ni])), perm(o1.rhs(U1))) > 1e-6)
+
+
+@pytest.mark.parametrize("dim,N,n,periodic,walls,ngeo", [(2, 3, [4, 3], [1, 0], WALLS2, 2),
+                                                         (3, 3, [2, 3, 2], [1, 1, 0], WALLS3, 1),
+                                                         (3, 4, [3, 2, 2], [1, 1, 1], {}, 2)])
+def test_reoriented_frames_generator(orc, dim, N, n, periodic, walls, ngeo):
+    """The vectorised generator of random element frames (used for the large bench mesh)
+    gives the same physical mesh: per element, the integrals of the right-hand side of a
+    smooth state equal the box frames' (the node order inside an element differs)."""
+    from cases import droplet_state, geometry_array
+    ms = mesh_spec(dim, N, n, periodic=periodic, walls=walls, geometry=dict(ngeo=ngeo, amp=0.05))
+    xn, conn = inputs.reoriented_frames(dim, N, n, periodic, ngeo, geometry_array(ms)[1], seed=9)
+    assert np.any(conn[:, :, 2] > 1)
+    o1 = oracle_objects(orc, ms, PAPER_PARAMS)
+    m2 = orc.make_mesh(dim, N, n + [1] * (3 - dim), [0.0] * 3, [1.0] * 3, periodic + [1] * (3 - dim), walls,
+                       geometry=(ngeo, xn), conn=conn)
+    o2 = orc.Oracle(m2, orc.make_params(**PAPER_PARAMS))
+    r1 = o1.rhs(o1.set_primitive(droplet_state(o1.node_coords(), (0.3, 1.8, 0.15), radius=0.3)))
+    r2 = o2.rhs(o2.set_primitive(droplet_state(o2.node_coords(), (0.3, 1.8, 0.15), radius=0.3)))
+    i1, i2 = (o1.node_weights() * r1).sum(axis=2), (o2.node_weights() * r2).sum(axis=2)
+    assert np.all(np.abs(i1 - i2).max(axis=1) < 1e-12 * np.abs(i1).max(axis=1))
