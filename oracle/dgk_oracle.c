@@ -40,6 +40,9 @@ static const double BV = 1.0 / 3.0;
 
 #define MAXP 10
 #define MAXG 9 /* geometry points per direction of a curved element */
+#define IDX(v, e, n, ne, np) (((size_t)(v) * (size_t)(ne) + (size_t)(e)) * (size_t)(np) + (size_t)(n))
+#define FIDX(v, e, f, fp, ne, nf, nfp) \
+    ((((size_t)(v) * (size_t)(ne) + (size_t)(e)) * (size_t)(nf) + (size_t)(f)) * (size_t)(nfp) + (size_t)(fp))
 
 /* ======================================================================== */
 /* Thermodynamics, Sec. 2.1                                                 */
@@ -297,6 +300,12 @@ typedef struct {
     int curved, ngeo;
     const double *xgeo; /* [d][e][(ngeo+1)^d], the caller's */
     const int *conn;    /* unstructured connectivity [e][2d][3], the caller's, or NULL */
+    const int *mortar;  /* mortar table [m][2^(d-1)][3], the caller's */
+    int nmortar, nsub;  /* mortars, sub-faces per mortar 2^(d-1) */
+    /* 1D mortar operators for the two halves h of a big face, eta_h(xi) = (xi + 2h - 1)/2:
+       Im[h][j][i] = l_i(eta_h(xi_j)) (big face point i to sub-face point j),
+       Pm[h][i][j] = w_j/(2 w_i) l_i(eta_h(xi_j)) (L2 projection back) */
+    double Im[2][MAXP * MAXP], Pm[2][MAXP * MAXP];
     double *Ja;         /* [e][n][dir][k]: J a^dir_k (contravariant basis times J) at the nodes */
     double *Jn;         /* [e][n]: Jacobian J at the nodes */
     double *Jf;         /* [e][f][fp][k]: J a^dir_k at the face points, f = 2 dir + side */
@@ -358,6 +367,19 @@ static int setup(const or_mesh *m, const or_params *p, ctx_t *c)
     or_lagrange_at(c->N, c->xi, -1.0, c->lm);
     or_lagrange_at(c->N, c->xi, 1.0, c->lp);
     if (m->conn && !m->xgeo) return -1;
+    if (m->nmortar && !m->conn) return -1;
+    c->mortar = m->mortar;
+    c->nmortar = m->nmortar;
+    c->nsub = c->d == 2 ? 2 : 4;
+    for (int h = 0; h < 2; ++h)
+        for (int j = 0; j < c->P; ++j) {
+            double l[MAXP];
+            or_lagrange_at(c->N, c->xi, 0.5 * (c->xi[j] + 2.0 * h - 1.0), l);
+            for (int i = 0; i < c->P; ++i) {
+                c->Im[h][j * c->P + i] = l[i];
+                c->Pm[h][i * c->P + j] = c->w[j] / (2.0 * c->w[i]) * l[i];
+            }
+        }
     if (m->xgeo) {
         c->ngeo = m->ngeo;
         c->xgeo = m->xgeo;
@@ -436,15 +458,101 @@ static int nb_face(const ctx_t *c, long e, int f)
 }
 
 /* The neighbour's face point matching face point fp of face f of element e (box: fp). */
+static int map_fp(const ctx_t *c, int o, int fp)
+{
+    int a = fp % c->P, b = fp / c->P, N = c->N;
+    int u = (o & 1) ? b : a, v = (o & 1) ? a : b;
+    if (o & 2) u = N - u;
+    if (o & 4) v = N - v;
+    return u + c->P * v;
+}
+
 static int nb_fp(const ctx_t *c, long e, int f, int fp)
 {
     if (!c->conn) return fp;
-    int o = c->conn[((size_t)e * 2 * c->d + f) * 3 + 2], N = c->N;
+    int o = c->conn[((size_t)e * 2 * c->d + f) * 3 + 2] & 7, N = c->N;
     int a = fp % c->P, b = fp / c->P;
     int u = (o & 1) ? b : a, v = (o & 1) ? a : b;
     if (o & 2) u = N - u;
     if (o & 4) v = N - v;
     return u + c->P * v;
+}
+
+/* Face kinds: conforming, wall, the small or the big side of a mortar. */
+#define F_CONF 0
+#define F_WALL 1
+#define F_SMALL 2
+#define F_BIG 3
+static int face_kind(const ctx_t *c, long e, int f)
+{
+    if (!c->conn) return neighbour(c, e, f / 2, f % 2) >= 0 ? F_CONF : F_WALL;
+    const int *t = c->conn + ((size_t)e * 2 * c->d + f) * 3;
+    if (t[0] <= -100) return F_BIG;
+    if (t[0] < 0) return F_WALL;
+    return (t[2] >> 3) ? F_SMALL : F_CONF;
+}
+
+/* Facing sign of two faces' metric orientations (J a^dir along +xi_dir of each element):
+   +1 for a plus and a minus face, -1 for two of the same side. */
+static double facing(int f, int fo) { return ((f ^ fo) & 1) ? 1.0 : -1.0; }
+
+/* The neighbour's values of the face field tr (variable v, layout FIDX) at the points of
+   face f of element e: conforming: the neighbour's trace at the matching points; small
+   side of a mortar: the big face's trace interpolated to the sub-face's points; big side:
+   the L2 projection of the small faces' traces.  scale multiplies the small faces'
+   values in the projection and divides the big face's in the interpolation (1 for plain
+   traces, 2^(d-1) for quantities carrying the surface element); with signed, each
+   neighbour value is multiplied by the facing sign of the two faces. */
+static void nb_trace(const ctx_t *c, const double *tr, int v, long e, int f, double scale, int signed_, double *out)
+{
+    long ne = c->ne;
+    int nf = 2 * c->d, nfp = c->nfp, P = c->P;
+    int kind = face_kind(c, e, f);
+    const int *t = c->conn ? c->conn + ((size_t)e * nf + f) * 3 : NULL;
+    if (kind == F_CONF) {
+        long nb = neighbour(c, e, f / 2, f % 2);
+        int fo = nb_face(c, e, f);
+        double sg = signed_ ? facing(f, fo) : 1.0;
+        for (int fp = 0; fp < nfp; ++fp) out[fp] = sg * tr[FIDX(v, nb, fo, nb_fp(c, e, f, fp), ne, nf, nfp)];
+        return;
+    }
+    if (kind == F_SMALL) {
+        long B = t[0];
+        int fB = t[1], o = t[2] & 7, pos = (t[2] >> 3) - 1, h0 = pos & 1, h1 = (pos >> 1) & 1;
+        double sg = (signed_ ? facing(f, fB) : 1.0) / scale;
+        for (int fp = 0; fp < nfp; ++fp) {
+            int q = map_fp(c, o, fp), u = q % P, w = q / P;
+            double acc = 0.0;
+            if (c->d == 2) {
+                for (int i = 0; i < P; ++i) acc += c->Im[h0][u * P + i] * tr[FIDX(v, B, fB, i, ne, nf, nfp)];
+            } else {
+                for (int j = 0; j < P; ++j)
+                    for (int i = 0; i < P; ++i)
+                        acc += c->Im[h0][u * P + i] * c->Im[h1][w * P + j] * tr[FIDX(v, B, fB, i + P * j, ne, nf, nfp)];
+            }
+            out[fp] = sg * acc;
+        }
+        return;
+    }
+    /* big side */
+    int m = -100 - t[0];
+    for (int fp = 0; fp < nfp; ++fp) out[fp] = 0.0;
+    for (int p = 0; p < c->nsub; ++p) {
+        const int *sb = c->mortar + ((size_t)m * c->nsub + p) * 3;
+        long S = sb[0];
+        int fS = sb[1], o = sb[2], h0 = p & 1, h1 = (p >> 1) & 1;
+        double sg = (signed_ ? facing(f, fS) : 1.0) * scale;
+        for (int fq = 0; fq < nfp; ++fq) {
+            int q = map_fp(c, o, fq), u = q % P, w = q / P;
+            double val = sg * tr[FIDX(v, S, fS, fq, ne, nf, nfp)];
+            if (c->d == 2) {
+                for (int i = 0; i < P; ++i) out[i] += c->Pm[h0][i * P + u] * val;
+            } else {
+                for (int j = 0; j < P; ++j)
+                    for (int i = 0; i < P; ++i) out[i + P * j] += c->Pm[h0][i * P + u] * c->Pm[h1][j * P + w] * val;
+            }
+        }
+    }
 }
 
 /* Wall table entry of face f of element e (box: f itself). */
@@ -578,7 +686,7 @@ static int setup_curved(ctx_t *c)
             for (int f = 0; f < nf; ++f) {
                 long nb = neighbour(c, e, f / 2, f % 2);
                 int fo = nb_face(c, e, f);
-                if (nb < 0 || nb < e || (nb == e && fo < f)) continue;
+                if (face_kind(c, e, f) != F_CONF || nb < e || (nb == e && fo < f)) continue;
                 double sg = -((f % 2) ? 1.0 : -1.0) * ((fo % 2) ? 1.0 : -1.0);
                 for (int fp = 0; fp < nfp; ++fp) {
                     int fq = nb_fp(c, e, f, fp);
@@ -818,9 +926,6 @@ static void source(const ctx_t *c, const double *U, const double *g, double *S)
 /* Right-hand side, Sec. 3.1                                                 */
 /* ======================================================================== */
 
-#define IDX(v, e, n, ne, np) (((size_t)(v) * (size_t)(ne) + (size_t)(e)) * (size_t)(np) + (size_t)(n))
-#define FIDX(v, e, f, fp, ne, nf, nfp) \
-    ((((size_t)(v) * (size_t)(ne) + (size_t)(e)) * (size_t)(nf) + (size_t)(f)) * (size_t)(nfp) + (size_t)(fp))
 
 /* Pass-1 lifted variables: (rho, u_1..u_d, c) at the nodes; the original model lifts
    (rho, u_1..u_d). */
@@ -1289,11 +1394,12 @@ static void lift_pass1_c(const ctx_t *c, const double *q, const double *tr, doub
         double fs[6 * MAXP * MAXP], out[3 * MAXP * MAXP * MAXP];
         for (int v = 0; v < nl; ++v) {
             for (int f = 0; f < nf; ++f) {
-                int dir = f / 2, s = f % 2, fo = nb_face(c, e, f);
-                long nb = neighbour(c, e, dir, s);
+                int wall = face_kind(c, e, f) == F_WALL;
+                double nbt[MAXP * MAXP];
+                if (!wall) nb_trace(c, tr, v, e, f, 1.0, 0, nbt);
                 for (int fp = 0; fp < nfp; ++fp) {
                     double own = tr[FIDX(v, e, f, fp, ne, nf, nfp)];
-                    if (nb >= 0) fs[f * nfp + fp] = 0.5 * (own + tr[FIDX(v, nb, fo, nb_fp(c, e, f, fp), ne, nf, nfp)]);
+                    if (!wall) fs[f * nfp + fp] = 0.5 * (own + nbt[fp]);
                     else fs[f * nfp + fp] = (v >= 1 && v <= d) ? 0.0 : own;
                 }
             }
@@ -1318,6 +1424,7 @@ static void lift_pass2_c(const ctx_t *c, const double *T, const double *grad, co
     /* traces: trT[e][f][fp], trG[k][e][f][fp] */
     double *trT = (double *)malloc(sizeof(double) * ne * nf * nfp);
     double *trG = (double *)malloc(sizeof(double) * d * ne * nf * nfp);
+    double *gJf = (double *)malloc(sizeof(double) * ne * nf * nfp); /* grad c . J a^dir on each face */
 #pragma omp parallel for schedule(static)
     for (long e = 0; e < ne; ++e)
         for (int f = 0; f < nf; ++f) {
@@ -1325,21 +1432,37 @@ static void lift_pass2_c(const ctx_t *c, const double *T, const double *grad, co
             trace_elem(c, T + (size_t)e * np, dir, s, trT + ((size_t)e * nf + f) * nfp);
             for (int k = 0; k < d; ++k)
                 trace_elem(c, grad + IDX(k * nl + vc, e, 0, ne, np), dir, s, trG + FIDX(k, e, f, 0, ne, nf, nfp));
+            for (int fp = 0; fp < nfp; ++fp) {
+                double acc = 0.0;
+                for (int k = 0; k < d; ++k) acc += trG[FIDX(k, e, f, fp, ne, nf, nfp)] * JF(c, e, f, fp, k);
+                gJf[((size_t)e * nf + f) * nfp + fp] = acc;
+            }
         }
 #pragma omp parallel for schedule(static)
     for (long e = 0; e < ne; ++e) {
         double Ts[6 * MAXP * MAXP], Gs[3][6 * MAXP * MAXP], out[3 * MAXP * MAXP * MAXP];
         for (int f = 0; f < nf; ++f) {
-            int dir = f / 2, s = f % 2, fo = nb_face(c, e, f);
-            long nb = neighbour(c, e, dir, s);
+            int fo = nb_face(c, e, f), kind = face_kind(c, e, f);
+            long nb = neighbour(c, e, f / 2, f % 2);
+            double nbT[MAXP * MAXP], nbD[MAXP * MAXP];
+            if (kind != F_WALL) nb_trace(c, trT, 0, e, f, 1.0, 0, nbT);
+            if (kind == F_SMALL || kind == F_BIG) nb_trace(c, gJf, 0, e, f, c->d == 2 ? 2.0 : 4.0, 1, nbD);
             for (int fp = 0; fp < nfp; ++fp) {
                 double tOwn = trT[((size_t)e * nf + f) * nfp + fp];
                 int fq = nb_fp(c, e, f, fp);
-                if (nb >= 0) {
-                    Ts[f * nfp + fp] = 0.5 * (tOwn + trT[((size_t)nb * nf + fo) * nfp + fq]);
+                if (kind != F_WALL) Ts[f * nfp + fp] = 0.5 * (tOwn + nbT[fp]);
+                if (kind == F_CONF) {
                     for (int k = 0; k < d; ++k)
                         Gs[k][f * nfp + fp] = 0.5 * (trG[FIDX(k, e, f, fp, ne, nf, nfp)] +
                                                      trG[FIDX(k, nb, fo, fq, ne, nf, nfp)]);
+                } else if (kind != F_WALL) {
+                    /* mortar: (grad c)* . J a = (own + neighbour's, interpolated or
+                       projected) / 2; only that product enters the lifting, so the face
+                       value is the own trace shifted along J a */
+                    double own = gJf[((size_t)e * nf + f) * nfp + fp], a2 = 0.0;
+                    for (int k = 0; k < d; ++k) a2 += JF(c, e, f, fp, k) * JF(c, e, f, fp, k);
+                    double dl = 0.5 * (nbD[fp] - own) / a2;
+                    for (int k = 0; k < d; ++k) Gs[k][f * nfp + fp] = trG[FIDX(k, e, f, fp, ne, nf, nfp)] + dl * JF(c, e, f, fp, k);
                 } else {
                     double nh[3], gm[3] = {0, 0, 0}, gmn = 0.0;
                     face_normal(c, e, f, fp, nh);
@@ -1365,6 +1488,7 @@ static void lift_pass2_c(const ctx_t *c, const double *T, const double *grad, co
     }
     free(trT);
     free(trG);
+    free(gJf);
 }
 
 /* F . a = sum_k a_k F_k of the full flux F = F^C - F^V along the vector a, from the
@@ -1433,6 +1557,41 @@ static void wall_flux_c(const ctx_t *c, int f, const double *U, const double *g,
    with F~* the numerical flux along the face metric J a^dir (oriented along +xi_dir):
    Rusanov F~* = (F_L.Ja + F_R.Ja)/2 - max(lam_L, lam_R)/2 (U_R - U_L), lam = |u.Ja| + s|Ja|
    (L on the minus side of the face), and at a wall |Ja| times the outward wall flux. */
+/* Rusanov flux along the face metric J a at the points of face f of element e (a
+   conforming face or the small side of a mortar): from the element's own traced record
+   (U, pass-1 gradients, grad T, lap c) and the neighbour's, at the matching points or
+   interpolated from the big face; F~* = (F_L . Ja + F_R . Ja)/2 - max(lam)/2 (U_R - U_L),
+   L the minus side along +xi_dir. */
+static void face_flux_pts(const ctx_t *c, const double *trall, int nq, long e, int f, double Fst[][MAXP * MAXP])
+{
+    long ne = c->ne;
+    int nf = 2 * c->d, nfp = c->nfp, nl = c->nl, nv = c->nv, d = c->d, s = f % 2;
+    double (*nbr)[MAXP * MAXP] = malloc(sizeof(double) * nq * MAXP * MAXP);
+    for (int q = 0; q < nq; ++q) nb_trace(c, trall, q, e, f, 1.0, 0, nbr[q]);
+    for (int fp = 0; fp < nfp; ++fp) {
+        double Uo[8], go[24], gTo[3], lapo, Un[8], gn[24], gTn[3], lapn, a[3];
+        for (int k = 0; k < 3; ++k) a[k] = JF(c, e, f, fp, k);
+        for (int v = 0; v < nv; ++v) { Uo[v] = trall[FIDX(v, e, f, fp, ne, nf, nfp)]; Un[v] = nbr[v][fp]; }
+        for (int k = 0; k < d * nl; ++k) { go[k] = trall[FIDX(nv + k, e, f, fp, ne, nf, nfp)]; gn[k] = nbr[nv + k][fp]; }
+        for (int k = 0; k < d; ++k) {
+            gTo[k] = trall[FIDX(nv + d * nl + k, e, f, fp, ne, nf, nfp)];
+            gTn[k] = nbr[nv + d * nl + k][fp];
+        }
+        lapo = trall[FIDX(nv + d * nl + d, e, f, fp, ne, nf, nfp)];
+        lapn = nbr[nv + d * nl + d][fp];
+        const double *UL = s ? Uo : Un, *UR = s ? Un : Uo;
+        const double *gL = s ? go : gn, *gR = s ? gn : go;
+        const double *tL = s ? gTo : gTn, *tR = s ? gTn : gTo;
+        double lL = s ? lapo : lapn, lR = s ? lapn : lapo;
+        double FL[8], FR[8], laL, laR;
+        flux_along(c, UL, gL, tL, lL, a, FL, &laL);
+        flux_along(c, UR, gR, tR, lR, a, FR, &laR);
+        double lam = laL > laR ? laL : laR;
+        for (int v = 0; v < nv; ++v) Fst[v][fp] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (UR[v] - UL[v]);
+    }
+    free(nbr);
+}
+
 static int rhs_core_c(const ctx_t *c, const double *U, double *Ut, double t, or_forcing_fn forcing, void *user)
 {
     long ne = c->ne;
@@ -1491,48 +1650,58 @@ static int rhs_core_c(const ctx_t *c, const double *U, double *Ut, double t, or_
         free(F);
     }
 
-    /* surface integral */
+    /* surface integral: F~* at the points of every face (walls: the wall flux; big sides
+       of mortars: the projection of the sub-faces' fluxes), lifted to the nodes */
 #pragma omp parallel for schedule(static)
     for (long e = 0; e < ne; ++e) {
         for (int f = 0; f < nf; ++f) {
-            int dir = f / 2, s = f % 2, fo = nb_face(c, e, f);
-            long nb = neighbour(c, e, dir, s);
-            for (int fp = 0; fp < nfp; ++fp) {
-                double Uo[8], go[24], gTo[3], lapo, Fstar[8], a[3];
-                int fq = nb_fp(c, e, f, fp);
-                for (int k = 0; k < 3; ++k) a[k] = JF(c, e, f, fp, k);
-                for (int v = 0; v < nv; ++v) Uo[v] = trall[FIDX(v, e, f, fp, ne, nf, nfp)];
-                for (int k = 0; k < d * nl; ++k) go[k] = trall[FIDX(nv + k, e, f, fp, ne, nf, nfp)];
-                for (int k = 0; k < d; ++k) gTo[k] = trall[FIDX(nv + d * nl + k, e, f, fp, ne, nf, nfp)];
-                lapo = trall[FIDX(nv + d * nl + d, e, f, fp, ne, nf, nfp)];
-                if (nb >= 0) {
-                    double Un[8], gn[24], gTn[3], lapn;
-                    for (int v = 0; v < nv; ++v) Un[v] = trall[FIDX(v, nb, fo, fq, ne, nf, nfp)];
-                    for (int k = 0; k < d * nl; ++k) gn[k] = trall[FIDX(nv + k, nb, fo, fq, ne, nf, nfp)];
-                    for (int k = 0; k < d; ++k) gTn[k] = trall[FIDX(nv + d * nl + k, nb, fo, fq, ne, nf, nfp)];
-                    lapn = trall[FIDX(nv + d * nl + d, nb, fo, fq, ne, nf, nfp)];
-                    const double *UL = s ? Uo : Un, *UR = s ? Un : Uo;
-                    const double *gL = s ? go : gn, *gR = s ? gn : go;
-                    const double *tL = s ? gTo : gTn, *tR = s ? gTn : gTo;
-                    double lL = s ? lapo : lapn, lR = s ? lapn : lapo;
-                    double FL[8], FR[8], laL, laR;
-                    flux_along(c, UL, gL, tL, lL, a, FL, &laL);
-                    flux_along(c, UR, gR, tR, lR, a, FR, &laR);
-                    double lam = laL > laR ? laL : laR;
-                    for (int v = 0; v < nv; ++v) Fstar[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (UR[v] - UL[v]);
-                } else {
-                    double nh[3], Fn[8];
+            int dir = f / 2, s = f % 2, kind = face_kind(c, e, f);
+            double Fst[8][MAXP * MAXP];
+            if (kind == F_WALL) {
+                for (int fp = 0; fp < nfp; ++fp) {
+                    double Uo[8], go[24], gTo[3], nh[3], Fn[8];
+                    for (int v = 0; v < nv; ++v) Uo[v] = trall[FIDX(v, e, f, fp, ne, nf, nfp)];
+                    for (int k = 0; k < d * nl; ++k) go[k] = trall[FIDX(nv + k, e, f, fp, ne, nf, nfp)];
+                    for (int k = 0; k < d; ++k) gTo[k] = trall[FIDX(nv + d * nl + k, e, f, fp, ne, nf, nfp)];
                     double sa = face_normal(c, e, f, fp, nh);
                     wall_flux_c(c, wall_of(c, e, f), Uo, go, gTo, nh, Fn);
-                    double nsign = s ? 1.0 : -1.0;
-                    for (int v = 0; v < nv; ++v) Fstar[v] = nsign * sa * Fn[v];
+                    for (int v = 0; v < nv; ++v) Fst[v][fp] = (s ? 1.0 : -1.0) * sa * Fn[v];
                 }
+            } else if (kind == F_BIG) {
+                /* the sub-faces' fluxes, as their elements compute them, turned to this
+                   face's orientation and surface element (x 2^(d-1)) and projected */
+                int m = -100 - c->conn[((size_t)e * nf + f) * 3], P_ = c->P;
+                for (int v = 0; v < nv; ++v)
+                    for (int fp = 0; fp < nfp; ++fp) Fst[v][fp] = 0.0;
+                for (int p = 0; p < c->nsub; ++p) {
+                    const int *sb = c->mortar + ((size_t)m * c->nsub + p) * 3;
+                    double Fs[8][MAXP * MAXP];
+                    face_flux_pts(c, trall, nq, sb[0], sb[1], Fs);
+                    double sg = facing(f, sb[1]) * (d == 2 ? 2.0 : 4.0);
+                    int h0 = p & 1, h1 = (p >> 1) & 1;
+                    for (int fq = 0; fq < nfp; ++fq) {
+                        int q = map_fp(c, sb[2], fq), u = q % P_, w = q / P_;
+                        for (int v = 0; v < nv; ++v) {
+                            double val = sg * Fs[v][fq];
+                            if (d == 2) {
+                                for (int i = 0; i < P_; ++i) Fst[v][i] += c->Pm[h0][i * P_ + u] * val;
+                            } else {
+                                for (int jj = 0; jj < P_; ++jj)
+                                    for (int i = 0; i < P_; ++i)
+                                        Fst[v][i + P_ * jj] += c->Pm[h0][i * P_ + u] * c->Pm[h1][jj * P_ + w] * val;
+                            }
+                        }
+                    }
+                }
+            } else {
+                face_flux_pts(c, trall, nq, e, f, Fst);
+            }
+            for (int fp = 0; fp < nfp; ++fp)
                 for (int l = 0; l < P; ++l) {
                     int n = fp_to_node(c, fp, dir, l);
                     double coef = s ? c->lp[l] / c->w[l] : -c->lm[l] / c->w[l];
-                    for (int v = 0; v < nv; ++v) Ut[IDX(v, e, n, ne, np)] -= coef * Fstar[v] / JN(c, e, n);
+                    for (int v = 0; v < nv; ++v) Ut[IDX(v, e, n, ne, np)] -= coef * Fst[v][fp] / JN(c, e, n);
                 }
-            }
         }
     }
 

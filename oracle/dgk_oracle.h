@@ -53,8 +53,16 @@ typedef struct {
        indices in increasing direction order, a fastest) to the neighbour's face point
        (a', b'): (u, v) = o & 1 ? (b, a) : (a, b); a' = o & 2 ? N - u : u;
        b' = o & 4 ? N - v : v (2D: one index, bit 1 only).  Elements may have any
-       orientation-preserving local frame. */
+       orientation-preserving local frame.
+       Mortars (non-conforming 2:1 faces, Sec. 3.1): a big face facing 2 (2D) or 4 (3D)
+       half-size faces has conn = (-100 - m, 0, 0), and mortar[m * 2^(dim-1) + p] =
+       (small element, its face, orientation) for the sub-face p (bit 0: upper half along
+       the big face's first tangential axis, bit 1: along its second); a small face has
+       conn = (big element, its face, o | (p + 1) << 3), o mapping the small face's points
+       onto the sub-face's points in the big face's frame. */
     const int *conn;
+    const int *mortar;
+    int nmortar;
 } or_mesh;
 
 typedef struct {

@@ -25,7 +25,8 @@ class OrMesh(C.Structure):
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("periodic", C.c_int * 3),
                 ("wall_kind", C.c_int * 6), ("wall_T", C.c_double * 6),
                 ("wall_theta_deg", C.c_double * 6), ("wall_gamma", (C.c_double * 4) * 6),
-                ("ngeo", C.c_int), ("xgeo", C.POINTER(C.c_double)), ("conn", C.POINTER(C.c_int))]
+                ("ngeo", C.c_int), ("xgeo", C.POINTER(C.c_double)), ("conn", C.POINTER(C.c_int)),
+                ("mortar", C.POINTER(C.c_int)), ("nmortar", C.c_int)]
 
 
 class OrParams(C.Structure):
@@ -92,7 +93,7 @@ def _check(rc, what):
         raise RuntimeError(f"oracle {what} failed with status {rc}")
 
 
-def make_mesh(dim, N, n, lo, hi, periodic, walls=None, geometry=None, conn=None):
+def make_mesh(dim, N, n, lo, hi, periodic, walls=None, geometry=None, conn=None, mortar=None):
     """walls: dict face -> (T_wall, theta_deg) for faces 0..5 (-x,+x,-y,+y,-z,+z): an
     isothermal no-slip wall; or (T_wall, theta_deg, gamma_1, gamma_2, gamma_3, gamma_4): a
     generalized Navier-slip wall (Eq. bc_nsk_alpha).
@@ -106,6 +107,11 @@ def make_mesh(dim, N, n, lo, hi, periodic, walls=None, geometry=None, conn=None)
         cn = np.ascontiguousarray(conn, dtype=np.int32)
         m.conn = cn.ctypes.data_as(C.POINTER(C.c_int))
         m._conn_keep = cn
+    if mortar is not None and len(mortar):
+        mt = np.ascontiguousarray(mortar, dtype=np.int32)
+        m.mortar = mt.ctypes.data_as(C.POINTER(C.c_int))
+        m.nmortar = int(mt.shape[0])
+        m._mortar_keep = mt
     if geometry is not None:
         ngeo, xgeo = geometry
         xgeo = np.ascontiguousarray(xgeo, dtype=np.float64)

@@ -400,3 +400,121 @@ def reoriented_frames(dim, N, n, periodic, ngeo, xgeo, seed):
             conn[:, f, 1] = np.where(wall, 0, f2)
             conn[:, f, 2] = np.where(wall, 0, o)
     return xnew, conn
+
+
+def _lagrange_equispaced_1d(g, x):
+    """Lagrange basis of the equispaced points t_a = -1 + 2a/g at the points x: [len(x)][g+1]."""
+    t = -1.0 + 2.0 * np.arange(g + 1) / g
+    L = np.ones((len(x), g + 1))
+    for a in range(g + 1):
+        for k in range(g + 1):
+            if k != a:
+                L[:, a] *= (x - t[k]) / (t[a] - t[k])
+    return L
+
+
+def refined_mesh(dim, N, n, periodic, walls, ngeo, amp=0.0, lo=None, hi=None):
+    """A 2:1 non-conforming mesh: the box mesh n (n[0] even) of [lo, hi] with the coarse
+    elements of the upper half in x split into 2^dim elements each.  Element maps: the
+    coarse elements sample the periodic map of box_geometry (degree ngeo); a fine element's
+    map is its parent's polynomial restricted to the fine element (so the hanging faces
+    are watertight).  Connectivity in the unstructured format with mortars (see the
+    oracle's header): conn [ne][2 dim][3], mortar [nm][2^(dim-1)][3]; every element keeps
+    the box frame.  walls: the faces (2 d + side) of the non-periodic directions.
+    Returns (xgeo, conn, mortar)."""
+    n = [int(v) for v in n[:dim]]
+    assert n[0] % 2 == 0
+    lo = lo or [0.0] * dim
+    hi = hi or [1.0] * dim
+    G = ngeo + 1
+    NG = G ** dim
+    xc = box_geometry(dim, n, lo, hi, ngeo, amp=amp)  # [dim][n_coarse][NG]
+    half = n[0] // 2
+    m = [2 * v for v in n]                             # fine lattice
+    cstride = [1, n[0], n[0] * (n[1] if dim > 1 else 1)]
+    # elements: coarse cells with ix < half, then fine cells with fx >= 2 half
+    coarse_cells = [c for c in np.ndindex(*reversed(n))]
+    coarse_cells = [tuple(reversed(c)) for c in coarse_cells if c[-1] < half]
+    fine_cells = [tuple(reversed(c)) for c in np.ndindex(*reversed(m)) if c[-1] >= 2 * half]
+    elem = {}
+    for k, c in enumerate(coarse_cells):
+        elem[("c",) + c] = k
+    nc = len(coarse_cells)
+    for k, c in enumerate(fine_cells):
+        elem[("f",) + c] = nc + k
+    ne = nc + len(fine_cells)
+
+    def owner(fc):
+        """element and level owning fine cell fc"""
+        cc = tuple(v // 2 for v in fc)
+        if cc[0] < half:
+            return elem[("c",) + cc], 0, cc
+        return elem[("f",) + tuple(fc)], 1, None
+
+    # geometry
+    xg = np.empty((dim, ne, NG))
+    gidx = np.arange(NG)
+    for k, c in enumerate(coarse_cells):
+        ce = sum(c[d] * cstride[d] for d in range(dim))
+        xg[:, k, :] = xc[:, ce, :]
+    t = -1.0 + 2.0 * np.arange(G) / ngeo
+    for s_off in np.ndindex(*([2] * dim)):
+        Ls = [_lagrange_equispaced_1d(ngeo, 0.5 * (t + 2 * s_off[d] - 1)) for d in range(dim)]  # [G_new][G_old]
+        W = np.ones((NG, NG))
+        for d in range(dim):
+            W *= Ls[d][(gidx // G ** d) % G][:, (gidx // G ** d) % G]
+        for k, c in enumerate(fine_cells):
+            if tuple(v % 2 for v in c) != s_off:
+                continue
+            parent = tuple(v // 2 for v in c)
+            ce = sum(parent[d] * cstride[d] for d in range(dim))
+            xg[:, nc + k, :] = xc[:, ce, :] @ W.T
+    # connectivity
+    conn = np.zeros((ne, 2 * dim, 3), dtype=np.int32)
+    mortar = []
+    for key, e in elem.items():
+        level, cell = key[0], key[1:]
+        for d in range(dim):
+            tang = [b for b in range(dim) if b != d]
+            for s in range(2):
+                f = 2 * d + s
+                if level == "c":
+                    base = [2 * v for v in cell]
+                    nd = base[d] + 2 if s else base[d] - 1
+                else:
+                    base = list(cell)
+                    nd = base[d] + 1 if s else base[d] - 1
+                if nd < 0 or nd >= m[d]:
+                    if not periodic[d]:
+                        conn[e, f] = (-1 - f, 0, 0)
+                        continue
+                    nd %= m[d]
+                if level == "c":
+                    cells = []
+                    for offs in np.ndindex(*([2] * (dim - 1))):
+                        fc = list(base)
+                        fc[d] = nd
+                        for j, b in enumerate(tang):
+                            fc[b] = base[b] + offs[j]
+                        cells.append((offs, owner(fc)))
+                    if all(o[1] == 0 for _, o in cells):
+                        conn[e, f] = (cells[0][1][0], 2 * d + 1 - s, 0)
+                    else:
+                        mid = len(mortar)
+                        sub = [None] * (2 ** (dim - 1))
+                        for offs, o in cells:
+                            p = sum(offs[j] << j for j in range(dim - 1))
+                            sub[p] = (o[0], 2 * d + 1 - s, 0)
+                        mortar.append(sub)
+                        conn[e, f] = (-100 - mid, 0, 0)
+                else:
+                    fc = list(base)
+                    fc[d] = nd
+                    nb, lev, cc = owner(fc)
+                    if lev == 1:
+                        conn[e, f] = (nb, 2 * d + 1 - s, 0)
+                    else:
+                        p = sum(((fc[b] - 2 * cc[b]) % 2) << j for j, b in enumerate(tang))
+                        conn[e, f] = (nb, 2 * d + 1 - s, (p + 1) << 3)
+    mort = np.array(mortar, dtype=np.int32).reshape(len(mortar), 2 ** (dim - 1), 3)
+    return xg, conn, mort

@@ -1,0 +1,78 @@
+"""Pins of the oracle's mortars (Sec. 3.1: non-conforming 2:1 faces).  A big face facing
+2 (2D) or 4 (3D) half-size faces: the small sides see the big side's traces interpolated
+to their points; the big side sees the L2 projection of the small sides' traces
+(lifting) and of their numerical fluxes, turned to its orientation and surface element
+(surface integral).  Meshes from inputs.refined_mesh: the upper half in x refined 2:1,
+so mortars sit at mid-domain and at the periodic wrap; fine elements carry their parent's
+exact geometry, so the hanging faces are watertight.
+
+Pinned by: uniform flow preserved (and rest against bent walls), mass conserved to
+round-off (momentum too without sources on periodic meshes), and a manufactured solution
+converging at the design order on refined curved meshes."""
+import numpy as np
+import pytest
+
+import mms_gen
+from cases import PAPER_PARAMS
+from paper_2208_05310_gb300 import inputs
+
+WALLS = {2: {2: (0.9, 90.0), 3: (0.9, 90.0)}, 3: {4: (0.9, 90.0), 5: (0.9, 90.0)}}
+
+
+def refined_oracle(orc, dim, N, n, periodic, walls, ngeo, amp, params):
+    xg, conn, mort = inputs.refined_mesh(dim, N, n, periodic, walls, ngeo, amp=amp)
+    ne = xg.shape[1]
+    m = orc.make_mesh(dim, N, [ne, 1, 1], [0.0] * 3, [1.0] * 3, list(periodic) + [1] * (3 - dim), walls,
+                      geometry=(ngeo, xg), conn=conn, mortar=mort)
+    return orc.Oracle(m, orc.make_params(**params)), mort
+
+
+CASES = [(2, 4, [4, 3], [1, 0], 2), (3, 3, [2, 2, 2], [1, 1, 1], 1), (3, 4, [2, 2, 2], [1, 1, 0], 2)]
+
+
+@pytest.mark.parametrize("dim,N,n,periodic,ngeo", CASES)
+def test_uniform_states_preserved(orc, dim, N, n, periodic, ngeo):
+    walls = WALLS[dim] if not all(periodic) else {}
+    o, mort = refined_oracle(orc, dim, N, n, periodic, walls, ngeo, 0.05, PAPER_PARAMS)
+    assert len(mort) > 0
+    prim = np.zeros((dim + 3, o.nelem, o.np))
+    if walls:  # at rest at the wall temperature, contact angle 90 degrees
+        prim[0], prim[dim + 1], prim[dim + 2] = 1.7, 0.9, 1.7
+    else:  # uniform flow
+        prim[0], prim[dim + 1], prim[dim + 2] = 0.6, 0.95, 0.6
+        prim[1:1 + dim] = np.array([0.3, -0.2, 0.1][:dim])[:, None, None]
+    Ut = o.rhs(o.set_primitive(prim))
+    assert np.abs(Ut).max() < 1e-10, np.abs(Ut).max(axis=(1, 2))
+
+
+@pytest.mark.parametrize("dim,N,n,periodic,ngeo", CASES)
+def test_conservation_across_mortars(orc, dim, N, n, periodic, ngeo):
+    walls = WALLS[dim] if not all(periodic) else {}
+    o, _ = refined_oracle(orc, dim, N, n, periodic, walls, ngeo, 0.05, PAPER_PARAMS)
+    W = o.node_weights()
+    prim = inputs.random_admissible(dim, o.nelem, o.np, 5)
+    Ut = o.rhs(o.set_primitive(prim))
+    assert abs((W * Ut[0]).sum()) < 1e-13 * (W * np.abs(Ut[0])).sum()
+    if not walls:
+        o0, _ = refined_oracle(orc, dim, N, n, periodic, walls, ngeo, 0.05, dict(PAPER_PARAMS, alpha=0.0))
+        Ut = o0.rhs(o0.set_primitive(prim))
+        for v in range(1, 1 + dim):
+            assert abs((W * Ut[v]).sum()) < 1e-12 * (W * np.abs(Ut[v])).sum(), v
+
+
+MMS = dict(gammaK=0.01, mu=0.01, kappa=0.02, cv=5.0, alpha=10.0, beta=10.0)
+
+
+@pytest.mark.parametrize("model,N,dt", [(1, 3, 1e-4), (2, 4, 3e-5)])
+def test_mms_convergence_with_mortars(orc, model, N, dt):
+    prm = dict(MMS, model=model)
+    lib, _, fo = mms_gen.build(prm)
+    errs = []
+    for nn in (4, 8):
+        o, _ = refined_oracle(orc, 2, N, [nn, nn], [1, 1], {}, 2, 0.04, prm)
+        x = o.node_coords()
+        nst = int(round(0.02 / dt))
+        U = o.run(mms_gen.exact_state(lib, x, 0.0), nst, dt, rk=4, forcing=fo)
+        errs.append(np.sqrt(((U - mms_gen.exact_state(lib, x, nst * dt)) ** 2).mean(axis=(1, 2))))
+    eoc = np.log2(errs[0] / errs[1])
+    assert np.all(eoc > N + 0.3), eoc
