@@ -155,8 +155,21 @@ int dgk_mesh_curved(dgk_ctx *ctx, const dgk_box_mesh *mesh, int ngeo, const doub
    its own orientation-preserving frame.  The tables must be symmetric (the neighbour's
    entry names e and f back) and match the element maps (the two elements' face metrics
    agree to 1e-6 relative); otherwise DGK_ERR_ARG.  Fewer than 2^31 elements.  Memory:
-   3 ints per element face on the device. */
-int dgk_mesh_unstructured(dgk_ctx *ctx, const dgk_box_mesh *mesh, int ngeo, const double *xgeo, const int *conn);
+   3 ints per element face on the device.
+   Mortars (Sec. 3.1: non-conforming faces, the mortar method): a big face facing
+   2^(dim-1) half-size faces (2:1 in each tangential direction) has conn = (-100 - m, 0, 0)
+   and mortar[(m * 2^(dim-1) + p) * 3 + 0..2] = (small element, its face, orientation) for
+   sub-face p (bit 0: the upper half along the big face's first tangential axis, bit 1:
+   along its second); the small face has conn = (big element, its face, o | (p + 1) << 3),
+   o mapping its points onto the sub-face's points in the big face's frame.  nmortar
+   mortars (mortar may be NULL when 0).  The small sides see the big side's traces
+   interpolated to their points, the big side the L2 projection of the small sides'
+   traces; each small side's numerical flux is evaluated from the big side's face state
+   interpolated to its points, and the big side's flux is the L2 projection of the small
+   sides' (conservative).  The big face's geometry must be the small faces' (a refinement
+   of its element map).  Mortar faces cost three small kernels per stage. */
+int dgk_mesh_unstructured(dgk_ctx *ctx, const dgk_box_mesh *mesh, int ngeo, const double *xgeo, const int *conn,
+                          const int *mortar, int nmortar);
 /* Problem sizes: elements, nodes per element (N+1)^dim, conserved variables dim+3. */
 int dgk_sizes(const dgk_ctx *ctx, long long *nelem, int *nodes_per_elem, int *nvar);
 /* Node coordinates x[d][e][n] (dim x nelem x np doubles). */

@@ -276,7 +276,11 @@ struct dgk_ctx {
     const dgk::CurvedTable *ct = nullptr;
     void *met = nullptr, *fmet = nullptr;
     double *metd = nullptr;
-    int *conn = nullptr;  // unstructured connectivity on the device, or null
+    int *conn = nullptr;  // unstructured connectivity on the device (mortar faces: slot entries), or null
+    // mortars: device table, slots, and the slot buffers of the effective neighbour data
+    long long nmort = 0, nslot = 0;
+    int *mort = nullptr;
+    void *mtr1 = nullptr, *mtr2 = nullptr, *mfd = nullptr, *mrec = nullptr;
     std::vector<double> xnodes;
     unsigned *status = nullptr;
     unsigned long long *redbuf = nullptr;
@@ -299,7 +303,8 @@ void free_buffers(dgk_ctx *c)
 {
     if (c->metd && (void *)c->metd != c->met) cudaFree(c->metd);
     void *ptrs[] = {c->U,  c->G,   c->Tbuf, c->coef, c->rhsbuf, c->partial, c->Utv,
-                    c->tr1, c->tr2, c->fd,   c->Us,   c->status, c->redbuf, c->met, c->fmet, c->conn};
+                    c->tr1, c->tr2, c->fd,   c->Us,   c->status, c->redbuf, c->met, c->fmet, c->conn,
+                    c->mort, c->mtr1, c->mtr2, c->mfd, c->mrec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     c->U = c->G = c->Tbuf = c->coef = c->rhsbuf = c->partial = nullptr;
@@ -307,6 +312,9 @@ void free_buffers(dgk_ctx *c)
     c->met = c->fmet = nullptr;
     c->metd = nullptr;
     c->conn = nullptr;
+    c->mort = nullptr;
+    c->mtr1 = c->mtr2 = c->mfd = c->mrec = nullptr;
+    c->nmort = c->nslot = 0;
     c->curved = false;
     c->ct = nullptr;
     c->xnodes.clear();
@@ -335,6 +343,11 @@ void fill_args(dgk_ctx *c, dgk::KArgs<R> &a)
     a.v.met = (const R *)c->met;
     a.v.fmet = (const R *)c->fmet;
     a.v.conn = c->conn;
+    a.v.mtr1 = (R *)c->mtr1;
+    a.v.mtr2 = (R *)c->mtr2;
+    a.v.mfd = (R *)c->mfd;
+    a.v.mrec = (R *)c->mrec;
+    a.v.mort = c->mort;
     a.v.out = c->Tbuf;
     a.v.coef = c->coef;
     a.v.status = c->status;
@@ -348,6 +361,10 @@ void fill_bulk(dgk::KArgs<R> &a, const dgk::Geom &g, const dgk::Phys &ph, const 
     for (int i = 0; i < dgk::kMaxP * dgk::kMaxP; ++i) {
         a.op.Dh[i] = (R)o.Dhat[i];
         a.op.Dm[i] = (R)o.Dm[i];
+        for (int h = 0; h < 2; ++h) {
+            a.op.Im[h][i] = (R)o.Im[h][i];
+            a.op.Pm[h][i] = (R)o.Pm[h][i];
+        }
     }
     for (int i = 0; i < dgk::kMaxP; ++i) {
         a.op.Lp[i] = (R)o.Lp[i];
@@ -399,6 +416,8 @@ int build_consts(dgk_ctx *c)
     }
     g.div0.init((unsigned)g.n[0]);
     g.div1.init((unsigned)g.n[1]);
+    g.nslot = c->nslot;
+    g.nmort = c->nmort;
     const dgk_params &q = c->prm;
     dgk::Phys ph{q.model, q.gammaK, q.mu, q.kappa, q.cv, q.alpha, q.beta,
                  0.5 * q.alpha, 0.5 * q.gammaK, 1.0 / (dgk::kRgas * q.cv)};
@@ -424,6 +443,10 @@ int build_consts(dgk_ctx *c)
         for (int j = 0; j < P; ++j) {
             o.Dhat[i * P + j] = c->op1.Dhat[i * P + j];
             o.Dm[i * P + j] = c->op1.D[i * P + j];
+            for (int h = 0; h < 2; ++h) {
+                o.Im[h][j * P + i] = c->op1.Im[h][j * P + i];
+                o.Pm[h][i * P + j] = c->op1.w[j] / (2.0 * c->op1.w[i]) * c->op1.Im[h][j * P + i];
+            }
         }
         o.Lp[i] = c->op1.lp[i] / c->op1.w[i];
         o.Lm[i] = c->op1.lm[i] / c->op1.w[i];
@@ -473,17 +496,35 @@ int event_pair(dgk_ctx *c, int cls, cudaEvent_t &a, cudaEvent_t &b)
 }
 
 // stage and set-up kernels of the mesh kind (box or curved elements)
+// (meshes with mortars: each stage kernel is followed by the mortar kernel that turns its
+// face output into the mortar slots' neighbour data)
 cudaError_t run_lift1(const dgk_ctx *c, const void *a)
 {
-    return c->curved ? c->ct->lift1(a, c->stream) : c->kt->lift1(a, c->stream);
+    if (!c->curved) return c->kt->lift1(a, c->stream);
+    cudaError_t err = c->ct->lift1(a, c->stream);
+    if (err == cudaSuccess && c->nmort) err = c->ct->mortar_traces(a, 1, (int)c->nmort, c->stream);
+    return err;
 }
 cudaError_t run_lift2vol(const dgk_ctx *c, const void *a)
 {
-    return c->curved ? c->ct->lift2vol(a, c->stream) : c->kt->lift2vol(a, c->stream);
+    if (!c->curved) return c->kt->lift2vol(a, c->stream);
+    cudaError_t err = c->ct->lift2vol(a, c->stream);
+    if (err == cudaSuccess && c->nmort) err = c->ct->mortar_flux(a, (int)c->nmort, c->stream);
+    return err;
 }
 cudaError_t run_surf(const dgk_ctx *c, const void *a, int mode, int stage)
 {
-    return c->curved ? c->ct->surf(a, mode, stage, c->stream) : c->kt->surf(a, mode, stage, c->stream);
+    if (!c->curved) return c->kt->surf(a, mode, stage, c->stream);
+    cudaError_t err = c->ct->surf(a, mode, stage, c->stream);
+    if (err == cudaSuccess && c->nmort && mode == 1) err = c->ct->mortar_traces(a, 0, (int)c->nmort, c->stream);
+    return err;
+}
+// new pass-1 traces of the current state (and their mortar slots)
+cudaError_t run_traces(const dgk_ctx *c)
+{
+    cudaError_t err = c->kt->traces(c->args(), c->stream);
+    if (err == cudaSuccess && c->curved && c->nmort) err = c->ct->mortar_traces(c->args(), 0, (int)c->nmort, c->stream);
+    return err;
 }
 cudaError_t run_nodeT(const dgk_ctx *c, int mode)
 {
@@ -529,7 +570,7 @@ int after_state_change(dgk_ctx *c)
 {
     size_t nstate = (size_t)c->NV * c->ne * c->NP;
     DGK_CUDA(cudaMemsetAsync(c->G, 0, nstate * sizeof(double), c->stream));
-    cudaError_t err = c->kt->traces(c->args(), c->stream);
+    cudaError_t err = run_traces(c);
     if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("trace kernel: ") + cudaGetErrorString(err));
     return DGK_OK;
 }
@@ -711,7 +752,8 @@ int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m)
     return DGK_OK;
 }
 
-static int mesh_curved_impl(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const double *xgeo, const int *conn)
+static int mesh_curved_impl(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const double *xgeo, const int *conn,
+                            const int *mortar, int nmortar)
 {
     if (!c || !m || !xgeo) return fail(DGK_ERR_ARG, "null argument");
     if (!c->have_params) return fail(DGK_ERR_STATE, "set params before the mesh");
@@ -728,18 +770,42 @@ static int mesh_curved_impl(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const d
         long long ne = 1;
         for (int d = 0; d < m->dim; ++d) ne *= m->n[d];
         if (ne >= (1LL << 31)) return fail(DGK_ERR_ARG, "unstructured meshes take fewer than 2^31 elements");
-        const int NF = 2 * m->dim;
+        const int NF = 2 * m->dim, nsub = m->dim == 2 ? 2 : 4;
+        if (nmortar < 0 || (nmortar > 0 && !mortar)) return fail(DGK_ERR_ARG, "bad mortar table");
+        auto o_ok = [&](int o) { return m->dim == 3 ? (o >= 0 && o < 8) : (o == 0 || o == 2); };
         for (long long e = 0; e < ne; ++e)
             for (int f = 0; f < NF; ++f) {
                 const int *t = conn + (e * NF + f) * 3;
+                if (t[0] <= -100) {  // the big side of mortar -100 - t[0]
+                    const long long mm = -100LL - t[0];
+                    if (mm >= nmortar) return fail(DGK_ERR_ARG, "a face names a mortar outside the table");
+                    for (int p = 0; p < nsub; ++p) {
+                        const int *sb = mortar + (mm * nsub + p) * 3;
+                        if (sb[0] < 0 || sb[0] >= ne || sb[1] < 0 || sb[1] >= NF || !o_ok(sb[2]))
+                            return fail(DGK_ERR_ARG, "mortar entry out of range");
+                        const int *back = conn + ((long long)sb[0] * NF + sb[1]) * 3;
+                        if (back[0] != e || back[1] != f || back[2] != (sb[2] | ((p + 1) << 3)))
+                            return fail(DGK_ERR_ARG, "a mortar's small face does not name the big face back");
+                    }
+                    continue;
+                }
                 if (t[0] < 0) {
                     const int w = -1 - t[0];
                     if (w >= NF || m->periodic[w / 2] || m->wall[w].kind != 1)
                         return fail(DGK_ERR_ARG, "a boundary face names no kind-1 wall of the wall table");
                     continue;
                 }
-                const bool o_ok = m->dim == 3 ? (t[2] >= 0 && t[2] < 8) : (t[2] == 0 || t[2] == 2);
-                if (t[0] >= ne || t[1] < 0 || t[1] >= NF || !o_ok) return fail(DGK_ERR_ARG, "connectivity entry out of range");
+                if (t[0] >= ne || t[1] < 0 || t[1] >= NF) return fail(DGK_ERR_ARG, "connectivity entry out of range");
+                const int pos = t[2] >> 3;
+                if (pos) {  // the small side of a mortar
+                    const int *big = conn + ((long long)t[0] * NF + t[1]) * 3;
+                    const long long mm = -100LL - big[0];
+                    if (big[0] > -100 || mm >= nmortar || pos > nsub) return fail(DGK_ERR_ARG, "a small face names no mortar");
+                    const int *sb = mortar + (mm * nsub + pos - 1) * 3;
+                    if (sb[0] != e || sb[1] != f || sb[2] != (t[2] & 7)) return fail(DGK_ERR_ARG, "mortar table mismatch");
+                    continue;
+                }
+                if (!o_ok(t[2])) return fail(DGK_ERR_ARG, "connectivity entry out of range");
                 const int *back = conn + ((long long)t[0] * NF + t[1]) * 3;
                 if (back[0] != e || back[1] != f) return fail(DGK_ERR_ARG, "connectivity is not symmetric");
             }
@@ -756,9 +822,53 @@ static int mesh_curved_impl(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const d
     std::string err;
     if (!dgk::host::curved_geometry(c->D, c->op1, ngeo, n, per, c->ne, xgeo, conn, geo, err)) return fail(DGK_ERR_ARG, err);
     if (conn) {
+        // mortar faces become slot entries (-1000 - slot, 1 on the big side); the device
+        // mortar table lists each mortar's faces and slots
         const size_t nc = (size_t)c->ne * c->NF * 3;
+        const int nsub = c->D == 2 ? 2 : 4, MT = 4 + 4 * nsub;
+        std::vector<int> cn(conn, conn + nc), mt((size_t)nmortar * MT, 0);
+        for (long long mm = 0; mm < nmortar; ++mm) {
+            const long long base = mm * (1 + nsub);
+            long long B = -1;
+            int fB = 0;
+            for (int p = 0; p < nsub; ++p) {
+                const int *sb = mortar + (mm * nsub + p) * 3;
+                const int *t = conn + ((long long)sb[0] * c->NF + sb[1]) * 3;
+                B = t[0];
+                fB = t[1];
+                mt[mm * MT + 4 + 4 * p + 0] = sb[0];
+                mt[mm * MT + 4 + 4 * p + 1] = sb[1];
+                mt[mm * MT + 4 + 4 * p + 2] = sb[2];
+                mt[mm * MT + 4 + 4 * p + 3] = (int)(base + 1 + p);
+                int *ts = &cn[((size_t)sb[0] * c->NF + sb[1]) * 3];
+                ts[0] = (int)(-1000 - (base + 1 + p));
+                ts[1] = 0;
+                ts[2] = 0;
+            }
+            mt[mm * MT + 0] = (int)B;
+            mt[mm * MT + 1] = fB;
+            mt[mm * MT + 2] = (int)base;
+            int *tb = &cn[((size_t)B * c->NF + fB) * 3];
+            tb[0] = (int)(-1000 - base);
+            tb[1] = 1;
+            tb[2] = 0;
+        }
         DGK_CUDA(cudaMalloc(&c->conn, nc * sizeof(int)));
-        DGK_CUDA(cudaMemcpy(c->conn, conn, nc * sizeof(int), cudaMemcpyHostToDevice));
+        DGK_CUDA(cudaMemcpy(c->conn, cn.data(), nc * sizeof(int), cudaMemcpyHostToDevice));
+        if (nmortar > 0) {
+            c->nmort = nmortar;
+            c->nslot = (long long)nmortar * (1 + nsub);
+            const size_t sl = (size_t)c->nslot * c->NFP * c->rsize;
+            const int NQ = c->NV + c->D * c->D + 2 * c->D + 1;
+            DGK_CUDA(cudaMalloc(&c->mort, mt.size() * sizeof(int)));
+            DGK_CUDA(cudaMemcpy(c->mort, mt.data(), mt.size() * sizeof(int), cudaMemcpyHostToDevice));
+            DGK_CUDA(cudaMalloc(&c->mtr1, c->NL * sl));
+            DGK_CUDA(cudaMalloc(&c->mtr2, 2 * sl));
+            DGK_CUDA(cudaMalloc(&c->mfd, (2 * c->NV + 1) * sl));
+            DGK_CUDA(cudaMalloc(&c->mrec, NQ * sl));
+            rc = build_consts(c);
+            if (rc) return rc;
+        }
     }
     const bool f32 = c->prm.precision == DGK_PREC_FP32BULK;
     c->ct = c->D == 2 ? (f32 ? dgk_ctable_2d_f32(c->N) : dgk_ctable_2d_f64(c->N))
@@ -791,13 +901,14 @@ static int mesh_curved_impl(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const d
 
 int dgk_mesh_curved(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const double *xgeo)
 {
-    return mesh_curved_impl(c, m, ngeo, xgeo, nullptr);
+    return mesh_curved_impl(c, m, ngeo, xgeo, nullptr, nullptr, 0);
 }
 
-int dgk_mesh_unstructured(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const double *xgeo, const int *conn)
+int dgk_mesh_unstructured(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const double *xgeo, const int *conn,
+                          const int *mortar, int nmortar)
 {
     if (!conn) return fail(DGK_ERR_ARG, "null connectivity");
-    return mesh_curved_impl(c, m, ngeo, xgeo, conn);
+    return mesh_curved_impl(c, m, ngeo, xgeo, conn, mortar, nmortar);
 }
 
 int dgk_sizes(const dgk_ctx *c, long long *nelem, int *np, int *nv)
@@ -852,7 +963,7 @@ int dgk_set_primitive(dgk_ctx *c, const double *prim, size_t count, int on_devic
     const long long nn = c->ne * c->NP;
     k_prim_partial<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->G, c->U, c->Tbuf, nn, c->D, c->prm.model);
     DGK_CUDA(cudaGetLastError());
-    cudaError_t err = c->kt->traces(c->args(), c->stream);
+    cudaError_t err = run_traces(c);
     if (err != cudaSuccess) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
     err = run_nodeT(c, 1);
     if (err != cudaSuccess) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));

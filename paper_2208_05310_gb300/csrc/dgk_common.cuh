@@ -79,6 +79,8 @@ struct Geom {
     double inv2h[3];  // 2 / h_d: d/dx = (2/h) d/dxi on the affine element
     long long ne;
     FastDiv div0, div1;  // by n[0], by n[1] (element index -> Cartesian coordinates)
+    long long nslot;     // mortar slots (unstructured meshes with mortars), else 0
+    long long nmort;     // mortars
 };
 
 template <typename R>
@@ -99,6 +101,7 @@ struct WallsR {
 struct Ops {
     double Dhat[kMaxP * kMaxP];
     double Dm[kMaxP * kMaxP];  // D_ij = l_j'(xi_i)
+    double Im[2][kMaxP * kMaxP], Pm[2][kMaxP * kMaxP];  // mortar interpolation / projection (see OpsR)
     double Lp[kMaxP], Lm[kMaxP], lp[kMaxP], lm[kMaxP], w[kMaxP];
 };
 

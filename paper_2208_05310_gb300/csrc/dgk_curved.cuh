@@ -215,7 +215,11 @@ __device__ __forceinline__ void face_flux_c(const Ctx<R> &a, int f, int w, bool 
 
 // Neighbour across face f of the slot's element: the element index (negative at a wall),
 // the neighbour's facing face fo, the face-point orientation o and the wall-table entry
-// w of a wall face.  Unstructured tables (v.conn) or the box's connectivity.
+// w of a wall face.  Unstructured tables (v.conn) or the box's connectivity.  A mortar face
+// returns kMortar - slot (<= kMortar), with fo = 1 on the big side: its neighbour data are
+// in the mortar slot, already interpolated or projected to this face's points.
+constexpr int kMortar = -1000;
+
 template <int D, int N, typename R>
 __device__ __forceinline__ long long face_nbr(const KView<R> &v, const Slot<D, N> &t, int f, int &fo, int &o, int &w)
 {
@@ -298,7 +302,8 @@ struct CLiftC {
                 const R own = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
                 int fo, o, w;
                 const long long b = face_nbr<D, N, R>(a.v, t, f, fo, o, w);
-                sCs[q] = b >= 0 ? R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, D + 1, b, fo, map_fp<S::P>(o, fp))]) : own;
+                if (b <= kMortar) sCs[q] = R(0.5) * (own + a.v.mtr1[((long long)(D + 1) * a.v.g.nslot + (kMortar - b)) * NFP + fp]);
+                else sCs[q] = b >= 0 ? R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, D + 1, b, fo, map_fp<S::P>(o, fp))]) : own;
             }
             stage_face_metrics<D, N, R>(a, t, sJf);
         }
@@ -508,7 +513,8 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
             for (int v = 0; v < NL; ++v) {
                 const R own = a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)];
                 R val;
-                if (b >= 0) val = R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, v, b, fo, fq)]);
+                if (b <= kMortar) val = R(0.5) * (own + a.v.mtr1[((long long)v * a.v.g.nslot + (kMortar - b)) * NFP + fp]);
+                else if (b >= 0) val = R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, v, b, fo, fq)]);
                 else val = (v >= 1 && v <= D) ? R(0) : own;
                 sQs[(f * NL + v) * NFP + fp] = val;
             }
@@ -529,7 +535,11 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
             const long long b = face_nbr<D, N, R>(a.v, t, f, fo, o, w);
             const R ownT = a.v.tr2[fidx<NF, NFP>(ne, 0, t.e, f, fp)];
             const R ownD = a.v.tr2[fidx<NF, NFP>(ne, 1, t.e, f, fp)];
-            if (b >= 0) {
+            if (b <= kMortar) {
+                const long long sl = kMortar - b, ns = a.v.g.nslot;
+                pT[j] = R(0.5) * (ownT + a.v.mtr2[sl * NFP + fp]);
+                pD[j] = R(0.5) * (ownD + a.v.mtr2[(ns + sl) * NFP + fp]);
+            } else if (b >= 0) {
                 const int fq = map_fp<P>(o, fp);
                 pT[j] = R(0.5) * (ownT + a.v.tr2[fidx<NF, NFP>(ne, 0, b, fo, fq)]);
                 // the neighbour traced grad c . J a along its own face orientation
@@ -753,10 +763,17 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
         for (int q = n; q < NF * NFP; q += NP) {
             const int f = q / NFP, fp = q % NFP;
             int f_nb, o_nb, w;
-            const bool wall = face_nbr<D, N, R>(a.v, t, f, f_nb, o_nb, w) < 0;
+            const long long bn = face_nbr<D, N, R>(a.v, t, f, f_nb, o_nb, w);
+            const bool wall = bn < 0 && bn > kMortar;
             R r[NQ], av[D];
 #pragma unroll
             for (int k = 0; k < NQ; ++k) r[k] = sR[(f * NQ + k) * NFP + fp];
+            if (bn <= kMortar && f_nb == 1) {
+                // big side of a mortar: its records go to the mortar kernel, which
+                // evaluates this side's flux at the small faces' points
+#pragma unroll
+                for (int k = 0; k < NQ; ++k) a.v.mrec[((long long)k * a.v.g.nslot + (kMortar - bn)) * NFP + fp] = r[k];
+            }
 #pragma unroll
             for (int k = 0; k < D; ++k) av[k] = sJf[(k * NF + f) * NFP + fp];
             R F[NV], lam;
@@ -781,6 +798,154 @@ __global__ void __launch_bounds__(Shape<D, N>::NT, curved_min_blocks(Shape<D, N>
     lift2volc_body<D, N, R>(a, blockIdx.x, smraw);
 }
 
+// ------------------------------------------------------------------ mortars
+//
+// A big face facing 2 (2D) or 4 (3D) half-size faces: the small sides' neighbour data are
+// the big side's interpolated to their points, the big side's the L2 projection of the
+// small sides' (Sec. 3.1, mortar method).  One block per mortar; the results go to the
+// mortar slots that the stage kernels read for these faces.
+
+template <int D>
+__host__ __device__ constexpr int mortar_stride() { return 4 + 4 * (D == 2 ? 2 : 4); }
+
+// which 0: the pass-1 traces (rho, u, c); which 1: the pass-2 traces (T and grad c . J a,
+// the latter signed to the receiving face's orientation and scaled by the surface-element
+// ratio 2^(D-1)).
+template <int D, int N, typename R>
+__global__ void __launch_bounds__(256) k_mortar_traces(KArgs<R> args, int which)
+{
+    using S = Shape<D, N>;
+    constexpr int P = S::P, NF = S::NF, NFP = S::NFP, NL = S::NL, NSUB = D == 2 ? 2 : 4;
+    const KView<R> &v = args.v;
+    const OpsR<R> &op = args.op;
+    const int *mt = v.mort + (long long)blockIdx.x * mortar_stride<D>();
+    const long long ne = v.g.ne, ns = v.g.nslot, B = mt[0];
+    const int fB = mt[1], sB = mt[2];
+    const int nvar = which ? 2 : NL;
+    const R *src = which ? v.tr2 : v.tr1;
+    R *dst = which ? v.mtr2 : v.mtr1;
+    const R scale = R(D == 2 ? 2 : 4);
+    for (int q = threadIdx.x; q < nvar * NSUB * NFP; q += blockDim.x) {
+        const int var = q / (NSUB * NFP), p = (q / NFP) % NSUB, fq = q % NFP;
+        const int *sb = mt + 4 + 4 * p;
+        const int qq = map_fp<P>(sb[2], fq), u = qq % P, w = qq / P, h0 = p & 1, h1 = (p >> 1) & 1;
+        R acc = R(0);
+        if (D == 2) {
+#pragma unroll
+            for (int i = 0; i < P; ++i) acc += op.Im[h0][u * P + i] * src[fidx<NF, NFP>(ne, var, B, fB, i)];
+        } else {
+            for (int j = 0; j < P; ++j) {
+                R row = R(0);
+#pragma unroll
+                for (int i = 0; i < P; ++i) row += op.Im[h0][u * P + i] * src[fidx<NF, NFP>(ne, var, B, fB, i + P * j)];
+                acc += op.Im[h1][w * P + j] * row;
+            }
+        }
+        if (which && var == 1) acc *= R(facing_sign(sb[1], fB)) / scale;
+        dst[((long long)var * ns + sb[3]) * NFP + fq] = acc;
+    }
+    for (int q = threadIdx.x; q < nvar * NFP; q += blockDim.x) {
+        const int var = q / NFP, ib = q % NFP, i = ib % P, j = ib / P;
+        R acc = R(0);
+        for (int p = 0; p < NSUB; ++p) {
+            const int *sb = mt + 4 + 4 * p;
+            const int h0 = p & 1, h1 = (p >> 1) & 1;
+            const R sg = which && var == 1 ? R(facing_sign(fB, sb[1])) * scale : R(1);
+            for (int fq = 0; fq < NFP; ++fq) {
+                const int qq = map_fp<P>(sb[2], fq), u = qq % P, w = qq / P;
+                const R wt = D == 2 ? op.Pm[h0][i * P + u] : op.Pm[h0][i * P + u] * op.Pm[h1][j * P + w];
+                acc += wt * sg * src[fidx<NF, NFP>(ne, var, sb[0], sb[1], fq)];
+            }
+        }
+        dst[((long long)var * ns + sB) * NFP + ib] = acc;
+    }
+}
+
+// Face data of mortars: at each small face point the big side's face record is
+// interpolated and its one-sided flux evaluated along the small face's metric (the small
+// side's slot); the small side's Rusanov flux, as k_surf_rk forms it, turned to the big
+// face's orientation and surface element (x 2^(D-1)) and projected, is the big side's
+// complete flux (written to its own face data, read by k_surf_rk as at a wall).
+template <int D, int N, typename R>
+__global__ void __launch_bounds__(256) k_mortar_flux(KArgs<R> args)
+{
+    using S = Shape<D, N>;
+    using FR = FaceRecC<D>;
+    constexpr int P = S::P, NF = S::NF, NFP = S::NFP, NV = S::NV, NQ = FR::NQ, NSUB = D == 2 ? 2 : 4;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    R *sF = reinterpret_cast<R *>(smraw);  // [NSUB][NV][NFP]
+    const Ctx<R> a{args.v, args.ph, args.pr, args.op};
+    const KView<R> &v = args.v;
+    const OpsR<R> &op = args.op;
+    const int *mt = v.mort + (long long)blockIdx.x * mortar_stride<D>();
+    const long long ne = v.g.ne, ns = v.g.nslot, B = mt[0], st = ne * NF * NFP;
+    const int fB = mt[1], sB = mt[2];
+    const R scale = R(D == 2 ? 2 : 4);
+    for (int q = threadIdx.x; q < NSUB * NFP; q += blockDim.x) {
+        const int p = q / NFP, fq = q % NFP;
+        const int *sb = mt + 4 + 4 * p;
+        const long long Se = sb[0];
+        const int fS = sb[1], sS = sb[3];
+        const int qq = map_fp<P>(sb[2], fq), u = qq % P, w = qq / P, h0 = p & 1, h1 = (p >> 1) & 1;
+        R r[NQ], av[D];
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            const R *rec = v.mrec + ((long long)k * ns + sB) * NFP;
+            R acc = R(0);
+            if (D == 2) {
+#pragma unroll
+                for (int i = 0; i < P; ++i) acc += op.Im[h0][u * P + i] * rec[i];
+            } else {
+                for (int j = 0; j < P; ++j) {
+                    R row = R(0);
+#pragma unroll
+                    for (int i = 0; i < P; ++i) row += op.Im[h0][u * P + i] * rec[i + P * j];
+                    acc += op.Im[h1][w * P + j] * row;
+                }
+            }
+            r[k] = acc;
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) av[k] = v.fmet[fidx<NF, NFP>(ne, k, Se, fS, fq)];
+        R F[NV], lam;
+        face_flux_c<D, R>(a, fS, fS, false, r, av, F, lam);
+        const long long so = sS * NFP + fq, sst = ns * NFP;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            v.mfd[k * sst + so] = r[k];
+            v.mfd[(NV + k) * sst + so] = F[k];
+        }
+        v.mfd[(2 * NV) * sst + so] = lam;
+        // the small side's numerical flux, as k_surf_rk forms it
+        const long long oo = (Se * NF + fS) * NFP + fq;
+        const bool side = fS & 1;
+        const R lmax = fmax(v.fd[(2 * NV) * st + oo], lam);
+        const R sg = R(facing_sign(fB, fS)) * scale;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const R Fo = v.fd[(NV + k) * st + oo], Fn = F[k];
+            const R Uo = v.fd[k * st + oo], Un = r[k];
+            const R FL = side ? Fo : Fn, FRv = side ? Fn : Fo, UL = side ? Uo : Un, UR = side ? Un : Uo;
+            sF[(p * NV + k) * NFP + fq] = sg * (R(0.5) * (FL + FRv) - R(0.5) * lmax * (UR - UL));
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NV * NFP; q += blockDim.x) {
+        const int k = q / NFP, ib = q % NFP, i = ib % P, j = ib / P;
+        R acc = R(0);
+        for (int p = 0; p < NSUB; ++p) {
+            const int *sb = mt + 4 + 4 * p;
+            const int h0 = p & 1, h1 = (p >> 1) & 1;
+            for (int fq = 0; fq < NFP; ++fq) {
+                const int qq = map_fp<P>(sb[2], fq), u = qq % P, w = qq / P;
+                const R wt = D == 2 ? op.Pm[h0][i * P + u] : op.Pm[h0][i * P + u] * op.Pm[h1][j * P + w];
+                acc += wt * sF[(p * NV + k) * NFP + fq];
+            }
+        }
+        v.fd[(NV + k) * st + (B * NF + fB) * NFP + ib] = acc;
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 
 struct CurvedTable {
@@ -789,6 +954,8 @@ struct CurvedTable {
     cudaError_t (*lift2vol)(const void *args, cudaStream_t s);
     cudaError_t (*surf)(const void *args, int mode, int stage, cudaStream_t s);
     cudaError_t (*nodeT)(const void *args, int mode, cudaStream_t s);
+    cudaError_t (*mortar_traces)(const void *args, int which, int nmort, cudaStream_t s);
+    cudaError_t (*mortar_flux)(const void *args, int nmort, cudaStream_t s);
 };
 
 template <int D, int N, typename R>
@@ -838,9 +1005,22 @@ struct CurvedLauncher {
         k_node_Tc<D, N, R><<<blocks(a), S::NT, sm_lift1, s>>>(a, mode);
         return cudaGetLastError();
     }
+    static cudaError_t mortar_traces(const void *p, int which, int nmort, cudaStream_t s)
+    {
+        const KArgs<R> &a = *static_cast<const KArgs<R> *>(p);
+        k_mortar_traces<D, N, R><<<nmort, 128, 0, s>>>(a, which);
+        return cudaGetLastError();
+    }
+    static cudaError_t mortar_flux(const void *p, int nmort, cudaStream_t s)
+    {
+        const KArgs<R> &a = *static_cast<const KArgs<R> *>(p);
+        constexpr size_t sm = (size_t)(D == 2 ? 2 : 4) * S::NV * S::NFP * sizeof(R);
+        k_mortar_flux<D, N, R><<<nmort, 128, sm, s>>>(a);
+        return cudaGetLastError();
+    }
     static const CurvedTable *table()
     {
-        static const CurvedTable t = {prepare, lift1, lift2vol, surf, nodeT};
+        static const CurvedTable t = {prepare, lift1, lift2vol, surf, nodeT, mortar_traces, mortar_flux};
         return &t;
     }
 };

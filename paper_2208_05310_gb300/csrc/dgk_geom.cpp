@@ -193,7 +193,8 @@ bool curved_geometry(int D, const Operators1D &op, int ngeo, const int n[3], con
                 const int *c = conn + (e * NF + f) * 3;
                 const long long nb = c[0];
                 const int fo = c[1], o = c[2];
-                if (nb < 0 || nb < e || (nb == e && fo < f)) continue;
+                // walls and both sides of mortars keep their own face metrics
+                if (nb < 0 || (o >> 3) || nb < e || (nb == e && fo < f)) continue;
                 const double sg = ((f ^ fo) & 1) ? 1.0 : -1.0;
                 for (int p = 0; p < NFP; ++p) {
                     const int a = p % P, b = p / P;

@@ -90,6 +90,8 @@ bool dg_operators(int N, Operators1D &op)
         for (int j = 0; j < P; ++j) op.Dhat[i * P + j] = -(op.w[j] / op.w[i]) * op.D[j * P + i];
     lagrange_eval(P, op.xi, lam, -1.0, op.lm);
     lagrange_eval(P, op.xi, lam, 1.0, op.lp);
+    for (int h = 0; h < 2; ++h)
+        for (int j = 0; j < P; ++j) lagrange_eval(P, op.xi, lam, 0.5 * (op.xi[j] + 2.0 * h - 1.0), &op.Im[h][j * P]);
     return true;
 }
 

@@ -12,6 +12,9 @@ struct Operators1D {
     double xi[16], w[16];
     double D[256], Dhat[256];
     double lm[16], lp[16];  // l_j(-1), l_j(+1)
+    // mortars: Im[h][j*P+i] = l_i((xi_j + 2h - 1)/2), the basis of a face at the points of
+    // its half h (h = 0 lower, 1 upper)
+    double Im[2][256];
 };
 
 bool gauss_legendre(int n, double *x, double *w);

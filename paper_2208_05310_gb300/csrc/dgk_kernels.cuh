@@ -58,6 +58,9 @@ struct OpsR {
     R Dh[kMaxP * kMaxP];
     R Dm[kMaxP * kMaxP];  // D_ij = l_j'(xi_i) (strong form, curved elements)
     R Lp[kMaxP], Lm[kMaxP], lp[kMaxP], lm[kMaxP];
+    // mortars of half-size faces h = 0, 1 (eta = (xi + 2h - 1)/2): Im[h][j*P+i] = l_i(eta_h(xi_j)),
+    // Pm[h][i*P+j] = w_j/(2 w_i) l_i(eta_h(xi_j))
+    R Im[2][kMaxP * kMaxP], Pm[2][kMaxP * kMaxP];
 };
 
 // Per-problem data: geometry, walls and device arrays.  Kernel parameters for a single
@@ -78,7 +81,13 @@ struct KView {
     const R *met;        // curved elements: [D*D+1][ne][NP] J a^dir_k (plane dir*D + k) and 1/J; box: null
     const R *fmet;       // curved elements: [D][ne][NF][NFP] J a^dir_k at the face points; box: null
     const int *conn;     // unstructured connectivity [ne][NF][3] (neighbour or -1 - wall, its face,
-                         // face-point orientation); null: the box's
+                         // face-point orientation; mortar faces: -1000 - slot, 1 on the big side);
+                         // null: the box's
+    R *mtr1, *mtr2, *mfd;  // mortar slots: the effective neighbour data of mortar faces ([NL], [2],
+                           // [2NV+1] x [nslot][NFP]); big sides' face records mrec [NQ][nslot][NFP]
+    R *mrec;
+    const int *mort;       // mortars [nmort][4 + 4 nsub]: (big element, its face, its slot, -), then per
+                           // sub-face p (small element, its face, orientation, its slot)
     double *out;         // rhs output [NV][ne][NP], or nodal T [ne][NP]
     const double *coef;  // device [A_0..A_4, B_0..B_4, dt] of this problem
     unsigned *status;
@@ -1040,11 +1049,17 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
             // own face metric, of the sign facing_sign relative to this element's
             long long b;
             int fo = 2 * dir + 1 - side, fq = fp;
+            long long slot = -1;  // the small side of a mortar: the neighbour's data are in the slot
             if (GEO && a.v.conn) {
                 const int *cn = a.v.conn + (t.e * NF + f) * 3;
                 b = cn[0] < 0 ? -1 : cn[0];
                 fo = cn[1];
                 fq = map_fp<P>(cn[2], fp);
+                if (cn[0] <= -1000 && cn[1] == 0) {
+                    slot = -1000 - cn[0];
+                    b = 0;
+                }
+                // the big side of a mortar holds its complete flux, as a wall does
             } else {
                 b = t.nbr(a.v.g, f);
             }
@@ -1052,10 +1067,30 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
             if (b < 0) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) sFs[(f * NV + v) * NFP + fp] = a.v.fd[(NV + v) * st + oo];
+            } else if (GEO) {
+                // curved elements: the neighbour's one-sided data, at the matching point of
+                // its face (signed to this face's orientation) or in the mortar slot
+                const R *fN = a.v.fd;
+                long long sN = st, iN = ((long long)b * NF + fo) * NFP + fq;
+                R sg = R(facing_sign(f, fo));
+                if (slot >= 0) {
+                    fN = a.v.mfd;
+                    sN = a.v.g.nslot * NFP;
+                    iN = slot * NFP + fp;
+                    sg = R(1);
+                }
+                const R lam = fmax(a.v.fd[(2 * NV) * st + oo], fN[(2 * NV) * sN + iN]);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const R Fo = a.v.fd[(NV + v) * st + oo], Fn = sg * fN[(NV + v) * sN + iN];
+                    const R Uo = a.v.fd[v * st + oo], Un = fN[v * sN + iN];
+                    const R FL = side ? Fo : Fn, FR = side ? Fn : Fo, UL = side ? Uo : Un, UR = side ? Un : Uo;
+                    sFs[(f * NV + v) * NFP + fp] = R(0.5) * (FL + FR) - R(0.5) * lam * (UR - UL);
+                }
             } else {
                 const long long ob = ((long long)b * NF + fo) * NFP + fq;
                 const long long iL = side ? oo : ob, iR = side ? ob : oo;
-                const R sL = GEO && !side ? R(facing_sign(f, fo)) : R(1), sR = GEO && side ? R(facing_sign(f, fo)) : R(1);
+                const R sL = R(1), sR = R(1);
                 if (FLUX == 1) {
                     hllc_face<D, R>(a.v.fd, st, iL, iR, dir, sFs + f * NV * NFP + fp, NFP);
                 } else {

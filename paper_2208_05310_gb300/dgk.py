@@ -76,7 +76,7 @@ def lib():
         "dgk_set_params": (i, [vp, C.POINTER(DgkParams)]),
         "dgk_mesh_box": (i, [vp, C.POINTER(DgkBoxMesh)]),
         "dgk_mesh_curved": (i, [vp, C.POINTER(DgkBoxMesh), i, dp]),
-        "dgk_mesh_unstructured": (i, [vp, C.POINTER(DgkBoxMesh), i, dp, C.POINTER(C.c_int)]),
+        "dgk_mesh_unstructured": (i, [vp, C.POINTER(DgkBoxMesh), i, dp, C.POINTER(C.c_int), C.POINTER(C.c_int), i]),
         "dgk_sizes": (i, [vp, C.POINTER(C.c_longlong), C.POINTER(i), C.POINTER(i)]),
         "dgk_node_coords": (i, [vp, vp, i]),
         "dgk_set_primitive": (i, [vp, vp, sz, i]),
@@ -244,15 +244,19 @@ class Context:
                "dgk_mesh_curved")
         self._sizes(dim)
 
-    def mesh_unstructured(self, dim, N, n, periodic, walls, ngeo, xgeo, conn):
+    def mesh_unstructured(self, dim, N, n, periodic, walls, ngeo, xgeo, conn, mortar=None):
         """Curved elements with unstructured connectivity (dgk_mesh_unstructured): conn is
-        an int array [nelem][2 dim][3]; n gives the element count as a product and, with
-        periodic, which entries of the wall table (walls) exist."""
+        an int array [nelem][2 dim][3], mortar an int array [nmortar][2^(dim-1)][3] or None;
+        n gives the element count as a product and, with periodic, which entries of the
+        wall table (walls) exist."""
         m = make_box_mesh(dim, N, n, [0.0] * 3, [1.0] * 3, periodic, walls)
         x = np.ascontiguousarray(xgeo, dtype=np.float64)
         cn = np.ascontiguousarray(conn, dtype=np.int32)
+        mt = np.ascontiguousarray(mortar if mortar is not None else np.zeros((0, 1, 3)), dtype=np.int32)
         _check(lib().dgk_mesh_unstructured(self._h, C.byref(m), int(ngeo), x.ctypes.data_as(C.POINTER(C.c_double)),
-                                           cn.ctypes.data_as(C.POINTER(C.c_int))), "dgk_mesh_unstructured")
+                                           cn.ctypes.data_as(C.POINTER(C.c_int)),
+                                           mt.ctypes.data_as(C.POINTER(C.c_int)), int(mt.shape[0])),
+                   "dgk_mesh_unstructured")
         self._sizes(dim)
 
     def _sizes(self, dim):

@@ -29,6 +29,17 @@ def geometry_array(mspec):
     return g["ngeo"], x
 
 
+def refined_arrays(mspec):
+    """(ngeo, xgeo, conn, mortar) of a specification whose geometry asks for "refine": the
+    upper half in x refined 2:1 with mortars (inputs.refined_mesh), or None."""
+    g = mspec.get("geometry")
+    if g is None or not g.get("refine"):
+        return None
+    xg, conn, mort = inputs.refined_mesh(mspec["dim"], mspec["N"], mspec["n"], mspec["periodic"], mspec["walls"],
+                                         g["ngeo"], amp=g.get("amp", 0.0), lo=mspec["lo"], hi=mspec["hi"])
+    return g["ngeo"], xg, conn, mort
+
+
 def unstructured_arrays(mspec):
     """(ngeo, xgeo, conn, node_index) of a specification whose geometry asks for
     "reorient": seed (the same mesh renumbered, elements in random local frames, with
@@ -43,6 +54,12 @@ def unstructured_arrays(mspec):
 
 
 def oracle_objects(orc, mspec, pspec):
+    d = mspec["dim"]
+    rf = refined_arrays(mspec)
+    if rf is not None:
+        m = orc.make_mesh(d, mspec["N"], [rf[1].shape[1], 1, 1], [0.0] * 3, [1.0] * 3, mspec["periodic"] + [1] * (3 - d),
+                          mspec["walls"], geometry=(rf[0], rf[1]), conn=rf[2], mortar=rf[3])
+        return orc.Oracle(m, orc.make_params(**pspec))
     un = unstructured_arrays(mspec)
     geo, conn = (geometry_array(mspec), None) if un is None else ((un[0], un[1]), un[2])
     m = orc.make_mesh(mspec["dim"], mspec["N"], mspec["n"] + [1] * (3 - mspec["dim"]),
@@ -125,6 +142,11 @@ def dgk_context(mspec, pspec, precision="fp64", rk=4):
     ctx = dgk.Context()
     ctx.set_params(rk=rk, precision=precision, **pspec)
     dim = mspec["dim"]
+    rf = refined_arrays(mspec)
+    if rf is not None:
+        ctx.mesh_unstructured(dim, mspec["N"], [rf[1].shape[1], 1, 1], mspec["periodic"] + [1] * (3 - dim),
+                              mspec["walls"], rf[0], rf[1], rf[2], rf[3])
+        return ctx
     un = unstructured_arrays(mspec)
     if un is not None:
         ctx.mesh_unstructured(dim, mspec["N"], mspec["n"] + [1] * (3 - dim), mspec["periodic"] + [1] * (3 - dim),

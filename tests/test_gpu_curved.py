@@ -54,6 +54,15 @@ CASES = {
                                        geometry=dict(ngeo=2, amp=0.04, reorient=6)), dict(PAPER_PARAMS)),
     "3d_N3_g1_nsk_unstr": (mesh_spec(3, 3, [2, 2, 2], geometry=dict(ngeo=1, amp=0.05, reorient=7)),
                            dict(PAPER_PARAMS, model=0)),
+    # mortars: the upper half in x refined 2:1 (hanging faces at mid-domain and the wrap)
+    "2d_N4_g2_walls_mortar": (mesh_spec(2, 4, [4, 3], periodic=[1, 0], walls=W2,
+                                        geometry=dict(ngeo=2, amp=0.05, refine=True)), dict(PAPER_PARAMS)),
+    "2d_N3_g2_periodic_m2_mortar": (mesh_spec(2, 3, [4, 4], geometry=dict(ngeo=2, amp=0.05, refine=True)),
+                                    dict(PAPER_PARAMS, model=2)),
+    "3d_N3_g1_periodic_mortar": (mesh_spec(3, 3, [2, 2, 2], geometry=dict(ngeo=1, amp=0.05, refine=True)),
+                                 dict(PAPER_PARAMS)),
+    "3d_N4_g2_walls_mortar": (mesh_spec(3, 4, [2, 2, 2], periodic=[1, 1, 0], walls=W3,
+                                        geometry=dict(ngeo=2, amp=0.04, refine=True)), dict(PAPER_PARAMS)),
 }
 
 
@@ -108,7 +117,8 @@ def test_curved_one_step_fp64(orc, name):
 
 
 @pytest.mark.parametrize("name", ["2d_N3_g3_walls_m2", "3d_N3_g1_walls", "3d_N5_g2_walls", "2d_N3_g2_nsk",
-                                  "3d_N5_g2_walls_unstr", "2d_N3_g3_walls_m2_unstr"])
+                                  "3d_N5_g2_walls_unstr", "2d_N3_g3_walls_m2_unstr", "2d_N4_g2_walls_mortar",
+                                  "3d_N4_g2_walls_mortar"])
 def test_curved_ten_steps_fp64(orc, name):
     ms, ps = CASES[name]
     o, g, Uo = _pair(orc, ms, ps, exact=False)
@@ -150,7 +160,8 @@ def test_curved_free_stream(precision, tol):
 CURVED32 = 2.0
 
 
-@pytest.mark.parametrize("name", ["2d_N3_g3_walls_m2", "3d_N3_g1_walls", "3d_N5_g2_walls", "3d_N3_g1_walls_unstr"])
+@pytest.mark.parametrize("name", ["2d_N3_g3_walls_m2", "3d_N3_g1_walls", "3d_N5_g2_walls", "3d_N3_g1_walls_unstr",
+                                  "3d_N4_g2_walls_mortar"])
 def test_curved_fp32_bulk_against_oracle(orc, name):
     ms, ps = CASES[name]
     o, g, Uo = _pair(orc, ms, ps, precision="fp32bulk", exact=False)
@@ -227,3 +238,37 @@ def test_unstructured_refusals():
     bad[e, f] = (-1, 0, 0)  # a wall on the periodic direction x (wall table entry 0)
     with pytest.raises(dgk.DgkError):
         build(bad)
+
+
+def test_mortar_mass_conservation_on_the_gpu():
+    """Mass is conserved across the mortars by the library too (the big side's flux is the
+    projection of the small sides' fluxes)."""
+    from paper_2208_05310_gb300 import dgk  # noqa: F401
+    import oracle as orc_mod
+    ms = mesh_spec(3, 4, [2, 2, 2], geometry=dict(ngeo=2, amp=0.05, refine=True))
+    o = oracle_objects(orc_mod, ms, PAPER_PARAMS)
+    W = o.node_weights()
+    g = dgk_context(ms, PAPER_PARAMS)
+    g.set_primitive(inputs.random_admissible(3, g.nelem, g.np, 4))
+    Ut = g.rhs()
+    assert abs((W * Ut[0]).sum()) < 1e-13 * (W * np.abs(Ut[0])).sum()
+
+
+def test_mortar_refusals():
+    from cases import refined_arrays
+    from paper_2208_05310_gb300 import dgk
+    ms = mesh_spec(2, 3, [4, 3], periodic=[1, 0], walls=W2, geometry=dict(ngeo=2, amp=0.05, refine=True))
+    ngeo, x, conn, mort = refined_arrays(ms)
+
+    def build(cn, mt):
+        g = dgk.Context()
+        g.set_params(**PAPER_PARAMS)
+        g.mesh_unstructured(2, 3, [x.shape[1], 1], [1, 0], W2, ngeo, x, cn, mt)
+
+    build(conn, mort)
+    bad = mort.copy()
+    bad[0, [0, 1]] = bad[0, [1, 0]]  # sub-faces swapped: the small faces do not name these positions
+    with pytest.raises(dgk.DgkError):
+        build(conn, bad)
+    with pytest.raises(dgk.DgkError):  # a mortar face without its table
+        build(conn, mort[:0])
