@@ -60,14 +60,20 @@ CURVED_GEOMETRY = dict(ngeo=2, amp=0.02)
 
 
 def mesh_arrays(m, wl):
-    """(ngeo, element maps, connectivity tables or None) of a workload's curved or
-    unstructured variant, or None for the box."""
+    """(ngeo, element maps, connectivity tables or None, mortar table or None) of a
+    workload's curved, unstructured or refined variant, or None for the box."""
+    if wl.get("refine"):
+        from paper_2208_05310_gb300 import inputs
+        g = wl["geometry"]
+        xg, conn, mort = inputs.refined_mesh(m["dim"], m["N"], m["n"], m["periodic"], m["walls"], g["ngeo"],
+                                             amp=g["amp"], lo=m["lo"], hi=m["hi"])
+        return g["ngeo"], xg, conn, mort
     geo = geometry_of(m, wl.get("geometry"))
     if geo is None or wl.get("reorient") is None:
-        return None if geo is None else (geo[0], geo[1], None)
+        return None if geo is None else (geo[0], geo[1], None, None)
     from paper_2208_05310_gb300 import inputs
     xn, conn = inputs.reoriented_frames(m["dim"], m["N"], m["n"], m["periodic"], geo[0], geo[1], wl["reorient"])
-    return geo[0], xn, conn
+    return geo[0], xn, conn, None
 
 
 def geometry_of(m, geo):
@@ -147,7 +153,8 @@ def ncu_traffic(kernel, workload):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha1") != kernel_sources_sha(curved="curved" in workload or "unstructured" in workload):
+    curved = any(k in workload for k in ("curved", "unstructured", "mortar"))
+    if vals.get("kernel_source_sha1") != kernel_sources_sha(curved=curved):
         return None
     try:
         return float(vals["dram_bytes_per_launch_full"])
@@ -240,9 +247,10 @@ def oracle_rate(wl, seconds_target=15.0, steps=None, sub=(6, 6, None)):
     nsub = [sub[d] if sub[d] else m["n"][d] for d in range(dim)]
     hi = [m["lo"][d] + nsub[d] * h[d] for d in range(dim)]
     arrs = mesh_arrays(dict(m, n=nsub, hi=hi), wl)
-    mesh = orc.make_mesh(dim, m["N"], nsub + [1] * (3 - dim), m["lo"] + [0.0] * (3 - dim), hi + [1.0] * (3 - dim),
+    ncount = nsub if not (arrs and arrs[3] is not None) else [arrs[1].shape[1], 1, 1]
+    mesh = orc.make_mesh(dim, m["N"], ncount + [1] * (3 - dim), m["lo"] + [0.0] * (3 - dim), hi + [1.0] * (3 - dim),
                          m["periodic"] + [1] * (3 - dim), m["walls"], geometry=arrs[:2] if arrs else None,
-                         conn=arrs[2] if arrs else None)
+                         conn=arrs[2] if arrs else None, mortar=arrs[3] if arrs else None)
     o = orc.Oracle(mesh, orc.make_params(**wl["params"]))
     rv, rl = orc.maxwell(wl["T0"])
     width = orc.interface_width(wl["T0"], 5.0, wl["params"]["gammaK"])
@@ -336,7 +344,8 @@ def run_ours(args, wl, rank, world, local_rank):
         dim = m["dim"]
         arrs = mesh_arrays(m, wl)
         if arrs and arrs[2] is not None:
-            ctx.mesh_unstructured(dim, m["N"], m["n"] + [1] * (3 - dim), m["periodic"] + [1] * (3 - dim), m["walls"],
+            ncount = m["n"] if arrs[3] is None else [arrs[1].shape[1], 1, 1]
+            ctx.mesh_unstructured(dim, m["N"], ncount + [1] * (3 - dim), m["periodic"] + [1] * (3 - dim), m["walls"],
                                   *arrs)
         elif arrs:
             ctx.mesh_curved(dim, m["N"], m["n"] + [1] * (3 - dim), m["periodic"] + [1] * (3 - dim), m["walls"],
@@ -399,7 +408,8 @@ def run_ours(args, wl, rank, world, local_rank):
     alg_bytes = kb[dom] * dof
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
-    kind = "" if not curved else ("unstructured" if wl.get("reorient") is not None else "curved")
+    kind = "" if not curved else ("mortar" if wl.get("refine") else
+                                  "unstructured" if wl.get("reorient") is not None else "curved")
     traffic = ncu_traffic(dom, args.workload + kind + ("_fp32" if rsize == 4 else "_fp64"))
     roofline = dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=traffic,
                     kernel=dom, peak_kind=peak_kind, alg_bytes_per_launch=alg_bytes,
@@ -644,10 +654,11 @@ def main():
                     help="0: the original NSK model (the workload's walls become periodic)")
     ap.add_argument("--walls", default="noslip", choices=["noslip", "slip"],
                     help="slip: generalized Navier-slip walls (gamma_1..4 = 1e-5, 0.1, 0.05, 1)")
-    ap.add_argument("--mesh", default="box", choices=["box", "curved", "unstructured"],
+    ap.add_argument("--mesh", default="box", choices=["box", "curved", "unstructured", "mortar"],
                     help="curved: the workload's box mapped to curved elements (degree-2 element maps of "
                          "x_k + 0.02 L_k sin(2 pi x_{k+1}/L_{k+1}); the walls are bent); unstructured: the same "
-                         "curved mesh with every element in a random local frame, connected through tables")
+                         "curved mesh with every element in a random local frame, connected through tables; mortar: the "
+                         "curved mesh at half the resolution with its upper half in x refined 2:1 (non-conforming faces)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -673,7 +684,7 @@ def main():
         # explicit step diverge on this mesh, in the oracle as well
         wl["mesh"] = dict(wl["mesh"], walls={f: (Tw, th, 1e-5, 0.1, 0.05, 1.0) for f, (Tw, th) in wl["mesh"]["walls"].items()})
         wl["name"] += ", Navier-slip walls"
-    if args.mesh in ("curved", "unstructured"):
+    if args.mesh in ("curved", "unstructured", "mortar"):
         if "batch" in wl or args.flux == "hllc" or args.walls != "noslip":
             print(json.dumps({"error": "curved elements: single problems, Rusanov flux, no-slip walls"}))
             return 2
@@ -682,6 +693,10 @@ def main():
         if args.mesh == "unstructured":
             wl["reorient"] = 2208
             wl["name"] += ", unstructured connectivity (every element in a random local frame)"
+        if args.mesh == "mortar":
+            wl["refine"] = True
+            wl["mesh"] = dict(wl["mesh"], n=[v // 2 for v in wl["mesh"]["n"]])
+            wl["name"] += ", half resolution with the upper half in x refined 2:1 (mortars)"
     if args.impl == "reference":
         return run_reference(args, wl, rank, world)
     if world > 1:
