@@ -386,7 +386,6 @@ static int setup(const or_mesh *m, const or_params *p, ctx_t *c)
         c->conn = m->conn;
         if (m->ngeo < 1 || m->ngeo > MAXG - 1) return -1;
         if (c->d == 2 ? m->ngeo > c->N : 2 * m->ngeo > c->N) return -1;
-        if (p->flux != 0) return -1;
         for (int f = 0; f < 2 * c->d; ++f)
             if (c->wall_kind[f] == 2) return -1;
         c->curved = 1;
@@ -834,6 +833,52 @@ static void hllc_flux(const ctx_t *c, const double *UL, double pL, double aL, co
     double Us[8];
     Us[0] = chi;
     for (int k = 0; k < d; ++k) Us[1 + k] = chi * (k == dir ? Ss : UK[1 + k] / rK);
+    Us[d + 1] = chi * (UK[d + 1] / rK + (Ss - uK) * (Ss + pK / (rK * (SK - uK))));
+    Us[d + 2] = chi * UK[d + 2] / rK;
+    for (int v = 0; v < nv; ++v) F[v] = FK[v] + SK * (Us[v] - UK[v]);
+}
+
+/* Convective flux along the vector a: sum_k a_k F^C_k. */
+static void conv_along(const ctx_t *c, const double *U, double pr, const double *a, double *Fa)
+{
+    double F[8];
+    for (int v = 0; v < c->nv; ++v) Fa[v] = 0.0;
+    for (int k = 0; k < c->d; ++k) {
+        conv_flux(c, U, pr, k, F);
+        for (int v = 0; v < c->nv; ++v) Fa[v] += a[k] * F[v];
+    }
+}
+
+/* HLLC flux along the unit normal nh (hllc_flux with e_dir replaced by nh): normal
+   velocities u.n; the star states keep the tangential velocity,
+   U*_K = chi_K (1, u_K + (S* - u_K.n) n, E_K/rho_K + (S* - u_K.n)(S* + p_K/(rho_K (S_K - u_K.n))),
+   c_K/rho_K). */
+static void hllc_normal(const ctx_t *c, const double *UL, double pL, double aL, const double *UR, double pR,
+                        double aR, const double *nh, double *F)
+{
+    int d = c->d, nv = c->nv;
+    double rL = UL[0], rR = UR[0], uL = 0.0, uR = 0.0;
+    for (int k = 0; k < d; ++k) {
+        uL += UL[1 + k] * nh[k];
+        uR += UR[1 + k] * nh[k];
+    }
+    uL /= rL;
+    uR /= rR;
+    double SL = fmin(uL - aL, uR - aR), SR = fmax(uL + aL, uR + aR);
+    double FL[8], FR[8];
+    conv_along(c, UL, pL, nh, FL);
+    conv_along(c, UR, pR, nh, FR);
+    if (SL >= 0.0) { for (int v = 0; v < nv; ++v) F[v] = FL[v]; return; }
+    if (SR <= 0.0) { for (int v = 0; v < nv; ++v) F[v] = FR[v]; return; }
+    double Ss = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) / (rL * (SL - uL) - rR * (SR - uR));
+    const double *UK = Ss >= 0.0 ? UL : UR;
+    const double *FK = Ss >= 0.0 ? FL : FR;
+    double SK = Ss >= 0.0 ? SL : SR, pK = Ss >= 0.0 ? pL : pR, uK = Ss >= 0.0 ? uL : uR;
+    double rK = UK[0];
+    double chi = rK * (SK - uK) / (SK - Ss);
+    double Us[8];
+    Us[0] = chi;
+    for (int k = 0; k < d; ++k) Us[1 + k] = chi * (UK[1 + k] / rK + (Ss - uK) * nh[k]);
     Us[d + 1] = chi * (UK[d + 1] / rK + (Ss - uK) * (Ss + pK / (rK * (SK - uK))));
     Us[d + 2] = chi * UK[d + 2] / rK;
     for (int v = 0; v < nv; ++v) F[v] = FK[v] + SK * (Us[v] - UK[v]);
@@ -1532,6 +1577,13 @@ static void wall_flux_c(const ctx_t *c, int f, const double *U, const double *g,
         conv_flux(c, Ug, pr, k, F);
         for (int v = 0; v < nv; ++v) Fg[v] += nh[k] * F[v];
     }
+    double Fc[8];
+    if (p->flux == 1) {
+        /* HLLC against the ghost along the outward normal, the fluid on the left */
+        hllc_normal(c, U, pr, a, Ug, pr, a, nh, Fc);
+    } else {
+        for (int v = 0; v < nv; ++v) Fc[v] = 0.5 * (Fi[v] + Fg[v]) - 0.5 * lam * (Ug[v] - U[v]);
+    }
     double divu = 0.0;
     for (int k = 0; k < d; ++k) divu += g[k * nl + 1 + k];
     double cm = U[d + 2];
@@ -1548,7 +1600,7 @@ static void wall_flux_c(const ctx_t *c, int f, const double *U, const double *g,
     for (int k = 0; k < d; ++k) gTn += gT[k] * nh[k];
     Fv[d + 1] = p->kappa * gTn - p->gammaK * cm * gn * divu;
     Fv[d + 2] = p->gammaK * p->beta * gn;
-    for (int v = 0; v < nv; ++v) Fn[v] = 0.5 * (Fi[v] + Fg[v]) - 0.5 * lam * (Ug[v] - U[v]) - Fv[v];
+    for (int v = 0; v < nv; ++v) Fn[v] = Fc[v] - Fv[v];
 }
 
 /* rhs_core on curved elements: the same stages with the metric terms,
@@ -1586,8 +1638,22 @@ static void face_flux_pts(const ctx_t *c, const double *trall, int nq, long e, i
         double FL[8], FR[8], laL, laR;
         flux_along(c, UL, gL, tL, lL, a, FL, &laL);
         flux_along(c, UR, gR, tR, lR, a, FR, &laR);
-        double lam = laL > laR ? laL : laR;
-        for (int v = 0; v < nv; ++v) Fst[v][fp] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (UR[v] - UL[v]);
+        if (c->prm.flux == 1) {
+            /* HLLC for the convective part along the unit normal (times the surface
+               element), central for the viscous part: F^V . a = F^C . a - F . a */
+            double TL = temperature(c, UL, gL), TR = temperature(c, UR, gR), sa = 0.0, nh[3] = {0, 0, 0};
+            for (int k = 0; k < d; ++k) sa += a[k] * a[k];
+            sa = sqrt(sa);
+            for (int k = 0; k < d; ++k) nh[k] = a[k] / sa;
+            double pL = flux_pressure(c, UL[0], TL), pR = flux_pressure(c, UR[0], TR), Fh[8], CL[8], CR[8];
+            hllc_normal(c, UL, pL, sound_speed(c, UL[0], TL), UR, pR, sound_speed(c, UR[0], TR), nh, Fh);
+            conv_along(c, UL, pL, a, CL);
+            conv_along(c, UR, pR, a, CR);
+            for (int v = 0; v < nv; ++v) Fst[v][fp] = sa * Fh[v] - 0.5 * ((CL[v] - FL[v]) + (CR[v] - FR[v]));
+        } else {
+            double lam = laL > laR ? laL : laR;
+            for (int v = 0; v < nv; ++v) Fst[v][fp] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (UR[v] - UL[v]);
+        }
     }
     free(nbr);
 }

@@ -42,8 +42,7 @@ typedef struct {
        t_a = -1 + 2a/ngeo, g = a + (ngeo+1)(b + (ngeo+1)c).  The element connectivity is
        the box's (n, periodic, walls); neighbouring elements must share their face
        points.  Requires ngeo <= N (2D) or 2 ngeo <= N (3D), so that the metric terms
-       are polynomials the scheme differentiates exactly; walls of kind 1 and the
-       Rusanov flux only. */
+       are polynomials the scheme differentiates exactly; walls of kind 1 only. */
     int ngeo;
     const double *xgeo;
     /* Unstructured connectivity (optional, with xgeo; NULL: the box's).  For face

@@ -185,8 +185,8 @@ def test_curved_input_checks(orc):
     assert sizes(mesh_spec(2, 3, [2, 2], geometry=dict(ngeo=1, rotation=np.diag([1.0, -1.0])))) != 0
     slip = {2: (0.85, 90.0, 0.0, 0.1, 0.0, 0.0), 3: (0.85, 90.0)}
     assert sizes(mesh_spec(2, 3, [2, 2], periodic=[1, 0], walls=slip, geometry=dict(ngeo=1))) != 0
-    with pytest.raises(RuntimeError):
-        oracle_objects(orc, mesh_spec(2, 3, [2, 2], geometry=dict(ngeo=1)), dict(PAPER_PARAMS, model=2, flux="hllc"))
+    # the HLLC flux (model 2) is taken along the face normal
+    oracle_objects(orc, mesh_spec(2, 3, [2, 2], geometry=dict(ngeo=1)), dict(PAPER_PARAMS, model=2, flux="hllc"))
 
 
 UNSTRUCTURED_CASES = {
@@ -260,3 +260,45 @@ def test_reoriented_frames_generator(orc, dim, N, n, periodic, walls, ngeo):
     r2 = o2.rhs(o2.set_primitive(droplet_state(o2.node_coords(), (0.3, 1.8, 0.15), radius=0.3)))
     i1, i2 = (o1.node_weights() * r1).sum(axis=2), (o2.node_weights() * r2).sum(axis=2)
     assert np.all(np.abs(i1 - i2).max(axis=1) < 1e-12 * np.abs(i1).max(axis=1))
+
+
+HLLC = dict(DT_PARAMS, model=2, flux="hllc")
+
+
+@pytest.mark.parametrize("name", ["2d_N3_walls", "3d_N3_walls"])
+def test_hllc_affine_map_equals_box(orc, name):
+    """HLLC along the face normal: on an affine map it reproduces the box's HLLC along
+    the coordinate directions (interior faces and the wall HLLC against the ghost)."""
+    ms = BOX_CASES[name]
+    ob = oracle_objects(orc, ms, HLLC)
+    oc = oracle_objects(orc, dict(ms, geometry=dict(ngeo=1)), HLLC)
+    prim = inputs.random_admissible(ms["dim"], ob.nelem, ob.np, 7)
+    err = rel_l2(oc.rhs(oc.set_primitive(prim)), ob.rhs(ob.set_primitive(prim)))
+    assert np.all(err < 1e-12), err
+
+
+@pytest.mark.parametrize("name", ["2d_walls", "3d_walls"])
+def test_hllc_rotated_box_rotates_the_rhs(orc, name):
+    ms, R = ROT_CASES[name]
+    d = ms["dim"]
+    ob = oracle_objects(orc, ms, HLLC)
+    orr = oracle_objects(orc, dict(ms, geometry=dict(ngeo=1, rotation=R)), HLLC)
+    prim = inputs.random_admissible(d, ob.nelem, ob.np, 3)
+    pr = prim.copy()
+    pr[1:1 + d] = np.einsum("kj,jen->ken", R, prim[1:1 + d])
+    Rb = ob.rhs(ob.set_primitive(prim))
+    exp = Rb.copy()
+    exp[1:1 + d] = np.einsum("kj,jen->ken", R, Rb[1:1 + d])
+    err = rel_l2(orr.rhs(orr.set_primitive(pr)), exp)
+    assert np.all(err < 1e-12), err
+
+
+def test_hllc_free_stream_and_conservation(orc):
+    ms = mesh_spec(3, 4, [2, 3, 2], geometry=dict(ngeo=2, amp=0.05))
+    o = oracle_objects(orc, ms, HLLC)
+    prim = np.zeros((6, o.nelem, o.np))
+    prim[0], prim[1], prim[2], prim[3], prim[4], prim[5] = 0.6, 0.3, -0.2, 0.1, 0.95, 0.6
+    assert np.abs(o.rhs(o.set_primitive(prim))).max() < 1e-10
+    W = o.node_weights()
+    Ut = o.rhs(o.set_primitive(inputs.random_admissible(3, o.nelem, o.np, 5)))
+    assert abs((W * Ut[0]).sum()) < 1e-13 * (W * np.abs(Ut[0])).sum()
