@@ -9,10 +9,13 @@
  *   total energy incl. alpha/2 (rho-c)^2 + gamma_K/2 |grad c|^2   Eq. (totalenergyalpha)
  *   relaxation model 1 (p in the flux, alpha rho grad(c - rho) as a source) or
  *   model 2 (modified pressure p + alpha/2 rho^2)          Eq. (navierstokeskorteweg_p), (..._palpha)
- *   DGSEM on Legendre-Gauss nodes, hexahedral (box) meshes, Rusanov flux, BR1 lifting of
- *   (rho, u, c), then of (T, grad c) for grad T and lap c, point-wise sources      Sec. 3.1
- *   isothermal no-slip walls with a static contact angle   Sec. 2.4, Eq. (bc_nsk_alpha),
+ *   DGSEM on Legendre-Gauss nodes; box meshes, curved elements, unstructured connectivity
+ *   and 2:1 mortars; Rusanov or (model 2) HLLC flux; BR1 lifting of (rho, u, c), then of
+ *   (T, grad c) for grad T and lap c; point-wise sources                Sec. 3.1, Sec. 4
+ *   isothermal no-slip walls with a static contact angle, generalized Navier-slip walls
+ *                                                          Sec. 2.4, Eq. (bc_nsk_alpha),
  *                                                          Eq. (helmfreesurftot_derivative)
+ *   the original NSK model on periodic meshes              Eq. (navierstokeskorteweg)
  *   low-storage RK: 3-stage (Williamson) or 5-stage 4th order (Carpenter-Kennedy)  Sec. 3.1
  *
  * Conventions for every call:
@@ -135,9 +138,10 @@ int dgk_mesh_box(dgk_ctx *ctx, const dgk_box_mesh *mesh);
    they are polynomials the scheme differentiates exactly, so a uniform flow is
    preserved.  Liftings use the strong BR1 form with the chain rule, the volume integral
    the contravariant fluxes F . J a^i, the faces the numerical flux along the face metric
-   (one per face point, shared by both elements).  Restrictions: the Rusanov flux, walls
-   of kind 1 only.  Errors: DGK_ERR_UNSUPPORTED for these, DGK_ERR_ARG for an element map
-   with J <= 0 at a node; otherwise as dgk_mesh_box.  Memory: the metric terms add
+   (one per face point, shared by both elements; Rusanov, or for model 2 HLLC along the
+   unit normal).  Restriction: walls of kind 1 only.  Errors: DGK_ERR_UNSUPPORTED for
+   others, DGK_ERR_ARG for an element map with J <= 0 at a node; otherwise as
+   dgk_mesh_box.  Memory: the metric terms add
    (dim^2 + 1) values per node in the bulk type and in double, and dim values per face
    point. */
 int dgk_mesh_curved(dgk_ctx *ctx, const dgk_box_mesh *mesh, int ngeo, const double *xgeo);

@@ -669,8 +669,6 @@ int dgk_set_params(dgk_ctx *c, const dgk_params *p)
         return fail(DGK_ERR_ARG, "parameters out of range");
     if (p->flux != DGK_FLUX_RUSANOV && p->flux != DGK_FLUX_HLLC) return fail(DGK_ERR_ARG, "flux must be Rusanov or HLLC");
     if (p->flux == DGK_FLUX_HLLC && p->model != 2) return fail(DGK_ERR_UNSUPPORTED, "the HLLC flux is for model 2");
-    if (c->have_mesh && c->curved && p->flux != DGK_FLUX_RUSANOV)
-        return fail(DGK_ERR_UNSUPPORTED, "curved elements use the Rusanov flux");
     if (c->have_mesh && p->precision != c->prm.precision)
         return fail(DGK_ERR_STATE, "precision is fixed once the mesh is built");
     c->prm = *p;
@@ -760,7 +758,6 @@ static int mesh_curved_impl(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const d
     if (m->dim != 2 && m->dim != 3) return fail(DGK_ERR_UNSUPPORTED, "dim must be 2 or 3");
     if (ngeo < 1 || (m->dim == 2 ? ngeo > m->N : 2 * ngeo > m->N))
         return fail(DGK_ERR_UNSUPPORTED, "curved elements need 1 <= ngeo <= N (2D) or 1 <= 2 ngeo <= N (3D)");
-    if (c->prm.flux != DGK_FLUX_RUSANOV) return fail(DGK_ERR_UNSUPPORTED, "curved elements use the Rusanov flux");
     for (int f = 0; f < 2 * m->dim; ++f)
         if (!m->periodic[f / 2] && m->wall[f].kind == 2)
             return fail(DGK_ERR_UNSUPPORTED, "curved elements take walls of kind 1 (no-slip contact angle)");
@@ -864,7 +861,7 @@ static int mesh_curved_impl(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const d
             DGK_CUDA(cudaMemcpy(c->mort, mt.data(), mt.size() * sizeof(int), cudaMemcpyHostToDevice));
             DGK_CUDA(cudaMalloc(&c->mtr1, c->NL * sl));
             DGK_CUDA(cudaMalloc(&c->mtr2, 2 * sl));
-            DGK_CUDA(cudaMalloc(&c->mfd, (2 * c->NV + 1) * sl));
+            DGK_CUDA(cudaMalloc(&c->mfd, (2 * c->NV + 3) * sl));
             DGK_CUDA(cudaMalloc(&c->mrec, NQ * sl));
             rc = build_consts(c);
             if (rc) return rc;

@@ -16,7 +16,7 @@
 // The metric arrays: met [D*D+1][ne][NP] (plane dir*D + k: J a^dir_k; plane D*D: 1/J) and
 // fmet [D][ne][NF][NFP] (J a^dir_k at face f = 2 dir + side, oriented along +xi_dir and
 // identical in the two elements that share the face).  Walls: isothermal no-slip
-// contact-angle walls (kind 1); Rusanov flux.
+// contact-angle walls (kind 1); Rusanov or (model 2) HLLC flux along the face normal.
 #pragma once
 
 #include "dgk_kernels.cuh"
@@ -130,7 +130,8 @@ __device__ __forceinline__ void flux_vec(const PhysR<R> &ph, const R *a, R rho, 
 // pressure and signal speed, minus the viscous flux tau(grad u-).n,
 // kappa grad T-.n - gamma_K c- g_n div u-, gamma_K beta g_n (contact-angle g_n).
 template <int D, typename R>
-__device__ __forceinline__ void face_flux_c(const Ctx<R> &a, int f, int w, bool wall, const R *r, const R *av, R *F, R &lam)
+__device__ __forceinline__ void face_flux_c(const Ctx<R> &a, int f, int w, bool wall, const R *r, const R *av, R *F, R &lam,
+                                            R &pf_out, R &s_out)
 {
     using FR = FaceRecC<D>;
     const PhysR<R> &ph = a.pr;
@@ -154,6 +155,8 @@ __device__ __forceinline__ void face_flux_c(const Ctx<R> &a, int f, int w, bool 
     const R pf = flux_pressure<R>(ph, rho, T, iomb);
     const R sig = signal_speed<R>(ph, rho, T, iomb);
     const R sa = sqrt(a2);
+    pf_out = pf;
+    s_out = sig;
     if (!wall) {
         flux_vec<D, R>(ph, av, rho, m, u, E, c, pf, du, gT, gc, r[FR::LAP], F);
         R un = R(0);
@@ -208,9 +211,16 @@ __device__ __forceinline__ void face_flux_c(const Ctx<R> &a, int f, int w, bool 
     Fv[D + 1] = ph.kap * gTn - ph.gK * c * gn * divu;
     Fv[D + 2] = ph.gKbeta * gn;
     const R scale = nsign * sa;
+    R Fc[D + 3];
+    if (ph.flux == 1) {
+        // HLLC against the ghost along the outward normal, the fluid on the left
+        hllc_vec<D, R>(Ui, Fi, pf, sig, irho, Ug, Fg, pf, sig, irho, nh, Fc);
+    } else {
 #pragma unroll
-    for (int v = 0; v < D + 3; ++v)
-        F[v] = scale * (R(0.5) * (Fi[v] + Fg[v]) - R(0.5) * lam * (Ug[v] - Ui[v]) - Fv[v]);
+        for (int v = 0; v < D + 3; ++v) Fc[v] = R(0.5) * (Fi[v] + Fg[v]) - R(0.5) * lam * (Ug[v] - Ui[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < D + 3; ++v) F[v] = scale * (Fc[v] - Fv[v]);
 }
 
 // Neighbour across face f of the slot's element: the element index (negative at a wall),
@@ -776,8 +786,8 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
             }
 #pragma unroll
             for (int k = 0; k < D; ++k) av[k] = sJf[(k * NF + f) * NFP + fp];
-            R F[NV], lam;
-            face_flux_c<D, R>(a, f, w, wall, r, av, F, lam);
+            R F[NV], lam, pf, sig;
+            face_flux_c<D, R>(a, f, w, wall, r, av, F, lam, pf, sig);
             const long long fo = (t.e * NF + f) * NFP + fp;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -785,6 +795,10 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
                 a.v.fd[(NV + v) * st + fo] = F[v];
             }
             a.v.fd[(2 * NV) * st + fo] = lam;
+            if (a.pr.flux == 1) {
+                a.v.fd[(2 * NV + 1) * st + fo] = pf;
+                a.v.fd[(2 * NV + 2) * st + fo] = sig;
+            }
         }
     }
 }
@@ -907,8 +921,8 @@ __global__ void __launch_bounds__(256) k_mortar_flux(KArgs<R> args)
         }
 #pragma unroll
         for (int k = 0; k < D; ++k) av[k] = v.fmet[fidx<NF, NFP>(ne, k, Se, fS, fq)];
-        R F[NV], lam;
-        face_flux_c<D, R>(a, fS, fS, false, r, av, F, lam);
+        R F[NV], lam, pf, sig;
+        face_flux_c<D, R>(a, fS, fS, false, r, av, F, lam, pf, sig);
         const long long so = sS * NFP + fq, sst = ns * NFP;
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
@@ -916,18 +930,25 @@ __global__ void __launch_bounds__(256) k_mortar_flux(KArgs<R> args)
             v.mfd[(NV + k) * sst + so] = F[k];
         }
         v.mfd[(2 * NV) * sst + so] = lam;
+        v.mfd[(2 * NV + 1) * sst + so] = pf;
+        v.mfd[(2 * NV + 2) * sst + so] = sig;
         // the small side's numerical flux, as k_surf_rk forms it
         const long long oo = (Se * NF + fS) * NFP + fq;
-        const bool side = fS & 1;
-        const R lmax = fmax(v.fd[(2 * NV) * st + oo], lam);
-        const R sg = R(facing_sign(fB, fS)) * scale;
+        R Uo[NV], Fo[NV], Fs[NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            const R Fo = v.fd[(NV + k) * st + oo], Fn = F[k];
-            const R Uo = v.fd[k * st + oo], Un = r[k];
-            const R FL = side ? Fo : Fn, FRv = side ? Fn : Fo, UL = side ? Uo : Un, UR = side ? Un : Uo;
-            sF[(p * NV + k) * NFP + fq] = sg * (R(0.5) * (FL + FRv) - R(0.5) * lmax * (UR - UL));
+            Uo[k] = v.fd[k * st + oo];
+            Fo[k] = v.fd[(NV + k) * st + oo];
         }
+        const R lo = v.fd[(2 * NV) * st + oo];
+        if (a.pr.flux == 1)
+            pair_flux_c<D, R, 1>(fS & 1, Uo, Fo, lo, v.fd[(2 * NV + 1) * st + oo], v.fd[(2 * NV + 2) * st + oo], r, F, lam,
+                                 pf, sig, av, Fs);
+        else
+            pair_flux_c<D, R, 0>(fS & 1, Uo, Fo, lo, R(0), R(0), r, F, lam, R(0), R(0), av, Fs);
+        const R sg = R(facing_sign(fB, fS)) * scale;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sF[(p * NV + k) * NFP + fq] = sg * Fs[k];
     }
     __syncthreads();
     for (int q = threadIdx.x; q < NV * NFP; q += blockDim.x) {
@@ -979,6 +1000,8 @@ struct CurvedLauncher {
             return err;
         if ((err = cudaFuncSetAttribute(k_surf_rk<D, N, R, 0, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_surf)))
             return err;
+        if ((err = cudaFuncSetAttribute(k_surf_rk<D, N, R, 0, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_surf)))
+            return err;
         return cudaFuncSetAttribute(k_node_Tc<D, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_lift1);
     }
     static cudaError_t lift1(const void *p, cudaStream_t s)
@@ -996,7 +1019,8 @@ struct CurvedLauncher {
     static cudaError_t surf(const void *p, int mode, int stage, cudaStream_t s)
     {
         const KArgs<R> &a = *static_cast<const KArgs<R> *>(p);
-        k_surf_rk<D, N, R, 0, 0, 1><<<blocks(a), S::NT, sm_surf, s>>>(a, mode, stage);
+        if (a.pr.flux == 1) k_surf_rk<D, N, R, 0, 1, 1><<<blocks(a), S::NT, sm_surf, s>>>(a, mode, stage);
+        else k_surf_rk<D, N, R, 0, 0, 1><<<blocks(a), S::NT, sm_surf, s>>>(a, mode, stage);
         return cudaGetLastError();
     }
     static cudaError_t nodeT(const void *p, int mode, cudaStream_t s)

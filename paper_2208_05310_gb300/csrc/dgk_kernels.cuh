@@ -1008,6 +1008,101 @@ __device__ __forceinline__ void write_traces(const Ctx<R> &a, const Slot<D, N, E
     }
 }
 
+// Convective flux along the vector a: (m.a, m (u.a) + p a, (rho e + p)(u.a), c (u.a)),
+// irho = 1/rho.
+template <int D, typename R>
+__device__ __forceinline__ void conv_vec(const R *U, R p, R irho, const R *a, R *F)
+{
+    R mn = R(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) mn += U[1 + k] * a[k];
+    const R un = mn * irho;
+    F[0] = mn;
+#pragma unroll
+    for (int k = 0; k < D; ++k) F[1 + k] = U[1 + k] * un + p * a[k];
+    F[D + 1] = (U[D + 1] + p) * un;
+    F[D + 2] = U[D + 2] * un;
+}
+
+// HLLC flux along the unit normal nh (hllc_flux with e_dir replaced by nh; FL, FR the
+// convective fluxes along nh): the star states keep the tangential velocity,
+// U*_K = chi (1, u_K + (S* - u_K.n) n, E/rho + (S* - u_K.n)(S* + p/(rho (S_K - u_K.n))), c/rho).
+template <int D, typename R>
+__device__ __forceinline__ void hllc_vec(const R *UL, const R *FL, R pL, R aL, R irL, const R *UR, const R *FR, R pR,
+                                         R aR, R irR, const R *nh, R *F)
+{
+    constexpr int NV = D + 3;
+    R mL = R(0), mR = R(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        mL += UL[1 + k] * nh[k];
+        mR += UR[1 + k] * nh[k];
+    }
+    const R rL = UL[0], rR = UR[0], uL = mL * irL, uR = mR * irR;
+    const R SL = fmin(uL - aL, uR - aR), SR = fmax(uL + aL, uR + aR);
+    if (SL >= R(0) || SR <= R(0)) {
+        const bool left = SL >= R(0);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] = left ? FL[v] : FR[v];
+        return;
+    }
+    const R Ss = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) / (rL * (SL - uL) - rR * (SR - uR));
+    const bool left = Ss >= R(0);
+    R UK[NV], FK[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        UK[v] = left ? UL[v] : UR[v];
+        FK[v] = left ? FL[v] : FR[v];
+    }
+    const R SK = left ? SL : SR, pK = left ? pL : pR, rK = UK[0], irK = left ? irL : irR, uK = left ? uL : uR;
+    const R chi = rK * (SK - uK) / (SK - Ss);
+    R Us[NV];
+    Us[0] = chi;
+#pragma unroll
+    for (int k = 0; k < D; ++k) Us[1 + k] = chi * (UK[1 + k] * irK + (Ss - uK) * nh[k]);
+    Us[D + 1] = chi * (UK[D + 1] * irK + (Ss - uK) * (Ss + pK * irK / (SK - uK)));
+    Us[D + 2] = chi * UK[D + 2] * irK;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = FK[v] + SK * (Us[v] - UK[v]);
+}
+
+// Numerical flux along the face metric av of an interior curved face point, from the
+// one-sided data of this face (o: U, F = (F^C - F^V).av, lambda, convective pressure,
+// sound speed) and of the neighbour (n: the same, F already along av); side 1: this
+// element is on the minus side along +xi_dir.  Rusanov, or (FLUX 1) HLLC along the unit
+// normal times |av| for the convective part with the central viscous part
+// F^V.av = F^C.av - F.av.
+template <int D, typename R, int FLUX>
+__device__ __forceinline__ void pair_flux_c(bool side, const R *Uo, const R *Fo, R lo, R po, R so, const R *Un,
+                                            const R *Fn, R ln, R pn, R sn, const R *av, R *out)
+{
+    constexpr int NV = D + 3;
+    const R *UL = side ? Uo : Un, *UR = side ? Un : Uo, *FL = side ? Fo : Fn, *FR = side ? Fn : Fo;
+    if (FLUX == 0) {
+        const R lam = fmax(lo, ln);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) out[v] = R(0.5) * (FL[v] + FR[v]) - R(0.5) * lam * (UR[v] - UL[v]);
+        return;
+    }
+    const R pL = side ? po : pn, pR = side ? pn : po, aL = side ? so : sn, aR = side ? sn : so;
+    R a2 = R(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) a2 += av[k] * av[k];
+    const R sa = sqrt(a2);
+    R nh[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) nh[k] = av[k] / sa;
+    const R irL = R(1) / UL[0], irR = R(1) / UR[0];
+    R hL[NV], hR[NV], Fh[NV], CL[NV], CR[NV];
+    conv_vec<D, R>(UL, pL, irL, nh, hL);
+    conv_vec<D, R>(UR, pR, irR, nh, hR);
+    hllc_vec<D, R>(UL, hL, pL, aL, irL, UR, hR, pR, aR, irR, nh, Fh);
+    conv_vec<D, R>(UL, pL, irL, av, CL);
+    conv_vec<D, R>(UR, pR, irR, av, CR);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v] = sa * Fh[v] - R(0.5) * ((CL[v] - FL[v]) + (CR[v] - FR[v]));
+}
+
 // mode 0: write U_t (double) to a.v.out; mode 1: RK stage `stage` with coefficients from
 // a.v.coef (G = A G + dt U_t; U = U + B G) and new traces.
 // FLUX: 0 Rusanov, 1 HLLC (a template parameter, so that each form keeps the register
@@ -1069,7 +1164,7 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
                 for (int v = 0; v < NV; ++v) sFs[(f * NV + v) * NFP + fp] = a.v.fd[(NV + v) * st + oo];
             } else if (GEO) {
                 // curved elements: the neighbour's one-sided data, at the matching point of
-                // its face (signed to this face's orientation) or in the mortar slot
+                // its face (its flux signed to this face's orientation) or in the mortar slot
                 const R *fN = a.v.fd;
                 long long sN = st, iN = ((long long)b * NF + fo) * NFP + fq;
                 R sg = R(facing_sign(f, fo));
@@ -1079,14 +1174,27 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
                     iN = slot * NFP + fp;
                     sg = R(1);
                 }
-                const R lam = fmax(a.v.fd[(2 * NV) * st + oo], fN[(2 * NV) * sN + iN]);
+                R Uo[NV], Fo[NV], Un[NV], Fn[NV], Fs[NV], av[D];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    const R Fo = a.v.fd[(NV + v) * st + oo], Fn = sg * fN[(NV + v) * sN + iN];
-                    const R Uo = a.v.fd[v * st + oo], Un = fN[v * sN + iN];
-                    const R FL = side ? Fo : Fn, FR = side ? Fn : Fo, UL = side ? Uo : Un, UR = side ? Un : Uo;
-                    sFs[(f * NV + v) * NFP + fp] = R(0.5) * (FL + FR) - R(0.5) * lam * (UR - UL);
+                    Uo[v] = a.v.fd[v * st + oo];
+                    Fo[v] = a.v.fd[(NV + v) * st + oo];
+                    Un[v] = fN[v * sN + iN];
+                    Fn[v] = sg * fN[(NV + v) * sN + iN];
                 }
+                R po = R(0), so = R(0), pn = R(0), sn = R(0);
+                if (FLUX == 1) {
+                    po = a.v.fd[(2 * NV + 1) * st + oo];
+                    so = a.v.fd[(2 * NV + 2) * st + oo];
+                    pn = fN[(2 * NV + 1) * sN + iN];
+                    sn = fN[(2 * NV + 2) * sN + iN];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) av[k] = a.v.fmet[fidx<NF, NFP>(ne, k, t.e, f, fp)];
+                }
+                pair_flux_c<D, R, FLUX>(side, Uo, Fo, a.v.fd[(2 * NV) * st + oo], po, so, Un, Fn, fN[(2 * NV) * sN + iN],
+                                        pn, sn, av, Fs);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sFs[(f * NV + v) * NFP + fp] = Fs[v];
             } else {
                 const long long ob = ((long long)b * NF + fo) * NFP + fq;
                 const long long iL = side ? oo : ob, iR = side ? ob : oo;

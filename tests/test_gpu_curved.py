@@ -63,6 +63,15 @@ CASES = {
                                  dict(PAPER_PARAMS)),
     "3d_N4_g2_walls_mortar": (mesh_spec(3, 4, [2, 2, 2], periodic=[1, 1, 0], walls=W3,
                                         geometry=dict(ngeo=2, amp=0.04, refine=True)), dict(PAPER_PARAMS)),
+    # model 2 with the HLLC flux (the paper's flux for model 2) along the face normal
+    "2d_N4_g2_walls_m2_hllc": (mesh_spec(2, 4, [4, 3], periodic=[1, 0], walls=W2, geometry=dict(ngeo=2, amp=0.05)),
+                               dict(PAPER_PARAMS, model=2, flux="hllc")),
+    "3d_N3_g1_walls_m2_hllc_unstr": (mesh_spec(3, 3, [2, 2, 3], periodic=[1, 1, 0], walls=W3,
+                                               geometry=dict(ngeo=1, amp=0.05, reorient=8)),
+                                     dict(PAPER_PARAMS, model=2, flux="hllc")),
+    "3d_N4_g2_walls_m2_hllc_mortar": (mesh_spec(3, 4, [2, 2, 2], periodic=[1, 1, 0], walls=W3,
+                                                geometry=dict(ngeo=2, amp=0.04, refine=True)),
+                                      dict(PAPER_PARAMS, model=2, flux="hllc")),
 }
 
 
@@ -118,7 +127,7 @@ def test_curved_one_step_fp64(orc, name):
 
 @pytest.mark.parametrize("name", ["2d_N3_g3_walls_m2", "3d_N3_g1_walls", "3d_N5_g2_walls", "2d_N3_g2_nsk",
                                   "3d_N5_g2_walls_unstr", "2d_N3_g3_walls_m2_unstr", "2d_N4_g2_walls_mortar",
-                                  "3d_N4_g2_walls_mortar"])
+                                  "3d_N4_g2_walls_mortar", "2d_N4_g2_walls_m2_hllc", "3d_N4_g2_walls_m2_hllc_mortar"])
 def test_curved_ten_steps_fp64(orc, name):
     ms, ps = CASES[name]
     o, g, Uo = _pair(orc, ms, ps, exact=False)
@@ -161,7 +170,7 @@ CURVED32 = 2.0
 
 
 @pytest.mark.parametrize("name", ["2d_N3_g3_walls_m2", "3d_N3_g1_walls", "3d_N5_g2_walls", "3d_N3_g1_walls_unstr",
-                                  "3d_N4_g2_walls_mortar"])
+                                  "3d_N4_g2_walls_mortar", "2d_N4_g2_walls_m2_hllc", "3d_N3_g1_walls_m2_hllc_unstr"])
 def test_curved_fp32_bulk_against_oracle(orc, name):
     ms, ps = CASES[name]
     o, g, Uo = _pair(orc, ms, ps, precision="fp32bulk", exact=False)
@@ -177,11 +186,8 @@ def test_curved_fp32_bulk_against_oracle(orc, name):
 def test_curved_refusals():
     from paper_2208_05310_gb300 import dgk
     ok = mesh_spec(2, 3, [2, 2], geometry=dict(ngeo=1))
-    with pytest.raises(dgk.DgkError):  # HLLC
-        dgk_context(ok, dict(PAPER_PARAMS, model=2, flux="hllc"))
-    g = dgk_context(ok, dict(PAPER_PARAMS, model=2))
-    with pytest.raises(dgk.DgkError):  # switching to HLLC on a curved mesh
-        g.set_params(**dict(PAPER_PARAMS, model=2, flux="hllc"))
+    with pytest.raises(dgk.DgkError):  # HLLC is for model 2
+        dgk_context(ok, dict(PAPER_PARAMS, model=1, flux="hllc"))
     with pytest.raises(dgk.DgkError):  # 2 ngeo > N in 3D
         dgk_context(mesh_spec(3, 3, [2, 2, 2], geometry=dict(ngeo=2)), PAPER_PARAMS)
     with pytest.raises(dgk.DgkError):  # an inverted element map
