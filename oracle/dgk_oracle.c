@@ -293,6 +293,7 @@ typedef struct {
     int wall_kind[6];
     double wall_T[6], wall_rv[6], wall_rl[6], wall_sigma[6], wall_theta[6];
     double wall_g[6][4]; /* kind 2: gamma_1..gamma_4 */
+    double wall_u[6][3]; /* kind 1: velocity of the wall (tangential) */
     double xi[MAXP], w[MAXP], Dhat[MAXP * MAXP], lm[MAXP], lp[MAXP];
     double Dm[MAXP * MAXP]; /* D_il = l_l'(xi_i) */
     or_params prm;
@@ -349,6 +350,11 @@ static int setup(const or_mesh *m, const or_params *p, ctx_t *c)
                     c->wall_g[f][k] = m->wall_gamma[f][k];
                 }
             }
+            for (int k = 0; k < 3; ++k) {
+                double uk = c->wall_kind[f] != 0 && k < c->d ? m->wall_u[f][k] : 0.0;
+                if (!isfinite(uk) || (uk != 0.0 && (c->wall_kind[f] != 1 || k == d))) return -1;
+                c->wall_u[f][k] = uk;
+            }
             if (c->wall_kind[f] != 0) {
                 if (p->model == 0) return -1; /* original NSK: periodic boxes only */
                 c->wall_T[f] = m->wall_T[f];
@@ -387,7 +393,8 @@ static int setup(const or_mesh *m, const or_params *p, ctx_t *c)
         if (m->ngeo < 1 || m->ngeo > MAXG - 1) return -1;
         if (c->d == 2 ? m->ngeo > c->N : 2 * m->ngeo > c->N) return -1;
         for (int f = 0; f < 2 * c->d; ++f)
-            if (c->wall_kind[f] == 2) return -1;
+            for (int k = 0; k < c->d; ++k)
+                if (c->wall_kind[f] == 2 || c->wall_u[f][k] != 0.0) return -1;
         c->curved = 1;
         return setup_curved(c);
     }
@@ -1001,7 +1008,8 @@ static void traces(const ctx_t *c, const double *q, int nvar, double *tr)
 }
 
 /* BR1 pass 1 (Sec. 3.1): central face values q* = (q- + q+)/2 of the interpolated nodal
-   (rho, u, c); at a no-slip wall rho* = rho-, u* = 0, c* = c- (Eq. (bc_assumptions)). */
+   (rho, u, c); at a no-slip wall rho* = rho-, u* = the wall's velocity (zero unless the
+   wall slides), c* = c- (Eq. (bc_assumptions)). */
 static void lift_pass1(const ctx_t *c, const double *q, const double *tr, double *grad)
 {
     long ne = c->ne;
@@ -1018,9 +1026,9 @@ static void lift_pass1(const ctx_t *c, const double *q, const double *tr, double
                         double own = tr[FIDX(v, e, f, fp, ne, nf, nfp)];
                         if (nb >= 0) qs[s][fp] = 0.5 * (own + tr[FIDX(v, nb, fo, fp, ne, nf, nfp)]);
                         else if (v >= 1 && v <= d)
-                            /* no-slip: u* = 0; Navier slip: no normal velocity, the
-                               tangential velocity of the fluid */
-                            qs[s][fp] = (c->wall_kind[f] == 2 && v != 1 + dir) ? own : 0.0;
+                            /* no-slip: u* = the wall's velocity; Navier slip: no normal
+                               velocity, the tangential velocity of the fluid */
+                            qs[s][fp] = (c->wall_kind[f] == 2 && v != 1 + dir) ? own : c->wall_u[f][v - 1];
                         else qs[s][fp] = own;
                     }
                 }
@@ -1137,9 +1145,11 @@ static void point_flux(const ctx_t *c, const double *U, const double *g, const d
    angle, gamma_1 = gamma_2 = gamma_4 = 0; kind 2: generalized Navier slip, below):
    convective part: Rusanov flux against the mirrored ghost state (rho, m - 2(m.n)n, rho e, c)
    with the same pressure and signal speed;
-   viscous part: tau(grad u-).n, energy kappa grad T-.n - gamma_K c- (grad c.n) div u-
-   (wall velocity zero, zeta_c = 0 from the relaxation condition with gamma_4 = 0), order
-   parameter gamma_K beta (grad c.n), with grad c.n from the contact-angle condition. */
+   viscous part: tau(grad u-).n, energy (tau(grad u-).n).u_wall + kappa grad T-.n
+   - gamma_K c- (grad c.n) div u- (the work of the traction on the wall's velocity, zero
+   unless the wall slides; zeta_c = 0 from the relaxation condition with gamma_4 = 0),
+   order parameter gamma_K beta (grad c.n), with grad c.n from the contact-angle
+   condition. */
 static void wall_flux(const ctx_t *c, int f, const double *U, const double *g, const double *gT,
                       double *Fn)
 {
@@ -1205,7 +1215,9 @@ static void wall_flux(const ctx_t *c, int f, const double *U, const double *g, c
             double tau = p->mu * (g[dir * nl + 1 + k] + g[k * nl + 1 + dir] - (k == dir ? 2.0 / 3.0 * divu : 0.0));
             Fv[1 + k] = tau * nsign;
         }
-        Fv[d + 1] = p->kappa * gT[dir] * nsign - p->gammaK * cm * gn * divu;
+        double work = 0.0;
+        for (int k = 0; k < d; ++k) work += Fv[1 + k] * c->wall_u[f][k];
+        Fv[d + 1] = work + p->kappa * gT[dir] * nsign - p->gammaK * cm * gn * divu;
         Fv[d + 2] = p->gammaK * p->beta * gn;
     }
     /* outward normal flux = nsign * Fconv - Fv */

@@ -31,11 +31,15 @@ typedef struct {
        periodic); kind 1: isothermal no-slip wall with static contact angle; kind 2:
        generalized Navier-slip wall, Eq. (bc_nsk_alpha), with the positive parameters
        gamma_1 (contact-angle hysteresis), gamma_2 (slip friction), gamma_3 (heat
-       transfer; the wall temperature is wall_T) and gamma_4 (relaxation). */
+       transfer; the wall temperature is wall_T) and gamma_4 (relaxation).
+       wall_u: velocity of a kind-1 wall sliding in its own plane (the moving isothermal
+       no-slip wall of the sliding-droplet case, Sec. 4; its normal component must be
+       zero); zero for kind 2, whose solid is at rest (Sec. 2.4), and on curved meshes. */
     int wall_kind[6];
     double wall_T[6];
     double wall_theta_deg[6];
     double wall_gamma[6][4];
+    double wall_u[6][3];
     /* Curved elements (optional; xgeo = NULL: the straight box lo..hi).  Element e maps
        the reference cube [-1,1]^dim by the polynomial of degree ngeo per direction that
        interpolates xgeo[k][e][g] (coordinate k) at the equispaced points

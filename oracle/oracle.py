@@ -25,7 +25,7 @@ class OrMesh(C.Structure):
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("periodic", C.c_int * 3),
                 ("wall_kind", C.c_int * 6), ("wall_T", C.c_double * 6),
                 ("wall_theta_deg", C.c_double * 6), ("wall_gamma", (C.c_double * 4) * 6),
-                ("ngeo", C.c_int), ("xgeo", C.POINTER(C.c_double)), ("conn", C.POINTER(C.c_int)),
+                ("wall_u", (C.c_double * 3) * 6), ("ngeo", C.c_int), ("xgeo", C.POINTER(C.c_double)), ("conn", C.POINTER(C.c_int)),
                 ("mortar", C.POINTER(C.c_int)), ("nmortar", C.c_int)]
 
 
@@ -95,8 +95,9 @@ def _check(rc, what):
 
 def make_mesh(dim, N, n, lo, hi, periodic, walls=None, geometry=None, conn=None, mortar=None):
     """walls: dict face -> (T_wall, theta_deg) for faces 0..5 (-x,+x,-y,+y,-z,+z): an
-    isothermal no-slip wall; or (T_wall, theta_deg, gamma_1, gamma_2, gamma_3, gamma_4): a
-    generalized Navier-slip wall (Eq. bc_nsk_alpha).
+    isothermal no-slip wall; (T_wall, theta_deg, (u_1, u_2, u_3)): the same wall sliding
+    with velocity u (tangential); or (T_wall, theta_deg, gamma_1, gamma_2, gamma_3,
+    gamma_4): a generalized Navier-slip wall (Eq. bc_nsk_alpha).
     geometry: None (the straight box) or (ngeo, xgeo), xgeo[dim][nelem][(ngeo+1)^dim] the
     element maps at equispaced points (see dgk_oracle.h); the array is kept alive by the
     returned mesh.
@@ -125,11 +126,16 @@ def make_mesh(dim, N, n, lo, hi, periodic, walls=None, geometry=None, conn=None,
         m.hi[d] = float(hi[d]) if d < dim else 1.0
         m.periodic[d] = int(periodic[d]) if d < dim else 1
     for f, spec in (walls or {}).items():
-        m.wall_kind[f] = 1 if len(spec) == 2 else 2
+        moving = len(spec) == 3
+        m.wall_kind[f] = 1 if len(spec) == 2 or moving else 2
         m.wall_T[f] = spec[0]
         m.wall_theta_deg[f] = spec[1]
-        for k, gk in enumerate(spec[2:6]):
-            m.wall_gamma[f][k] = gk
+        if moving:
+            for k, uk in enumerate(spec[2]):
+                m.wall_u[f][k] = uk
+        else:
+            for k, gk in enumerate(spec[2:6]):
+                m.wall_gamma[f][k] = gk
     return m
 
 
