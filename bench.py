@@ -39,7 +39,8 @@ UNIT = "DOF-stage/s"
 def kernel_bytes_per_node(dim, N, rsize, flux="rusanov", curved=False):
     """curved: the curved-element kernels read in addition the metric terms (dim^2 + 1
     values per node: J a^i and 1/J) and the face metrics (dim values per face point) in
-    the lifting kernels, and 1/J in k_surf_rk."""
+    the lifting kernels, and 1/J in k_surf_rk (with HLLC also the face metrics, for the
+    unit normal)."""
     nv, nl = dim + 3, dim + 2
     f = 2 * dim / (N + 1)  # face points per node (own faces)
     nfd = 2 * nv + (3 if flux == "hllc" else 1)  # face data values (HLLC: + pressure, sound speed)
@@ -50,7 +51,8 @@ def kernel_bytes_per_node(dim, N, rsize, flux="rusanov", curved=False):
     surf = rsize * nfd * f + rsize * nv + 8 * nv * 4 + rsize * nl * f + shadow_w
     if curved:
         geo = rsize * (dim * dim + 1) + rsize * dim * f
-        return {"k_lift1c": lift1 + geo, "k_lift2volc": lift2 + geo, "k_surf_rk": surf + rsize}
+        surf += rsize + (rsize * dim * f if flux == "hllc" else 0)
+        return {"k_lift1c": lift1 + geo, "k_lift2volc": lift2 + geo, "k_surf_rk": surf}
     return {"k_lift1": lift1, "k_lift2vol": lift2, "k_surf_rk": surf}
 
 
@@ -685,8 +687,8 @@ def main():
         wl["mesh"] = dict(wl["mesh"], walls={f: (Tw, th, 1e-5, 0.1, 0.05, 1.0) for f, (Tw, th) in wl["mesh"]["walls"].items()})
         wl["name"] += ", Navier-slip walls"
     if args.mesh in ("curved", "unstructured", "mortar"):
-        if "batch" in wl or args.flux == "hllc" or args.walls != "noslip":
-            print(json.dumps({"error": "curved elements: single problems, Rusanov flux, no-slip walls"}))
+        if "batch" in wl or args.walls != "noslip":
+            print(json.dumps({"error": "curved elements: single problems, no-slip walls"}))
             return 2
         wl["geometry"] = dict(CURVED_GEOMETRY)
         wl["name"] += ", curved elements (degree-2 maps, walls bent by 2% of the height)"

@@ -12,7 +12,7 @@
  *   DGSEM on Legendre-Gauss nodes; box meshes, curved elements, unstructured connectivity
  *   and 2:1 mortars; Rusanov or (model 2) HLLC flux; BR1 lifting of (rho, u, c), then of
  *   (T, grad c) for grad T and lap c; point-wise sources                Sec. 3.1, Sec. 4
- *   isothermal no-slip walls with a static contact angle, generalized Navier-slip walls
+ *   isothermal no-slip walls (at rest or sliding) with a static contact angle, Navier-slip walls
  *                                                          Sec. 2.4, Eq. (bc_nsk_alpha),
  *                                                          Eq. (helmfreesurftot_derivative)
  *   the original NSK model on periodic meshes              Eq. (navierstokeskorteweg)
@@ -94,12 +94,19 @@ typedef struct {
    Navier-slip wall, Eq. bc_nsk_alpha with the non-negative parameters gamma[0..3] =
    gamma_1 (contact-angle hysteresis), gamma_2 (slip friction), gamma_3 (heat transfer
    to the wall at T_wall) and gamma_4 (relaxation condition); the fluid slips along the
-   wall (no normal velocity). */
+   wall (no normal velocity).
+   u_wall: velocity of a kind-1 wall sliding in its own plane (the moving no-slip wall of
+   the sliding-droplet case, Sec. 4): the lifting takes u* = u_wall at the wall and the
+   wall's traction does the work (tau n) . u_wall in the energy flux.  Components beyond
+   dim are ignored; the normal component must be zero, and so must the whole vector for
+   kind 2 (the solid is at rest, Sec. 2.4) and on curved meshes (DGK_ERR_ARG /
+   DGK_ERR_UNSUPPORTED otherwise). */
 typedef struct {
     int kind;
     double T_wall;
     double theta_deg;
-    double gamma[4];  /* kind 2 only */
+    double gamma[4];    /* kind 2 only */
+    double u_wall[3];   /* kind 1 only; zero: a wall at rest */
 } dgk_wall;
 
 /* Cartesian box mesh of hexahedral (dim 3) or quadrilateral (dim 2) elements. */

@@ -396,6 +396,7 @@ void fill_bulk(dgk::KArgs<R> &a, const dgk::Geom &g, const dgk::Phys &ph, const 
         a.v.wr.g3[f] = (R)w.g[f][2];
         a.v.wr.g1gK[f] = (R)(w.g[f][0] / ph.gK);
         a.v.wr.g1g4[f] = (R)(w.g[f][0] * w.g[f][3]);
+        for (int k = 0; k < 3; ++k) a.v.wr.uw[f][k] = (R)w.u[f][k];
         a.v.wr.K[f] = (R)w.K[f];
         a.v.wr.rl[f] = (R)w.rl[f];
         a.v.wr.rv[f] = (R)w.rv[f];
@@ -431,6 +432,7 @@ int build_consts(dgk_ctx *c)
             return fail(DGK_ERR_THERMO, "wall temperature has no saturation states (need 0 < T_wall < 1)");
         w.kind[f] = wf.kind;
         for (int k = 0; k < 4; ++k) w.g[f][k] = wf.kind == 2 ? wf.gamma[k] : 0.0;
+        for (int k = 0; k < c->D; ++k) w.u[f][k] = wf.kind == 1 ? wf.u_wall[k] : 0.0;
         w.Tw[f] = wf.T_wall;
         w.rv[f] = rv;
         w.rl[f] = rl;
@@ -698,6 +700,9 @@ int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m)
                     for (int k = 0; k < 4; ++k)
                         if (!(w.gamma[k] >= 0.0) || !std::isfinite(w.gamma[k]))
                             return fail(DGK_ERR_ARG, "wall parameters gamma_1..gamma_4 must be finite and non-negative");
+                for (int k = 0; k < m->dim; ++k)
+                    if (!std::isfinite(w.u_wall[k]) || (w.u_wall[k] != 0.0 && (w.kind != 1 || k == d)))
+                        return fail(DGK_ERR_ARG, "a wall velocity must be finite, tangential and on a no-slip wall");
             }
         }
     }
@@ -758,9 +763,13 @@ static int mesh_curved_impl(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const d
     if (m->dim != 2 && m->dim != 3) return fail(DGK_ERR_UNSUPPORTED, "dim must be 2 or 3");
     if (ngeo < 1 || (m->dim == 2 ? ngeo > m->N : 2 * ngeo > m->N))
         return fail(DGK_ERR_UNSUPPORTED, "curved elements need 1 <= ngeo <= N (2D) or 1 <= 2 ngeo <= N (3D)");
-    for (int f = 0; f < 2 * m->dim; ++f)
+    for (int f = 0; f < 2 * m->dim; ++f) {
         if (!m->periodic[f / 2] && m->wall[f].kind == 2)
             return fail(DGK_ERR_UNSUPPORTED, "curved elements take walls of kind 1 (no-slip contact angle)");
+        for (int k = 0; k < m->dim; ++k)
+            if (!m->periodic[f / 2] && m->wall[f].u_wall[k] != 0.0)
+                return fail(DGK_ERR_UNSUPPORTED, "curved elements take walls at rest");
+    }
     if (conn) {
         // the tables: neighbours in range and pointing back, orientations of the
         // dimension, walls of the box's wall table (kind 1)

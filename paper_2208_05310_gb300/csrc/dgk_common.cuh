@@ -48,6 +48,7 @@ struct Walls {
     int kind[6];
     double Tw[6], rv[6], rl[6], K[6];
     double g[6][4];  // kind 2 (generalized Navier slip): gamma_1..gamma_4
+    double u[6][3];  // kind 1: velocity of a sliding wall (tangential)
 };
 
 // Division of 32-bit unsigned integers by an invariant divisor d >= 1 with a multiply-high
@@ -93,6 +94,7 @@ struct WallsR {
     R K[6], rl[6], rv[6], Tw[6];
     int kind[6];                        // 1 no-slip isothermal, 2 generalized Navier slip
     R g1[6], g2[6], g3[6], g1gK[6], g1g4[6];  // kind 2: gamma_1, gamma_2, gamma_3, gamma_1/gamma_K, gamma_1 gamma_4
+    R uw[6][3];                         // kind 1: velocity of a sliding wall (tangential; zero at rest)
 };
 
 // 1D operators on the P = N+1 Legendre-Gauss nodes (Sec. 3.1):

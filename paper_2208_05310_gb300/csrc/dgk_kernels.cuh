@@ -653,9 +653,14 @@ __device__ __forceinline__ void face_flux(const Ctx<R> &a, int f, int dir, bool 
         F[D + 2] -= nsign * ph.gKbeta * gnn;
         return;
     }
+    // isothermal no-slip wall: the traction does work on the wall's velocity (a sliding wall)
+    R work = R(0);
 #pragma unroll
-    for (int k = 0; k < D; ++k) F[1 + k] -= tau[k];
-    F[D + 1] -= ph.kap * gTd - nsign * ph.gK * c * gn * divu;
+    for (int k = 0; k < D; ++k) {
+        F[1 + k] -= tau[k];
+        work += tau[k] * a.v.wr.uw[f][k];
+    }
+    F[D + 1] -= work + ph.kap * gTd - nsign * ph.gK * c * gn * divu;
     F[D + 2] -= nsign * ph.gKbeta * gn;
 }
 
@@ -727,8 +732,9 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
                 const R own = a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)];
                 R val;
                 if (b >= 0) val = R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, v, b, 2 * dir + 1 - side, fp)]);
-                // walls: u* = 0 (no slip), or the fluid's tangential velocity (Navier slip)
-                else val = (v >= 1 && v <= D && (a.v.wr.kind[f] != 2 || v == 1 + dir)) ? R(0) : own;
+                // walls: u* = the wall's velocity (no slip; zero unless the wall slides), or
+                // the fluid's tangential velocity (Navier slip)
+                else val = (v >= 1 && v <= D && (a.v.wr.kind[f] != 2 || v == 1 + dir)) ? a.v.wr.uw[f][v - 1] : own;
                 sQs[(f * NL + v) * NFP + fp] = val;
             }
         }

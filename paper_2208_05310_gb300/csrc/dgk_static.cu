@@ -113,6 +113,7 @@ int fill(dgk::KArgs<R> &a, const dgk_params &q, const dgk_box_mesh &m, const dgk
         a.v.wr.g3[f] = (R)g3;
         a.v.wr.g1gK[f] = (R)(g1 / q.gammaK);
         a.v.wr.g1g4[f] = (R)(g1 * g4);
+        for (int k = 0; k < 3; ++k) a.v.wr.uw[f][k] = (R)(wf.kind == 1 && k < D ? wf.u_wall[k] : 0.0);
         a.v.wr.rl[f] = (R)rl;
         a.v.wr.rv[f] = (R)rv;
         a.v.wr.Tw[f] = (R)m.wall[f].T_wall;
@@ -180,6 +181,9 @@ extern "C" int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *m, const 
                 for (int k = 0; k < 4; ++k)
                     if (!(w.gamma[k] >= 0.0) || !std::isfinite(w.gamma[k]))
                         return fail_static(DGK_ERR_ARG, "wall parameters gamma_1..gamma_4 must be finite and non-negative");
+            for (int k = 0; k < D; ++k)
+                if (!std::isfinite(w.u_wall[k]) || (w.u_wall[k] != 0.0 && (w.kind != 1 || k == d)))
+                    return fail_static(DGK_ERR_ARG, "a wall velocity must be finite, tangential and on a no-slip wall");
         }
         ne *= m->n[d];
     }

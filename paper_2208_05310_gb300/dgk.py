@@ -31,14 +31,19 @@ class DgkParams(C.Structure):
 
 
 class DgkWall(C.Structure):
-    _fields_ = [("kind", C.c_int), ("T_wall", C.c_double), ("theta_deg", C.c_double), ("gamma", C.c_double * 4)]
+    _fields_ = [("kind", C.c_int), ("T_wall", C.c_double), ("theta_deg", C.c_double), ("gamma", C.c_double * 4),
+                ("u_wall", C.c_double * 3)]
 
 
 def _wall(spec):
-    """(T_wall, theta_deg): isothermal no-slip wall; (T_wall, theta_deg, gamma_1, gamma_2,
-    gamma_3, gamma_4): generalized Navier-slip wall."""
+    """(T_wall, theta_deg): isothermal no-slip wall; (T_wall, theta_deg, (u_1, u_2, u_3)):
+    the same wall sliding with velocity u; (T_wall, theta_deg, gamma_1, gamma_2, gamma_3,
+    gamma_4): generalized Navier-slip wall."""
     if len(spec) == 2:
         return DgkWall(1, spec[0], spec[1])
+    if len(spec) == 3:
+        u = list(spec[2]) + [0.0] * (3 - len(spec[2]))
+        return DgkWall(1, spec[0], spec[1], (C.c_double * 4)(), (C.c_double * 3)(*u))
     return DgkWall(2, spec[0], spec[1], (C.c_double * 4)(*spec[2:6]))
 
 
@@ -169,8 +174,9 @@ def make_params(model=1, rk=4, precision="fp64", gammaK=1e-4, mu=0.01, kappa=1.0
 
 
 def make_box_mesh(dim, N, n, lo, hi, periodic, walls=None):
-    """walls: {face: (T_wall, theta_deg)} (no-slip) or {face: (T_wall, theta_deg, g1, g2, g3, g4)}
-    (Navier slip), faces 0..5 = -x,+x,-y,+y,-z,+z."""
+    """walls: {face: (T_wall, theta_deg)} (no-slip), {face: (T_wall, theta_deg, (u_1, u_2, u_3))}
+    (no-slip, sliding with velocity u) or {face: (T_wall, theta_deg, g1, g2, g3, g4)} (Navier
+    slip), faces 0..5 = -x,+x,-y,+y,-z,+z."""
     m = DgkBoxMesh()
     m.dim, m.N = dim, N
     for d in range(3):
@@ -228,7 +234,8 @@ class Context:
         _check(lib().dgk_set_params(self._h, C.byref(p)), "dgk_set_params")
 
     def mesh_box(self, dim, N, n, lo, hi, periodic, walls=None):
-        """walls: {face: (T_wall, theta_deg)} (no-slip) or {face: (T_wall, theta_deg, g1, g2, g3, g4)}
+        """walls: {face: (T_wall, theta_deg)} (no-slip), {face: (T_wall, theta_deg, (u_1, u_2, u_3))}
+        (sliding no-slip) or {face: (T_wall, theta_deg, g1, g2, g3, g4)}
     (Navier slip), faces 0..5 = -x,+x,-y,+y,-z,+z."""
         m = make_box_mesh(dim, N, n, lo, hi, periodic, walls)
         _check(lib().dgk_mesh_box(self._h, C.byref(m)), "dgk_mesh_box")

@@ -66,6 +66,12 @@ CASES = {
     "3d_N3_slip_m2": (mesh_spec(3, 3, [2, 2, 3], periodic=[1, 1, 0], walls={4: (0.85, 60.0, 0.03, 0.05, 0.2, 0.3),
                                                                             5: (0.8, 90.0, 0.0, 0.5, 1.0, 0.0)}),
                       dict(PAPER_PARAMS, model=2)),
+    # sliding no-slip walls (the moving wall of the sliding-droplet case, Sec. 4)
+    "2d_N4_sliding": (mesh_spec(2, 4, [3, 3], periodic=[1, 0], walls={2: (0.85, 60.0), 3: (0.8, 120.0, (0.3, 0.0, 0.0))}),
+                      dict(PAPER_PARAMS)),
+    "3d_N3_sliding_m2_hllc": (mesh_spec(3, 3, [2, 2, 3], periodic=[1, 1, 0],
+                                        walls={4: (0.85, 60.0, (0.0, 0.1, 0.0)), 5: (0.85, 90.0, (0.2, -0.1, 0.0))}),
+                              dict(PAPER_PARAMS, model=2, flux="hllc")),
     "2d_single_element": (mesh_spec(2, 3, [1, 1]), dict(PAPER_PARAMS)),
     "3d_single_element_walls": (mesh_spec(3, 3, [1, 1, 1], periodic=[1, 1, 0],
                                           walls={4: (0.85, 45.0), 5: (0.85, 135.0)}), dict(PAPER_PARAMS)),
@@ -149,7 +155,7 @@ def test_one_step_parity_fp64(orc, name):
     assert np.all(err < TOL64), err
 
 
-@pytest.mark.parametrize("name,rk", [("2d_N3_walls", 3), ("3d_N3_walls", 4), ("2d_N4_periodic_m2", 4)])
+@pytest.mark.parametrize("name,rk", [("2d_N3_walls", 3), ("3d_N3_walls", 4), ("2d_N4_periodic_m2", 4), ("2d_N4_sliding", 4)])
 def test_ten_steps_parity_fp64(orc, name, rk):
     ms, ps = CASES[name]
     o, g, Uo = _state_pair(orc, ms, ps, rk=rk)
@@ -203,7 +209,8 @@ def tol32_step(dim):
 
 
 @pytest.mark.parametrize("name", ["2d_N3_walls", "3d_N3_walls", "3d_N5_walls", "2d_N4_periodic_m2", "2d_N4_walls_m2_hllc",
-                                  "3d_N3_walls_m2_hllc", "2d_N4_slip", "3d_N3_slip_m2"])
+                                  "3d_N3_walls_m2_hllc", "2d_N4_slip", "3d_N3_slip_m2", "2d_N4_sliding",
+                                  "3d_N3_sliding_m2_hllc"])
 def test_fp32_bulk_against_oracle(orc, name):
     ms, ps = CASES[name]
     o, g, Uo = _state_pair(orc, ms, ps, precision="fp32bulk")
@@ -255,3 +262,13 @@ def test_integer_conversions_match_hardware():
                   1.1754943508222875e-38, 1.0, -1.0, 2.0 ** 127, 2.0 ** -126]),
     ])
     assert dgk.check_conversions(x) == 0
+
+
+def test_sliding_wall_refusals():
+    from paper_2208_05310_gb300 import dgk
+    with pytest.raises(dgk.DgkError):  # a normal component
+        dgk_context(mesh_spec(2, 3, [2, 2], periodic=[1, 0], walls={2: (0.85, 90.0), 3: (0.85, 90.0, (0.1, 0.2, 0.0))}),
+                    PAPER_PARAMS)
+    with pytest.raises(dgk.DgkError):  # curved elements take walls at rest
+        dgk_context(mesh_spec(2, 3, [2, 2], periodic=[1, 0], walls={2: (0.85, 90.0), 3: (0.85, 90.0, (0.1, 0.0, 0.0))},
+                              geometry=dict(ngeo=1)), PAPER_PARAMS)
