@@ -312,8 +312,9 @@ struct CLiftC {
                 const R own = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
                 int fo, o, w;
                 const long long b = face_nbr<D, N, R>(a.v, t, f, fo, o, w);
-                if (b <= kMortar) sCs[q] = R(0.5) * (own + a.v.mtr1[((long long)(D + 1) * a.v.g.nslot + (kMortar - b)) * NFP + fp]);
-                else sCs[q] = b >= 0 ? R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, D + 1, b, fo, map_fp<S::P>(o, fp))]) : own;
+                if (b >= 0) sCs[q] = R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, D + 1, b, fo, map_fp<S::P>(o, fp))]);
+                else if (b <= kMortar) sCs[q] = R(0.5) * (own + a.v.mtr1[((long long)(D + 1) * a.v.g.nslot + (kMortar - b)) * NFP + fp]);
+                else sCs[q] = own;
             }
             stage_face_metrics<D, N, R>(a, t, sJf);
         }
@@ -518,15 +519,23 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
             const int f = q / NFP, fp = q % NFP;
             int fo, o, w;
             const long long b = face_nbr<D, N, R>(a.v, t, f, fo, o, w);
-            const int fq = map_fp<P>(o, fp);
+            // one branch per kind of face, so that each point issues only its own loads
+            if (b >= 0) {
+                const int fq = map_fp<P>(o, fp);
 #pragma unroll
-            for (int v = 0; v < NL; ++v) {
-                const R own = a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)];
-                R val;
-                if (b <= kMortar) val = R(0.5) * (own + a.v.mtr1[((long long)v * a.v.g.nslot + (kMortar - b)) * NFP + fp]);
-                else if (b >= 0) val = R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, v, b, fo, fq)]);
-                else val = (v >= 1 && v <= D) ? R(0) : own;
-                sQs[(f * NL + v) * NFP + fp] = val;
+                for (int v = 0; v < NL; ++v)
+                    sQs[(f * NL + v) * NFP + fp] =
+                        R(0.5) * (a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)] + a.v.tr1[fidx<NF, NFP>(ne, v, b, fo, fq)]);
+            } else if (b <= kMortar) {
+                const long long sl = kMortar - b;
+#pragma unroll
+                for (int v = 0; v < NL; ++v)
+                    sQs[(f * NL + v) * NFP + fp] = R(0.5) * (a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)] +
+                                                             a.v.mtr1[((long long)v * a.v.g.nslot + sl) * NFP + fp]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < NL; ++v)
+                    sQs[(f * NL + v) * NFP + fp] = (v >= 1 && v <= D) ? R(0) : a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)];
             }
         }
         stage_face_metrics<D, N, R>(a, t, sJf);
