@@ -352,7 +352,8 @@ static int setup(const or_mesh *m, const or_params *p, ctx_t *c)
             }
             for (int k = 0; k < 3; ++k) {
                 double uk = c->wall_kind[f] != 0 && k < c->d ? m->wall_u[f][k] : 0.0;
-                if (!isfinite(uk) || (uk != 0.0 && (c->wall_kind[f] != 1 || k == d))) return -1;
+                /* box walls: tangential; curved walls: projected on the tangent plane per point */
+                if (!isfinite(uk) || (uk != 0.0 && (c->wall_kind[f] != 1 || (k == d && !m->xgeo)))) return -1;
                 c->wall_u[f][k] = uk;
             }
             if (c->wall_kind[f] != 0) {
@@ -392,9 +393,6 @@ static int setup(const or_mesh *m, const or_params *p, ctx_t *c)
         c->conn = m->conn;
         if (m->ngeo < 1 || m->ngeo > MAXG - 1) return -1;
         if (c->d == 2 ? m->ngeo > c->N : 2 * m->ngeo > c->N) return -1;
-        for (int f = 0; f < 2 * c->d; ++f)
-            for (int k = 0; k < c->d; ++k)
-                if (c->wall_kind[f] == 2 || c->wall_u[f][k] != 0.0) return -1;
         c->curved = 1;
         return setup_curved(c);
     }
@@ -1440,8 +1438,10 @@ static double face_normal(const ctx_t *c, long e, int f, int fp, double *nh)
     return sa;
 }
 
-/* BR1 pass 1 on curved elements: face values as in lift_pass1 (central; at a no-slip
-   wall rho* = rho-, u* = 0, c* = c-), gradients by grad_curved. */
+/* BR1 pass 1 on curved elements: face values as in lift_pass1 (central; at a wall
+   rho* = rho-, c* = c-, and u* the part of the wall's velocity (no slip) or of the fluid's
+   velocity (Navier slip) tangential to the wall, u* = b - (b.n) n), gradients by
+   grad_curved. */
 static void lift_pass1_c(const ctx_t *c, const double *q, const double *tr, double *grad)
 {
     long ne = c->ne;
@@ -1457,7 +1457,16 @@ static void lift_pass1_c(const ctx_t *c, const double *q, const double *tr, doub
                 for (int fp = 0; fp < nfp; ++fp) {
                     double own = tr[FIDX(v, e, f, fp, ne, nf, nfp)];
                     if (!wall) fs[f * nfp + fp] = 0.5 * (own + nbt[fp]);
-                    else fs[f * nfp + fp] = (v >= 1 && v <= d) ? 0.0 : own;
+                    else if (v >= 1 && v <= d) {
+                        int w = wall_of(c, e, f);
+                        double nh[3], b[3], bn = 0.0;
+                        face_normal(c, e, f, fp, nh);
+                        for (int k = 0; k < d; ++k) {
+                            b[k] = c->wall_kind[w] == 2 ? tr[FIDX(1 + k, e, f, fp, ne, nf, nfp)] : c->wall_u[w][k];
+                            bn += b[k] * nh[k];
+                        }
+                        fs[f * nfp + fp] = b[v - 1] - bn * nh[v - 1];
+                    } else fs[f * nfp + fp] = own;
                 }
             }
             grad_curved(c, e, q + IDX(v, e, 0, ne, np), fs, out);
@@ -1467,11 +1476,13 @@ static void lift_pass1_c(const ctx_t *c, const double *q, const double *tr, doub
     }
 }
 
-/* BR1 pass 2 on curved elements: grad T (T* central, T_wall at walls) and
-   lap c = sum_k [BR1 gradient of the lifted d c/d x_k]_k, whose face values are the
-   central means of the interpolated d c/d x_k; at a wall the interpolated gradient with
-   its normal component replaced by the contact-angle value,
-   g* = g- + (g_n - g-.n) n (only g*.n enters the lifting). */
+/* BR1 pass 2 on curved elements: grad T (T* central; at walls T_wall, or the fluid's
+   trace at a Navier-slip wall) and lap c = sum_k [BR1 gradient of the lifted
+   d c/d x_k]_k, whose face values are the central means of the interpolated d c/d x_k;
+   at a wall the interpolated gradient with its normal component replaced by the
+   contact-angle value, g* = g- + (g_n - g-.n) n (only g*.n enters the lifting), with
+   the gamma_1 div u- term of a Navier-slip wall (div u- traced from the pass-1
+   gradients). */
 static void lift_pass2_c(const ctx_t *c, const double *T, const double *grad, const double *trq,
                          double *gT, double *lap)
 {
@@ -1528,8 +1539,15 @@ static void lift_pass2_c(const ctx_t *c, const double *T, const double *grad, co
                         gmn += gm[k] * nh[k];
                     }
                     int w = wall_of(c, e, f);
-                    double gn = wall_gn(c, w, trq[FIDX(vc, e, f, fp, ne, nf, nfp)], 0.0);
-                    Ts[f * nfp + fp] = c->wall_T[w];
+                    double divu = 0.0;
+                    if (c->wall_kind[w] == 2)
+                        for (int k = 0; k < d; ++k) {
+                            double tk[MAXP * MAXP];
+                            trace_elem(c, grad + IDX(k * nl + 1 + k, e, 0, ne, np), f / 2, f % 2, tk);
+                            divu += tk[fp];
+                        }
+                    double gn = wall_gn(c, w, trq[FIDX(vc, e, f, fp, ne, nf, nfp)], divu);
+                    Ts[f * nfp + fp] = c->wall_kind[w] == 2 ? tOwn : c->wall_T[w];
                     for (int k = 0; k < d; ++k) Gs[k][f * nfp + fp] = gm[k] + (gn - gmn) * nh[k];
                 }
             }
@@ -1565,10 +1583,15 @@ static void flux_along(const ctx_t *c, const double *U, const double *g, const d
     *lam = fabs(un) + sound_speed(c, U[0], temperature(c, U, g)) * sqrt(an);
 }
 
-/* Outward normal flux through a no-slip contact-angle wall with unit outward normal nh,
-   per unit area (wall_flux for a general normal): Rusanov against the ghost
-   (rho, m - 2(m.n)n, rho e, c) with equal pressure and signal speed, minus the viscous
-   flux tau(grad u-).n, kappa grad T-.n - gamma_K c- g_n div u-, gamma_K beta g_n. */
+/* Outward normal flux through a wall with unit outward normal nh, per unit area
+   (wall_flux for a general normal): Rusanov against the ghost (rho, m - 2(m.n)n, rho e, c)
+   with equal pressure and signal speed, minus the viscous flux.  Kind 1 (no slip):
+   tau(grad u-).n, (tau n).u_w + kappa grad T-.n - gamma_K c- g_n div u-, gamma_K beta g_n,
+   with u_w the wall's velocity projected on the tangent plane.  Kind 2 (Navier slip,
+   Eq. (bc_nsk_alpha)): the normal traction (n.tau n) n of the fluid plus the tangential
+   traction t = gamma_1 div u- (grad c- - (grad c-.n) n) - gamma_2 (u- - (u-.n) n), its work
+   t.u-, the heat flux -gamma_3 (1/T_wall - 1/T-), zeta_c = -gamma_1 gamma_4 div u-, and
+   g_n with the gamma_1 term. */
 static void wall_flux_c(const ctx_t *c, int f, const double *U, const double *g, const double *gT,
                         const double *nh, double *Fn)
 {
@@ -1608,10 +1631,33 @@ static void wall_flux_c(const ctx_t *c, int f, const double *U, const double *g,
             t += p->mu * (g[j * nl + 1 + k] + g[k * nl + 1 + j] - (k == j ? 2.0 / 3.0 * divu : 0.0)) * nh[j];
         Fv[1 + k] = t;
     }
-    double gTn = 0.0;
-    for (int k = 0; k < d; ++k) gTn += gT[k] * nh[k];
-    Fv[d + 1] = p->kappa * gTn - p->gammaK * cm * gn * divu;
-    Fv[d + 2] = p->gammaK * p->beta * gn;
+    if (c->wall_kind[f] == 2) {
+        double g1 = c->wall_g[f][0], g2 = c->wall_g[f][1], g3 = c->wall_g[f][2], g4 = c->wall_g[f][3];
+        double tnn = 0.0, gcn = 0.0, un = 0.0, work = 0.0, u[3];
+        for (int k = 0; k < d; ++k) {
+            u[k] = U[1 + k] / U[0];
+            tnn += Fv[1 + k] * nh[k];
+            gcn += g[k * nl + d + 1] * nh[k];
+            un += u[k] * nh[k];
+        }
+        for (int k = 0; k < d; ++k) {
+            double tk = g1 * divu * (g[k * nl + d + 1] - gcn * nh[k]) - g2 * (u[k] - un * nh[k]);
+            Fv[1 + k] = tnn * nh[k] + tk;
+            work += tk * u[k];
+        }
+        double zeta = -g1 * g4 * divu;
+        Fv[d + 1] = work - g3 * (1.0 / c->wall_T[f] - 1.0 / T) - p->gammaK * cm * gn * divu + p->gammaK * gn * zeta;
+        Fv[d + 2] = p->gammaK * p->beta * gn;
+    } else {
+        double gTn = 0.0, uwn = 0.0, work = 0.0;
+        for (int k = 0; k < d; ++k) {
+            gTn += gT[k] * nh[k];
+            uwn += c->wall_u[f][k] * nh[k];
+        }
+        for (int k = 0; k < d; ++k) work += Fv[1 + k] * (c->wall_u[f][k] - uwn * nh[k]);
+        Fv[d + 1] = work + p->kappa * gTn - p->gammaK * cm * gn * divu;
+        Fv[d + 2] = p->gammaK * p->beta * gn;
+    }
     for (int v = 0; v < nv; ++v) Fn[v] = Fc[v] - Fv[v];
 }
 

@@ -33,8 +33,9 @@ typedef struct {
        gamma_1 (contact-angle hysteresis), gamma_2 (slip friction), gamma_3 (heat
        transfer; the wall temperature is wall_T) and gamma_4 (relaxation).
        wall_u: velocity of a kind-1 wall sliding in its own plane (the moving isothermal
-       no-slip wall of the sliding-droplet case, Sec. 4; its normal component must be
-       zero); zero for kind 2, whose solid is at rest (Sec. 2.4), and on curved meshes. */
+       no-slip wall of the sliding-droplet case, Sec. 4; on the box its normal component
+       must be zero, on curved elements it is projected on the local tangent plane); zero
+       for kind 2, whose solid is at rest (Sec. 2.4). */
     int wall_kind[6];
     double wall_T[6];
     double wall_theta_deg[6];
@@ -46,7 +47,8 @@ typedef struct {
        t_a = -1 + 2a/ngeo, g = a + (ngeo+1)(b + (ngeo+1)c).  The element connectivity is
        the box's (n, periodic, walls); neighbouring elements must share their face
        points.  Requires ngeo <= N (2D) or 2 ngeo <= N (3D), so that the metric terms
-       are polynomials the scheme differentiates exactly; walls of kind 1 only. */
+       are polynomials the scheme differentiates exactly.  Walls as above, along the local
+       normal; a wall velocity is projected on the local tangent plane. */
     int ngeo;
     const double *xgeo;
     /* Unstructured connectivity (optional, with xgeo; NULL: the box's).  For face

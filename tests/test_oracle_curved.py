@@ -5,7 +5,9 @@ fluxes along the face metric).  None of these compares the path with itself:
 * an affine map of the box reproduces the straight-box discretisation (its weak-form
   lifting and diagonal metrics are pinned by the other oracle tests);
 * a rotated box gives the rotated right-hand side (mass, energy, c unchanged, momentum
-  rotated): this catches transposed metric terms and wrong normals, also at walls;
+  rotated): this catches transposed metric terms and wrong normals, also at walls
+  (no-slip, sliding with a rotated wall velocity, and Navier slip, whose tractions and
+  tangential projections then run along oblique normals);
 * a uniform state is preserved on curved elements (discrete metric identities and one
   face metric for both elements), also at rest against bent walls at 90 degrees;
 * mass (and, without sources, momentum) is conserved on a periodic curved mesh;
@@ -20,6 +22,22 @@ from paper_2208_05310_gb300 import inputs
 
 WALLS2 = {2: (0.85, 60.0), 3: (0.8, 120.0)}
 WALLS3 = {4: (0.85, 60.0), 5: (0.8, 120.0)}
+# Navier slip below (all of gamma_1..4), a sliding no-slip wall above
+SLIP2 = {2: (0.9, 70.0, 0.02, 0.1, 0.3, 0.5), 3: (0.85, 110.0, (0.3, 0.0, 0.0))}
+SLIP3 = {4: (0.85, 60.0, 0.03, 0.05, 0.2, 0.3), 5: (0.8, 100.0, (0.2, -0.1, 0.0))}
+
+
+def _rotated_walls(walls, R):
+    """The wall table of the rotated box: sliding velocities rotated with the box."""
+    out = {}
+    for f, spec in walls.items():
+        if len(spec) == 3:
+            u = np.zeros(R.shape[0])
+            u[:] = spec[2][:R.shape[0]]
+            out[f] = spec[:2] + (tuple(R @ u) + (0.0,) * (3 - R.shape[0]),)
+        else:
+            out[f] = spec
+    return out
 # beta = 1 keeps the relaxation bound 2/(alpha beta) from deciding max_dt
 DT_PARAMS = dict(PAPER_PARAMS, beta=1.0)
 
@@ -39,6 +57,8 @@ BOX_CASES = {
     "2d_N3_walls": mesh_spec(2, 3, [4, 3], periodic=[1, 0], walls=WALLS2),
     "2d_N4_periodic": mesh_spec(2, 4, [3, 3]),
     "3d_N3_walls": mesh_spec(3, 3, [2, 3, 2], periodic=[1, 1, 0], walls=WALLS3),
+    "2d_N3_slip_sliding": mesh_spec(2, 3, [4, 3], periodic=[1, 0], walls=SLIP2),
+    "3d_N3_slip_sliding": mesh_spec(3, 3, [2, 3, 2], periodic=[1, 1, 0], walls=SLIP3),
 }
 
 
@@ -65,6 +85,8 @@ ROT_CASES = {
     "2d_walls": (mesh_spec(2, 3, [4, 3], periodic=[1, 0], walls=WALLS2), _rot2(-1.1)),
     "3d_periodic": (mesh_spec(3, 3, [2, 2, 3]), _rot3([1.0, 2.0, 0.5], 0.7)),
     "3d_walls": (mesh_spec(3, 3, [3, 2, 2], periodic=[1, 1, 0], walls=WALLS3), _rot3([-0.3, 1.0, 0.8], 2.0)),
+    "2d_slip_sliding": (mesh_spec(2, 3, [4, 3], periodic=[1, 0], walls=SLIP2), _rot2(0.9)),
+    "3d_slip_sliding": (mesh_spec(3, 3, [3, 2, 2], periodic=[1, 1, 0], walls=SLIP3), _rot3([0.5, -1.0, 0.3], 1.3)),
 }
 
 
@@ -72,7 +94,7 @@ ROT_CASES = {
 def test_rotated_box_rotates_the_rhs(orc, name):
     ms, R = ROT_CASES[name]
     d = ms["dim"]
-    mr = dict(ms, geometry=dict(ngeo=1, rotation=R))
+    mr = dict(ms, geometry=dict(ngeo=1, rotation=R), walls=_rotated_walls(ms["walls"], R))
     ob, orr = oracle_objects(orc, ms, DT_PARAMS), oracle_objects(orc, mr, DT_PARAMS)
     assert np.abs(orr.node_coords() - np.einsum("kj,jen->ken", R, ob.node_coords())).max() < 1e-14
     prim = inputs.random_admissible(d, ob.nelem, ob.np, 3)
@@ -104,11 +126,14 @@ def test_free_stream_on_curved_elements(orc, dim, N, ngeo, n):
     assert np.abs(Ut).max() < 1e-10, np.abs(Ut).max(axis=(1, 2))
 
 
+@pytest.mark.parametrize("slip", [False, True])
 @pytest.mark.parametrize("dim,N,ngeo,n", [(2, 4, 2, [4, 3]), (3, 4, 2, [2, 2, 3])])
-def test_rest_against_bent_walls(orc, dim, N, ngeo, n):
+def test_rest_against_bent_walls(orc, dim, N, ngeo, n, slip):
     """Uniform fluid at rest at the wall temperature, contact angle 90 degrees: the walls
-    (bent by the map) exert the pressure only, which the curved volume terms balance."""
-    walls = {2 * (dim - 1): (0.9, 90.0), 2 * (dim - 1) + 1: (0.9, 90.0)}
+    (bent by the map) exert the pressure only, which the curved volume terms balance.
+    Navier-slip walls (all gamma non-zero) exert no traction and no heat flux on it."""
+    wk = (0.9, 90.0, 0.02, 0.1, 0.3, 0.5) if slip else (0.9, 90.0)
+    walls = {2 * (dim - 1): wk, 2 * (dim - 1) + 1: wk}
     per = [1] * (dim - 1) + [0]
     ms = mesh_spec(dim, N, n, periodic=per, walls=walls, geometry=dict(ngeo=ngeo, amp=0.05))
     o = oracle_objects(orc, ms, PAPER_PARAMS)
@@ -183,8 +208,9 @@ def test_curved_input_checks(orc):
     assert sizes(mesh_spec(2, 3, [2, 2], geometry=dict(ngeo=4))) != 0       # ngeo > N in 2D
     # a reflection inverts the elements (J < 0)
     assert sizes(mesh_spec(2, 3, [2, 2], geometry=dict(ngeo=1, rotation=np.diag([1.0, -1.0])))) != 0
-    slip = {2: (0.85, 90.0, 0.0, 0.1, 0.0, 0.0), 3: (0.85, 90.0)}
-    assert sizes(mesh_spec(2, 3, [2, 2], periodic=[1, 0], walls=slip, geometry=dict(ngeo=1))) != 0
+    # a wall velocity along the wall's box axis: refused on the box, projected on curved walls
+    slide = {2: (0.85, 90.0), 3: (0.85, 90.0, (0.1, 0.2, 0.0))}
+    assert sizes(mesh_spec(2, 3, [2, 2], periodic=[1, 0], walls=slide, geometry=dict(ngeo=1))) == 0
     # the HLLC flux (model 2) is taken along the face normal
     oracle_objects(orc, mesh_spec(2, 3, [2, 2], geometry=dict(ngeo=1)), dict(PAPER_PARAMS, model=2, flux="hllc"))
 
