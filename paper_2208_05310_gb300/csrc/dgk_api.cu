@@ -681,7 +681,9 @@ int dgk_set_params(dgk_ctx *c, const dgk_params *p)
     return DGK_OK;
 }
 
-int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m)
+// curved_walls: a wall velocity may have a component along the wall's box axis (it is
+// projected on the tangent plane of the curved wall at each point)
+static int mesh_box_impl(dgk_ctx *c, const dgk_box_mesh *m, bool curved_walls)
 {
     if (!c || !m) return fail(DGK_ERR_ARG, "null argument");
     if (!c->have_params) return fail(DGK_ERR_STATE, "set params before the mesh");
@@ -701,7 +703,7 @@ int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m)
                         if (!(w.gamma[k] >= 0.0) || !std::isfinite(w.gamma[k]))
                             return fail(DGK_ERR_ARG, "wall parameters gamma_1..gamma_4 must be finite and non-negative");
                 for (int k = 0; k < m->dim; ++k)
-                    if (!std::isfinite(w.u_wall[k]) || (w.u_wall[k] != 0.0 && (w.kind != 1 || k == d)))
+                    if (!std::isfinite(w.u_wall[k]) || (w.u_wall[k] != 0.0 && (w.kind != 1 || (k == d && !curved_walls))))
                         return fail(DGK_ERR_ARG, "a wall velocity must be finite, tangential and on a no-slip wall");
             }
         }
@@ -755,6 +757,8 @@ int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m)
     return DGK_OK;
 }
 
+int dgk_mesh_box(dgk_ctx *c, const dgk_box_mesh *m) { return mesh_box_impl(c, m, false); }
+
 static int mesh_curved_impl(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const double *xgeo, const int *conn,
                             const int *mortar, int nmortar)
 {
@@ -763,13 +767,6 @@ static int mesh_curved_impl(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const d
     if (m->dim != 2 && m->dim != 3) return fail(DGK_ERR_UNSUPPORTED, "dim must be 2 or 3");
     if (ngeo < 1 || (m->dim == 2 ? ngeo > m->N : 2 * ngeo > m->N))
         return fail(DGK_ERR_UNSUPPORTED, "curved elements need 1 <= ngeo <= N (2D) or 1 <= 2 ngeo <= N (3D)");
-    for (int f = 0; f < 2 * m->dim; ++f) {
-        if (!m->periodic[f / 2] && m->wall[f].kind == 2)
-            return fail(DGK_ERR_UNSUPPORTED, "curved elements take walls of kind 1 (no-slip contact angle)");
-        for (int k = 0; k < m->dim; ++k)
-            if (!m->periodic[f / 2] && m->wall[f].u_wall[k] != 0.0)
-                return fail(DGK_ERR_UNSUPPORTED, "curved elements take walls at rest");
-    }
     if (conn) {
         // the tables: neighbours in range and pointing back, orientations of the
         // dimension, walls of the box's wall table (kind 1)
@@ -797,8 +794,8 @@ static int mesh_curved_impl(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const d
                 }
                 if (t[0] < 0) {
                     const int w = -1 - t[0];
-                    if (w >= NF || m->periodic[w / 2] || m->wall[w].kind != 1)
-                        return fail(DGK_ERR_ARG, "a boundary face names no kind-1 wall of the wall table");
+                    if (w >= NF || m->periodic[w / 2] || (m->wall[w].kind != 1 && m->wall[w].kind != 2))
+                        return fail(DGK_ERR_ARG, "a boundary face names no wall of the wall table");
                     continue;
                 }
                 if (t[0] >= ne || t[1] < 0 || t[1] >= NF) return fail(DGK_ERR_ARG, "connectivity entry out of range");
@@ -816,7 +813,7 @@ static int mesh_curved_impl(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const d
                 if (back[0] != e || back[1] != f) return fail(DGK_ERR_ARG, "connectivity is not symmetric");
             }
     }
-    int rc = dgk_mesh_box(c, m);  // validates the rest and allocates the stage buffers
+    int rc = mesh_box_impl(c, m, true);  // validates the rest and allocates the stage buffers
     if (rc) return rc;
     c->have_mesh = false;
     int n[3], per[3];

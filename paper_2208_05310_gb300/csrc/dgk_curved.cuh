@@ -208,8 +208,38 @@ __device__ __forceinline__ void face_flux_c(const Ctx<R> &a, int f, int w, bool 
         for (int j = 0; j < D; ++j) s += (du[j][k] + du[k][j]) * nh[j];
         Fv[1 + k] = ph.mu * s - ph.two_thirds_mu * divu * nh[k];
     }
-    Fv[D + 1] = ph.kap * gTn - ph.gK * c * gn * divu;
-    Fv[D + 2] = ph.gKbeta * gn;
+    if (a.v.wr.kind[w] == 2) {
+        // generalized Navier slip (Eq. bc_nsk_alpha) along the unit normal: the fluid's
+        // normal traction plus the tangential traction gamma_1 div u (grad c)_t - gamma_2 u_t,
+        // its work on the fluid, the heat flux -gamma_3 (1/T_wall - 1/T),
+        // zeta = -gamma_1 gamma_4 div u, grad c . n with the gamma_1 div u term
+        R tnn = R(0), gcn = R(0), work = R(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            tnn += Fv[1 + k] * nh[k];
+            gcn += gc[k] * nh[k];
+        }
+        const R g1d = a.v.wr.g1[w] * divu, g2 = a.v.wr.g2[w];
+        const R gnn = gn + a.v.wr.g1gK[w] * divu;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const R tk = g1d * (gc[k] - gcn * nh[k]) - g2 * (u[k] - un * nh[k]);
+            Fv[1 + k] = tnn * nh[k] + tk;
+            work += tk * u[k];
+        }
+        const R qn = -a.v.wr.g3[w] * (R(1) / a.v.wr.Tw[w] - R(1) / T);
+        Fv[D + 1] = work + qn - ph.gK * c * gnn * divu - ph.gK * gnn * a.v.wr.g1g4[w] * divu;
+        Fv[D + 2] = ph.gKbeta * gnn;
+    } else {
+        // no slip: the traction works on the wall's velocity, projected on the tangent plane
+        R uwn = R(0), work = R(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) uwn += a.v.wr.uw[w][k] * nh[k];
+#pragma unroll
+        for (int k = 0; k < D; ++k) work += Fv[1 + k] * (a.v.wr.uw[w][k] - uwn * nh[k]);
+        Fv[D + 1] = work + ph.kap * gTn - ph.gK * c * gn * divu;
+        Fv[D + 2] = ph.gKbeta * gn;
+    }
     const R scale = nsign * sa;
     R Fc[D + 3];
     if (ph.flux == 1) {
@@ -472,6 +502,8 @@ struct K2CSmem {
     static constexpr int X3 = XN + (S::NV + 1) * S::NP;
     static constexpr int XA = X1 > X2 ? X1 : X2;
     static constexpr int X = XA > X3 ? XA : X3;
+    static constexpr int WG = XA;                  // per face: gamma_1/gamma_K of a Navier-slip wall, else 0
+    static_assert(WG + S::NF <= X, "no room for the wall factors");
     static constexpr int per_elem = G + GT + JF + X;
 };
 
@@ -533,9 +565,22 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
                     sQs[(f * NL + v) * NFP + fp] = R(0.5) * (a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)] +
                                                              a.v.mtr1[((long long)v * a.v.g.nslot + sl) * NFP + fp]);
             } else {
+                // walls: rho*, c* one-sided; u* the part of the wall's velocity (no slip) or
+                // of the fluid's (Navier slip) tangential to the wall, b - (b.Ja/|Ja|^2) Ja
+                const bool slip = a.v.wr.kind[w] == 2;
+                R bv[D], av[D], ba = R(0), aa = R(0);
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    av[k] = a.v.fmet[fidx<NF, NFP>(ne, k, t.e, f, fp)];
+                    bv[k] = slip ? a.v.tr1[fidx<NF, NFP>(ne, 1 + k, t.e, f, fp)] : a.v.wr.uw[w][k];
+                    ba += bv[k] * av[k];
+                    aa += av[k] * av[k];
+                }
+                const R sb = ba / aa;
 #pragma unroll
                 for (int v = 0; v < NL; ++v)
-                    sQs[(f * NL + v) * NFP + fp] = (v >= 1 && v <= D) ? R(0) : a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)];
+                    sQs[(f * NL + v) * NFP + fp] =
+                        (v >= 1 && v <= D) ? bv[v - 1] - sb * av[v - 1] : a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)];
             }
         }
         stage_face_metrics<D, N, R>(a, t, sJf);
@@ -558,11 +603,13 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
                 const long long sl = kMortar - b, ns = a.v.g.nslot;
                 pT[j] = R(0.5) * (ownT + a.v.mtr2[sl * NFP + fp]);
                 pD[j] = R(0.5) * (ownD + a.v.mtr2[(ns + sl) * NFP + fp]);
+                if (fp == 0) sX[M::WG + f] = R(0);
             } else if (b >= 0) {
                 const int fq = map_fp<P>(o, fp);
                 pT[j] = R(0.5) * (ownT + a.v.tr2[fidx<NF, NFP>(ne, 0, b, fo, fq)]);
                 // the neighbour traced grad c . J a along its own face orientation
                 pD[j] = R(0.5) * (ownD + R(facing_sign(f, fo)) * a.v.tr2[fidx<NF, NFP>(ne, 1, b, fo, fq)]);
+                if (fp == 0) sX[M::WG + f] = R(0);
             } else {
                 const R cm = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
                 const R gn = a.v.wr.K[w] * (cm - a.v.wr.rl[w]) * (cm - a.v.wr.rv[w]);
@@ -572,8 +619,13 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
                     const R x = a.v.fmet[fidx<NF, NFP>(ne, k, t.e, f, fp)];
                     a2 += x * x;
                 }
-                pT[j] = a.v.wr.Tw[w];
+                // isothermal wall: T* = T_wall; Navier-slip wall: the fluid's trace (the wall
+                // heat flux enters the energy flux) and, added with the pass-2 lines once
+                // div u is known, (gamma_1/gamma_K) div u in the contact-angle value
+                const bool slip = a.v.wr.kind[w] == 2;
+                pT[j] = slip ? ownT : a.v.wr.Tw[w];
                 pD[j] = (side ? R(1) : R(-1)) * sqrt(a2) * gn;
+                if (fp == 0) sX[M::WG + f] = slip ? a.v.wr.g1gK[w] : R(0);
             }
         }
     }
@@ -673,6 +725,28 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
                 load_line<P, R>(sG + (k * NL + D + 1) * NP, base, stride, x);
                 dm_line<P, R>(a.op, x, y);
                 store_line<P, R>(sRG + (dir * D + k) * NP, base, stride, y);
+            }
+        }
+        // Navier-slip wall ends of the (dir, line) tasks above, by the same threads:
+        // nsign |J a| (gamma_1/gamma_K) div u- joins the contact-angle value
+        for (int q = n; q < D * NFP; q += NP) {
+            const int dir = q / NFP, line = q % NFP;
+            const R wgm = sX[M::WG + 2 * dir], wgp = sX[M::WG + 2 * dir + 1];
+            if (wgm != R(0) || wgp != R(0)) {
+                const int base = line_base<P>(line, dir), stride = line_stride<P>(dir);
+                R x[P], tm, tp, dvm = R(0), dvp = R(0), am = R(0), ap = R(0);
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    load_line<P, R>(sG + (k * NL + 1 + k) * NP, base, stride, x);
+                    trace_pair<P, R>(a.op, x, tm, tp);
+                    dvm += tm;
+                    dvp += tp;
+                    const R jm = sJf[(k * NF + 2 * dir) * NFP + line], jp = sJf[(k * NF + 2 * dir + 1) * NFP + line];
+                    am += jm * jm;
+                    ap += jp * jp;
+                }
+                sDs[(2 * dir) * NFP + line] -= sqrt(am) * wgm * dvm;
+                sDs[(2 * dir + 1) * NFP + line] += sqrt(ap) * wgp * dvp;
             }
         }
     }

@@ -244,7 +244,8 @@ class Context:
     def mesh_curved(self, dim, N, n, periodic, walls, ngeo, xgeo):
         """Curved elements with the box's connectivity (dgk_mesh_curved): xgeo is a float64
         array [dim][nelem][(ngeo+1)^dim] of the element maps at equispaced reference
-        points; walls as for mesh_box (kind 1 only)."""
+        points; walls as for mesh_box (along the local normal; a wall velocity is projected
+        on the local tangent plane)."""
         m = make_box_mesh(dim, N, n, [0.0] * 3, [1.0] * 3, periodic, walls)
         x = np.ascontiguousarray(xgeo, dtype=np.float64)
         _check(lib().dgk_mesh_curved(self._h, C.byref(m), int(ngeo), x.ctypes.data_as(C.POINTER(C.c_double))),

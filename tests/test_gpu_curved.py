@@ -25,6 +25,13 @@ pytestmark = pytest.mark.gpu
 
 W2 = {2: (0.85, 60.0), 3: (0.8, 120.0)}
 W3 = {4: (0.85, 60.0), 5: (0.85, 90.0)}
+# Navier slip below (all of gamma_1..4), a sliding no-slip wall above (the walls of the
+# sliding-droplet case, Sec. 4; on bent walls the wall velocity is projected on the tangent plane)
+S2 = {2: (0.9, 70.0, 0.02, 0.1, 0.3, 0.5), 3: (0.85, 110.0, (0.3, 0.0, 0.0))}
+S3 = {4: (0.85, 60.0, 0.03, 0.05, 0.2, 0.3), 5: (0.8, 100.0, (0.2, -0.1, 0.0))}
+# gamma_1 / gamma_K = 1: the multi-step cases (a hysteresis coupling of 300 makes the explicit
+# step diverge on the refined 3D mesh within four steps, in the oracle as well)
+S3G = {4: (0.85, 60.0, 1e-4, 0.05, 0.2, 0.3), 5: (0.8, 100.0, (0.2, -0.1, 0.0))}
 R2 = np.array([[np.cos(0.6), -np.sin(0.6)], [np.sin(0.6), np.cos(0.6)]])
 
 CASES = {
@@ -72,6 +79,14 @@ CASES = {
     "3d_N4_g2_walls_m2_hllc_mortar": (mesh_spec(3, 4, [2, 2, 2], periodic=[1, 1, 0], walls=W3,
                                                 geometry=dict(ngeo=2, amp=0.04, refine=True)),
                                       dict(PAPER_PARAMS, model=2, flux="hllc")),
+    # Navier-slip and sliding walls on bent walls, through tables, with mortars
+    "2d_N4_g2_slip_sliding": (mesh_spec(2, 4, [4, 3], periodic=[1, 0], walls=S2, geometry=dict(ngeo=2, amp=0.05)),
+                              dict(PAPER_PARAMS)),
+    "3d_N3_g1_slip_sliding_m2_hllc_unstr": (mesh_spec(3, 3, [2, 2, 3], periodic=[1, 1, 0], walls=S3,
+                                                      geometry=dict(ngeo=1, amp=0.05, reorient=9)),
+                                            dict(PAPER_PARAMS, model=2, flux="hllc")),
+    "3d_N4_g2_slip_sliding_mortar": (mesh_spec(3, 4, [2, 2, 2], periodic=[1, 1, 0], walls=S3G,
+                                               geometry=dict(ngeo=2, amp=0.04, refine=True)), dict(PAPER_PARAMS)),
 }
 
 
@@ -127,7 +142,8 @@ def test_curved_one_step_fp64(orc, name):
 
 @pytest.mark.parametrize("name", ["2d_N3_g3_walls_m2", "3d_N3_g1_walls", "3d_N5_g2_walls", "2d_N3_g2_nsk",
                                   "3d_N5_g2_walls_unstr", "2d_N3_g3_walls_m2_unstr", "2d_N4_g2_walls_mortar",
-                                  "3d_N4_g2_walls_mortar", "2d_N4_g2_walls_m2_hllc", "3d_N4_g2_walls_m2_hllc_mortar"])
+                                  "3d_N4_g2_walls_mortar", "2d_N4_g2_walls_m2_hllc", "3d_N4_g2_walls_m2_hllc_mortar",
+                                  "2d_N4_g2_slip_sliding", "3d_N4_g2_slip_sliding_mortar"])
 def test_curved_ten_steps_fp64(orc, name):
     ms, ps = CASES[name]
     o, g, Uo = _pair(orc, ms, ps, exact=False)
@@ -170,7 +186,8 @@ CURVED32 = 2.0
 
 
 @pytest.mark.parametrize("name", ["2d_N3_g3_walls_m2", "3d_N3_g1_walls", "3d_N5_g2_walls", "3d_N3_g1_walls_unstr",
-                                  "3d_N4_g2_walls_mortar", "2d_N4_g2_walls_m2_hllc", "3d_N3_g1_walls_m2_hllc_unstr"])
+                                  "3d_N4_g2_walls_mortar", "2d_N4_g2_walls_m2_hllc", "3d_N3_g1_walls_m2_hllc_unstr",
+                                  "2d_N4_g2_slip_sliding", "3d_N3_g1_slip_sliding_m2_hllc_unstr"])
 def test_curved_fp32_bulk_against_oracle(orc, name):
     ms, ps = CASES[name]
     o, g, Uo = _pair(orc, ms, ps, precision="fp32bulk", exact=False)
@@ -192,9 +209,18 @@ def test_curved_refusals():
         dgk_context(mesh_spec(3, 3, [2, 2, 2], geometry=dict(ngeo=2)), PAPER_PARAMS)
     with pytest.raises(dgk.DgkError):  # an inverted element map
         dgk_context(mesh_spec(2, 3, [2, 2], geometry=dict(ngeo=1, rotation=np.diag([1.0, -1.0]))), PAPER_PARAMS)
-    slip = {2: (0.85, 90.0, 0.0, 0.1, 0.0, 0.0), 3: (0.85, 90.0)}
-    with pytest.raises(dgk.DgkError):  # Navier-slip walls
-        dgk_context(mesh_spec(2, 3, [2, 2], periodic=[1, 0], walls=slip, geometry=dict(ngeo=1)), PAPER_PARAMS)
+    # a wall velocity along the wall's box axis is projected on curved walls, not refused
+    dgk_context(mesh_spec(2, 3, [2, 2], periodic=[1, 0], walls={2: (0.85, 90.0, (0.1, 0.2, 0.0)), 3: (0.85, 90.0)},
+                          geometry=dict(ngeo=1, amp=0.05)), PAPER_PARAMS)
+    # a velocity on a Navier-slip wall is refused (its solid is at rest)
+    import ctypes as C
+    ms = mesh_spec(2, 3, [2, 2], periodic=[1, 0], walls={2: (0.85, 90.0), 3: (0.85, 90.0, 0.0, 0.1, 0.0, 0.0)})
+    m = dgk.make_box_mesh(2, 3, [2, 2, 1], [0.0] * 3, [1.0] * 3, [1, 0, 1], ms["walls"])
+    m.wall[3].u_wall[0] = 0.1
+    x = np.ascontiguousarray(inputs.box_geometry(2, [2, 2], [0.0, 0.0], [1.0, 1.0], 1), dtype=np.float64)
+    g = dgk.Context()
+    g.set_params(**PAPER_PARAMS)
+    assert dgk.lib().dgk_mesh_curved(g._h, C.byref(m), 1, x.ctypes.data_as(C.POINTER(C.c_double))) != 0
 
 
 def test_unstructured_equals_structured_on_the_gpu(orc):

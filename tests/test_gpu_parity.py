@@ -269,6 +269,3 @@ def test_sliding_wall_refusals():
     with pytest.raises(dgk.DgkError):  # a normal component
         dgk_context(mesh_spec(2, 3, [2, 2], periodic=[1, 0], walls={2: (0.85, 90.0), 3: (0.85, 90.0, (0.1, 0.2, 0.0))}),
                     PAPER_PARAMS)
-    with pytest.raises(dgk.DgkError):  # curved elements take walls at rest
-        dgk_context(mesh_spec(2, 3, [2, 2], periodic=[1, 0], walls={2: (0.85, 90.0), 3: (0.85, 90.0, (0.1, 0.0, 0.0))},
-                              geometry=dict(ngeo=1)), PAPER_PARAMS)
