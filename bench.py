@@ -654,9 +654,10 @@ def main():
                     help="hllc runs the workload with relaxation model 2 and the HLLC flux")
     ap.add_argument("--model", type=int, default=None, choices=[0, 1, 2],
                     help="0: the original NSK model (the workload's walls become periodic)")
-    ap.add_argument("--walls", default="noslip", choices=["noslip", "slip", "sliding"],
+    ap.add_argument("--walls", default="noslip", choices=["noslip", "slip", "sliding", "slip-sliding"],
                     help="slip: generalized Navier-slip walls (gamma_1..4 = 1e-5, 0.1, 0.05, 1); sliding: the top "
-                         "wall slides with u = (0.5, 0, 0), the wall velocity of the sliding-droplet case")
+                         "wall slides with u = (0.5, 0, 0), the wall velocity of the sliding-droplet case; "
+                         "slip-sliding: the walls of that case (Navier slip below, the sliding no-slip wall above)")
     ap.add_argument("--mesh", default="box", choices=["box", "curved", "unstructured", "mortar"],
                     help="curved: the workload's box mapped to curved elements (degree-2 element maps of "
                          "x_k + 0.02 L_k sin(2 pi x_{k+1}/L_{k+1}); the walls are bent); unstructured: the same "
@@ -682,19 +683,22 @@ def main():
             wl["name"] += ", original NSK model, periodic in every direction"
         else:
             wl["name"] += f", model {args.model}"
-    if args.walls == "slip" and wl["mesh"]["walls"]:
+    if args.walls in ("slip", "slip-sliding") and wl["mesh"]["walls"]:
         # gamma_1 / gamma_K = 0.1: a hysteresis coupling of 200 (gamma_1 = 0.02) makes the
         # explicit step diverge on this mesh, in the oracle as well
-        wl["mesh"] = dict(wl["mesh"], walls={f: (Tw, th, 1e-5, 0.1, 0.05, 1.0) for f, (Tw, th) in wl["mesh"]["walls"].items()})
-        wl["name"] += ", Navier-slip walls"
-    if args.walls == "sliding" and wl["mesh"]["walls"]:
+        ws = wl["mesh"]["walls"]
+        top = max(ws)
+        wl["mesh"] = dict(wl["mesh"], walls={f: (Tw, th) + ((1e-5, 0.1, 0.05, 1.0) if args.walls == "slip" or f != top else ())
+                                             for f, (Tw, th) in ws.items()})
+        wl["name"] += ", Navier-slip walls" if args.walls == "slip" else ", Navier-slip bottom wall"
+    if args.walls in ("sliding", "slip-sliding") and wl["mesh"]["walls"]:
         top = max(wl["mesh"]["walls"])
         wl["mesh"] = dict(wl["mesh"], walls=dict(wl["mesh"]["walls"]))
         wl["mesh"]["walls"][top] = tuple(wl["mesh"]["walls"][top][:2]) + ((0.5, 0.0, 0.0),)
         wl["name"] += ", top wall sliding with u = (0.5, 0, 0)"
     if args.mesh in ("curved", "unstructured", "mortar"):
-        if "batch" in wl or args.walls != "noslip":
-            print(json.dumps({"error": "curved elements: single problems, no-slip walls"}))
+        if "batch" in wl:
+            print(json.dumps({"error": "curved elements: single problems"}))
             return 2
         wl["geometry"] = dict(CURVED_GEOMETRY)
         wl["name"] += ", curved elements (degree-2 maps, walls bent by 2% of the height)"
