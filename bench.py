@@ -237,7 +237,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_rate(wl, seconds_target=15.0, steps=None, sub=(6, 6, None)):
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_rate(wl, seconds_target=15.0, steps=None, sub=(6, 6, None), single_thread=False):
     """FP64 oracle DOF-stage/s on a sub-box of the workload with the same N and element
     size (periodic laterally, the workload's walls in z)."""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
@@ -272,8 +293,17 @@ def oracle_rate(wl, seconds_target=15.0, steps=None, sub=(6, 6, None)):
     total_steps = nsteps if nsteps else 1
     total_t = tt if nsteps else t1
     assert np.isfinite(U).all()
-    return dict(rate=dof * stages * total_steps / total_t, cores=orc.num_threads(), dof=dof, steps=total_steps,
-                seconds=total_t, sub=f"a {nsub} sub-box")
+    cores = orc.num_threads()
+    single = None
+    if single_thread:
+        # the same sub-box on one thread, one RK step
+        orc.set_num_threads(1)
+        t0 = time.perf_counter()
+        U = o.run(U, 1, dt, rk=wl["rk"])
+        single = dof * stages / (time.perf_counter() - t0)
+        orc.set_num_threads(cores)
+    return dict(rate=dof * stages * total_steps / total_t, cores=cores, dof=dof, steps=total_steps,
+                seconds=total_t, sub=f"a {nsub} sub-box", single=single)
 
 
 def oracle_rate_batch(wl, steps, nsample=2):
@@ -321,7 +351,8 @@ def run_reference(args, wl, rank, world):
                 ms_per_step=1e3 * r["seconds"] / r["steps"], higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic", impl="reference",
                 config=dict(workload=wl["name"], sample=sample, stages_per_step=5 if wl["rk"] == 4 else 3),
-                cpu_baseline=dict(value=r["rate"], unit=UNIT, cores=r["cores"], kind="oracle", sample=sample),
+                cpu_baseline=dict(value=r["rate"], unit=UNIT, cores=r["cores"], kind="oracle", sample=sample,
+                                  cpu_model=cpu_model()),
                 e2e=dict(value=r["rate"], unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     del r_w
     print(json.dumps(line), flush=True)
@@ -460,10 +491,10 @@ def run_ours(args, wl, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = oracle_rate(wl, seconds_target=args.cpu_seconds)
+        r = oracle_rate(wl, seconds_target=args.cpu_seconds, single_thread=True)
         cpu = dict(value=r["rate"], unit=UNIT, cores=r["cores"], kind="oracle",
                    sample=f"{r['steps']} RK steps on {r['sub']} of the workload ({r['dof']} nodes), "
-                          f"{r['seconds']:.1f} s")
+                          f"{r['seconds']:.1f} s", single_thread_value=r["single"], cpu_model=cpu_model())
 
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,

@@ -122,6 +122,8 @@ int  or_run(const or_mesh *m, const or_params *p, double *U, int nsteps, double 
 int  or_max_dt(const or_mesh *m, const or_params *p, const double *U, double cfl, double dfl, double *dt);
 int  or_diagnostics(const or_mesh *m, const or_params *p, const double *U, double *out);
 int  or_num_threads(void);
+/* Threads of the parallel element loops from now on (OpenMP; n >= 1). */
+void or_set_num_threads(int n);
 
 #define OR_NDIAG 8  /* mass, mom_x, mom_y, mom_z, energy, -entropy, ||rho-c||_2, max|u| */
 

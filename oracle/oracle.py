@@ -77,6 +77,8 @@ def lib():
         L.or_max_dt.argtypes = [mp, pp, dp, C.c_double, C.c_double, dp]
         L.or_diagnostics.argtypes = [mp, pp, dp, dp]
         L.or_num_threads.restype = C.c_int
+        L.or_set_num_threads.restype = None
+        L.or_set_num_threads.argtypes = [C.c_int]
         L.or_conv_point.argtypes = [pp, C.c_int, C.c_int, dp, C.c_double, dp]
         L.or_hllc_point.argtypes = [pp, C.c_int, C.c_int, dp, C.c_double, dp, C.c_double, dp]
         L.or_rusanov_point.argtypes = [pp, C.c_int, C.c_int, dp, C.c_double, dp, C.c_double, dp]
@@ -297,3 +299,7 @@ class Oracle:
 
 def num_threads():
     return lib().or_num_threads()
+
+
+def set_num_threads(n):
+    lib().or_set_num_threads(int(n))
