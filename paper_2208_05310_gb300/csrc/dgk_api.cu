@@ -287,6 +287,11 @@ struct dgk_ctx {
     double coef_h[11] = {0};
     bool coef_valid = false;
     cudaGraphExec_t graph = nullptr;
+    // dgk_run_host: staging buffers, copy streams and their events
+    double *stage_in = nullptr, *stage_out = nullptr;
+    size_t stage_count = 0;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_in_ready = nullptr, ev_in_free = nullptr, ev_out_ready = nullptr, ev_out_free = nullptr;
     bool timing = false;
     std::vector<cudaEvent_t> events;
     size_t events_used = 0;
@@ -322,6 +327,10 @@ void free_buffers(dgk_ctx *c)
     c->redbuf = nullptr;
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
+    if (c->stage_in) cudaFree(c->stage_in);
+    if (c->stage_out) cudaFree(c->stage_out);
+    c->stage_in = c->stage_out = nullptr;
+    c->stage_count = 0;
 }
 
 void drop_graph(dgk_ctx *c)
@@ -646,8 +655,14 @@ void dgk_destroy(dgk_ctx *c)
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->s_in) cudaStreamSynchronize(c->s_in);
+    if (c->s_out) cudaStreamSynchronize(c->s_out);
     free_buffers(c);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    for (cudaEvent_t e : {c->ev_in_ready, c->ev_in_free, c->ev_out_ready, c->ev_out_free})
+        if (e) cudaEventDestroy(e);
+    if (c->s_in) cudaStreamDestroy(c->s_in);
+    if (c->s_out) cudaStreamDestroy(c->s_out);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -1067,6 +1082,66 @@ int dgk_run(dgk_ctx *c, int nsteps, double dt)
         }
     }
     for (int s = 0; s < nsteps; ++s) DGK_CUDA(cudaGraphLaunch(c->graph, c->stream));
+    return DGK_OK;
+}
+
+int dgk_run_host(dgk_ctx *c, const double *const *in, double *const *out, int nitems, size_t count, int nsteps,
+                 double dt)
+{
+    int rc = ready(c);
+    if (rc) return rc;
+    const size_t nstate = (size_t)c->NV * c->ne * c->NP;
+    if (!in || !out || nitems < 0 || count != nstate) return fail(DGK_ERR_ARG, "bad arrays, count or nitems");
+    if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) return fail(DGK_ERR_ARG, "nsteps < 0 or dt not positive");
+    for (int i = 0; i < nitems; ++i)
+        if (!in[i] || !out[i]) return fail(DGK_ERR_ARG, "null host pointer");
+    if (nitems == 0) return DGK_OK;
+    DGK_CUDA(cudaSetDevice(c->device));
+    if (c->stage_count != nstate) {
+        if (c->stage_in) cudaFree(c->stage_in);
+        if (c->stage_out) cudaFree(c->stage_out);
+        c->stage_in = c->stage_out = nullptr;
+        c->stage_count = 0;
+        DGK_CUDA(cudaMalloc(&c->stage_in, nstate * sizeof(double)));
+        DGK_CUDA(cudaMalloc(&c->stage_out, nstate * sizeof(double)));
+        c->stage_count = nstate;
+    }
+    if (!c->s_in) {
+        DGK_CUDA(cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking));
+        DGK_CUDA(cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking));
+        for (cudaEvent_t *e : {&c->ev_in_ready, &c->ev_in_free, &c->ev_out_ready, &c->ev_out_free})
+            DGK_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    const size_t bytes = nstate * sizeof(double);
+    // the copy streams start after the work already queued on the context's stream
+    DGK_CUDA(cudaEventRecord(c->ev_in_free, c->stream));
+    DGK_CUDA(cudaEventRecord(c->ev_out_free, c->stream));
+    DGK_CUDA(cudaStreamWaitEvent(c->s_in, c->ev_in_free, 0));
+    DGK_CUDA(cudaStreamWaitEvent(c->s_out, c->ev_out_free, 0));
+    DGK_CUDA(cudaMemcpyAsync(c->stage_in, in[0], bytes, cudaMemcpyHostToDevice, c->s_in));
+    DGK_CUDA(cudaEventRecord(c->ev_in_ready, c->s_in));
+    for (int i = 0; i < nitems; ++i) {
+        // item i in: staging -> state (the staging buffer is then free for item i+1)
+        DGK_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in_ready, 0));
+        DGK_CUDA(cudaMemcpyAsync(c->U, c->stage_in, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        DGK_CUDA(cudaEventRecord(c->ev_in_free, c->stream));
+        if ((rc = after_state_change(c))) return rc;
+        if (i + 1 < nitems) {
+            DGK_CUDA(cudaStreamWaitEvent(c->s_in, c->ev_in_free, 0));
+            DGK_CUDA(cudaMemcpyAsync(c->stage_in, in[i + 1], bytes, cudaMemcpyHostToDevice, c->s_in));
+            DGK_CUDA(cudaEventRecord(c->ev_in_ready, c->s_in));
+        }
+        if ((rc = dgk_run(c, nsteps, dt))) return rc;
+        // item i out: state -> staging once the previous item has left it, then to the host
+        DGK_CUDA(cudaStreamWaitEvent(c->stream, c->ev_out_free, 0));
+        DGK_CUDA(cudaMemcpyAsync(c->stage_out, c->U, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        DGK_CUDA(cudaEventRecord(c->ev_out_ready, c->stream));
+        DGK_CUDA(cudaStreamWaitEvent(c->s_out, c->ev_out_ready, 0));
+        DGK_CUDA(cudaMemcpyAsync(out[i], c->stage_out, bytes, cudaMemcpyDeviceToHost, c->s_out));
+        DGK_CUDA(cudaEventRecord(c->ev_out_free, c->s_out));
+    }
+    DGK_CUDA(cudaStreamSynchronize(c->s_out));
+    DGK_CUDA(cudaStreamSynchronize(c->stream));
     return DGK_OK;
 }
 

@@ -58,6 +58,7 @@ class DgkError(RuntimeError):
 
 EXPORTS = ("dgk_create", "dgk_destroy", "dgk_set_params", "dgk_mesh_box", "dgk_mesh_curved", "dgk_mesh_unstructured", "dgk_sizes", "dgk_node_coords",
            "dgk_set_primitive", "dgk_upload_state", "dgk_download_state", "dgk_rhs", "dgk_rk_step", "dgk_run",
+           "dgk_run_host",
            "dgk_max_dt", "dgk_diagnostics", "dgk_status", "dgk_set_timing", "dgk_kernel_time", "dgk_maxwell",
            "dgk_sigma_vl", "dgk_interface_width", "dgk_status_string", "dgk_last_error", "dgk_check_conversions",
            "dgk_rhs_static", "dgk_node_temperature_pressure", "dgk_batch_create", "dgk_batch_destroy",
@@ -90,6 +91,7 @@ def lib():
         "dgk_rhs": (i, [vp, vp, sz, i]),
         "dgk_rk_step": (i, [vp, d]),
         "dgk_run": (i, [vp, i, d]),
+        "dgk_run_host": (i, [vp, C.POINTER(vp), C.POINTER(vp), i, sz, i, d]),
         "dgk_max_dt": (i, [vp, d, d, dp]),
         "dgk_diagnostics": (i, [vp, dp]),
         "dgk_node_temperature_pressure": (i, [vp, vp, vp, sz, i]),
@@ -305,6 +307,24 @@ class Context:
 
     def run(self, nsteps, dt):
         _check(lib().dgk_run(self._h, int(nsteps), float(dt)), "dgk_run")
+
+    def run_host(self, inputs, outputs, nsteps, dt):
+        """Independent states through host memory, pipelined (dgk_run_host): each of
+        inputs[i] is uploaded, advanced nsteps steps of dt and read into outputs[i].
+        inputs, outputs: equal-length sequences of host float64 arrays (numpy, or CPU
+        tensors; page-locked memory lets the copies overlap the steps)."""
+        if len(inputs) != len(outputs):
+            raise DgkError("inputs and outputs differ in length")
+        n = len(inputs)
+        pi, po = (C.c_void_p * max(n, 1))(), (C.c_void_p * max(n, 1))()
+        count = int(np.prod(self.shape()))
+        for k in range(n):
+            for arr, tab in ((inputs[k], pi), (outputs[k], po)):
+                ptr, m, dev = _ptr(arr)
+                if dev or m != count:
+                    raise DgkError("run_host takes host arrays of the state's size")
+                tab[k] = ptr
+        _check(lib().dgk_run_host(self._h, pi, po, n, count, int(nsteps), float(dt)), "dgk_run_host")
 
     def max_dt(self, cfl=0.9, dfl=0.4):
         dt = C.c_double()
