@@ -98,9 +98,9 @@ typedef struct {
    u_wall: velocity of a kind-1 wall sliding in its own plane (the moving no-slip wall of
    the sliding-droplet case, Sec. 4): the lifting takes u* = u_wall at the wall and the
    wall's traction does the work (tau n) . u_wall in the energy flux.  Components beyond
-   dim are ignored; the normal component must be zero, and so must the whole vector for
-   kind 2 (the solid is at rest, Sec. 2.4) and on curved meshes (DGK_ERR_ARG /
-   DGK_ERR_UNSUPPORTED otherwise). */
+   dim are ignored.  On box meshes the normal component must be zero; on curved meshes
+   the velocity is projected on the tangent plane at each wall point.  Kind 2 takes
+   none (the solid is at rest, Sec. 2.4).  DGK_ERR_ARG otherwise. */
 typedef struct {
     int kind;
     double T_wall;
@@ -146,9 +146,10 @@ int dgk_mesh_box(dgk_ctx *ctx, const dgk_box_mesh *mesh);
    preserved.  Liftings use the strong BR1 form with the chain rule, the volume integral
    the contravariant fluxes F . J a^i, the faces the numerical flux along the face metric
    (one per face point, shared by both elements; Rusanov, or for model 2 HLLC along the
-   unit normal).  Restriction: walls of kind 1 only.  Errors: DGK_ERR_UNSUPPORTED for
-   others, DGK_ERR_ARG for an element map with J <= 0 at a node; otherwise as
-   dgk_mesh_box.  Memory: the metric terms add
+   unit normal).  Walls of both kinds, along the local normal (Navier slip: the
+   tangential projections and tractions of Eq. bc_nsk_alpha with the local normal; a
+   sliding wall's velocity projected on the tangent plane).  Errors: DGK_ERR_ARG for an
+   element map with J <= 0 at a node; otherwise as dgk_mesh_box.  Memory: the metric terms add
    (dim^2 + 1) values per node in the bulk type and in double, and dim values per face
    point. */
 int dgk_mesh_curved(dgk_ctx *ctx, const dgk_box_mesh *mesh, int ngeo, const double *xgeo);
@@ -156,7 +157,7 @@ int dgk_mesh_curved(dgk_ctx *ctx, const dgk_box_mesh *mesh, int ngeo, const doub
    hexahedral meshes): as dgk_mesh_curved, with the element neighbours given by tables
    instead of the box's index arithmetic.  mesh gives dim, N, the element count
    (n[0] n[1] n[2]) and the wall table (wall[w] for the faces that name wall w; those
-   walls' directions must be non-periodic, kind 1); lo/hi and the element layout are
+   walls' directions must be non-periodic, kind 1 or 2); lo/hi and the element layout are
    ignored.  conn (host, caller-owned, read during the call): for face f = 2 dir + side of
    element e (in the element's own reference frame), conn[(e * 2dim + f) * 3 + 0..2] =
    (neighbour element, the neighbour's face, orientation), or (-1 - w, 0, 0) on wall w.

@@ -784,7 +784,7 @@ static int mesh_curved_impl(dgk_ctx *c, const dgk_box_mesh *m, int ngeo, const d
         return fail(DGK_ERR_UNSUPPORTED, "curved elements need 1 <= ngeo <= N (2D) or 1 <= 2 ngeo <= N (3D)");
     if (conn) {
         // the tables: neighbours in range and pointing back, orientations of the
-        // dimension, walls of the box's wall table (kind 1)
+        // dimension, walls of the box's wall table
         long long ne = 1;
         for (int d = 0; d < m->dim; ++d) ne *= m->n[d];
         if (ne >= (1LL << 31)) return fail(DGK_ERR_ARG, "unstructured meshes take fewer than 2^31 elements");

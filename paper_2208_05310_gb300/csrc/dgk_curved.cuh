@@ -16,7 +16,8 @@
 // The metric arrays: met [D*D+1][ne][NP] (plane dir*D + k: J a^dir_k; plane D*D: 1/J) and
 // fmet [D][ne][NF][NFP] (J a^dir_k at face f = 2 dir + side, oriented along +xi_dir and
 // identical in the two elements that share the face).  Walls: isothermal no-slip
-// contact-angle walls (kind 1); Rusanov or (model 2) HLLC flux along the face normal.
+// contact-angle walls, at rest or sliding, and generalized Navier-slip walls, along the
+// local normal; Rusanov or (model 2) HLLC flux along the face normal.
 #pragma once
 
 #include "dgk_kernels.cuh"
