@@ -20,6 +20,9 @@ TOL = {"fp64": 1e-12, "fp32bulk": 2e-4}  # the FP64 and FP32-bulk right-hand-sid
 CASES = [
     (mesh_spec(3, 3, [3, 2, 4], periodic=[1, 1, 0], walls={4: (0.85, 60.0), 5: (0.8, 120.0)}), dict(PAPER_PARAMS)),
     (mesh_spec(2, 4, [5, 3]), dict(PAPER_PARAMS, model=2)),
+    # a Navier-slip wall and a sliding no-slip wall
+    (mesh_spec(3, 3, [3, 2, 4], periodic=[1, 1, 0],
+               walls={4: (0.85, 60.0, 0.03, 0.05, 0.2, 0.3), 5: (0.8, 120.0, (0.2, -0.1, 0.0))}), dict(PAPER_PARAMS)),
 ]
 
 
@@ -48,7 +51,7 @@ def _static_args(ms, ps, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32bulk"])
-@pytest.mark.parametrize("case", [0, 1])
+@pytest.mark.parametrize("case", [0, 1, 2])
 def test_static_rhs_matches_context_rhs(case, precision):
     import torch
 
