@@ -1106,42 +1106,50 @@ int dgk_run_host(dgk_ctx *c, const double *const *in, double *const *out, int ni
         DGK_CUDA(cudaMalloc(&c->stage_out, nstate * sizeof(double)));
         c->stage_count = nstate;
     }
-    if (!c->s_in) {
-        DGK_CUDA(cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking));
-        DGK_CUDA(cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking));
-        for (cudaEvent_t *e : {&c->ev_in_ready, &c->ev_in_free, &c->ev_out_ready, &c->ev_out_free})
-            DGK_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-    }
+    for (cudaStream_t *st : {&c->s_in, &c->s_out})
+        if (!*st) DGK_CUDA(cudaStreamCreateWithFlags(st, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&c->ev_in_ready, &c->ev_in_free, &c->ev_out_ready, &c->ev_out_free})
+        if (!*e) DGK_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     const size_t bytes = nstate * sizeof(double);
-    // the copy streams start after the work already queued on the context's stream
-    DGK_CUDA(cudaEventRecord(c->ev_in_free, c->stream));
-    DGK_CUDA(cudaEventRecord(c->ev_out_free, c->stream));
-    DGK_CUDA(cudaStreamWaitEvent(c->s_in, c->ev_in_free, 0));
-    DGK_CUDA(cudaStreamWaitEvent(c->s_out, c->ev_out_free, 0));
-    DGK_CUDA(cudaMemcpyAsync(c->stage_in, in[0], bytes, cudaMemcpyHostToDevice, c->s_in));
-    DGK_CUDA(cudaEventRecord(c->ev_in_ready, c->s_in));
-    for (int i = 0; i < nitems; ++i) {
-        // item i in: staging -> state (the staging buffer is then free for item i+1)
-        DGK_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in_ready, 0));
-        DGK_CUDA(cudaMemcpyAsync(c->U, c->stage_in, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    // the pipeline; on an error it stops enqueueing, and the streams are drained below so
+    // that no copy touches the caller's buffers after the return
+    auto pipeline = [&]() -> int {
+        // the copy streams start after the work already queued on the context's stream
         DGK_CUDA(cudaEventRecord(c->ev_in_free, c->stream));
-        if ((rc = after_state_change(c))) return rc;
-        if (i + 1 < nitems) {
-            DGK_CUDA(cudaStreamWaitEvent(c->s_in, c->ev_in_free, 0));
-            DGK_CUDA(cudaMemcpyAsync(c->stage_in, in[i + 1], bytes, cudaMemcpyHostToDevice, c->s_in));
-            DGK_CUDA(cudaEventRecord(c->ev_in_ready, c->s_in));
+        DGK_CUDA(cudaEventRecord(c->ev_out_free, c->stream));
+        DGK_CUDA(cudaStreamWaitEvent(c->s_in, c->ev_in_free, 0));
+        DGK_CUDA(cudaStreamWaitEvent(c->s_out, c->ev_out_free, 0));
+        DGK_CUDA(cudaMemcpyAsync(c->stage_in, in[0], bytes, cudaMemcpyHostToDevice, c->s_in));
+        DGK_CUDA(cudaEventRecord(c->ev_in_ready, c->s_in));
+        for (int i = 0; i < nitems; ++i) {
+            // item i in: staging -> state (the staging buffer is then free for item i+1)
+            DGK_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in_ready, 0));
+            DGK_CUDA(cudaMemcpyAsync(c->U, c->stage_in, bytes, cudaMemcpyDeviceToDevice, c->stream));
+            DGK_CUDA(cudaEventRecord(c->ev_in_free, c->stream));
+            int r = after_state_change(c);
+            if (r) return r;
+            if (i + 1 < nitems) {
+                DGK_CUDA(cudaStreamWaitEvent(c->s_in, c->ev_in_free, 0));
+                DGK_CUDA(cudaMemcpyAsync(c->stage_in, in[i + 1], bytes, cudaMemcpyHostToDevice, c->s_in));
+                DGK_CUDA(cudaEventRecord(c->ev_in_ready, c->s_in));
+            }
+            if ((r = dgk_run(c, nsteps, dt))) return r;
+            // item i out: state -> staging once the previous item has left it, then to the host
+            DGK_CUDA(cudaStreamWaitEvent(c->stream, c->ev_out_free, 0));
+            DGK_CUDA(cudaMemcpyAsync(c->stage_out, c->U, bytes, cudaMemcpyDeviceToDevice, c->stream));
+            DGK_CUDA(cudaEventRecord(c->ev_out_ready, c->stream));
+            DGK_CUDA(cudaStreamWaitEvent(c->s_out, c->ev_out_ready, 0));
+            DGK_CUDA(cudaMemcpyAsync(out[i], c->stage_out, bytes, cudaMemcpyDeviceToHost, c->s_out));
+            DGK_CUDA(cudaEventRecord(c->ev_out_free, c->s_out));
         }
-        if ((rc = dgk_run(c, nsteps, dt))) return rc;
-        // item i out: state -> staging once the previous item has left it, then to the host
-        DGK_CUDA(cudaStreamWaitEvent(c->stream, c->ev_out_free, 0));
-        DGK_CUDA(cudaMemcpyAsync(c->stage_out, c->U, bytes, cudaMemcpyDeviceToDevice, c->stream));
-        DGK_CUDA(cudaEventRecord(c->ev_out_ready, c->stream));
-        DGK_CUDA(cudaStreamWaitEvent(c->s_out, c->ev_out_ready, 0));
-        DGK_CUDA(cudaMemcpyAsync(out[i], c->stage_out, bytes, cudaMemcpyDeviceToHost, c->s_out));
-        DGK_CUDA(cudaEventRecord(c->ev_out_free, c->s_out));
-    }
-    DGK_CUDA(cudaStreamSynchronize(c->s_out));
-    DGK_CUDA(cudaStreamSynchronize(c->stream));
+        return DGK_OK;
+    };
+    rc = pipeline();
+    const cudaError_t e1 = cudaStreamSynchronize(c->s_in), e2 = cudaStreamSynchronize(c->s_out),
+                      e3 = cudaStreamSynchronize(c->stream);
+    if (rc) return rc;
+    for (cudaError_t e : {e1, e2, e3})
+        if (e != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("dgk_run_host: ") + cudaGetErrorString(e));
     return DGK_OK;
 }
 
