@@ -269,3 +269,46 @@ def test_sliding_wall_refusals():
     with pytest.raises(dgk.DgkError):  # a normal component
         dgk_context(mesh_spec(2, 3, [2, 2], periodic=[1, 0], walls={2: (0.85, 90.0), 3: (0.85, 90.0, (0.1, 0.2, 0.0))}),
                     PAPER_PARAMS)
+
+
+def test_box_mesh_and_call_refusals():
+    """Input checks of the C ABI (no kernel runs for a refused call): polynomial degree and
+    dimension ranges, walls on every non-periodic face, wall parameters, wall
+    temperatures with saturation states, the element-count limit (refused before any
+    allocation), call order, array sizes and step sizes."""
+    from paper_2208_05310_gb300 import dgk, inputs
+
+    def ctx():
+        g = dgk.Context()
+        g.set_params(**PAPER_PARAMS)
+        return g
+
+    g = ctx()
+    with pytest.raises(dgk.DgkError):  # call order: no mesh yet
+        g.rhs(np.zeros(10))
+    for N in (1, 6):
+        with pytest.raises(dgk.DgkError):
+            ctx().mesh_box(2, N, [2, 2, 1], [0, 0, 0], [1, 1, 1], [1, 1, 1])
+    with pytest.raises(dgk.DgkError):
+        ctx().mesh_box(4, 3, [2, 2, 2], [0, 0, 0], [1, 1, 1], [1, 1, 1])
+    with pytest.raises(dgk.DgkError):  # a non-periodic direction without walls
+        ctx().mesh_box(2, 3, [2, 2, 1], [0, 0, 0], [1, 1, 1], [1, 0, 1])
+    with pytest.raises(dgk.DgkError):  # a negative Navier-slip parameter
+        ctx().mesh_box(2, 3, [2, 2, 1], [0, 0, 0], [1, 1, 1], [1, 0, 1],
+                       {2: (0.85, 90.0, 0.0, -0.1, 0.0, 0.0), 3: (0.85, 90.0)})
+    with pytest.raises(dgk.DgkError):  # no saturation states above the critical temperature
+        ctx().mesh_box(2, 3, [2, 2, 1], [0, 0, 0], [1, 1, 1], [1, 0, 1], {2: (1.2, 90.0), 3: (0.85, 90.0)})
+    with pytest.raises(dgk.DgkError):  # 2^33 elements
+        ctx().mesh_box(3, 3, [2 ** 16, 2 ** 16, 2], [0, 0, 0], [1, 1, 1], [1, 1, 1])
+    with pytest.raises(dgk.DgkError):  # an empty extent
+        ctx().mesh_box(2, 3, [2, 2, 1], [0, 0, 0], [1, 0, 1], [1, 1, 1])
+    g = ctx()
+    g.mesh_box(2, 3, [2, 2, 1], [0, 0, 0], [1, 1, 1], [1, 1, 1])
+    with pytest.raises(dgk.DgkError):  # a state of the wrong size
+        g.upload_state(np.zeros(g.nv * g.nelem * g.np - 1))
+    g.set_primitive(inputs.random_admissible(2, g.nelem, g.np, 1))
+    for dt in (0.0, -1.0, float("nan")):
+        with pytest.raises(dgk.DgkError):
+            g.run(1, dt)
+    with pytest.raises(dgk.DgkError):
+        g.run(-1, 1e-4)
