@@ -518,3 +518,154 @@ def refined_mesh(dim, N, n, periodic, walls, ngeo, amp=0.0, lo=None, hi=None):
                         conn[e, f] = (nb, 2 * d + 1 - s, (p + 1) << 3)
     mort = np.array(mortar, dtype=np.int32).reshape(len(mortar), 2 ** (dim - 1), 3)
     return xg, conn, mort
+
+
+def _orient_code(dim, P, src, dst):
+    """The face-point orientation code o (the format of the connectivity tables: (u, v) =
+    o & 1 ? (b, a) : (a, b); a' = o & 2 ? N - u : u; b' = o & 4 ? N - v : v) that maps
+    every point src[i] = (a, b) to dst[i] = (a', b'); 2D points have b = 0."""
+    N = P - 1
+    for o in (range(8) if dim == 3 else (0, 2)):
+        ok = True
+        for (a, b), (a2, b2) in zip(src, dst):
+            u, v = (b, a) if o & 1 else (a, b)
+            u = N - u if o & 2 else u
+            v = N - v if o & 4 else v
+            if (u, v) != (a2, b2):
+                ok = False
+                break
+        if ok:
+            return o
+    raise ValueError("no orientation code maps the face points")
+
+
+def reoriented_refined(dim, N, ngeo, xgeo, conn, mortar, seed):
+    """A mesh in the unstructured format whose elements all use the box frame (face-point
+    orientations 0, e.g. refined_mesh's) with every element given a random
+    orientation-preserving local frame, numbering kept: element maps, conforming faces,
+    walls and mortars (sub-face order and face-point orientations in the new frames).
+    Returns (xgeo', conn', mortar', node_index) with node_index[e][n'] = e * NP + n of the
+    same node in the original frames."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ne = xgeo.shape[1]
+    P, G = N + 1, ngeo + 1
+    NP, NG, NFP = P ** dim, G ** dim, P ** (dim - 1)
+    frames = _frames(dim, ne, rng)
+
+    def flat(idx, K):
+        return sum(idx[a] * K ** a for a in range(dim))
+
+    def unflat(v, K):
+        return [(v // K ** a) % K for a in range(dim)]
+
+    xnew = np.empty_like(xgeo)
+    node_index = np.empty((ne, NP), dtype=np.int64)
+    for e in range(ne):
+        fr = frames[e]
+        for g in range(NG):
+            xnew[:, e, g] = xgeo[:, e, flat(_old_index(dim, G, fr, unflat(g, G)), G)]
+        for q in range(NP):
+            node_index[e, q] = e * NP + flat(_old_index(dim, P, fr, unflat(q, P)), P)
+
+    def new_face(e, f_old):
+        p, sg = frames[e]
+        a = p.index(f_old // 2)
+        return 2 * a + ((f_old % 2) if sg[a] > 0 else 1 - (f_old % 2))
+
+    def old_face_point(e, f_new, t):
+        """old face index and old tangential indices (increasing old axes) of the point
+        with new tangential indices t on new face f_new of element e"""
+        a_n = f_new // 2
+        idx, j = [0] * dim, 0
+        for a in range(dim):
+            if a == a_n:
+                idx[a] = (P - 1) * (f_new % 2)
+            else:
+                idx[a] = t[j]
+                j += 1
+        old = _old_index(dim, P, frames[e], idx)
+        d_old = frames[e][0][a_n]
+        s_old = (f_new % 2) if frames[e][1][a_n] > 0 else 1 - (f_new % 2)
+        return 2 * d_old + s_old, [old[b] for b in range(dim) if b != d_old]
+
+    pts = [(a, b) for b in range(P if dim == 3 else 1) for a in range(P)]
+
+    def new_point_of_old(e, f_old, t_old):
+        """new tangential indices on e's new face of the point with old tangential t_old"""
+        f_new = new_face(e, f_old)
+        for t in pts:
+            if old_face_point(e, f_new, list(t)[:dim - 1])[1] == list(t_old):
+                return t
+        raise AssertionError("face point not found")
+
+    conn_new = np.zeros_like(conn)
+    mort_new = np.array(mortar, copy=True) if mortar is not None and len(mortar) else None
+    nsub = 2 ** (dim - 1)
+    for e in range(ne):
+        for f_old in range(2 * dim):
+            nb, fo, oo = (int(v) for v in conn[e, f_old])
+            f_new = new_face(e, f_old)
+            if nb < 0 and nb > -100:  # wall
+                conn_new[e, f_new] = (nb, 0, 0)
+                continue
+            if nb <= -100:  # the big side of a mortar: its sub-faces in the new frame
+                m = -100 - nb
+                conn_new[e, f_new] = (nb, 0, 0)
+                for p_old in range(nsub):
+                    s, fs, os_ = (int(v) for v in mortar[m][p_old])
+                    assert os_ == 0
+                    # the sub-face's new index: halves along the big face's new tangential axes
+                    h_old = [(p_old >> j) & 1 for j in range(dim - 1)]
+                    # a point of the sub-face in the big face's old tangential indices on the
+                    # doubled lattice (half h, local index i -> 2 P h + i), mapped to the new frame
+                    src, dst = [], []
+                    p_new = None
+                    for t in pts:
+                        t_s = list(t)[:dim - 1]
+                        # small face point (new frame) -> old tangential indices (box frame,
+                        # the same order as the big face's old tangential axes)
+                        _, t_old = old_face_point(s, new_face(s, fs), t_s)
+                        big = [P * h_old[j] + t_old[j] for j in range(dim - 1)]
+                        # the same lattice point in the big face's new frame (lattice of 2P)
+                        bn = _big_new(dim, P, frames[e], f_old, big)
+                        hn = [bn[j] // P for j in range(dim - 1)]
+                        ln = [bn[j] % P for j in range(dim - 1)]
+                        pn = sum(hn[j] << j for j in range(dim - 1))
+                        assert p_new is None or p_new == pn
+                        p_new = pn
+                        src.append(tuple(t_s) + ((0,) if dim == 2 else ()))
+                        dst.append(tuple(ln) + ((0,) if dim == 2 else ()))
+                    o = _orient_code(dim, P, src, dst)
+                    fs_new = new_face(s, fs)
+                    mort_new[m][p_new] = (s, fs_new, o)
+                    conn_new[s, fs_new] = (e, f_new, o | ((p_new + 1) << 3))
+                continue
+            if oo >> 3:  # the small side: written with its mortar above
+                continue
+            # conforming face: the neighbour's point for each of e's points
+            fo_new = new_face(nb, fo)
+            src, dst = [], []
+            for t in pts:
+                t_e = list(t)[:dim - 1]
+                _, t_old = old_face_point(e, f_new, t_e)
+                t_nb = new_point_of_old(nb, fo, t_old)
+                src.append(tuple(t_e) + ((0,) if dim == 2 else ()))
+                dst.append(tuple(list(t_nb)[:dim - 1]) + ((0,) if dim == 2 else ()))
+            conn_new[e, f_new] = (nb, fo_new, _orient_code(dim, P, src, dst))
+    return xnew, conn_new, mort_new, node_index
+
+
+def _big_new(dim, P, frame, f_old, big_old):
+    """Tangential indices, in the new frame, of a point on the doubled (2P) lattice of an
+    element's face given in the old frame's tangential indices (increasing old axes)."""
+    p, sg = frame
+    d_old = f_old // 2
+    t_old_axes = [b for b in range(dim) if b != d_old]
+    a_n = p.index(d_old)
+    t_new_axes = [a for a in range(dim) if a != a_n]
+    out = []
+    for a in t_new_axes:
+        ob = p[a]
+        v = big_old[t_old_axes.index(ob)]
+        out.append(v if sg[a] > 0 else 2 * P - 1 - v)
+    return out

@@ -31,12 +31,16 @@ def geometry_array(mspec):
 
 def refined_arrays(mspec):
     """(ngeo, xgeo, conn, mortar) of a specification whose geometry asks for "refine": the
-    upper half in x refined 2:1 with mortars (inputs.refined_mesh), or None."""
+    upper half in x refined 2:1 with mortars (inputs.refined_mesh; with "reorient": seed,
+    every element in a random local frame, inputs.reoriented_refined), or None."""
     g = mspec.get("geometry")
     if g is None or not g.get("refine"):
         return None
     xg, conn, mort = inputs.refined_mesh(mspec["dim"], mspec["N"], mspec["n"], mspec["periodic"], mspec["walls"],
                                          g["ngeo"], amp=g.get("amp", 0.0), lo=mspec["lo"], hi=mspec["hi"])
+    if g.get("reorient") is not None:  # every element in a random local frame
+        xg, conn, mort, _ = inputs.reoriented_refined(mspec["dim"], mspec["N"], g["ngeo"], xg, conn, mort,
+                                                      g["reorient"])
     return g["ngeo"], xg, conn, mort
 
 

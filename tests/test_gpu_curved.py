@@ -87,6 +87,17 @@ CASES = {
                                             dict(PAPER_PARAMS, model=2, flux="hllc")),
     "3d_N4_g2_slip_sliding_mortar": (mesh_spec(3, 4, [2, 2, 2], periodic=[1, 1, 0], walls=S3G,
                                                geometry=dict(ngeo=2, amp=0.04, refine=True)), dict(PAPER_PARAMS)),
+    # mortars with every element in a random local frame (sub-face order and face-point
+    # orientations of all kinds)
+    "2d_N3_g2_walls_mortar_unstr": (mesh_spec(2, 3, [4, 3], periodic=[1, 0], walls=W2,
+                                              geometry=dict(ngeo=2, amp=0.05, refine=True, reorient=5)),
+                                    dict(PAPER_PARAMS)),
+    "3d_N4_g2_walls_m2_hllc_mortar_unstr": (mesh_spec(3, 4, [2, 2, 2], periodic=[1, 1, 0], walls=W3,
+                                                      geometry=dict(ngeo=2, amp=0.04, refine=True, reorient=7)),
+                                            dict(PAPER_PARAMS, model=2, flux="hllc")),
+    "3d_N3_g1_slip_sliding_mortar_unstr": (mesh_spec(3, 3, [2, 2, 2], periodic=[1, 1, 0], walls=S3G,
+                                                     geometry=dict(ngeo=1, amp=0.05, refine=True, reorient=8)),
+                                           dict(PAPER_PARAMS)),
 }
 
 
@@ -143,7 +154,8 @@ def test_curved_one_step_fp64(orc, name):
 @pytest.mark.parametrize("name", ["2d_N3_g3_walls_m2", "3d_N3_g1_walls", "3d_N5_g2_walls", "2d_N3_g2_nsk",
                                   "3d_N5_g2_walls_unstr", "2d_N3_g3_walls_m2_unstr", "2d_N4_g2_walls_mortar",
                                   "3d_N4_g2_walls_mortar", "2d_N4_g2_walls_m2_hllc", "3d_N4_g2_walls_m2_hllc_mortar",
-                                  "2d_N4_g2_slip_sliding", "3d_N4_g2_slip_sliding_mortar"])
+                                  "2d_N4_g2_slip_sliding", "3d_N4_g2_slip_sliding_mortar",
+                                  "3d_N4_g2_walls_m2_hllc_mortar_unstr", "3d_N3_g1_slip_sliding_mortar_unstr"])
 def test_curved_ten_steps_fp64(orc, name):
     ms, ps = CASES[name]
     o, g, Uo = _pair(orc, ms, ps, exact=False)
@@ -185,9 +197,19 @@ def test_curved_free_stream(precision, tol):
 CURVED32 = 2.0
 
 
+# Curved mortar meshes with model 2: the convective pressure carries alpha/2 rho^2 ~ 160
+# (alpha = 100, rho ~ 1.8), and in FP32 the face metrics of a big face and of its curved
+# sub-faces cancel that term only to FP32 rounding (~1e-5 absolute per flux value), which
+# the energy accumulates.  Measured rho e errors after 10 steps: flat mortars 6e-8 (Rusanov)
+# and 1.3e-7 (HLLC), curved conforming 5e-8, curved mortars 4.6e-7 (Rusanov), 3.9e-6
+# (HLLC) and 8.2e-6 (HLLC, random frames); FP64 parity stays at 1e-12.
+MORTAR_M2_ENERGY = 50.0
+
+
 @pytest.mark.parametrize("name", ["2d_N3_g3_walls_m2", "3d_N3_g1_walls", "3d_N5_g2_walls", "3d_N3_g1_walls_unstr",
                                   "3d_N4_g2_walls_mortar", "2d_N4_g2_walls_m2_hllc", "3d_N3_g1_walls_m2_hllc_unstr",
-                                  "2d_N4_g2_slip_sliding", "3d_N3_g1_slip_sliding_m2_hllc_unstr"])
+                                  "2d_N4_g2_slip_sliding", "3d_N3_g1_slip_sliding_m2_hllc_unstr",
+                                  "2d_N3_g2_walls_mortar_unstr", "3d_N4_g2_walls_m2_hllc_mortar_unstr"])
 def test_curved_fp32_bulk_against_oracle(orc, name):
     ms, ps = CASES[name]
     o, g, Uo = _pair(orc, ms, ps, precision="fp32bulk", exact=False)
@@ -197,7 +219,10 @@ def test_curved_fp32_bulk_against_oracle(orc, name):
     g.run(10, dt)
     g.status()
     e_st = rel_l2(g.download_state(), o.run(Uo, 10, dt, rk=4))
-    assert np.all(e_st < CURVED32 * tol32_step(ms["dim"])), e_st
+    tol = CURVED32 * tol32_step(ms["dim"])
+    if ms["geometry"].get("refine") and ps.get("model", 1) == 2:
+        tol[ms["dim"] + 1] *= MORTAR_M2_ENERGY
+    assert np.all(e_st < tol), e_st
 
 
 def test_curved_refusals():
@@ -243,6 +268,30 @@ def test_unstructured_equals_structured_on_the_gpu(orc):
     gs.status()
     gu.status()
     assert np.all(rel_l2(gu.download_state(), perm(gs.download_state())) < TOL64)
+
+
+def test_reoriented_mortar_mesh_equals_box_frames_on_the_gpu():
+    """The library on the refined mesh with every element in a random local frame against
+    the library on the same mesh in the box frames, permuted (FP64, 1e-12)."""
+    ms = mesh_spec(3, 4, [2, 2, 2], periodic=[1, 1, 0], walls=W3, geometry=dict(ngeo=2, amp=0.04, refine=True))
+    mu = dict(ms, geometry=dict(ms["geometry"], reorient=11))
+    from cases import refined_arrays
+    ngeo, xg, conn, mort = refined_arrays(ms)
+    ni = inputs.reoriented_refined(3, 4, ngeo, xg, conn, mort, 11)[3]
+    gs, gu = dgk_context(ms, PAPER_PARAMS), dgk_context(mu, PAPER_PARAMS)
+    perm = lambda A: A.reshape(A.shape[0], -1)[:, ni.ravel()]
+    prim = inputs.random_admissible(3, gs.nelem, gs.np, 9)
+    gs.set_primitive(prim)
+    gu.set_primitive(np.ascontiguousarray(perm(prim).reshape(prim.shape)))
+    assert np.all(rel_l2(gu.rhs(), perm(gs.rhs()).reshape(prim.shape[0], gs.nelem, gs.np)) < TOL64)
+    dt = 0.5 * gs.max_dt()
+    assert abs(gu.max_dt() / gs.max_dt() - 1) < 1e-12
+    gs.run(3, dt)
+    gu.run(3, dt)
+    gs.status()
+    gu.status()
+    assert np.all(rel_l2(gu.download_state(), perm(gs.download_state()).reshape(prim.shape[0], gs.nelem, gs.np))
+                  < TOL64)
 
 
 def test_unstructured_refusals():

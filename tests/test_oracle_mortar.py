@@ -76,3 +76,46 @@ def test_mms_convergence_with_mortars(orc, model, N, dt):
         errs.append(np.sqrt(((U - mms_gen.exact_state(lib, x, nst * dt)) ** 2).mean(axis=(1, 2))))
     eoc = np.log2(errs[0] / errs[1])
     assert np.all(eoc > N + 0.3), eoc
+
+
+REORIENT = [(2, 3, [4, 3], [1, 0], 2, 5), (3, 3, [2, 2, 2], [1, 1, 0], 1, 6), (3, 4, [2, 2, 2], [1, 1, 1], 2, 7)]
+
+
+@pytest.mark.parametrize("params", [dict(PAPER_PARAMS), dict(PAPER_PARAMS, model=2, flux="hllc")])
+@pytest.mark.parametrize("dim,N,n,periodic,ngeo,seed", REORIENT)
+def test_reoriented_refined_mesh(orc, dim, N, n, periodic, ngeo, seed, params):
+    """The refined mesh with every element in a random local frame (inputs.reoriented_refined:
+    mortar sub-faces renumbered and face-point orientations of all eight kinds) is the
+    same discretisation as in the box frames: coordinates, right-hand side, max_dt and
+    diagnostics to 1e-12 after the node permutation.  A wrong orientation bit on one
+    mortar sub-face changes the result."""
+    walls = WALLS[dim] if not all(periodic) else {}
+    xg, conn, mort = inputs.refined_mesh(dim, N, n, periodic, walls, ngeo, amp=0.05)
+    xn, cn, mn, ni = inputs.reoriented_refined(dim, N, ngeo, xg, conn, mort, seed)
+    ne = xg.shape[1]
+
+    def oracle(x, c, m):
+        mesh = orc.make_mesh(dim, N, [ne, 1, 1], [0.0] * 3, [1.0] * 3, list(periodic) + [1] * (3 - dim), walls,
+                             geometry=(ngeo, x), conn=c, mortar=m)
+        return orc.Oracle(mesh, orc.make_params(**params))
+
+    o1, o2 = oracle(xg, conn, mort), oracle(xn, cn, mn)
+    perm = lambda A: A.reshape(A.shape[0], -1)[:, ni.ravel()].reshape(A.shape)
+    assert np.abs(o2.node_coords() - perm(o1.node_coords())).max() < 1e-14
+    prim = inputs.random_admissible(dim, ne, o1.np, 3)
+    U1, U2 = o1.set_primitive(prim), o2.set_primitive(perm(prim))
+    R1, R2 = o1.rhs(U1), o2.rhs(U2)
+    err = np.sqrt(((R2 - perm(R1)) ** 2).sum(axis=(1, 2)) / (perm(R1) ** 2).sum(axis=(1, 2)))
+    assert np.all(err < 1e-12), err
+    assert abs(o2.max_dt(U2) / o1.max_dt(U1) - 1) < 1e-12
+    d1, d2 = o1.diagnostics(U1), o2.diagnostics(U2)
+    for k in d1:
+        assert abs(d2[k] - d1[k]) <= 1e-12 * max(1.0, abs(d1[k])), k
+    # a wrong orientation on one sub-face (both table entries, so that they stay consistent)
+    bad_m, bad_c = mn.copy(), cn.copy()
+    s, fs, o = (int(v) for v in bad_m[0, 0])
+    o_bad = o ^ (2 if dim == 2 else 4)
+    bad_m[0, 0, 2] = o_bad
+    bad_c[s, fs, 2] = o_bad | (int(bad_c[s, fs, 2]) >> 3 << 3)
+    Rb = oracle(xn, bad_c, bad_m).rhs(U2)
+    assert np.abs(Rb - R2).max() > 1e-6 * np.abs(R2).max()
