@@ -669,3 +669,88 @@ def _big_new(dim, P, frame, f_old, big_old):
         v = big_old[t_old_axes.index(ob)]
         out.append(v if sg[a] > 0 else 2 * P - 1 - v)
     return out
+
+
+def graded_mesh(dim, N, n, periodic, walls, ngeo, level_of, amp=0.0, lo=None, hi=None):
+    """A 2:1-balanced non-conforming mesh with several refinement levels: the box mesh n of
+    [lo, hi] whose coarse cell c (integer coordinates) is split into 2^(dim L) cells of
+    level L = level_of(c) (neighbouring coarse cells may differ by one level at most).
+    Element maps: each cell samples its coarse cell's periodic map (box_geometry, degree
+    ngeo) restricted to the cell, so hanging faces are watertight.  Connectivity in the
+    unstructured format with mortars, every element in the box frame; walls: the faces
+    (2 d + side) of the non-periodic directions.  Returns (xgeo, conn, mortar)."""
+    n = [int(v) for v in n[:dim]]
+    lo = lo or [0.0] * dim
+    hi = hi or [1.0] * dim
+    G = ngeo + 1
+    NG = G ** dim
+    xc = box_geometry(dim, n, lo, hi, ngeo, amp=amp)
+    cstride = [int(np.prod(n[:d])) for d in range(dim)]
+    levels = {}
+    for c in np.ndindex(*reversed(n)):
+        c = tuple(reversed(c))
+        levels[c] = int(level_of(c))
+    # leaves: (level, integer coordinates on that level's lattice)
+    leaves = []
+    for c, L in levels.items():
+        for sub in np.ndindex(*([2 ** L] * dim)):
+            leaves.append((L, tuple(c[d] * 2 ** L + sub[d] for d in range(dim))))
+    index = {leaf: k for k, leaf in enumerate(leaves)}
+    ne = len(leaves)
+    t = -1.0 + 2.0 * np.arange(G) / ngeo
+    gidx = np.arange(NG)
+    xg = np.empty((dim, ne, NG))
+    for k, (L, q) in enumerate(leaves):
+        c = tuple(v >> L for v in q)
+        ce = sum(c[d] * cstride[d] for d in range(dim))
+        W = np.ones((NG, NG))
+        for d in range(dim):
+            off = q[d] - (c[d] << L)
+            Ld = _lagrange_equispaced_1d(ngeo, -1.0 + (2.0 * off + 1.0 + t) / 2 ** L)  # [G_new][G_old]
+            W *= Ld[(gidx // G ** d) % G][:, (gidx // G ** d) % G]
+        xg[:, k, :] = xc[:, ce, :] @ W.T
+
+    def wrap(L, q, d):
+        """q on level L moved into the domain along d (periodic), or None outside"""
+        m = n[d] << L
+        if 0 <= q[d] < m:
+            return q
+        if not periodic[d]:
+            return None
+        qq = list(q)
+        qq[d] %= m
+        return tuple(qq)
+
+    conn = np.zeros((ne, 2 * dim, 3), dtype=np.int32)
+    mortar = []
+    for k, (L, q) in enumerate(leaves):
+        for d in range(dim):
+            tang = [b for b in range(dim) if b != d]
+            for s in range(2):
+                f = 2 * d + s
+                qn = list(q)
+                qn[d] += 1 if s else -1
+                qn = wrap(L, tuple(qn), d)
+                if qn is None:
+                    conn[k, f] = (-1 - f, 0, 0)
+                    continue
+                if (L, qn) in index:  # same level
+                    conn[k, f] = (index[(L, qn)], 2 * d + 1 - s, 0)
+                elif L > 0 and (L - 1, tuple(v >> 1 for v in qn)) in index:  # coarser: small side
+                    big = (L - 1, tuple(v >> 1 for v in qn))
+                    p = sum(((q[b] & 1) << j) for j, b in enumerate(tang))
+                    conn[k, f] = (index[big], 2 * d + 1 - s, (p + 1) << 3)
+                else:  # finer: the big side of a mortar
+                    sub = [None] * (2 ** (dim - 1))
+                    for offs in np.ndindex(*([2] * (dim - 1))):
+                        qf = [2 * v for v in qn]
+                        qf[d] = 2 * qn[d] + (1 - s)
+                        for j, b in enumerate(tang):
+                            qf[b] += offs[j]
+                        leaf = (L + 1, tuple(qf))
+                        assert leaf in index, "the mesh is not 2:1 balanced"
+                        sub[sum(offs[j] << j for j in range(dim - 1))] = (index[leaf], 2 * d + 1 - s, 0)
+                    conn[k, f] = (-100 - len(mortar), 0, 0)
+                    mortar.append(sub)
+    mort = np.array(mortar, dtype=np.int32).reshape(len(mortar), 2 ** (dim - 1), 3)
+    return xg, conn, mort

@@ -29,15 +29,33 @@ def geometry_array(mspec):
     return g["ngeo"], x
 
 
+def graded_levels(nx):
+    """Refinement levels of the coarse columns in x of a graded mesh: two levels in the
+    middle quarter, one in the bands beside it, none elsewhere (2:1 balanced, also across
+    the periodic wrap); nx a multiple of 8."""
+    def level(c):
+        x = (8 * c[0]) // nx
+        return 2 if x in (3, 4) else (1 if x in (2, 5) else 0)
+    return level
+
+
 def refined_arrays(mspec):
     """(ngeo, xgeo, conn, mortar) of a specification whose geometry asks for "refine": the
-    upper half in x refined 2:1 with mortars (inputs.refined_mesh; with "reorient": seed,
-    every element in a random local frame, inputs.reoriented_refined), or None."""
+    upper half in x refined 2:1 with mortars (inputs.refined_mesh), or with "graded": two
+    levels of 2:1 refinement in the middle of x (inputs.graded_mesh, graded_levels); with
+    "reorient": seed, every element in a random local frame (inputs.reoriented_refined);
+    else None."""
     g = mspec.get("geometry")
-    if g is None or not g.get("refine"):
+    if g is None or not (g.get("refine") or g.get("graded")):
         return None
-    xg, conn, mort = inputs.refined_mesh(mspec["dim"], mspec["N"], mspec["n"], mspec["periodic"], mspec["walls"],
-                                         g["ngeo"], amp=g.get("amp", 0.0), lo=mspec["lo"], hi=mspec["hi"])
+    if g.get("graded"):
+        xg, conn, mort = inputs.graded_mesh(mspec["dim"], mspec["N"], mspec["n"], mspec["periodic"], mspec["walls"],
+                                            g["ngeo"], graded_levels(mspec["n"][0]), amp=g.get("amp", 0.0),
+                                            lo=mspec["lo"], hi=mspec["hi"])
+    else:
+        xg, conn, mort = inputs.refined_mesh(mspec["dim"], mspec["N"], mspec["n"], mspec["periodic"],
+                                             mspec["walls"], g["ngeo"], amp=g.get("amp", 0.0), lo=mspec["lo"],
+                                             hi=mspec["hi"])
     if g.get("reorient") is not None:  # every element in a random local frame
         xg, conn, mort, _ = inputs.reoriented_refined(mspec["dim"], mspec["N"], g["ngeo"], xg, conn, mort,
                                                       g["reorient"])

@@ -98,6 +98,12 @@ CASES = {
     "3d_N3_g1_slip_sliding_mortar_unstr": (mesh_spec(3, 3, [2, 2, 2], periodic=[1, 1, 0], walls=S3G,
                                                      geometry=dict(ngeo=1, amp=0.05, refine=True, reorient=8)),
                                            dict(PAPER_PARAMS)),
+    # two levels of 2:1 refinement in the middle of x (mortars between levels 0 | 1 and 1 | 2)
+    "2d_N3_g2_walls_graded": (mesh_spec(2, 3, [8, 4], periodic=[1, 0], walls=W2,
+                                        geometry=dict(ngeo=2, amp=0.05, graded=True)), dict(PAPER_PARAMS)),
+    "3d_N3_g1_walls_m2_graded_unstr": (mesh_spec(3, 3, [8, 2, 2], periodic=[1, 1, 0], walls=W3,
+                                                 geometry=dict(ngeo=1, amp=0.05, graded=True, reorient=4)),
+                                       dict(PAPER_PARAMS, model=2)),
 }
 
 
@@ -155,7 +161,8 @@ def test_curved_one_step_fp64(orc, name):
                                   "3d_N5_g2_walls_unstr", "2d_N3_g3_walls_m2_unstr", "2d_N4_g2_walls_mortar",
                                   "3d_N4_g2_walls_mortar", "2d_N4_g2_walls_m2_hllc", "3d_N4_g2_walls_m2_hllc_mortar",
                                   "2d_N4_g2_slip_sliding", "3d_N4_g2_slip_sliding_mortar",
-                                  "3d_N4_g2_walls_m2_hllc_mortar_unstr", "3d_N3_g1_slip_sliding_mortar_unstr"])
+                                  "3d_N4_g2_walls_m2_hllc_mortar_unstr", "3d_N3_g1_slip_sliding_mortar_unstr",
+                                  "2d_N3_g2_walls_graded"])
 def test_curved_ten_steps_fp64(orc, name):
     ms, ps = CASES[name]
     o, g, Uo = _pair(orc, ms, ps, exact=False)

@@ -119,3 +119,50 @@ def test_reoriented_refined_mesh(orc, dim, N, n, periodic, ngeo, seed, params):
     bad_c[s, fs, 2] = o_bad | (int(bad_c[s, fs, 2]) >> 3 << 3)
     Rb = oracle(xn, bad_c, bad_m).rhs(U2)
     assert np.abs(Rb - R2).max() > 1e-6 * np.abs(R2).max()
+
+
+GRADED = [(2, 3, [8, 2], 2), (3, 3, [8, 2, 2], 1)]
+
+
+@pytest.mark.parametrize("dim,N,n,ngeo", GRADED)
+def test_graded_mesh_two_levels(orc, dim, N, n, ngeo):
+    """Two levels of 2:1 refinement (coarse | 2:1 | 4:1 | 2:1 | coarse in x: mortars between
+    levels 0 and 1 and between levels 1 and 2): a uniform flow is preserved on the periodic
+    curved mesh, mass is conserved to round-off with walls, and the mesh in random local
+    frames equals the box frames."""
+    from cases import graded_levels
+    per = [1] * dim
+    xg, conn, mort = inputs.graded_mesh(dim, N, n, per, {}, ngeo, graded_levels(n[0]), amp=0.05)
+    ne = xg.shape[1]
+    # mortars: two level-0 | level-1 interfaces (one big face per coarse cell of the
+    # cross-section) and two level-1 | level-2 interfaces (2^(dim-1) per coarse cell)
+    cross = int(np.prod(n[1:]))
+    assert len(mort) == 2 * cross + 2 * cross * 2 ** (dim - 1)
+
+    def oracle(x, c, m, periodic, walls, params=PAPER_PARAMS):
+        mesh = orc.make_mesh(dim, N, [ne, 1, 1], [0.0] * 3, [1.0] * 3, list(periodic) + [1] * (3 - dim), walls,
+                             geometry=(ngeo, x), conn=c, mortar=m)
+        return orc.Oracle(mesh, orc.make_params(**params))
+
+    o = oracle(xg, conn, mort, per, {})
+    prim = np.zeros((dim + 3, ne, o.np))
+    prim[0], prim[dim + 1], prim[dim + 2] = 0.6, 0.95, 0.6
+    prim[1:1 + dim] = np.array([0.3, -0.2, 0.1][:dim])[:, None, None]
+    assert np.abs(o.rhs(o.set_primitive(prim))).max() < 1e-10
+    # walls in the last direction
+    pw = per[:-1] + [0]
+    walls = WALLS[dim]
+    xg2, conn2, mort2 = inputs.graded_mesh(dim, N, n, pw, walls, ngeo, graded_levels(n[0]), amp=0.05)
+    ow = oracle(xg2, conn2, mort2, pw, walls)
+    W = ow.node_weights()
+    Ut = ow.rhs(ow.set_primitive(inputs.random_admissible(dim, ne, ow.np, 5)))
+    assert abs((W * Ut[0]).sum()) < 1e-13 * (W * np.abs(Ut[0])).sum()
+    # random local frames
+    xn, cn, mn, ni = inputs.reoriented_refined(dim, N, ngeo, xg2, conn2, mort2, 13)
+    orr = oracle(xn, cn, mn, pw, walls)
+    perm = lambda A: A.reshape(A.shape[0], -1)[:, ni.ravel()].reshape(A.shape)
+    prim2 = inputs.random_admissible(dim, ne, ow.np, 6)
+    R1 = ow.rhs(ow.set_primitive(prim2))
+    R2 = orr.rhs(orr.set_primitive(perm(prim2)))
+    err = np.sqrt(((R2 - perm(R1)) ** 2).sum(axis=(1, 2)) / (perm(R1) ** 2).sum(axis=(1, 2)))
+    assert np.all(err < 1e-12), err
