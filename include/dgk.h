@@ -305,8 +305,17 @@ int dgk_batch_autotune(dgk_batch *b, int *out);
    Results do not depend on it: every element's arithmetic is the same. */
 int dgk_batch_set_config(dgk_batch *b, const int *cfg);
 /* Synchronise; per_problem (nullable, nprob ints) receives each problem's status.
-   Returns the first error: barrier timeout, then any problem's error. */
+   Returns the first error: barrier timeout, then any problem's error.  After a barrier
+   timeout the barrier's arrival counter is reset here; the problems' states are then
+   partly advanced and must be set again before the next run. */
 int dgk_batch_status(dgk_batch *b, int *per_problem);
+/* Spin limit of the persistent form's grid barriers, in GPU clock cycles (cycles >= 1;
+   default 4e9, about 2 s at 2 GHz).  A block that waits longer latches the barrier
+   status and returns, and dgk_batch_status() reports DGK_ERR_TIMEOUT: the kernel never
+   hangs on a missing block.  Synchronises the batch's stream; takes effect at the next
+   dgk_batch_run (the limit is part of the parameters each step rebinds).  A limit of a
+   few cycles makes the barrier waits run out, which exercises that error path. */
+int dgk_batch_set_barrier_limit(dgk_batch *b, long long cycles);
 
 /* ---------------- allocation-free right-hand side ----------------
  *
@@ -318,23 +327,31 @@ int dgk_batch_status(dgk_batch *b, int *per_problem);
  *
  * dgk_rhs_static computes exactly what dgk_rhs computes, for the state U (device
  * pointer, SoA [nvar][nelem][np] FP64, read only) into Ut (device pointer, same layout),
- * on cuda_stream (NULL: the default stream) of the current device, with the parameters
- * and mesh passed in.  It creates no context and calls no cudaMalloc, cudaFree or other
- * allocating routine: every intermediate array lives in one file-scope device array of
+ * each holding count = nvar*nelem*np doubles of the mesh passed in, on cuda_stream
+ * (NULL: the default stream) of the current device, with the parameters and mesh passed
+ * in.  It creates no context and calls no cudaMalloc, cudaFree or other allocating
+ * routine: every intermediate array lives in one file-scope device array of
  * DGK_STATIC_SCRATCH_BYTES bytes inside libdgk, which every GPU that loads the library
  * holds until the process exits.  Asynchronous: synchronise cuda_stream before reading Ut.
  *   - Size limit: a mesh whose intermediates need more than DGK_STATIC_SCRATCH_BYTES is
  *     rejected with DGK_ERR_ARG and dgk_last_error() says so (e.g. 3D N = 5 in FP64 fits
- *     about 1490 elements, in the FP32-bulk form about 2900).
+ *     about 1490 elements, in the FP32-bulk form about 2900).  A count that does not
+ *     match the mesh is rejected with DGK_ERR_ARG before any device work.
+ *   - status (nullable): receives the call's device status word, DGK_STATUS_* bits (0: the
+ *     kernels found every node finite and inside the EoS domain), copied in stream order
+ *     after the kernels.  Host or device memory; with pageable host memory the copy, and
+ *     so the call, waits for the kernels to finish.
  *   - The first call on a device looks up the scratch array's device address (once per
  *     device, with that device current); make that first call before any stream capture.
  *   - All calls share the array and it keeps the last call's contents; each call clears
- *     the only value that must start at zero.  Calls that overlap on the GPU (different
- *     streams or host threads) race on the array: serialise them.
- *   - Device-side state checks are latched in the scratch and not reported.
+ *     the only value that must start at zero (the status word).  Calls that overlap on
+ *     the GPU (different streams or host threads) race on the array: serialise them.
  */
 #define DGK_STATIC_SCRATCH_BYTES (64u << 20)
-int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *mesh, const double *U, double *Ut, void *cuda_stream);
+#define DGK_STATUS_NONFINITE 1u /* a non-finite density, temperature or energy at some node */
+#define DGK_STATUS_DOMAIN 2u    /* a density outside (0, 1/b) or a temperature <= 0 at some node */
+int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *mesh, const double *U, double *Ut, size_t count,
+                   void *cuda_stream, unsigned *status);
 
 const char *dgk_status_string(int status);
 /* Text of the most recent error in this thread (empty if none). */

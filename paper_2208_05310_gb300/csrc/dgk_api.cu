@@ -1330,6 +1330,9 @@ int dgk_interface_width(double T, double cv, double gammaK, double *width)
 
 // ====================================================================== batched ensembles
 
+// default spin limit of the persistent form's grid barriers: about 2 s at 2 GHz
+constexpr long long kBarrierLimitDefault = 4000000000LL;
+
 struct dgk_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -1493,7 +1496,7 @@ int dgk_batch_create(dgk_batch **out, int device, void *cuda_stream, const dgk_p
         }
         b->L.bar = b->d_bar;
         b->L.status = b->d_bar + 2;
-        b->L.bar_limit = 4000000000LL;  // about 2 s at 2 GHz
+        b->L.bar_limit = kBarrierLimitDefault;
         rc = batch_build_tiles(b);
     }
     if (rc) {
@@ -1589,6 +1592,15 @@ int dgk_batch_status(dgk_batch *b, int *per_problem)
         if (!first && rc) first = rc;
     }
     return first;
+}
+
+int dgk_batch_set_barrier_limit(dgk_batch *b, long long cycles)
+{
+    if (!b || cycles < 1) return fail(DGK_ERR_ARG, "the barrier limit must be at least one cycle");
+    DGK_CUDA(cudaStreamSynchronize(b->stream));
+    b->L.bar_limit = cycles;
+    DGK_CUDA(dgk::batch_upload_args(b->L, b->d_args));
+    return DGK_OK;
 }
 
 int dgk_batch_autotune(dgk_batch *b, int *out)

@@ -11,7 +11,8 @@
 // Consequences, stated once here and in include/dgk.h:
 //   - every GPU that loads libdgk holds this array until the process exits;
 //   - all calls share the array and it keeps the last call's contents; the only value
-//     that must start at zero (the device status word) is cleared by each call;
+//     that must start at zero (the device status word) is cleared by each call, and its
+//     value after the kernels is copied to the caller's status pointer if one is given;
 //   - calls that overlap on the GPU (on different streams, or from different host
 //     threads) race on the array: the caller must serialise them;
 //   - the first call on a device looks up the array's device address (once per device,
@@ -156,9 +157,13 @@ void place(dgk::KArgs<R> &a, unsigned char *base, const double *U, double *Ut, i
 
 }  // namespace
 
-extern "C" int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *m, const double *U, double *Ut, void *cuda_stream)
+extern "C" int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *m, const double *U, double *Ut, size_t count,
+                              void *cuda_stream, unsigned *status)
 {
     if (!p || !m || !U || !Ut) return fail_static(DGK_ERR_ARG, "null argument");
+    // the mesh's shape first: every later check indexes by dim
+    if (m->dim != 2 && m->dim != 3) return fail_static(DGK_ERR_UNSUPPORTED, "dim must be 2 or 3");
+    if (m->N < 2 || m->N > 5) return fail_static(DGK_ERR_UNSUPPORTED, "N must be 2..5");
     if (p->model < 0 || p->model > 2) return fail_static(DGK_ERR_UNSUPPORTED, "model must be 0, 1 or 2");
     for (int d = 0; d < m->dim && p->model == 0; ++d)
         if (!m->periodic[d]) return fail_static(DGK_ERR_UNSUPPORTED, "the original NSK model runs on periodic boxes");
@@ -167,8 +172,6 @@ extern "C" int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *m, const 
     if (p->flux == DGK_FLUX_HLLC && p->model != 2) return fail_static(DGK_ERR_UNSUPPORTED, "the HLLC flux is for model 2");
     if (!(p->gammaK > 0) || !(p->mu >= 0) || !(p->kappa >= 0) || !(p->cv > 0) || !(p->alpha >= 0) || !(p->beta >= 0))
         return fail_static(DGK_ERR_ARG, "parameters out of range");
-    if (m->dim != 2 && m->dim != 3) return fail_static(DGK_ERR_UNSUPPORTED, "dim must be 2 or 3");
-    if (m->N < 2 || m->N > 5) return fail_static(DGK_ERR_UNSUPPORTED, "N must be 2..5");
     const int D = m->dim, P = m->N + 1;
     const int NP = D == 2 ? P * P : P * P * P, NFP = D == 2 ? P : P * P, NV = D + 3, NL = D + 2, NF = 2 * D;
     long long ne = 1;
@@ -185,8 +188,12 @@ extern "C" int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *m, const 
                 if (!std::isfinite(w.u_wall[k]) || (w.u_wall[k] != 0.0 && (w.kind != 1 || k == d)))
                     return fail_static(DGK_ERR_ARG, "a wall velocity must be finite, tangential and on a no-slip wall");
         }
+        // n[d] < 2^31 and ne < 2^32 before the multiply: the product stays below 2^63
         ne *= m->n[d];
+        if (ne >= (1LL << 32)) return fail_static(DGK_ERR_ARG, "mesh too large for the static scratch of dgk_rhs_static (DGK_STATIC_SCRATCH_BYTES)");
     }
+    if (count != (size_t)NV * (size_t)ne * (size_t)NP)
+        return fail_static(DGK_ERR_ARG, "count must be nvar * nelem * np of the mesh");
     const bool f32 = p->precision == DGK_PREC_FP32BULK;
     const size_t rs = f32 ? sizeof(float) : sizeof(double);
     const size_t need = 256 + align256((size_t)NV * ne * NP * rs) + align256((size_t)NL * ne * NF * NFP * rs) +
@@ -222,5 +229,9 @@ extern "C" int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *m, const 
     if (kt->traces(args, s) != cudaSuccess || kt->lift1(args, s) != cudaSuccess || kt->lift2vol(args, s) != cudaSuccess ||
         kt->surf(args, 0, 0, s) != cudaSuccess)
         return fail_static(DGK_ERR_CUDA, "kernel launch failed");
+    // the status word of this call, in stream order (pageable host memory: the copy, and
+    // so the call, waits for the kernels)
+    if (status && cudaMemcpyAsync(status, base, sizeof(unsigned), cudaMemcpyDefault, s) != cudaSuccess)
+        return fail_static(DGK_ERR_CUDA, "reading the status word failed");
     return DGK_OK;
 }

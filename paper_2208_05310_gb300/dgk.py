@@ -63,7 +63,7 @@ EXPORTS = ("dgk_create", "dgk_destroy", "dgk_set_params", "dgk_mesh_box", "dgk_m
            "dgk_sigma_vl", "dgk_interface_width", "dgk_status_string", "dgk_last_error", "dgk_check_conversions",
            "dgk_rhs_static", "dgk_node_temperature_pressure", "dgk_batch_create", "dgk_batch_destroy",
            "dgk_batch_problem", "dgk_batch_set_dt", "dgk_batch_run", "dgk_batch_autotune", "dgk_batch_status",
-           "dgk_batch_set_config")
+           "dgk_batch_set_config", "dgk_batch_set_barrier_limit")
 
 
 def lib():
@@ -103,6 +103,7 @@ def lib():
         "dgk_batch_autotune": (i, [vp, C.POINTER(i)]),
         "dgk_batch_status": (i, [vp, C.POINTER(i)]),
         "dgk_batch_set_config": (i, [vp, C.POINTER(i)]),
+        "dgk_batch_set_barrier_limit": (i, [vp, C.c_longlong]),
         "dgk_status": (i, [vp]),
         "dgk_set_timing": (i, [vp, i]),
         "dgk_kernel_time": (i, [vp, i, dp, C.POINTER(C.c_longlong)]),
@@ -110,7 +111,7 @@ def lib():
         "dgk_sigma_vl": (i, [d, d, d, dp]),
         "dgk_interface_width": (i, [d, d, d, dp]),
         "dgk_check_conversions": (i, [vp, sz, i, C.POINTER(C.c_ulonglong)]),
-        "dgk_rhs_static": (i, [C.POINTER(DgkParams), C.POINTER(DgkBoxMesh), vp, vp, vp]),
+        "dgk_rhs_static": (i, [C.POINTER(DgkParams), C.POINTER(DgkBoxMesh), vp, vp, sz, vp, C.POINTER(C.c_uint)]),
         "dgk_status_string": (C.c_char_p, [i]),
         "dgk_last_error": (C.c_char_p, []),
     }
@@ -191,17 +192,30 @@ def make_box_mesh(dim, N, n, lo, hi, periodic, walls=None):
     return m
 
 
-def rhs_static(params, mesh, U, Ut, stream=None):
+def rhs_static(params, mesh, U, Ut, stream=None, status=False):
     """dgk_rhs_static: right-hand side of the device state U into the device array Ut
     without any device allocation (see include/dgk.h).  U, Ut: contiguous float64 CUDA
-    tensors of shape (nvar, nelem, np); stream: a torch.cuda.Stream or None (default
-    stream).  Asynchronous."""
+    tensors of nvar*nelem*np elements for the mesh passed in; stream: a
+    torch.cuda.Stream or None (default stream).  Asynchronous, unless status is true:
+    then the call waits for the kernels and returns the device status word (0, or
+    DGK_STATUS_* bits)."""
     pu, nu, du = _ptr(U)
     po, no, do = _ptr(Ut)
-    if not (du and do) or nu != no:
-        raise DgkError("U and Ut must be device tensors of equal size")
+    dim, P = mesh.dim, mesh.N + 1
+    if dim not in (2, 3):
+        raise DgkError("mesh.dim must be 2 or 3")
+    count = (dim + 3) * int(np.prod([int(mesh.n[d]) for d in range(dim)], dtype=object)) * P ** dim
+    if not (du and do) or nu != count or no != count:
+        raise DgkError(f"U and Ut must be device tensors of nvar*nelem*np = {count} doubles for this mesh")
     h = C.c_void_p(stream.cuda_stream) if stream is not None else C.c_void_p()
-    _check(lib().dgk_rhs_static(C.byref(params), C.byref(mesh), pu, po, h), "dgk_rhs_static")
+    st = C.c_uint(0)
+    _check(lib().dgk_rhs_static(C.byref(params), C.byref(mesh), pu, po, count, h, C.byref(st) if status else None),
+           "dgk_rhs_static")
+    return st.value if status else None
+
+
+STATUS_NONFINITE = 1
+STATUS_DOMAIN = 2
 
 
 # ---------------- context ----------------
@@ -428,6 +442,15 @@ class Batch:
         """form: "persistent" or "grouped"."""
         cfg = (C.c_int * 5)(("persistent", "grouped").index(form), blocks_per_sm, k3, k4, k5)
         _check(lib().dgk_batch_set_config(self._h, cfg), "dgk_batch_set_config")
+
+    def set_barrier_limit(self, cycles):
+        """Spin limit of the persistent form's grid barriers, in GPU clock cycles."""
+        _check(lib().dgk_batch_set_barrier_limit(self._h, int(cycles)), "dgk_batch_set_barrier_limit")
+
+    def status_code(self):
+        """Synchronise; the first error code (0 if none), without raising."""
+        per = (C.c_int * len(self.problems))()
+        return lib().dgk_batch_status(self._h, per)
 
     def status(self):
         """Synchronise; raise on the first error (barrier timeout, then any problem's)."""

@@ -174,3 +174,33 @@ def test_batch_refuses_hllc():
     _, meshes = ensemble(2, 3, (4, 6))
     with pytest.raises(dgk.DgkError):
         dgk.Batch(meshes, **dict(PAPER_PARAMS, model=2, flux="hllc"))
+
+
+def test_batch_barrier_timeout_is_reported_and_recoverable():
+    """The persistent form's grid barrier gives up after its spin limit: with a limit of
+    one clock cycle the early blocks' waits run out, the kernel returns (no hang) and
+    dgk_batch_status reports DGK_ERR_TIMEOUT.  With the default limit restored and the
+    states set again, the next run succeeds and equals a clean run bit for bit."""
+    from paper_2208_05310_gb300 import dgk
+    specs, meshes = ensemble(6, 23, (6, 16))
+    b, prims, dts = _batch(meshes, specs)
+    b.set_config("persistent", 1, 1, 1, 1)
+    b.run(2)
+    b.status()
+    clean = [q.download_state() for q in b.problems]
+    for q, prim in zip(b.problems, prims):
+        q.set_primitive(prim)
+    b.set_barrier_limit(1)
+    b.run(1)
+    assert b.status_code() == -9  # DGK_ERR_TIMEOUT
+    assert b.status_code() == 0   # reported once, then cleared
+    b.set_barrier_limit(4_000_000_000)  # the default
+    for q, prim in zip(b.problems, prims):
+        q.set_primitive(prim)
+    b.run(2)
+    assert all(rc == 0 for rc in b.status())
+    for q, u in zip(b.problems, clean):
+        assert np.array_equal(q.download_state(), u)
+    with pytest.raises(dgk.DgkError):
+        b.set_barrier_limit(0)
+    b.close()

@@ -15,8 +15,11 @@ over the sampled element's nodes, the difference of the increments dt*U_t (dt th
 oracle's stable step for the sub-box) relative to the element's state, with the floors
 of rel_l2.  FP64: 1e-12, the bar for conserved variables; FP32-bulk: the per-variable
 bounds of one step of the FP32-bulk parity tests.  (At rest, U_t is round-off in the
-quiescent liquid and vapour and in the z-momentum everywhere, so a ratio of U_t norms
-would compare round-off with round-off.)  The relative right-hand-side error is printed.
+quiescent liquid and vapour and in the z-momentum away from the walls, so a ratio of
+U_t norms there would compare round-off with round-off.)  At the three interface
+samples, where U_t is not round-off, the right-hand side's own relative error is
+asserted too: 1e-12 (FP64) and 2e-4 (FP32-bulk; 4e-4 on curved elements), per variable
+whose oracle U_t is above round-off.
 
 The curved variant (the bench's `--mesh curved`: degree-2 maps, walls bent) gives the
 oracle's sub-box the full mesh's element maps of its elements; the sub-box's own seams
@@ -32,6 +35,7 @@ pytestmark = pytest.mark.gpu
 # interface (bridge radius 0.5 about x = y = 1) at mid-height and at both walls, liquid
 # core, vapour, vapour next to the bottom wall
 SAMPLES = [(47, 32, 16), (16, 32, 0), (32, 47, 31), (31, 32, 8), (5, 5, 16), (48, 48, 1)]
+INTERFACE = SAMPLES[:3]
 
 
 def _sub_box(orc, wl, ix, iy, iz, W=9, geo=None):
@@ -97,3 +101,12 @@ def test_fullsize_sampled_rhs(orc, precision, mesh):
         if mesh == "curved" and precision != "fp64":
             tol = 2.0 * tol
         assert np.all(err < tol), ((ix, iy, iz), err, tol)
+        if (ix, iy, iz) in INTERFACE:
+            # at the interface U_t itself is not round-off: its relative error per variable
+            # at the right-hand-side tolerances (variables whose oracle U_t is at round-off
+            # level relative to the largest, such as the z-momentum of the bridge at
+            # mid-height, are left to the increment check above)
+            rn = np.sqrt((ref ** 2).sum(axis=1))
+            live = rn > 1e-9 * rn.max()
+            rtol = 1e-12 if precision == "fp64" else (2e-4 if mesh == "box" else 4e-4)
+            assert np.all(rhs_err[live] < rtol), ((ix, iy, iz), rhs_err, live)
