@@ -62,7 +62,8 @@ extern "C" {
 #define DGK_FLUX_RUSANOV 0   /* Rusanov flux (the paper's flux for model 1) */
 #define DGK_FLUX_HLLC 1      /* HLLC flux (the paper's flux for model 2) */
 
-#define DGK_NDIAG 8 /* mass, momentum x/y/z, total energy, -int rho eta, ||rho-c||_2, max|u| */
+#define DGK_NDIAG 9 /* mass, momentum x/y/z, total energy, -int rho eta, ||rho-c||_2, max|u|,
+                       int Pi (rate of entropy production) */
 
 typedef struct dgk_ctx dgk_ctx;
 
@@ -209,8 +210,16 @@ int dgk_rhs(dgk_ctx *ctx, double *Ut, size_t count, int on_device);
    U = U + B_s G, fused into the surface kernel).  Asynchronous. */
 int dgk_rk_step(dgk_ctx *ctx, double dt);
 /* nsteps RK steps of size dt, launched as a captured CUDA graph of one step.
-   Asynchronous; check dgk_status() afterwards. */
-int dgk_run(dgk_ctx *ctx, int nsteps, double dt);
+   Asynchronous; check dgk_status() afterwards.
+   Diagnostics inside the run: with diag_every > 0 and diag_out non-null, after every
+   diag_every-th step the integral diagnostics of dgk_diagnostics() are taken on the device
+   (a second captured graph: no host round trip per sample) and stored; at the end the
+   nsteps / diag_every samples, DGK_NDIAG doubles each in step order, are copied to
+   diag_out (device or host memory; host memory: the call then waits for the run).  The
+   samples do not change the trajectory (bitwise the same states as without them), and
+   each equals dgk_diagnostics() called after that step.  diag_every = 0 or diag_out
+   NULL: no samples.  Device buffers for the samples are allocated on first use. */
+int dgk_run(dgk_ctx *ctx, int nsteps, double dt, int diag_every, double *diag_out);
 /* Independent problems through host memory, pipelined: for i = 0..nitems-1 the state
    becomes in[i] (as dgk_upload_state: the RK register is reset), advances nsteps RK
    steps of size dt (as dgk_run), and is read into out[i].  in[i] and out[i] are host
@@ -229,8 +238,12 @@ int dgk_run_host(dgk_ctx *ctx, const double *const *in, double *const *out, int 
 /* Largest stable step for the current state: min of CFL/((2N+1) max sum_d (|u_d|+s)/h_d),
    DFL/((2N+1)^2 nu_max sum_d h_d^-2) and 2/(alpha beta); s^2 = c_s^2 + alpha rho. */
 int dgk_max_dt(dgk_ctx *ctx, double cfl, double dfl, double *dt);
-/* Integral diagnostics (Gauss quadrature, FP64, fixed summation order):
-   out[DGK_NDIAG] = mass, momentum x, y, z, total energy, -int rho eta, ||rho - c||_2, max|u|. */
+/* Integral diagnostics (Gauss quadrature, FP64 sums in a fixed order on the device):
+   out[DGK_NDIAG] = mass, momentum x, y, z, total energy, -int rho eta, ||rho - c||_2,
+   max|u|, and int Pi, the rate of entropy production (Sec. 2.3):
+   Pi = tau : grad u / T + kappa |grad T|^2 / T^2 + beta (gamma_K lap c + alpha (rho - c))^2 / T
+   (the last term for the relaxation models) with the scheme's lifted gradients (the
+   bulk type computes Pi per node; the sums are FP64).  Synchronises. */
 int dgk_diagnostics(dgk_ctx *ctx, double *out);
 /* Nodal temperature (recovered from the total energy with the lifted grad c, as the
    scheme does) and pressure p(rho, T) (Eq. pressure), each nelem*np doubles [e][n];
@@ -242,6 +255,14 @@ int dgk_status(dgk_ctx *ctx);
    accounting: which = 0 lift1, 1 lift2+volume, 2 surface+RK.  Enabled by dgk_set_timing. */
 int dgk_set_timing(dgk_ctx *ctx, int enable);
 int dgk_kernel_time(dgk_ctx *ctx, int which, double *ms_total, long long *launches);
+
+/* Measured fused multiply-add throughput of device `device` (flops per second, 2 per
+   FMA): precision DGK_PREC_FP64 for double, DGK_PREC_FP32BULK for float.  The roof of
+   the arithmetic-bound kernels (the FP64 form's kernels are bound by the FP64 pipe): a
+   grid of 8 blocks of 256 threads per SM, each thread running 8 independent FMA chains,
+   best of five event-timed launches after a warm-up.  Allocates and frees a small
+   output array; synchronises the device.  The paper has no counterpart (measurement). */
+int dgk_fma_peak(int device, int precision, double *flops_per_s);
 
 /* ---------------- thermodynamics (host) ---------------- */
 

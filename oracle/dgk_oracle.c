@@ -2075,9 +2075,66 @@ int or_max_dt(const or_mesh *m, const or_params *p, const double *U, double cfl,
     return 0;
 }
 
+/* Rate of entropy production at the nodes (Sec. 2.3: the relaxation model's production
+   rate after Eq. (navierstokeskorteweg_alpha), the original model's after
+   Eq. (energyfluxnsk)), from the thermodynamic fluxes of the scheme:
+     Pi = tau : grad u / T + kappa |grad T|^2 / T^2 + beta chi^2 / T,
+     tau = mu (grad u + grad u^T - 2/3 div u I),  chi = gamma_K lap c + alpha (rho - c),
+   the last term for the relaxation models only.  Reading: the printed viscous part
+   (4/3 mu |div u|^2 + mu |D_dev|^2) does not follow from the stress of the same section
+   under the Stokes hypothesis; the dissipation of that stress, tau : grad u
+   (= 2 mu |D_dev|^2 in 3D), is used, and the heat term is the Fourier flux kappa grad T
+   paired with grad(1/T).  Gradients are the scheme's: lifted grad u (pass 1), grad T and
+   lap c (pass 2).  Pi[e][n]. */
+static int entropy_production(const ctx_t *c, const double *U, double *Pi)
+{
+    long ne = c->ne;
+    int np = c->np, d = c->d, nl = c->nl;
+    const or_params *p = &c->prm;
+    work_t w;
+    if (work_alloc(c, &w)) { work_free(&w); return -2; }
+    primitives(c, U, w.q);
+    traces(c, w.q, nl, w.trq);
+    if (c->curved) lift_pass1_c(c, w.q, w.trq, w.grad);
+    else lift_pass1(c, w.q, w.trq, w.grad);
+    node_temperature(c, U, w.grad, w.T);
+    if (c->curved) lift_pass2_c(c, w.T, w.grad, w.trq, w.gT, w.lap);
+    else lift_pass2(c, w.T, w.grad, w.trq, w.gT, w.lap);
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < ne; ++e)
+        for (int n = 0; n < np; ++n) {
+            double g[3 * 8], du[3][3];
+            gather_grad(c, w.grad, e, n, g);
+            /* du[i][k] = d u_k / d x_i */
+            for (int i = 0; i < d; ++i)
+                for (int k = 0; k < d; ++k) du[i][k] = g[i * nl + 1 + k];
+            double divu = 0.0;
+            for (int k = 0; k < d; ++k) divu += du[k][k];
+            double diss = 0.0; /* tau : grad u = sum_ik tau_ik du_k/dx_i */
+            for (int i = 0; i < d; ++i)
+                for (int k = 0; k < d; ++k) {
+                    double tik = p->mu * (du[i][k] + du[k][i] - (i == k ? 2.0 / 3.0 * divu : 0.0));
+                    diss += tik * du[i][k];
+                }
+            double T = w.T[(size_t)e * np + n], gT2 = 0.0;
+            for (int k = 0; k < d; ++k) {
+                double gk = w.gT[IDX(k, e, n, ne, np)];
+                gT2 += gk * gk;
+            }
+            double pi = diss / T + p->kappa * gT2 / (T * T);
+            if (p->model != 0) {
+                double chi = p->gammaK * w.lap[(size_t)e * np + n] + p->alpha * (U[IDX(0, e, n, ne, np)] - U[IDX(d + 2, e, n, ne, np)]);
+                pi += p->beta * chi * chi / T;
+            }
+            Pi[(size_t)e * np + n] = pi;
+        }
+    work_free(&w);
+    return 0;
+}
+
 /* Integral diagnostics with the collocated Gauss quadrature:
    out = (mass, momentum x, y, z, total energy, mathematical entropy -int rho eta,
-          ||rho - c||_2, max |u|). */
+          ||rho - c||_2, max |u|, int Pi (the rate of entropy production, above)). */
 int or_diagnostics(const or_mesh *m, const or_params *p, const double *U, double *out)
 {
     ctx_t c;
@@ -2085,7 +2142,8 @@ int or_diagnostics(const or_mesh *m, const or_params *p, const double *U, double
     long ne = c.ne;
     int np = c.np, d = c.d;
     double *T = (double *)malloc(sizeof(double) * ne * np);
-    if (!T) { teardown(&c); return -2; }
+    double *Pi = (double *)malloc(sizeof(double) * ne * np);
+    if (!T || !Pi || entropy_production(&c, U, Pi)) { free(T); free(Pi); teardown(&c); return -2; }
     or_temperature(m, p, U, T);
     double J = 1.0;
     for (int k = 0; k < d; ++k) J *= 0.5 * c.h[k];
@@ -2109,9 +2167,11 @@ int or_diagnostics(const or_mesh *m, const or_params *p, const double *U, double
                 out[6] += W * dc * dc;
             }
             if (sqrt(u2) > out[7]) out[7] = sqrt(u2);
+            out[8] += W * Pi[(size_t)e * np + n];
         }
     out[6] = sqrt(out[6]);
     free(T);
+    free(Pi);
     teardown(&c);
     return 0;
 }

@@ -125,7 +125,8 @@ int  or_num_threads(void);
 /* Threads of the parallel element loops from now on (OpenMP; n >= 1). */
 void or_set_num_threads(int n);
 
-#define OR_NDIAG 8  /* mass, mom_x, mom_y, mom_z, energy, -entropy, ||rho-c||_2, max|u| */
+#define OR_NDIAG 9  /* mass, mom_x, mom_y, mom_z, energy, -entropy, ||rho-c||_2, max|u|,
+                        int Pi (rate of entropy production) */
 
 #ifdef __cplusplus
 }

@@ -16,8 +16,9 @@ import build as _build  # noqa: E402
 
 _lib = None
 
-OR_NDIAG = 8
-DIAG_NAMES = ("mass", "mom_x", "mom_y", "mom_z", "energy", "neg_entropy", "rho_minus_c_l2", "max_u")
+OR_NDIAG = 9
+DIAG_NAMES = ("mass", "mom_x", "mom_y", "mom_z", "energy", "neg_entropy", "rho_minus_c_l2", "max_u",
+              "entropy_production")
 
 
 class OrMesh(C.Structure):

@@ -20,7 +20,7 @@ NVFLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler"
            "-I" + CSRC, "-I" + INC] + GENCODE
 
 UNITS = ["dgk_k2d_f64.cu", "dgk_k2d_f32.cu", "dgk_k3d_f64.cu", "dgk_k3d_f32.cu", "dgk_c2d_f64.cu", "dgk_c2d_f32.cu",
-         "dgk_c3d_f64.cu", "dgk_c3d_f32.cu", "dgk_api.cu", "dgk_static.cu", "dgk_batch.cu", "dgk_host_math.cpp",
+         "dgk_c3d_f64.cu", "dgk_c3d_f32.cu", "dgk_api.cu", "dgk_static.cu", "dgk_batch.cu", "dgk_peak.cu", "dgk_host_math.cpp",
          "dgk_geom.cpp"]
 
 

@@ -173,15 +173,18 @@ __global__ void k_dt_reduce_c(const double *U, const double *T, long long ne, No
     }
 }
 
-// Per-block partial sums of the integral diagnostics (fixed tree order; the host sums
-// the blocks in index order, so the result is deterministic).
-__global__ void k_diag_partial(const double *U, const double *T, long long ne, NodeInfo ni, dgk::Phys ph,
-                               double *partial)
+// Per-block partial sums of the integral diagnostics (fixed tree order), reduced over the
+// blocks by k_diag_final in a fixed order, so that the result is deterministic.  Pi: the
+// nodal rate of entropy production (k_entropy_prod).
+constexpr int kNDiag = DGK_NDIAG;
+__global__ void k_diag_partial(const double *U, const double *T, const double *Pi, long long ne, NodeInfo ni,
+                               dgk::Phys ph, double *partial)
 {
-    __shared__ double s[8][256];
+    __shared__ double s[kNDiag][256];
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nn = ne * ni.NP;
-    double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double q[kNDiag];
+    for (int k = 0; k < kNDiag; ++k) q[k] = 0.0;
     if (i < nn) {
         const int n = (int)(i % ni.NP);
         double W = ni.met ? 1.0 / ni.met[(long long)(ni.D * ni.D) * nn + i] : ni.J;
@@ -199,19 +202,51 @@ __global__ void k_diag_partial(const double *U, const double *T, long long ne, N
         // -rho eta = -(rho R cv ln T - rho R ln(b rho / (1 - b rho)))
         q[5] = -W * (rho * dgk::kRgas * ph.cv * log(t) - rho * dgk::kRgas * log(dgk::kBvdw * rho / (1.0 - dgk::kBvdw * rho)));
         double dc = rho - U[(ni.D + 2) * nn + i];
-        q[6] = W * dc * dc;
+        q[6] = ph.model != 0 ? W * dc * dc : 0.0;
         q[7] = sqrt(u2);
+        q[8] = W * Pi[i];
     }
-    for (int k = 0; k < 8; ++k) s[k][threadIdx.x] = q[k];
+    for (int k = 0; k < kNDiag; ++k) s[k][threadIdx.x] = q[k];
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
-            for (int k = 0; k < 7; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + o];
-            s[7][threadIdx.x] = fmax(s[7][threadIdx.x], s[7][threadIdx.x + o]);
+            for (int k = 0; k < kNDiag; ++k)
+                s[k][threadIdx.x] = k == 7 ? fmax(s[k][threadIdx.x], s[k][threadIdx.x + o]) : s[k][threadIdx.x] + s[k][threadIdx.x + o];
         }
         __syncthreads();
     }
-    if (threadIdx.x < 8) partial[(long long)blockIdx.x * 8 + threadIdx.x] = s[threadIdx.x][0];
+    if (threadIdx.x < kNDiag) partial[(long long)blockIdx.x * kNDiag + threadIdx.x] = s[threadIdx.x][0];
+}
+
+// Sum (max for max|u|) of the nb block partials: thread j takes the fixed block range
+// [j nb/256, (j+1) nb/256) in order, then a fixed tree over the 256 threads.  Writes
+// out[0..kNDiag) (||rho - c||_2 as the square root of its sum); with a counter, at the
+// slot out + kNDiag * (*counter) and then advances the counter (samples of a run).
+__global__ void __launch_bounds__(256) k_diag_final(const double *partial, long long nb, double *out, unsigned *counter)
+{
+    __shared__ double s[kNDiag][256];
+    const long long lo = nb * threadIdx.x / 256, hi = nb * (threadIdx.x + 1) / 256;
+    double q[kNDiag];
+    for (int k = 0; k < kNDiag; ++k) q[k] = 0.0;
+    for (long long b = lo; b < hi; ++b)
+        for (int k = 0; k < kNDiag; ++k) {
+            const double v = partial[b * kNDiag + k];
+            q[k] = k == 7 ? fmax(q[k], v) : q[k] + v;
+        }
+    for (int k = 0; k < kNDiag; ++k) s[k][threadIdx.x] = q[k];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int k = 0; k < kNDiag; ++k)
+                s[k][threadIdx.x] = k == 7 ? fmax(s[k][threadIdx.x], s[k][threadIdx.x + o]) : s[k][threadIdx.x] + s[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < kNDiag) {
+        double *dst = out + (counter ? (long long)kNDiag * (*counter) : 0);
+        dst[threadIdx.x] = threadIdx.x == 6 ? sqrt(s[6][0]) : s[threadIdx.x][0];
+    }
+    __syncthreads();
+    if (counter && threadIdx.x == 0) *counter += 1;
 }
 
 // p(rho, T) at the nodes (Eq. pressure), from the nodal temperature in T
@@ -284,6 +319,12 @@ struct dgk_ctx {
     std::vector<double> xnodes;
     unsigned *status = nullptr;
     unsigned long long *redbuf = nullptr;
+    // diagnostics: nodal entropy production, block partials, one result, the samples of
+    // dgk_run and their counter, and the captured graph of one sample
+    double *pibuf = nullptr, *diagout = nullptr, *samples = nullptr;
+    unsigned *diag_counter = nullptr;
+    size_t samples_cap = 0;
+    cudaGraphExec_t diag_graph = nullptr;
     double coef_h[11] = {0};
     bool coef_valid = false;
     cudaGraphExec_t graph = nullptr;
@@ -309,7 +350,7 @@ void free_buffers(dgk_ctx *c)
     if (c->metd && (void *)c->metd != c->met) cudaFree(c->metd);
     void *ptrs[] = {c->U,  c->G,   c->Tbuf, c->coef, c->rhsbuf, c->partial, c->Utv,
                     c->tr1, c->tr2, c->fd,   c->Us,   c->status, c->redbuf, c->met, c->fmet, c->conn,
-                    c->mort, c->mtr1, c->mtr2, c->mfd, c->mrec};
+                    c->mort, c->mtr1, c->mtr2, c->mfd, c->mrec, c->pibuf, c->diagout, c->samples, c->diag_counter};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     c->U = c->G = c->Tbuf = c->coef = c->rhsbuf = c->partial = nullptr;
@@ -325,8 +366,13 @@ void free_buffers(dgk_ctx *c)
     c->xnodes.clear();
     c->status = nullptr;
     c->redbuf = nullptr;
+    c->pibuf = c->diagout = c->samples = nullptr;
+    c->diag_counter = nullptr;
+    c->samples_cap = 0;
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
+    if (c->diag_graph) cudaGraphExecDestroy(c->diag_graph);
+    c->diag_graph = nullptr;
     if (c->stage_in) cudaFree(c->stage_in);
     if (c->stage_out) cudaFree(c->stage_out);
     c->stage_in = c->stage_out = nullptr;
@@ -337,6 +383,8 @@ void drop_graph(dgk_ctx *c)
 {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
+    if (c->diag_graph) cudaGraphExecDestroy(c->diag_graph);
+    c->diag_graph = nullptr;
 }
 
 template <typename R>
@@ -600,6 +648,48 @@ NodeInfo node_info(const dgk_ctx *c)
     for (int i = 0; i < c->P; ++i) ni.w[i] = c->op1.w[i];
     ni.met = c->curved ? c->metd : nullptr;
     return ni;
+}
+
+// Buffers of the diagnostics (allocated on first use).
+int diag_buffers(dgk_ctx *c)
+{
+    const long long nn = c->ne * c->NP;
+    const long long nb = (nn + 255) / 256;
+    if (!c->pibuf) DGK_CUDA(cudaMalloc(&c->pibuf, (size_t)nn * sizeof(double)));
+    if (!c->partial) DGK_CUDA(cudaMalloc(&c->partial, (size_t)nb * kNDiag * sizeof(double)));
+    if (!c->diagout) DGK_CUDA(cudaMalloc(&c->diagout, kNDiag * sizeof(double)));
+    if (!c->diag_counter) DGK_CUDA(cudaMalloc(&c->diag_counter, sizeof(unsigned)));
+    return DGK_OK;
+}
+
+// The integral diagnostics of the current state, reduced on the device into dst
+// (DGK_NDIAG doubles; with a counter at dst + DGK_NDIAG * (*counter), which then
+// advances): nodal temperature, the pass-2 traces of the state (k_lift1, which the next
+// stage recomputes identically), the nodal rate of entropy production, block partials,
+// the fixed-order final sum.  Enqueued on the context's stream; capturable.
+int enqueue_diag(dgk_ctx *c, double *dst, unsigned *counter)
+{
+    cudaError_t err = run_nodeT(c, 0);
+    if (err == cudaSuccess) err = run_lift1(c, c->args());
+    if (err == cudaSuccess) {
+        if (c->prm.precision == DGK_PREC_FP32BULK) {
+            dgk::KArgs<float> b = c->a32;
+            b.v.out = c->pibuf;
+            err = c->curved ? c->ct->entropy_prod(&b, c->stream) : c->kt->entropy_prod(&b, c->stream);
+        } else {
+            dgk::KArgs<double> b = c->a64;
+            b.v.out = c->pibuf;
+            err = c->curved ? c->ct->entropy_prod(&b, c->stream) : c->kt->entropy_prod(&b, c->stream);
+        }
+    }
+    if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("diagnostics: ") + cudaGetErrorString(err));
+    const long long nn = c->ne * c->NP;
+    const long long nb = (nn + 255) / 256;
+    k_diag_partial<<<(unsigned)nb, 256, 0, c->stream>>>(c->U, c->Tbuf, c->pibuf, c->ne, node_info(c), c->a64.ph,
+                                                        c->partial);
+    k_diag_final<<<1, 256, 0, c->stream>>>(c->partial, nb, dst, counter);
+    DGK_CUDA(cudaGetLastError());
+    return DGK_OK;
 }
 
 }  // namespace
@@ -1055,33 +1145,80 @@ int dgk_rk_step(dgk_ctx *c, double dt)
     return launch_step(c, c->timing);
 }
 
-int dgk_run(dgk_ctx *c, int nsteps, double dt)
+int dgk_run(dgk_ctx *c, int nsteps, double dt, int diag_every, double *diag_out)
 {
     int rc = ready(c);
     if (rc) return rc;
     if (nsteps < 0) return fail(DGK_ERR_ARG, "nsteps < 0");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(DGK_ERR_ARG, "dt must be positive");
+    if (diag_every < 0) return fail(DGK_ERR_ARG, "diag_every < 0");
     if ((rc = set_coef(c, dt))) return rc;
-    if (c->timing) {
-        for (int s = 0; s < nsteps; ++s)
-            if ((rc = launch_step(c, true))) return rc;
-        return DGK_OK;
+    const int nsamp = (diag_every > 0 && diag_out) ? nsteps / diag_every : 0;
+    if (nsamp > 0) {
+        if ((rc = diag_buffers(c))) return rc;
+        const size_t need = (size_t)nsamp * kNDiag;
+        if (need > c->samples_cap) {
+            if (c->diag_graph) cudaGraphExecDestroy(c->diag_graph);
+            c->diag_graph = nullptr;
+            if (c->samples) cudaFree(c->samples);
+            c->samples = nullptr;
+            c->samples_cap = 0;
+            DGK_CUDA(cudaMalloc(&c->samples, need * sizeof(double)));
+            c->samples_cap = need;
+        }
+        DGK_CUDA(cudaMemsetAsync(c->diag_counter, 0, sizeof(unsigned), c->stream));
     }
-    if (!c->graph && nsteps > 0) {
-        cudaGraph_t g;
-        DGK_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        rc = launch_step(c, false);
-        cudaError_t err = cudaStreamEndCapture(c->stream, &g);
-        if (rc) return rc;
-        if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(err));
-        err = cudaGraphInstantiate(&c->graph, g, 0);
-        cudaGraphDestroy(g);
-        if (err != cudaSuccess) {
-            c->graph = nullptr;
-            return fail(DGK_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(err));
+    if (c->timing) {
+        for (int s = 0; s < nsteps; ++s) {
+            if ((rc = launch_step(c, true))) return rc;
+            if (nsamp > 0 && (s + 1) % diag_every == 0 && (s + 1) / diag_every <= nsamp &&
+                (rc = enqueue_diag(c, c->samples, c->diag_counter)))
+                return rc;
+        }
+    } else {
+        if (!c->graph && nsteps > 0) {
+            cudaGraph_t g;
+            DGK_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            rc = launch_step(c, false);
+            cudaError_t err = cudaStreamEndCapture(c->stream, &g);
+            if (rc) return rc;
+            if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(err));
+            err = cudaGraphInstantiate(&c->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (err != cudaSuccess) {
+                c->graph = nullptr;
+                return fail(DGK_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(err));
+            }
+        }
+        if (nsamp > 0 && !c->diag_graph) {
+            cudaGraph_t g;
+            DGK_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            rc = enqueue_diag(c, c->samples, c->diag_counter);
+            cudaError_t err = cudaStreamEndCapture(c->stream, &g);
+            if (rc) return rc;
+            if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("diagnostics capture: ") + cudaGetErrorString(err));
+            err = cudaGraphInstantiate(&c->diag_graph, g, 0);
+            cudaGraphDestroy(g);
+            if (err != cudaSuccess) {
+                c->diag_graph = nullptr;
+                return fail(DGK_ERR_CUDA, std::string("diagnostics instantiate: ") + cudaGetErrorString(err));
+            }
+        }
+        for (int s = 0; s < nsteps; ++s) {
+            DGK_CUDA(cudaGraphLaunch(c->graph, c->stream));
+            if (nsamp > 0 && (s + 1) % diag_every == 0 && (s + 1) / diag_every <= nsamp)
+                DGK_CUDA(cudaGraphLaunch(c->diag_graph, c->stream));
         }
     }
-    for (int s = 0; s < nsteps; ++s) DGK_CUDA(cudaGraphLaunch(c->graph, c->stream));
+    if (nsamp > 0) {
+        DGK_CUDA(cudaMemcpyAsync(diag_out, c->samples, (size_t)nsamp * kNDiag * sizeof(double), cudaMemcpyDefault,
+                                 c->stream));
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, diag_out) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            DGK_CUDA(cudaStreamSynchronize(c->stream));
+        }
+    }
     return DGK_OK;
 }
 
@@ -1133,7 +1270,7 @@ int dgk_run_host(dgk_ctx *c, const double *const *in, double *const *out, int ni
                 DGK_CUDA(cudaMemcpyAsync(c->stage_in, in[i + 1], bytes, cudaMemcpyHostToDevice, c->s_in));
                 DGK_CUDA(cudaEventRecord(c->ev_in_ready, c->s_in));
             }
-            if ((r = dgk_run(c, nsteps, dt))) return r;
+            if ((r = dgk_run(c, nsteps, dt, 0, nullptr))) return r;
             // item i out: state -> staging once the previous item has left it, then to the host
             DGK_CUDA(cudaStreamWaitEvent(c->stream, c->ev_out_free, 0));
             DGK_CUDA(cudaMemcpyAsync(c->stage_out, c->U, bytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -1198,22 +1335,10 @@ int dgk_diagnostics(dgk_ctx *c, double *out)
     int rc = ready(c);
     if (rc) return rc;
     if (!out) return fail(DGK_ERR_ARG, "null output");
-    cudaError_t err = run_nodeT(c, 0);
-    if (err) return fail(DGK_ERR_CUDA, cudaGetErrorString(err));
-    const long long nn = c->ne * c->NP;
-    const unsigned nb = (unsigned)((nn + 255) / 256);
-    if (!c->partial) DGK_CUDA(cudaMalloc(&c->partial, (size_t)nb * 8 * sizeof(double)));
-    k_diag_partial<<<nb, 256, 0, c->stream>>>(c->U, c->Tbuf, c->ne, node_info(c), c->a64.ph, c->partial);
-    DGK_CUDA(cudaGetLastError());
-    std::vector<double> h((size_t)nb * 8);
-    DGK_CUDA(cudaMemcpyAsync(h.data(), c->partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if ((rc = diag_buffers(c))) return rc;
+    if ((rc = enqueue_diag(c, c->diagout, nullptr))) return rc;
+    DGK_CUDA(cudaMemcpyAsync(out, c->diagout, kNDiag * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     DGK_CUDA(cudaStreamSynchronize(c->stream));
-    for (int k = 0; k < DGK_NDIAG; ++k) out[k] = 0.0;
-    for (unsigned b = 0; b < nb; ++b) {
-        for (int k = 0; k < 7; ++k) out[k] += h[(size_t)b * 8 + k];
-        out[7] = std::fmax(out[7], h[(size_t)b * 8 + 7]);
-    }
-    out[6] = std::sqrt(out[6]);
     return DGK_OK;
 }
 

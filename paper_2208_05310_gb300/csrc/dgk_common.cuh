@@ -334,4 +334,35 @@ __device__ __forceinline__ void source_terms(const PhysR<R> &ph, R rho, const R 
     S[D + 2] = ph.alphabeta * (rho - c);
 }
 
+// Rate of entropy production at a node (Sec. 2.3; the relaxation model's rate after
+// Eq. navierstokeskorteweg_alpha, the original model's after Eq. energyfluxnsk), from the
+// scheme's lifted gradients du[i][k] = d u_k / d x_i, grad T and lap c:
+//   Pi = tau : grad u / T + kappa |grad T|^2 / T^2 + beta chi^2 / T,
+//   tau = mu (grad u + grad u^T - 2/3 div u I),  chi = gamma_K lap c + alpha (rho - c),
+// the last term for the relaxation models only (the dissipation of the stated stress
+// under the Stokes hypothesis; the Fourier flux kappa grad T paired with grad(1/T)).
+template <int D, typename R>
+__device__ __forceinline__ R entropy_production(const PhysR<R> &ph, R rho, R c, R T, const R du[D][D], const R *gT,
+                                                R lap)
+{
+    R divu = R(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) divu += du[k][k];
+    R diss = R(0), gT2 = R(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        gT2 += gT[i] * gT[i];
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+            diss += ph.mu * (du[i][k] + du[k][i] - (i == k ? R(2.0 / 3.0) * divu : R(0))) * du[i][k];
+    }
+    const R iT = R(1) / T;
+    R pi = diss * iT + ph.kap * gT2 * iT * iT;
+    if (ph.model != 0) {
+        const R chi = ph.gK * lap + ph.alpha * (rho - c);
+        pi += ph.beta * chi * chi * iT;
+    }
+    return pi;
+}
+
 }  // namespace dgk

@@ -525,7 +525,9 @@ __device__ __forceinline__ const R *face_source_c(int k, const R *sG, const R *s
     return sN + NV * NP;
 }
 
-template <int D, int N, typename R>
+// DIAG 1: the same liftings, then the rate of entropy production of each node into
+// a.v.out[e][n] (double) in place of the volume integral and the face data.
+template <int D, int N, typename R, int DIAG = 0>
 __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, unsigned char *smraw)
 {
     using S = Shape<D, N>;
@@ -784,6 +786,10 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
         pf = flux_pressure<R>(a.pr, rho, T, R(1) / (R(1) - R(kBvdw) * rho));
         source_terms<D, R>(a.pr, rho, u, c, g, S_);
     }
+    if constexpr (DIAG != 0) {
+        if (t.valid) a.v.out[t.e * NP + n] = to_f64<R>(entropy_production<D, R>(a.pr, rho, c, T, du, gT, lap));
+        return;
+    }
     __syncthreads();  // pass-2 buffers dead before the volume buffers reuse sX
 
     // ---- volume integral of the contravariant fluxes: acc_i = sum_dir sum_l Dhat_il (F.Ja^dir)_l
@@ -894,6 +900,16 @@ __global__ void __launch_bounds__(Shape<D, N>::NT, curved_min_blocks(Shape<D, N>
     extern __shared__ __align__(16) unsigned char smraw[];
     const Ctx<R> a{args.v, args.ph, args.pr, args.op};
     lift2volc_body<D, N, R>(a, blockIdx.x, smraw);
+}
+
+// rate of entropy production at the nodes (diagnostics; needs the pass-2 traces of the
+// current state, written by k_lift1c and its mortar kernel)
+template <int D, int N, typename R>
+__global__ void __launch_bounds__(Shape<D, N>::NT) k_entropy_prodc(KArgs<R> args)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const Ctx<R> a{args.v, args.ph, args.pr, args.op};
+    lift2volc_body<D, N, R, 1>(a, blockIdx.x, smraw);
 }
 
 // ------------------------------------------------------------------ mortars
@@ -1061,6 +1077,7 @@ struct CurvedTable {
     cudaError_t (*nodeT)(const void *args, int mode, cudaStream_t s);
     cudaError_t (*mortar_traces)(const void *args, int which, int nmort, cudaStream_t s);
     cudaError_t (*mortar_flux)(const void *args, int nmort, cudaStream_t s);
+    cudaError_t (*entropy_prod)(const void *args, cudaStream_t s);
 };
 
 template <int D, int N, typename R>
@@ -1086,7 +1103,15 @@ struct CurvedLauncher {
             return err;
         if ((err = cudaFuncSetAttribute(k_surf_rk<D, N, R, 0, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_surf)))
             return err;
+        if ((err = cudaFuncSetAttribute(k_entropy_prodc<D, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_lift2)))
+            return err;
         return cudaFuncSetAttribute(k_node_Tc<D, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_lift1);
+    }
+    static cudaError_t entropy_prod(const void *p, cudaStream_t s)
+    {
+        const KArgs<R> &a = *static_cast<const KArgs<R> *>(p);
+        k_entropy_prodc<D, N, R><<<blocks(a), S::NT, sm_lift2, s>>>(a);
+        return cudaGetLastError();
     }
     static cudaError_t lift1(const void *p, cudaStream_t s)
     {
@@ -1128,7 +1153,7 @@ struct CurvedLauncher {
     }
     static const CurvedTable *table()
     {
-        static const CurvedTable t = {prepare, lift1, lift2vol, surf, nodeT, mortar_traces, mortar_flux};
+        static const CurvedTable t = {prepare, lift1, lift2vol, surf, nodeT, mortar_traces, mortar_flux, entropy_prod};
         return &t;
     }
 };

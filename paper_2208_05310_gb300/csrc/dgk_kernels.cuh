@@ -703,7 +703,9 @@ struct K2Smem {
     static constexpr int per_elem = G + GT + X;
 };
 
-template <int D, int N, typename R, int EB = 0>
+// DIAG 1: the same liftings, then the rate of entropy production of each node into
+// a.v.out[e][n] (double) in place of the volume integral and the face data.
+template <int D, int N, typename R, int EB = 0, int DIAG = 0>
 __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, unsigned char *smraw)
 {
     using S = Shape<D, N, EB>;
@@ -872,6 +874,10 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
         pf = flux_pressure<R>(a.pr, rho, T, R(1) / (R(1) - R(kBvdw) * rho));
         source_terms<D, R>(a.pr, rho, u, c, g, S_);
     }
+    if constexpr (DIAG != 0) {
+        if (t.valid) a.v.out[t.e * NP + n] = to_f64<R>(entropy_production<D, R>(a.pr, rho, c, T, du, gT, lap));
+        return;
+    }
     __syncthreads();  // sT, sTs, sDs, sLp are dead before the volume buffers reuse sX
 
     // ---- volume integral, direction by direction: acc_i += (2/h) sum_l Dhat_il F_l
@@ -980,6 +986,16 @@ __global__ void __launch_bounds__(Shape<D, N, EB>::NT, min_blocks(Shape<D, N, EB
     extern __shared__ __align__(16) unsigned char smraw[];
     const Ctx<R> a{args.v, args.ph, args.pr, args.op};
     lift2vol_body<D, N, R, EB>(a, blockIdx.x, smraw);
+}
+
+// rate of entropy production at the nodes (diagnostics; needs the pass-2 traces of the
+// current state, written by k_lift1)
+template <int D, int N, typename R, int EB = 0>
+__global__ void __launch_bounds__(Shape<D, N, EB>::NT) k_entropy_prod(KArgs<R> args)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const Ctx<R> a{args.v, args.ph, args.pr, args.op};
+    lift2vol_body<D, N, R, EB, 1>(a, blockIdx.x, smraw);
 }
 
 // ------------------------------------------------------------------ kernel 3

@@ -14,6 +14,7 @@ struct KernelTable {
     cudaError_t (*surf)(const void *args, int mode, int stage, cudaStream_t s);
     cudaError_t (*traces)(const void *args, cudaStream_t s);
     cudaError_t (*nodeT)(const void *args, int mode, cudaStream_t s);
+    cudaError_t (*entropy_prod)(const void *args, cudaStream_t s);  // rate of entropy production into out
     int elems_per_block;
     int threads_per_block;
     size_t smem_lift1, smem_lift2vol, smem_surf;
@@ -38,7 +39,15 @@ struct Launcher {
         if ((err = cudaFuncSetAttribute(k_surf_rk<D, N, R, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_surf)))
             return err;
         if ((err = cudaFuncSetAttribute(k_traces<D, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_traces))) return err;
+        if ((err = cudaFuncSetAttribute(k_entropy_prod<D, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_lift2)))
+            return err;
         return cudaFuncSetAttribute(k_node_T<D, N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_lift1);
+    }
+    static cudaError_t entropy_prod(const void *p, cudaStream_t s)
+    {
+        const KArgs<R> &a = *static_cast<const KArgs<R> *>(p);
+        k_entropy_prod<D, N, R><<<blocks(a), S::NT, sm_lift2, s>>>(a);
+        return cudaGetLastError();
     }
     static cudaError_t lift1(const void *p, cudaStream_t s)
     {
@@ -73,7 +82,8 @@ struct Launcher {
     }
     static const KernelTable *table()
     {
-        static const KernelTable t = {prepare, lift1, lift2vol, surf, traces, nodeT, S::EPB, S::NT, sm_lift1, sm_lift2, sm_surf};
+        static const KernelTable t = {prepare, lift1,  lift2vol, surf,     traces,   nodeT, entropy_prod,
+                                      S::EPB,  S::NT, sm_lift1, sm_lift2, sm_surf};
         return &t;
     }
 };

@@ -18,8 +18,9 @@ LIB_PATH = os.path.join(PKG, "libdgk.so")
 
 DGK_PREC = {"fp64": 0, "fp32bulk": 1}
 DGK_FLUX = {"rusanov": 0, "hllc": 1}
-NDIAG = 8
-DIAG_NAMES = ("mass", "mom_x", "mom_y", "mom_z", "energy", "neg_entropy", "rho_minus_c_l2", "max_u")
+NDIAG = 9
+DIAG_NAMES = ("mass", "mom_x", "mom_y", "mom_z", "energy", "neg_entropy", "rho_minus_c_l2", "max_u",
+              "entropy_production")
 
 _lib = None
 
@@ -63,7 +64,7 @@ EXPORTS = ("dgk_create", "dgk_destroy", "dgk_set_params", "dgk_mesh_box", "dgk_m
            "dgk_sigma_vl", "dgk_interface_width", "dgk_status_string", "dgk_last_error", "dgk_check_conversions",
            "dgk_rhs_static", "dgk_node_temperature_pressure", "dgk_batch_create", "dgk_batch_destroy",
            "dgk_batch_problem", "dgk_batch_set_dt", "dgk_batch_run", "dgk_batch_autotune", "dgk_batch_status",
-           "dgk_batch_set_config", "dgk_batch_set_barrier_limit")
+           "dgk_batch_set_config", "dgk_batch_set_barrier_limit", "dgk_fma_peak")
 
 
 def lib():
@@ -90,7 +91,7 @@ def lib():
         "dgk_download_state": (i, [vp, vp, sz, i]),
         "dgk_rhs": (i, [vp, vp, sz, i]),
         "dgk_rk_step": (i, [vp, d]),
-        "dgk_run": (i, [vp, i, d]),
+        "dgk_run": (i, [vp, i, d, i, vp]),
         "dgk_run_host": (i, [vp, C.POINTER(vp), C.POINTER(vp), i, sz, i, d]),
         "dgk_max_dt": (i, [vp, d, d, dp]),
         "dgk_diagnostics": (i, [vp, dp]),
@@ -111,6 +112,7 @@ def lib():
         "dgk_sigma_vl": (i, [d, d, d, dp]),
         "dgk_interface_width": (i, [d, d, d, dp]),
         "dgk_check_conversions": (i, [vp, sz, i, C.POINTER(C.c_ulonglong)]),
+        "dgk_fma_peak": (i, [i, i, dp]),
         "dgk_rhs_static": (i, [C.POINTER(DgkParams), C.POINTER(DgkBoxMesh), vp, vp, sz, vp, C.POINTER(C.c_uint)]),
         "dgk_status_string": (C.c_char_p, [i]),
         "dgk_last_error": (C.c_char_p, []),
@@ -169,6 +171,13 @@ def check_conversions(x):
     bad = C.c_ulonglong()
     _check(lib().dgk_check_conversions(x.ctypes.data, x.size, 0, C.byref(bad)), "dgk_check_conversions")
     return bad.value
+
+
+def fma_peak(device=0, precision="fp64"):
+    """Measured FMA throughput of the device in flops/s (dgk_fma_peak)."""
+    v = C.c_double()
+    _check(lib().dgk_fma_peak(int(device), DGK_PREC[precision], C.byref(v)), "dgk_fma_peak")
+    return v.value
 
 
 def make_params(model=1, rk=4, precision="fp64", gammaK=1e-4, mu=0.01, kappa=1.0 / 150.0, cv=5.0, alpha=100.0,
@@ -319,8 +328,21 @@ class Context:
     def rk_step(self, dt):
         _check(lib().dgk_rk_step(self._h, float(dt)), "dgk_rk_step")
 
-    def run(self, nsteps, dt):
-        _check(lib().dgk_run(self._h, int(nsteps), float(dt)), "dgk_run")
+    def run(self, nsteps, dt, diag_every=0, diag_out=None):
+        """nsteps steps of dt (dgk_run).  With diag_every > 0: returns the diagnostics taken
+        on the device after every diag_every-th step, a (nsteps // diag_every, NDIAG)
+        array -- into diag_out if given (a float64 numpy array or CUDA tensor of that
+        size), else into a new numpy array."""
+        if not diag_every:
+            _check(lib().dgk_run(self._h, int(nsteps), float(dt), 0, None), "dgk_run")
+            return None
+        nsamp = int(nsteps) // int(diag_every)
+        out = np.zeros((nsamp, NDIAG)) if diag_out is None else diag_out
+        ptr, n, _ = _ptr(out)
+        if n != nsamp * NDIAG:
+            raise DgkError(f"diag_out must hold {nsamp * NDIAG} doubles")
+        _check(lib().dgk_run(self._h, int(nsteps), float(dt), int(diag_every), ptr), "dgk_run")
+        return out
 
     def run_host(self, inputs, outputs, nsteps, dt):
         """Independent states through host memory, pipelined (dgk_run_host): each of

@@ -160,7 +160,13 @@ def test_batch_full_ensemble_sampled():
     b.run(20)
     assert all(rc == 0 for rc in b.status())
     m1 = [q.diagnostics()["mass"] for q in b.problems]
-    assert np.max(np.abs(np.array(m1) / np.array(m0) - 1.0)) < 1e-6
+    # the FP32-bulk U_t is formed in float: an element's volume and surface mass terms
+    # cancel only to float rounding (~6e-8 of the largest term), so each step moves the
+    # mass by ~dt * 6e-8 * sum |flux terms|, a few 1e-13 per step here (measured 3.5e-12
+    # after 20 steps); the FP64 form holds it to ~1e-16 per step
+    drift = np.max(np.abs(np.array(m1) / np.array(m0) - 1.0))
+    print(f"ensemble mass drift over 20 steps: {drift:.2e}")
+    assert drift < 1e-11
     sizes = [ms["n"][0] * ms["N"] for ms in meshes]
     for k in sorted({0, 255, int(np.argmax(sizes)), int(np.argmin(sizes))}):
         ref = _single(meshes[k], prims[k], dts[k], 20)
