@@ -164,6 +164,27 @@ def ncu_traffic(kernel, workload):
         return None
 
 
+def ncu_flops(kernel, workload):
+    """Executed FP64 flops per node (2 per DFMA + DADD + DMUL, from the ncu counters of
+    the committed summary) and the summary's DRAM bytes per launch, while the summary
+    matches the current kernel sources; else (None, None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    if not os.path.exists(path):
+        return None, None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha1") != kernel_sources_sha():
+        return None, None
+    try:
+        return float(vals["fp64_flops_per_node"]), float(vals["dram_bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None, None
+
+
 def replica_max(v, dist=None, device="cuda"):
     """Max of a per-rank time over all ranks (replicas run independent problems; the
     slowest rank sets the whole job's time).  dist: torch.distributed or None."""
@@ -471,6 +492,25 @@ def run_ours(args, wl, rank, world, local_rank):
         ms64 = max_over_ranks(e0.elapsed_time(e1))
         c64.status()
         fp64 = dict(value=dof * stages * k64 * world / (ms64 / 1e3), unit=UNIT, steps=k64, ms_per_step=ms64 / k64)
+        # the FP64 form against its arithmetic roof: the dominant kernel's executed FP64 flops
+        # per launch (ncu counters of the committed summary) over its CUDA-event launch
+        # time, against the FP64 FMA throughput measured now on this GPU
+        c64.set_timing(True)
+        c64.run(1, dt)
+        k64t = {}
+        for k, name in enumerate(("k_lift1c", "k_lift2volc", "k_surf_rk") if curved else ("k_lift1", "k_lift2vol", "k_surf_rk")):
+            k64t[name] = c64.kernel_time(k)
+        c64.set_timing(False)
+        c64.status()
+        dom64 = max(k64t, key=lambda k: k64t[k][0])
+        avg64 = k64t[dom64][0] / max(k64t[dom64][1], 1)
+        fl_node, traffic64 = (None, None) if curved else ncu_flops(dom64, args.workload + "_fp64")
+        peak64 = dgk.fma_peak(local_rank, "fp64") / 1e12
+        ach64 = fl_node * dof / (avg64 / 1e3) / 1e12 if fl_node else None
+        fp64["roofline"] = dict(bound="fp64_alu", kernel=dom64, achieved=ach64, peak=peak64, unit="TFLOP/s",
+                                frac=(ach64 / peak64) if ach64 else None, peak_kind="measured (dgk_fma_peak, this run)",
+                                flops_per_node=fl_node, avg_launch_ms=avg64, traffic=traffic64,
+                                share={k: v[0] / sum(t for t, _ in k64t.values()) for k, v in k64t.items()})
         # the headline form against the FP64 form from the same initial state after the same
         # steps: relative L2 difference per conserved variable
         k_acc = max(args.accuracy_steps, 1 + k64)

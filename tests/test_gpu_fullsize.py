@@ -15,14 +15,15 @@ over the sampled element's nodes, the difference of the increments dt*U_t (dt th
 oracle's stable step for the sub-box) relative to the element's state, with the floors
 of rel_l2.  FP64: 1e-12, the bar for conserved variables; FP32-bulk: the per-variable
 bounds of one step of the FP32-bulk parity tests.  (At rest, U_t is round-off in the
-quiescent liquid and vapour and in the z-momentum away from the walls, and at the
-interface it comes from the jump term lambda (U+ - U-) of the Rusanov flux, the
-difference of two traces that agree to about 1e-5 of their size, which magnifies the
-rounding of either trace about 1e5-fold: measured up to 7e-11 (FP64) and 4.5e-4
-(FP32-bulk) relative in the interface samples' rho.)  The same samples on the state
-with a smooth velocity field added (periodic with the box, 0.02..0.05 in magnitude),
-where U_t is led by the transport terms, assert the right-hand side's own relative
-error per variable too: 1e-12 (FP64) and 2e-4 (FP32-bulk; 4e-4 on curved elements).
+quiescent liquid and vapour and in the z-momentum away from the walls.  At the
+interface it is led by the jump term lambda (U+ - U-) of the Rusanov flux (lambda ~ 13,
+the steep profile leaves jumps between elements), the difference of two interpolated
+traces, whose rounding it magnifies: measured 2e-12 (box), 7e-11 (curved) in FP64 and
+4.5e-4 in FP32-bulk relative in the interface samples' rho, with or without flow.)
+The same samples on the state with a smooth velocity field added (periodic with the
+box, 0.02..0.05 in magnitude) assert, away from the interface where U_t is then led by
+transport, the right-hand side's own relative error per variable too: 1e-12 (FP64) and
+2e-4 (FP32-bulk; 4e-4 on curved elements).
 
 The curved variant (the bench's `--mesh curved`: degree-2 maps, walls bent) gives the
 oracle's sub-box the full mesh's element maps of its elements; the sub-box's own seams
@@ -38,6 +39,7 @@ pytestmark = pytest.mark.gpu
 # interface (bridge radius 0.5 about x = y = 1) at mid-height and at both walls, liquid
 # core, vapour, vapour next to the bottom wall
 SAMPLES = [(47, 32, 16), (16, 32, 0), (32, 47, 31), (31, 32, 8), (5, 5, 16), (48, 48, 1)]
+INTERFACE = SAMPLES[:3]
 
 
 def _sub_box(orc, wl, ix, iy, iz, W=9, geo=None):
@@ -116,10 +118,10 @@ def test_fullsize_sampled_rhs(orc, precision, mesh, state):
         if mesh == "curved" and precision != "fp64":
             tol = 2.0 * tol
         assert np.all(err < tol), ((ix, iy, iz), err, tol)
-        if state == "moving":
-            # U_t led by transport: its relative error per variable at the right-hand-side
-            # tolerances (variables whose oracle U_t is at round-off level relative to the
-            # largest are left to the increment check above)
+        if state == "moving" and (ix, iy, iz) not in INTERFACE:
+            # away from the interface U_t is led by transport: its relative error per
+            # variable at the right-hand-side tolerances (variables whose oracle U_t is at
+            # round-off level relative to the largest are left to the increment check)
             rn = np.sqrt((ref ** 2).sum(axis=1))
             live = rn > 1e-9 * rn.max()
             rtol = 1e-12 if precision == "fp64" else (2e-4 if mesh == "box" else 4e-4)
