@@ -316,12 +316,14 @@ int dgk_batch_run(dgk_batch *b, int nsteps);
    blocks per tile k_N for each degree N -- and keeps the fastest.  Every candidate runs three steps from the current states,
    which are restored afterwards; the status words are cleared after tuning (tuning
    refuses to start, returning the error, if a problem already reports one).
-   out (nullable, 7 ints) = {form, blocks_per_sm, k_3, k_4, k_5, microseconds per step of
-   the best persistent candidate, microseconds per step of the grouped form}. */
+   out (nullable, 7 ints) = {form (0, 1 or 2 as for dgk_batch_set_config), blocks_per_sm,
+   k_3, k_4, k_5, microseconds per step of the best persistent candidate (either
+   allocation), microseconds per step of the grouped form}. */
 int dgk_batch_autotune(dgk_batch *b, int *out);
-/* Set the form and decomposition directly: cfg = {form (0 persistent, 1 grouped),
-   blocks_per_sm (1..the occupancy limit of the persistent kernel), k_3, k_4, k_5 (>= 1;
-   element blocks per tile of the persistent form; the grouped form ignores them and
+/* Set the form and decomposition directly: cfg = {form (0 persistent, 1 grouped,
+   2 persistent compiled for 2 blocks per SM: 128 registers instead of 80 with spills),
+   blocks_per_sm (1..the occupancy limit of that persistent kernel), k_3, k_4, k_5 (>= 1;
+   element blocks per tile of the persistent forms; the grouped form ignores them and
    blocks_per_sm)}.
    Results do not depend on it: every element's arithmetic is the same. */
 int dgk_batch_set_config(dgk_batch *b, const int *cfg);

@@ -1470,8 +1470,9 @@ struct dgk_batch {
     int *d_probN = nullptr, *d_tiles = nullptr;
     unsigned *d_bar = nullptr;  // [0..1] barrier, [2] status
     void *d_args = nullptr;     // device copy of the kernel parameters
-    int form = 0;               // 0 persistent launch per stage, 1 grouped launches per phase
-    int sms = 0, max_bps = 1, bps = 1;
+    int form = 0;               // 0 persistent launch per stage (80-register allocation), 1 grouped
+                                // launches per phase, 2 persistent with the 128-register allocation
+    int sms = 0, max_bps = 1, max_bps_wide = 1, bps = 1;
     int k[3] = {1, 1, 1};
     size_t tiles_cap = 0;
     cudaGraphExec_t graph = nullptr;
@@ -1539,7 +1540,7 @@ int batch_launch_step(dgk_batch *b)
     cudaError_t e0 = dgk::batch_bind_args(b->d_args, b->stream);
     if (e0 != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("batch parameters: ") + cudaGetErrorString(e0));
     for (int s = 0; s < ns; ++s) {
-        cudaError_t err = b->form == 0 ? dgk::batch_stage_launch(b->sms * b->bps, s, b->stream)
+        cudaError_t err = b->form != 1 ? dgk::batch_stage_launch(b->sms * b->bps, s, b->stream, b->form == 2)
                                        : dgk::batch_phase_launches(b->L.ntiles, s, b->stream);
         if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("batched stage launch: ") + cudaGetErrorString(err));
     }
@@ -1585,8 +1586,8 @@ int dgk_batch_create(dgk_batch **out, int device, void *cuda_stream, const dgk_p
     }
     std::vector<dgk::KView<float>> views;
     for (dgk_ctx *c : b->probs) views.push_back(c->a32.v);
-    int maxb = 0;
-    if (!rc && dgk::batch_prepare(&maxb) != cudaSuccess) rc = fail(DGK_ERR_CUDA, "batched kernel set-up failed");
+    int maxb = 0, maxw = 0;
+    if (!rc && dgk::batch_prepare(&maxb, &maxw) != cudaSuccess) rc = fail(DGK_ERR_CUDA, "batched kernel set-up failed");
     if (!rc && maxb < 1) rc = fail(DGK_ERR_UNSUPPORTED, "batched kernel does not fit on an SM");
     if (!rc && (cudaMalloc(&b->d_views, views.size() * sizeof(views[0])) != cudaSuccess ||
                 cudaMalloc(&b->d_probN, b->probN.size() * sizeof(int)) != cudaSuccess ||
@@ -1601,6 +1602,7 @@ int dgk_batch_create(dgk_batch **out, int device, void *cuda_stream, const dgk_p
         cudaGetDeviceProperties(&prop, device);
         b->sms = prop.multiProcessorCount;
         b->max_bps = maxb;
+        b->max_bps_wide = maxw > 0 ? maxw : 1;
         b->bps = maxb;
         b->L.views = b->d_views;
         b->L.prob_N = b->d_probN;
@@ -1690,8 +1692,9 @@ int dgk_batch_run(dgk_batch *b, int nsteps)
 int dgk_batch_set_config(dgk_batch *b, const int *cfg)
 {
     if (!b || !cfg) return fail(DGK_ERR_ARG, "null argument");
-    if (cfg[0] != 0 && cfg[0] != 1) return fail(DGK_ERR_ARG, "form must be 0 (persistent) or 1 (grouped)");
-    if (cfg[1] < 1 || cfg[1] > b->max_bps) return fail(DGK_ERR_ARG, "blocks per SM out of range");
+    if (cfg[0] < 0 || cfg[0] > 2)
+        return fail(DGK_ERR_ARG, "form must be 0 (persistent), 1 (grouped) or 2 (persistent, wide allocation)");
+    if (cfg[1] < 1 || cfg[1] > (cfg[0] == 2 ? b->max_bps_wide : b->max_bps)) return fail(DGK_ERR_ARG, "blocks per SM out of range");
     for (int i = 2; i < 5; ++i)
         if (cfg[i] < 1) return fail(DGK_ERR_ARG, "element blocks per tile must be positive");
     DGK_CUDA(cudaStreamSynchronize(b->stream));
@@ -1787,6 +1790,18 @@ int dgk_batch_autotune(dgk_batch *b, int *out)
         if (!rc && ms < best) { best = ms; best_bps = bps; best_form = 0; }
         if (!rc && ms < best_form_ms[0]) best_form_ms[0] = ms;
     }
+    // the persistent form with the 128-register allocation
+    if (!rc) {
+        b->form = 2;
+        rc = batch_build_tiles(b);
+        for (int bps = 1; bps <= b->max_bps_wide && !rc; ++bps) {
+            b->bps = bps;
+            float ms = 0;
+            rc = time_config(ms);
+            if (!rc && ms < best) { best = ms; best_bps = bps; best_form = 2; }
+            if (!rc && ms < best_form_ms[0]) best_form_ms[0] = ms;
+        }
+    }
     b->bps = best_bps;
     if (!rc) {
         b->form = 1;
@@ -1797,8 +1812,8 @@ int dgk_batch_autotune(dgk_batch *b, int *out)
     }
     b->form = best_form;
     if (!rc) rc = batch_build_tiles(b);
-    // element blocks per tile: the persistent form only
-    for (int n = 0; n < 3 && !rc && b->form == 0; ++n) {
+    // element blocks per tile: the persistent forms only
+    for (int n = 0; n < 3 && !rc && b->form != 1; ++n) {
         bool used = false;
         for (int q : b->probN) used |= (q == n + 3);
         if (!used) continue;

@@ -18,7 +18,8 @@
 // launches per stage, no grid barrier): one kernel holds the bodies of all three phases
 // and degrees, and its register allocation is that of the heaviest of the nine, which
 // caps the persistent form's occupancy; the grouped kernels each carry one phase.  The
-// autotuner times both forms.
+// autotuner times the grouped form and the persistent kernel compiled for three and for
+// two resident blocks per SM.
 #include <cuda_runtime.h>
 
 #include "dgk_launch.cuh"
@@ -82,8 +83,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, un
 // functions below read physics constants and operators as constant-bank operands.
 __constant__ BatchArgs<float> c_batch;
 
-// One element block of one problem for one phase, in a function of its own (not
-// inlined), so that the nine (degree, phase) bodies get separate register allocations.
 // One element block of one problem for one phase.
 template <int N, int PHASE>
 __device__ __forceinline__ void phase_block(const KView<float> &v, long long blk, unsigned char *sm, int stage)
@@ -133,11 +132,12 @@ __device__ __forceinline__ void run_phase(int stage, KView<float> *sv, int *sh)
     run_tiles<5, PHASE>(tile, b.ntiles, stage, sv, sh);
 }
 
-#ifndef DGK_BATCH_MIN_BLOCKS
-#define DGK_BATCH_MIN_BLOCKS 3  // resident blocks per SM the register allocation targets
-#endif
-
-__global__ void __launch_bounds__(kBatchThreads, DGK_BATCH_MIN_BLOCKS) k_batch_stage(int stage)
+// MB: resident blocks per SM the register allocation targets.  One kernel holds the
+// bodies of all three phases and degrees, so its allocation is that of the heaviest of
+// the nine: 80 registers with spills at MB = 3, 128 registers with few spills at MB = 2
+// (the autotuner times both).
+template <int MB>
+__global__ void __launch_bounds__(kBatchThreads, MB) k_batch_stage(int stage)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     KView<float> *sv = reinterpret_cast<KView<float> *>(smraw);
@@ -217,11 +217,17 @@ namespace dgk {
 
 size_t batch_smem() { return batch_smem_bytes<float>(); }
 
-cudaError_t batch_prepare(int *max_blocks_per_sm)
+cudaError_t batch_prepare(int *max_blocks_per_sm, int *max_blocks_per_sm_wide)
 {
-    cudaError_t err = cudaFuncSetAttribute(k_batch_stage, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t err = cudaFuncSetAttribute(k_batch_stage<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)batch_smem_bytes<float>());
     if (err) return err;
+    if ((err = cudaFuncSetAttribute(k_batch_stage<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)batch_smem_bytes<float>())))
+        return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm_wide, k_batch_stage<2>, kBatchThreads,
+                                                             batch_smem_bytes<float>())))
+        return err;
     if ((err = cudaFuncSetAttribute(k_batch_phase<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)phase_smem_bytes<float, 0>())))
         return err;
@@ -231,7 +237,7 @@ cudaError_t batch_prepare(int *max_blocks_per_sm)
     if ((err = cudaFuncSetAttribute(k_batch_phase<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)phase_smem_bytes<float, 2>())))
         return err;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_batch_stage, kBatchThreads,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, k_batch_stage<3>, kBatchThreads,
                                                          batch_smem_bytes<float>());
 }
 
@@ -264,7 +270,8 @@ cudaError_t batch_bind_args(const void *dev, cudaStream_t s)
     return cudaMemcpyToSymbolAsync(c_batch, dev, sizeof(BatchArgs<float>), 0, cudaMemcpyDeviceToDevice, s);
 }
 
-cudaError_t batch_stage_launch(int grid, int stage, cudaStream_t s)
+// wide: the 128-register allocation (k_batch_stage<2>)
+cudaError_t batch_stage_launch(int grid, int stage, cudaStream_t s, bool wide)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -276,7 +283,7 @@ cudaError_t batch_stage_launch(int grid, int stage, cudaStream_t s)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch_stage, stage);
+    return wide ? cudaLaunchKernelEx(&cfg, k_batch_stage<2>, stage) : cudaLaunchKernelEx(&cfg, k_batch_stage<3>, stage);
 }
 
 cudaError_t batch_phase_launches(int ntiles, int stage, cudaStream_t s)

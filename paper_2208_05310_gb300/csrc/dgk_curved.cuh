@@ -1051,19 +1051,25 @@ __global__ void __launch_bounds__(256) k_mortar_flux(KArgs<R> args)
         for (int k = 0; k < NV; ++k) sF[(p * NV + k) * NFP + fq] = sg * Fs[k];
     }
     __syncthreads();
+    // the projection accumulates in double: its weights and the small sides' fluxes are
+    // bulk-type values whose products are exact in double, so the big side's flux is the
+    // projection of the small sides' fluxes to one rounding.  (With model 2 the momentum
+    // flux carries p + alpha/2 rho^2 ~ 1e2 |J a|; summed in float over the 2^(D-1) NFP
+    // terms, its rounding broke the mortar's conservation by ~1e-5 |J a| per face and step.)
     for (int q = threadIdx.x; q < NV * NFP; q += blockDim.x) {
         const int k = q / NFP, ib = q % NFP, i = ib % P, j = ib / P;
-        R acc = R(0);
+        double acc = 0.0;
         for (int p = 0; p < NSUB; ++p) {
             const int *sb = mt + 4 + 4 * p;
             const int h0 = p & 1, h1 = (p >> 1) & 1;
             for (int fq = 0; fq < NFP; ++fq) {
                 const int qq = map_fp<P>(sb[2], fq), u = qq % P, w = qq / P;
-                const R wt = D == 2 ? op.Pm[h0][i * P + u] : op.Pm[h0][i * P + u] * op.Pm[h1][j * P + w];
-                acc += wt * sF[(p * NV + k) * NFP + fq];
+                const double wt = D == 2 ? to_f64<R>(op.Pm[h0][i * P + u])
+                                         : to_f64<R>(op.Pm[h0][i * P + u]) * to_f64<R>(op.Pm[h1][j * P + w]);
+                acc += wt * to_f64<R>(sF[(p * NV + k) * NFP + fq]);
             }
         }
-        v.fd[(NV + k) * st + (B * NF + fB) * NFP + ib] = acc;
+        v.fd[(NV + k) * st + (B * NF + fB) * NFP + ib] = to_bulk<R>(acc);
     }
 }
 

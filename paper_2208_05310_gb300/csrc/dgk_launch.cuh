@@ -102,10 +102,10 @@ struct BatchLaunch {
 };
 size_t batch_smem();
 size_t batch_args_bytes();
-cudaError_t batch_prepare(int *max_blocks_per_sm);
+cudaError_t batch_prepare(int *max_blocks_per_sm, int *max_blocks_per_sm_wide);
 cudaError_t batch_upload_args(const BatchLaunch &L, void *dev);
 cudaError_t batch_bind_args(const void *dev, cudaStream_t s);
-cudaError_t batch_stage_launch(int grid, int stage, cudaStream_t s);
+cudaError_t batch_stage_launch(int grid, int stage, cudaStream_t s, bool wide);
 cudaError_t batch_phase_launches(int ntiles, int stage, cudaStream_t s);
 
 }  // namespace dgk

@@ -457,12 +457,13 @@ class Batch:
         """Time the persistent and grouped forms and the tile lengths; keep the fastest."""
         out = (C.c_int * 7)()
         _check(lib().dgk_batch_autotune(self._h, out), "dgk_batch_autotune")
-        return dict(form=("persistent", "grouped")[out[0]], blocks_per_sm=out[1], k3=out[2], k4=out[3], k5=out[4],
+        return dict(form=("persistent", "grouped", "persistent-wide")[out[0]], blocks_per_sm=out[1], k3=out[2], k4=out[3], k5=out[4],
                     persistent_ms=out[5] / 1e3, grouped_ms=out[6] / 1e3)
 
     def set_config(self, form, blocks_per_sm, k3, k4, k5):
-        """form: "persistent" or "grouped"."""
-        cfg = (C.c_int * 5)(("persistent", "grouped").index(form), blocks_per_sm, k3, k4, k5)
+        """form: "persistent", "grouped" or "persistent-wide" (the persistent kernel compiled
+        for two blocks per SM: 128 registers)."""
+        cfg = (C.c_int * 5)(("persistent", "grouped", "persistent-wide").index(form), blocks_per_sm, k3, k4, k5)
         _check(lib().dgk_batch_set_config(self._h, cfg), "dgk_batch_set_config")
 
     def set_barrier_limit(self, cycles):

@@ -226,6 +226,7 @@ def test_curved_fp32_bulk_against_oracle(orc, name):
     g.run(10, dt)
     g.status()
     e_st = rel_l2(g.download_state(), o.run(Uo, 10, dt, rk=4))
+    print(f"{name}: FP32-bulk after 10 steps {np.array2string(e_st, precision=2)}")
     tol = CURVED32 * tol32_step(ms["dim"])
     if ms["geometry"].get("refine") and ps.get("model", 1) == 2:
         tol[ms["dim"] + 1] *= MORTAR_M2_ENERGY
