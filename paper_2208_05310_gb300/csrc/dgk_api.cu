@@ -413,7 +413,7 @@ void fill_args(dgk_ctx *c, dgk::KArgs<R> &a)
 // constants in the bulk type, derived once on the host
 template <typename R>
 void fill_bulk(dgk::KArgs<R> &a, const dgk::Geom &g, const dgk::Phys &ph, const dgk::Walls &w, const dgk::Ops &o,
-               int flux)
+               int flux, int P)
 {
     for (int i = 0; i < dgk::kMaxP * dgk::kMaxP; ++i) {
         a.op.Dh[i] = (R)o.Dhat[i];
@@ -430,6 +430,7 @@ void fill_bulk(dgk::KArgs<R> &a, const dgk::Geom &g, const dgk::Phys &ph, const 
         a.op.lm[i] = (R)o.lm[i];
     }
     for (int d = 0; d < 3; ++d) a.v.gr.inv2h[d] = (R)g.inv2h[d];
+    dgk::fill_pairs(a.op, P);
     dgk::PhysR<R> &p = a.pr;
     p.model = ph.model;
     p.gK = (R)ph.gK;
@@ -515,8 +516,8 @@ int build_consts(dgk_ctx *c)
     }
     c->a64.v.g = c->a32.v.g = g;
     c->a64.ph = c->a32.ph = ph;
-    fill_bulk(c->a64, g, ph, w, o, c->prm.flux);
-    fill_bulk(c->a32, g, ph, w, o, c->prm.flux);
+    fill_bulk(c->a64, g, ph, w, o, c->prm.flux, c->P);
+    fill_bulk(c->a32, g, ph, w, o, c->prm.flux, c->P);
     return DGK_OK;
 }
 
@@ -1620,6 +1621,7 @@ int dgk_batch_create(dgk_batch **out, int device, void *cuda_stream, const dgk_p
                 o.lp[i] = (float)op.lp[i];
                 o.lm[i] = (float)op.lm[i];
             }
+            dgk::fill_pairs(o, n + 1);
         }
         b->L.bar = b->d_bar;
         b->L.status = b->d_bar + 2;

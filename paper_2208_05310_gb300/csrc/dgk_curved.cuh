@@ -842,13 +842,9 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
 #pragma unroll
             for (int k = 0; k < NQ; ++k) {
                 const R *src = face_source_c<D, N, R>(k, sG, sGT, sN);
-                R am = R(0), ap = R(0);
-#pragma unroll
-                for (int l = 0; l < P; ++l) {
-                    const R x = src[base + l * stride];
-                    am += a.op.lm[l] * x;
-                    ap += a.op.lp[l] * x;
-                }
+                R x[P], am, ap;
+                load_line<P, R>(src, base, stride, x);
+                trace_pair<P, R>(a.op, x, am, ap);
                 sR[((2 * dir) * NQ + k) * NFP + line] = am;
                 sR[((2 * dir + 1) * NQ + k) * NFP + line] = ap;
             }

@@ -55,13 +55,35 @@ __host__ __device__ constexpr int min_blocks(int threads_per_block, int threads_
 // 1D operators in the bulk type (see Ops).
 template <typename R>
 struct OpsR {
+    // Row pairs of Dhat for the packed float contractions: Dh2[2 (p P + l) + h] =
+    // Dhat_{2p+h, l} (rows 2p and 2p+1 side by side); traces side by side:
+    // lmp[2 l] = l_l(-1), lmp[2 l + 1] = l_l(+1).  Filled by fill_pairs() from Dh, lm, lp.
+    alignas(8) R Dh2[kMaxP * kMaxP];
+    alignas(8) R lmp[2 * kMaxP];
     R Dh[kMaxP * kMaxP];
     R Dm[kMaxP * kMaxP];  // D_ij = l_j'(xi_i) (strong form, curved elements)
-    R Lp[kMaxP], Lm[kMaxP], lp[kMaxP], lm[kMaxP];
+    alignas(8) R Lp[kMaxP];
+    alignas(8) R Lm[kMaxP];
+    R lp[kMaxP], lm[kMaxP];
     // mortars of half-size faces h = 0, 1 (eta = (xi + 2h - 1)/2): Im[h][j*P+i] = l_i(eta_h(xi_j)),
     // Pm[h][i*P+j] = w_j/(2 w_i) l_i(eta_h(xi_j))
     R Im[2][kMaxP * kMaxP], Pm[2][kMaxP * kMaxP];
 };
+
+// The packed layouts of OpsR (Dh2, lmp) from its Dh, lm, lp, for P nodes per line.
+template <typename R>
+__host__ void fill_pairs(OpsR<R> &o, int P)
+{
+    for (int p = 0; 2 * p + 1 < P; ++p)
+        for (int l = 0; l < P; ++l) {
+            o.Dh2[2 * (p * P + l)] = o.Dh[(2 * p) * P + l];
+            o.Dh2[2 * (p * P + l) + 1] = o.Dh[(2 * p + 1) * P + l];
+        }
+    for (int l = 0; l < P; ++l) {
+        o.lmp[2 * l] = o.lm[l];
+        o.lmp[2 * l + 1] = o.lp[l];
+    }
+}
 
 // Per-problem data: geometry, walls and device arrays.  Kernel parameters for a single
 // problem; shared memory in the batched kernel.
@@ -128,18 +150,76 @@ __device__ __forceinline__ void store_line(R *f, int base, int stride, const R y
     for (int l = 0; l < P; ++l) f[base + l * stride] = y[l];
 }
 
+// ---- packed float arithmetic: fma.rn.f32x2 / mul.rn.f32x2 on two floats side by side
+// in a 64-bit register pair, rounded as the two scalar operations are.  The line
+// contractions below are instruction-issue bound; packing halves their FMA instructions.
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long r, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+template <typename R>
+__device__ __forceinline__ unsigned long long f2_at(const R *p)  // two adjacent floats
+{
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    return f2_pack(v.x, v.y);
+}
+
 // BR1 lifting along one line (Sec. 3.1, weak form, collocated Gauss quadrature):
 //   y_i = (2/h) [ sum_l Dhat_il x_l + Lp_i q*_+ - Lm_i q*_- ]
+// (float: rows in pairs, packed; the face terms as two FMAs after the sum)
 template <int P, typename R>
 __device__ __forceinline__ void lift_line(const OpsR<R> &o, const R x[P], R qm, R qp, R s, R y[P])
 {
+    if constexpr (sizeof(R) == 4) {
+        unsigned long long xb[P];
 #pragma unroll
-    for (int i = 0; i < P; ++i) {
-        R acc = R(0);
+        for (int l = 0; l < P; ++l) xb[l] = f2_pack(x[l], x[l]);
+        const unsigned long long qpb = f2_pack(qp, qp), qmb = f2_pack(-qm, -qm), sb = f2_pack(s, s);
 #pragma unroll
-        for (int l = 0; l < P; ++l) acc += o.Dh[i * P + l] * x[l];
-        acc += o.Lp[i] * qp - o.Lm[i] * qm;
-        y[i] = s * acc;
+        for (int p = 0; 2 * p + 1 < P; ++p) {
+            unsigned long long acc = f2_pack(0.0f, 0.0f);
+#pragma unroll
+            for (int l = 0; l < P; ++l) acc = f2_fma(f2_at(&o.Dh2[2 * (p * P + l)]), xb[l], acc);
+            acc = f2_fma(f2_at(&o.Lp[2 * p]), qpb, acc);
+            acc = f2_fma(f2_at(&o.Lm[2 * p]), qmb, acc);
+            f2_unpack(f2_mul(sb, acc), y[2 * p], y[2 * p + 1]);
+        }
+        if (P % 2) {
+            constexpr int i = P - 1;
+            R acc = R(0);
+#pragma unroll
+            for (int l = 0; l < P; ++l) acc += o.Dh[i * P + l] * x[l];
+            acc += o.Lp[i] * qp;
+            acc += o.Lm[i] * (-qm);
+            y[i] = s * acc;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            R acc = R(0);
+#pragma unroll
+            for (int l = 0; l < P; ++l) acc += o.Dh[i * P + l] * x[l];
+            acc += o.Lp[i] * qp - o.Lm[i] * qm;
+            y[i] = s * acc;
+        }
     }
 }
 
@@ -147,27 +227,55 @@ __device__ __forceinline__ void lift_line(const OpsR<R> &o, const R x[P], R qm, 
 template <int P, typename R>
 __device__ __forceinline__ void dhat_line(const OpsR<R> &o, const R x[P], R s, R y[P])
 {
+    if constexpr (sizeof(R) == 4) {
+        unsigned long long xb[P];
 #pragma unroll
-    for (int i = 0; i < P; ++i) {
-        R acc = R(0);
+        for (int l = 0; l < P; ++l) xb[l] = f2_pack(x[l], x[l]);
+        const unsigned long long sb = f2_pack(s, s);
 #pragma unroll
-        for (int l = 0; l < P; ++l) acc += o.Dh[i * P + l] * x[l];
-        y[i] = s * acc;
+        for (int p = 0; 2 * p + 1 < P; ++p) {
+            unsigned long long acc = f2_pack(0.0f, 0.0f);
+#pragma unroll
+            for (int l = 0; l < P; ++l) acc = f2_fma(f2_at(&o.Dh2[2 * (p * P + l)]), xb[l], acc);
+            f2_unpack(f2_mul(sb, acc), y[2 * p], y[2 * p + 1]);
+        }
+        if (P % 2) {
+            constexpr int i = P - 1;
+            R acc = R(0);
+#pragma unroll
+            for (int l = 0; l < P; ++l) acc += o.Dh[i * P + l] * x[l];
+            y[i] = s * acc;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            R acc = R(0);
+#pragma unroll
+            for (int l = 0; l < P; ++l) acc += o.Dh[i * P + l] * x[l];
+            y[i] = s * acc;
+        }
     }
 }
 
-// traces of one line at xi = -1 and xi = +1
+// traces of one line at xi = -1 and xi = +1 (float: the two traces packed)
 template <int P, typename R>
 __device__ __forceinline__ void trace_pair(const OpsR<R> &o, const R x[P], R &tm, R &tp)
 {
-    R am = R(0), ap = R(0);
+    if constexpr (sizeof(R) == 4) {
+        unsigned long long acc = f2_pack(0.0f, 0.0f);
 #pragma unroll
-    for (int l = 0; l < P; ++l) {
-        am += o.lm[l] * x[l];
-        ap += o.lp[l] * x[l];
+        for (int l = 0; l < P; ++l) acc = f2_fma(f2_at(&o.lmp[2 * l]), f2_pack(x[l], x[l]), acc);
+        f2_unpack(acc, tm, tp);
+    } else {
+        R am = R(0), ap = R(0);
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            am += o.lm[l] * x[l];
+            ap += o.lp[l] * x[l];
+        }
+        tm = am;
+        tp = ap;
     }
-    tm = am;
-    tp = ap;
 }
 
 template <int NF, int NFP>
@@ -938,13 +1046,9 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
 #pragma unroll
             for (int k = 0; k < NQ; ++k) {
                 const R *src = face_source<D, N, R, EB>(k, dir, sG, sGT, sN);
-                R am = R(0), ap = R(0);
-#pragma unroll
-                for (int l = 0; l < P; ++l) {
-                    const R x = src[base + l * stride];
-                    am += a.op.lm[l] * x;
-                    ap += a.op.lp[l] * x;
-                }
+                R x[P], am, ap;
+                load_line<P, R>(src, base, stride, x);
+                trace_pair<P, R>(a.op, x, am, ap);
                 sR[((2 * dir) * NQ + k) * NFP + line] = am;
                 sR[((2 * dir + 1) * NQ + k) * NFP + line] = ap;
             }

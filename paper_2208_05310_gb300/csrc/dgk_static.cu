@@ -127,6 +127,7 @@ int fill(dgk::KArgs<R> &a, const dgk_params &q, const dgk_box_mesh &m, const dgk
         a.op.lp[i] = (R)op.lp[i];
         a.op.lm[i] = (R)op.lm[i];
     }
+    dgk::fill_pairs(a.op, P);
     return DGK_OK;
 }
 
