@@ -292,8 +292,6 @@ int dgk_check_conversions(const double *x, size_t n, int on_device, unsigned lon
  * Each problem has its own time step.  The problems are ordinary contexts owned by the
  * batch: use dgk_batch_problem() with the single-problem calls (set-up, download,
  * diagnostics, max_dt).
- * All batches of a process share one constant-memory parameter block, rebound at the
- * start of every step: batches on different streams must not run at the same time.
  */
 typedef struct dgk_batch dgk_batch;
 /* p: common parameters (precision must be DGK_PREC_FP32BULK, flux DGK_FLUX_RUSANOV);
@@ -336,7 +334,7 @@ int dgk_batch_status(dgk_batch *b, int *per_problem);
    default 4e9, about 2 s at 2 GHz).  A block that waits longer latches the barrier
    status and returns, and dgk_batch_status() reports DGK_ERR_TIMEOUT: the kernel never
    hangs on a missing block.  Synchronises the batch's stream; takes effect at the next
-   dgk_batch_run (the limit is part of the parameters each step rebinds).  A limit of a
+   dgk_batch_run (the limit is a kernel parameter; the step graph is captured again).  A limit of a
    few cycles makes the barrier waits run out, which exercises that error path. */
 int dgk_batch_set_barrier_limit(dgk_batch *b, long long cycles);
 

@@ -325,7 +325,7 @@ struct dgk_ctx {
     unsigned *diag_counter = nullptr;
     size_t samples_cap = 0;
     cudaGraphExec_t diag_graph = nullptr;
-    double coef_h[11] = {0};
+    double coef_h[12] = {0};  // A_0..A_4, B_0..B_4, dt, number of stages
     bool coef_valid = false;
     cudaGraphExec_t graph = nullptr;
     // dgk_run_host: staging buffers, copy streams and their events
@@ -526,9 +526,10 @@ int set_coef(dgk_ctx *c, double dt)
     int ns;
     double A[5] = {0}, B[5] = {0};
     rk_table(c->prm.rk, ns, A, B);
-    double h[11];
+    double h[12];
     for (int s = 0; s < 5; ++s) { h[s] = A[s]; h[5 + s] = B[s]; }
     h[10] = dt;
+    h[11] = ns;
     if (c->coef_valid && std::memcmp(h, c->coef_h, sizeof(h)) == 0) return DGK_OK;
     std::memcpy(c->coef_h, h, sizeof(h));
     DGK_CUDA(cudaMemcpyAsync(c->coef, c->coef_h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
@@ -1470,7 +1471,6 @@ struct dgk_batch {
     dgk::KView<float> *d_views = nullptr;
     int *d_probN = nullptr, *d_tiles = nullptr;
     unsigned *d_bar = nullptr;  // [0..1] barrier, [2] status
-    void *d_args = nullptr;     // device copy of the kernel parameters
     int form = 0;               // 0 persistent launch per stage (80-register allocation), 1 grouped
                                 // launches per phase, 2 persistent with the 128-register allocation
     int sms = 0, max_bps = 1, max_bps_wide = 1, bps = 1;
@@ -1529,20 +1529,16 @@ int batch_build_tiles(dgk_batch *b)
     b->L.tile_blk = b->d_tiles + nt;
     b->L.tile_len = b->d_tiles + 2 * nt;
     b->L.ntiles = (int)nt;
-    if (!b->d_args) DGK_CUDA(cudaMalloc(&b->d_args, dgk::batch_args_bytes()));
-    DGK_CUDA(dgk::batch_upload_args(b->L, b->d_args));
-    batch_drop_graph(b);
+    batch_drop_graph(b);  // the launches carry the tile table and the parameters by value
     return DGK_OK;
 }
 
 int batch_launch_step(dgk_batch *b)
 {
     const int ns = b->prm.rk == 3 ? 3 : 5;
-    cudaError_t e0 = dgk::batch_bind_args(b->d_args, b->stream);
-    if (e0 != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("batch parameters: ") + cudaGetErrorString(e0));
     for (int s = 0; s < ns; ++s) {
-        cudaError_t err = b->form != 1 ? dgk::batch_stage_launch(b->sms * b->bps, s, b->stream, b->form == 2)
-                                       : dgk::batch_phase_launches(b->L.ntiles, s, b->stream);
+        cudaError_t err = b->form != 1 ? dgk::batch_stage_launch(b->L, b->sms * b->bps, s, b->stream, b->form == 2)
+                                       : dgk::batch_phase_launches(b->L, s, b->stream);
         if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("batched stage launch: ") + cudaGetErrorString(err));
     }
     return DGK_OK;
@@ -1647,7 +1643,6 @@ void dgk_batch_destroy(dgk_batch *b)
     if (b->d_probN) cudaFree(b->d_probN);
     if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->d_bar) cudaFree(b->d_bar);
-    if (b->d_args) cudaFree(b->d_args);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -1729,7 +1724,7 @@ int dgk_batch_set_barrier_limit(dgk_batch *b, long long cycles)
     if (!b || cycles < 1) return fail(DGK_ERR_ARG, "the barrier limit must be at least one cycle");
     DGK_CUDA(cudaStreamSynchronize(b->stream));
     b->L.bar_limit = cycles;
-    DGK_CUDA(dgk::batch_upload_args(b->L, b->d_args));
+    batch_drop_graph(b);  // a kernel parameter: the step graph is captured again
     return DGK_OK;
 }
 

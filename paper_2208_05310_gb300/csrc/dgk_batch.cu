@@ -12,7 +12,7 @@
 // Work items ("tiles") are runs of K consecutive element blocks of one problem; the
 // tile table is built on the host from the autotuned K per degree.  Each block copies
 // the tile's problem view (geometry, walls, array pointers) into shared memory; physics
-// constants and the operators of the three degrees live in constant memory.
+// constants and the operators of the three degrees are a kernel parameter.
 //
 // A second, grouped form runs each phase as an ordinary launch over all tiles (three
 // launches per stage, no grid barrier): one kernel holds the bodies of all three phases
@@ -78,16 +78,16 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, un
     return ok != 0;
 }
 
-// Batch parameters in constant memory: refreshed from the batch's device copy by a
-// device-to-device copy at the start of every step, so that the per-(degree, phase)
-// functions below read physics constants and operators as constant-bank operands.
-__constant__ BatchArgs<float> c_batch;
+// The batch parameters are a kernel parameter (__grid_constant__): physics constants and
+// the operators of the three degrees are read as parameter-bank operands, also as the
+// 64-bit pairs of the packed float contractions.
 
 // One element block of one problem for one phase.
 template <int N, int PHASE>
-__device__ __forceinline__ void phase_block(const KView<float> &v, long long blk, unsigned char *sm, int stage)
+__device__ __forceinline__ void phase_block(const BatchArgs<float> &b, const KView<float> &v, long long blk,
+                                            unsigned char *sm, int stage)
 {
-    const Ctx<float> a{v, c_batch.ph, c_batch.pr, c_batch.op[N - 3]};
+    const Ctx<float> a{v, b.ph, b.pr, b.op[N - 3]};
     if (PHASE == 0) lift1_body<2, N, float>(a, blk, sm);
     else if (PHASE == 1) lift2vol_body<2, N, float>(a, blk, sm);
     else surf_rk_body<2, N, float>(a, blk, sm, 1, stage);
@@ -99,9 +99,8 @@ __device__ __forceinline__ void phase_block(const KView<float> &v, long long blk
 // register allocator with the union of their live ranges across the back edge and
 // spills heavily, whereas three single-body loops allocate about like the bodies alone.
 template <int N, int PHASE>
-__device__ __forceinline__ int run_tiles(int tile, int end, int stage, KView<float> *sv, int *sh)
+__device__ __forceinline__ int run_tiles(const BatchArgs<float> &b, int tile, int end, int stage, KView<float> *sv, int *sh)
 {
-    const BatchArgs<float> &b = c_batch;
     unsigned char *sm = reinterpret_cast<unsigned char *>(sv) + kBatchViewBytes;
     for (; tile < end; tile += gridDim.x) {
         const int p = b.tile_prob[tile];
@@ -115,7 +114,7 @@ __device__ __forceinline__ int run_tiles(int tile, int end, int stage, KView<flo
         __syncthreads();
         const int blk0 = sh[0], len = sh[1];
         for (int j = 0; j < len; ++j) {
-            phase_block<N, PHASE>(*sv, blk0 + j, sm, stage);
+            phase_block<N, PHASE>(b, *sv, blk0 + j, sm, stage);
             __syncthreads();
         }
     }
@@ -123,13 +122,12 @@ __device__ __forceinline__ int run_tiles(int tile, int end, int stage, KView<flo
 }
 
 template <int PHASE>
-__device__ __forceinline__ void run_phase(int stage, KView<float> *sv, int *sh)
+__device__ __forceinline__ void run_phase(const BatchArgs<float> &b, int stage, KView<float> *sv, int *sh)
 {
-    const BatchArgs<float> &b = c_batch;
     int tile = blockIdx.x;
-    tile = run_tiles<3, PHASE>(tile, b.tile_split[0], stage, sv, sh);
-    tile = run_tiles<4, PHASE>(tile, b.tile_split[1], stage, sv, sh);
-    run_tiles<5, PHASE>(tile, b.ntiles, stage, sv, sh);
+    tile = run_tiles<3, PHASE>(b, tile, b.tile_split[0], stage, sv, sh);
+    tile = run_tiles<4, PHASE>(b, tile, b.tile_split[1], stage, sv, sh);
+    run_tiles<5, PHASE>(b, tile, b.ntiles, stage, sv, sh);
 }
 
 // MB: resident blocks per SM the register allocation targets.  One kernel holds the
@@ -137,17 +135,16 @@ __device__ __forceinline__ void run_phase(int stage, KView<float> *sv, int *sh)
 // the nine: 80 registers with spills at MB = 3, 128 registers with few spills at MB = 2
 // (the autotuner times both).
 template <int MB>
-__global__ void __launch_bounds__(kBatchThreads, MB) k_batch_stage(int stage)
+__global__ void __launch_bounds__(kBatchThreads, MB) k_batch_stage(const __grid_constant__ BatchArgs<float> b, int stage)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     KView<float> *sv = reinterpret_cast<KView<float> *>(smraw);
     __shared__ int sh[2];
-    const BatchArgs<float> &b = c_batch;
-    run_phase<0>(stage, sv, sh);
+    run_phase<0>(b, stage, sv, sh);
     if (!grid_barrier(b.bar, gridDim.x, b.status, b.bar_limit)) return;
-    run_phase<1>(stage, sv, sh);
+    run_phase<1>(b, stage, sv, sh);
     if (!grid_barrier(b.bar, gridDim.x, b.status, b.bar_limit)) return;
-    run_phase<2>(stage, sv, sh);
+    run_phase<2>(b, stage, sv, sh);
 }
 
 // Grouped form: one ordinary launch per phase over the element blocks of all problems
@@ -163,12 +160,12 @@ template <> struct PhaseBudget<1> { static constexpr int min_blocks = 4; };
 template <> struct PhaseBudget<2> { static constexpr int min_blocks = 3; };
 
 template <int PHASE>
-__global__ void __launch_bounds__(kBatchThreads, PhaseBudget<PHASE>::min_blocks) k_batch_phase(int stage)
+__global__ void __launch_bounds__(kBatchThreads, PhaseBudget<PHASE>::min_blocks)
+    k_batch_phase(const __grid_constant__ BatchArgs<float> b, int stage)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     KView<float> *sv = reinterpret_cast<KView<float> *>(smraw);
     __shared__ int sN, sblk;
-    const BatchArgs<float> &b = c_batch;
     const int tile = blockIdx.x;
     const int p = b.tile_prob[tile];
     const unsigned *src = reinterpret_cast<const unsigned *>(b.views + p);
@@ -181,9 +178,9 @@ __global__ void __launch_bounds__(kBatchThreads, PhaseBudget<PHASE>::min_blocks)
     __syncthreads();
     const int N = sN;
     unsigned char *sm = smraw + kBatchViewBytes;
-    if (N == 3) phase_block<3, PHASE>(*sv, sblk, sm, stage);
-    else if (N == 4) phase_block<4, PHASE>(*sv, sblk, sm, stage);
-    else phase_block<5, PHASE>(*sv, sblk, sm, stage);
+    if (N == 3) phase_block<3, PHASE>(b, *sv, sblk, sm, stage);
+    else if (N == 4) phase_block<4, PHASE>(b, *sv, sblk, sm, stage);
+    else phase_block<5, PHASE>(b, *sv, sblk, sm, stage);
 }
 
 template <typename R, int PHASE>
@@ -241,10 +238,8 @@ cudaError_t batch_prepare(int *max_blocks_per_sm, int *max_blocks_per_sm_wide)
                                                          batch_smem_bytes<float>());
 }
 
-size_t batch_args_bytes() { return sizeof(BatchArgs<float>); }
-
-// Fill the batch's device copy of the kernel parameters (host -> device, synchronous).
-cudaError_t batch_upload_args(const BatchLaunch &L, void *dev)
+namespace {
+BatchArgs<float> batch_args(const BatchLaunch &L)
 {
     BatchArgs<float> b;
     b.views = L.views;
@@ -261,18 +256,14 @@ cudaError_t batch_upload_args(const BatchLaunch &L, void *dev)
     b.bar = L.bar;
     b.status = L.status;
     b.bar_limit = L.bar_limit;
-    return cudaMemcpy(dev, &b, sizeof(b), cudaMemcpyHostToDevice);
+    return b;
 }
-
-// One step's parameters into constant memory (device-to-device, capturable).
-cudaError_t batch_bind_args(const void *dev, cudaStream_t s)
-{
-    return cudaMemcpyToSymbolAsync(c_batch, dev, sizeof(BatchArgs<float>), 0, cudaMemcpyDeviceToDevice, s);
-}
+}  // namespace
 
 // wide: the 128-register allocation (k_batch_stage<2>)
-cudaError_t batch_stage_launch(int grid, int stage, cudaStream_t s, bool wide)
+cudaError_t batch_stage_launch(const BatchLaunch &L, int grid, int stage, cudaStream_t s, bool wide)
 {
+    const BatchArgs<float> b = batch_args(L);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kBatchThreads);
@@ -283,14 +274,15 @@ cudaError_t batch_stage_launch(int grid, int stage, cudaStream_t s, bool wide)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return wide ? cudaLaunchKernelEx(&cfg, k_batch_stage<2>, stage) : cudaLaunchKernelEx(&cfg, k_batch_stage<3>, stage);
+    return wide ? cudaLaunchKernelEx(&cfg, k_batch_stage<2>, b, stage) : cudaLaunchKernelEx(&cfg, k_batch_stage<3>, b, stage);
 }
 
-cudaError_t batch_phase_launches(int ntiles, int stage, cudaStream_t s)
+cudaError_t batch_phase_launches(const BatchLaunch &L, int stage, cudaStream_t s)
 {
-    k_batch_phase<0><<<ntiles, kBatchThreads, phase_smem_bytes<float, 0>(), s>>>(stage);
-    k_batch_phase<1><<<ntiles, kBatchThreads, phase_smem_bytes<float, 1>(), s>>>(stage);
-    k_batch_phase<2><<<ntiles, kBatchThreads, phase_smem_bytes<float, 2>(), s>>>(stage);
+    const BatchArgs<float> b = batch_args(L);
+    k_batch_phase<0><<<L.ntiles, kBatchThreads, phase_smem_bytes<float, 0>(), s>>>(b, stage);
+    k_batch_phase<1><<<L.ntiles, kBatchThreads, phase_smem_bytes<float, 1>(), s>>>(b, stage);
+    k_batch_phase<2><<<L.ntiles, kBatchThreads, phase_smem_bytes<float, 2>(), s>>>(b, stage);
     return cudaGetLastError();
 }
 

@@ -182,6 +182,56 @@ __device__ __forceinline__ unsigned long long f2_at(const R *p)  // two adjacent
     return f2_pack(v.x, v.y);
 }
 
+// task q -> (plane v, line) of a line task over NPL planes of NFP lines.  Lines along z
+// (stride NFP, consecutive lines in consecutive banks) with NFP > 32: warp w takes lines
+// 0..31 of plane w, the last NFP-32 lines of every plane follow, so that no warp spans
+// two planes (plane offsets of NP words shift the banks); other directions: plane-major.
+template <int NPL, int NFP>
+__device__ __forceinline__ void line_task(int dir, int q, int &v, int &line)
+{
+    if (NFP > 32 && dir == 2) {
+        if (q < 32 * NPL) {
+            v = q >> 5;
+            line = q & 31;
+        } else {
+            const int r = q - 32 * NPL;
+            v = r / (NFP - 32);
+            line = 32 + r % (NFP - 32);
+        }
+    } else {
+        v = q / NFP;
+        line = q % NFP;
+    }
+}
+
+// x-lines (stride 1) of an even number of floats starting on an 8-byte boundary: float2
+template <int P, typename R>
+__device__ __forceinline__ void load_line_v2(const R *f, int base, R x[P])
+{
+    const float2 *p = reinterpret_cast<const float2 *>(f + base);
+#pragma unroll
+    for (int l = 0; l < P / 2; ++l) { const float2 t = p[l]; x[2 * l] = t.x; x[2 * l + 1] = t.y; }
+}
+template <int P, typename R>
+__device__ __forceinline__ void store_line_v2(R *f, int base, const R y[P])
+{
+    float2 *p = reinterpret_cast<float2 *>(f + base);
+#pragma unroll
+    for (int l = 0; l < P / 2; ++l) p[l] = make_float2(y[2 * l], y[2 * l + 1]);
+}
+template <int P, typename R, int PER_ELEM>
+__device__ __forceinline__ void load_line_d(int dir, const R *f, int base, int stride, R x[P])
+{
+    if (sizeof(R) == 4 && P % 2 == 0 && PER_ELEM % 2 == 0 && dir == 0) load_line_v2<P, R>(f, base, x);
+    else load_line<P, R>(f, base, stride, x);
+}
+template <int P, typename R, int PER_ELEM>
+__device__ __forceinline__ void store_line_d(int dir, R *f, int base, int stride, const R y[P])
+{
+    if (sizeof(R) == 4 && P % 2 == 0 && PER_ELEM % 2 == 0 && dir == 0) store_line_v2<P, R>(f, base, y);
+    else store_line<P, R>(f, base, stride, y);
+}
+
 // BR1 lifting along one line (Sec. 3.1, weak form, collocated Gauss quadrature):
 //   y_i = (2/h) [ sum_l Dhat_il x_l + Lp_i q*_+ - Lm_i q*_- ]
 // (float: rows in pairs, packed; the face terms as two FMAs after the sum)
@@ -802,7 +852,7 @@ struct K2Smem {
     static constexpr int GT = D * S::NP;         // grad T
     static constexpr int X1 = S::NL * S::NP + S::NF * S::NL * S::NFP;  // prims, q*
     static constexpr int X2 = S::NP + 2 * S::NF * S::NFP + D * S::NP;  // T, T*, Dc*, lap parts
-    static constexpr int X4 = 2 * S::NV * S::NP;                       // volume: F, acc
+    static constexpr int X4 = (1 + D) * S::NV * S::NP;                 // volume: F, acc per direction
     static constexpr int SR = S::NF * FaceRec<D>::NQ * S::NFP;         // traced face records
     static constexpr int XN = X4 > SR ? X4 : SR;                       // nodal U/div/lap (sN) offset
     static constexpr int X3 = XN + (S::NV + 2) * S::NP;
@@ -891,13 +941,14 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
         for (int dir = 0; dir < D; ++dir) {
             const int stride = line_stride<P>(dir);
             for (int q = n; q < NL * NFP; q += NP) {
-                const int v = q / NFP, line = q % NFP;
+                int v, line;
+                line_task<NL, NFP>(dir, q, v, line);
                 const int base = line_base<P>(line, dir);
                 R x[P], y[P];
-                load_line<P, R>(sQ + v * NP, base, stride, x);
+                load_line_d<P, R, M::per_elem>(dir, sQ + v * NP, base, stride, x);
                 lift_line<P, R>(a.op, x, sQs[((2 * dir) * NL + v) * NFP + line], sQs[((2 * dir + 1) * NL + v) * NFP + line],
                                 a.v.gr.inv2h[dir], y);
-                store_line<P, R>(sG + (dir * NL + v) * NP, base, stride, y);
+                store_line_d<P, R, M::per_elem>(dir, sG + (dir * NL + v) * NP, base, stride, y);
             }
         }
     }
@@ -1002,16 +1053,13 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
         if (t.valid) {
             const int stride = line_stride<P>(dir);
             for (int q = n; q < NV * NFP; q += NP) {
-                const int v = q / NFP, line = q % NFP;
+                int v, line;
+                line_task<NV, NFP>(dir, q, v, line);
                 const int base = line_base<P>(line, dir);
                 R x[P], y[P];
-                load_line<P, R>(sF + v * NP, base, stride, x);
+                load_line_d<P, R, M::per_elem>(dir, sF + v * NP, base, stride, x);
                 dhat_line<P, R>(a.op, x, a.v.gr.inv2h[dir], y);
-                if (dir > 0) {
-#pragma unroll
-                    for (int l = 0; l < P; ++l) y[l] += sAcc[v * NP + base + l * stride];
-                }
-                store_line<P, R>(sAcc + v * NP, base, stride, y);
+                store_line_d<P, R, M::per_elem>(dir, sAcc + (dir * NV + v) * NP, base, stride, y);
             }
         }
         __syncthreads();
@@ -1019,7 +1067,12 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
     R *sN = sX + M::XN;  // nodal U, div u, lap c (clear of sF, sAcc and the traced records)
     if (t.valid) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) a.v.Utv[((long long)v * ne + t.e) * NP + n] = S_[v] - sAcc[v * NP + n];
+        for (int v = 0; v < NV; ++v) {
+            R acc = sAcc[v * NP + n];
+#pragma unroll
+            for (int d = 1; d < D; ++d) acc += sAcc[(d * NV + v) * NP + n];
+            a.v.Utv[((long long)v * ne + t.e) * NP + n] = S_[v] - acc;
+        }
         sN[n] = rho;
 #pragma unroll
         for (int k = 0; k < D; ++k) sN[(1 + k) * NP + n] = m[k];
@@ -1041,7 +1094,14 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
     R *sR = sX;  // clear of sN; sF and sAcc are dead
     if (t.valid) {
         for (int q = n; q < D * NFP; q += NP) {
-            const int dir = q / NFP, line = q % NFP;
+            int dir, line;
+            if (NFP > 32) {
+                if (q < 32 * D) { dir = q >> 5; line = q & 31; }
+                else { const int r = q - 32 * D; dir = r / (NFP - 32); line = 32 + r % (NFP - 32); }
+            } else {
+                dir = q / NFP;
+                line = q % NFP;
+            }
             const int base = line_base<P>(line, dir), stride = line_stride<P>(dir);
 #pragma unroll
             for (int k = 0; k < NQ; ++k) {
@@ -1253,6 +1313,12 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
         const Slot<D, N, EB> t(a.v.g, blk);
     R *sFs = reinterpret_cast<R *>(smraw) + (size_t)t.le * M::per_elem;
     const long long ne = a.v.g.ne;
+    // The RK register G is not read at a stage with A = 0 (the first stage of both schemes:
+    // G = dt U_t there), nor written at the last stage of a step (the next step's first
+    // stage does not read it): 96 B of FP64 traffic per node and step saved.
+    // coef = [A_0..A_4, B_0..B_4, dt, number of stages].
+    const bool readG = mode != 0 && a.v.coef[stage] != 0.0;
+    const bool writeG = mode != 0 && stage + 1 < (int)a.v.coef[11];
     // issue the node loads first so that their latency overlaps the face phase
     R utv[NV];
     double u0[NV], g0[NV];
@@ -1265,7 +1331,7 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
             utv[v] = a.v.Utv[idx];
             if (mode != 0 && !SURF_LATE) {
                 u0[v] = a.v.U[idx];
-                g0[v] = a.v.G[idx];
+                g0[v] = readG ? a.v.G[idx] : 0.0;
             }
         }
     }
@@ -1386,7 +1452,7 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
         for (int v = 0; v < NV; ++v) {
             const long long idx = ((long long)v * ne + t.e) * NP + t.n;
             u0[v] = a.v.U[idx];
-            g0[v] = a.v.G[idx];
+            g0[v] = readG ? a.v.G[idx] : 0.0;
         }
     }
     double Ud[NV];
@@ -1402,7 +1468,7 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
             if constexpr (sizeof(R) == 8) gg = A * g0[v] + dt * Ut[v];
             else gg = fma(A, g0[v], to_f64<R>(dtR * Ut[v]));
             const double uu = fma(B, gg, u0[v]);
-            a.v.G[idx] = gg;
+            if (writeG) a.v.G[idx] = gg;
             a.v.U[idx] = uu;
             Ud[v] = uu;
         }

@@ -101,12 +101,9 @@ struct BatchLaunch {
     long long bar_limit;                               // barrier spin limit (cycles)
 };
 size_t batch_smem();
-size_t batch_args_bytes();
 cudaError_t batch_prepare(int *max_blocks_per_sm, int *max_blocks_per_sm_wide);
-cudaError_t batch_upload_args(const BatchLaunch &L, void *dev);
-cudaError_t batch_bind_args(const void *dev, cudaStream_t s);
-cudaError_t batch_stage_launch(int grid, int stage, cudaStream_t s, bool wide);
-cudaError_t batch_phase_launches(int ntiles, int stage, cudaStream_t s);
+cudaError_t batch_stage_launch(const BatchLaunch &L, int grid, int stage, cudaStream_t s, bool wide);
+cudaError_t batch_phase_launches(const BatchLaunch &L, int stage, cudaStream_t s);
 
 }  // namespace dgk
 
