@@ -622,11 +622,11 @@ def batch_measure(wl, local_rank, steps, warmup, unbatched=True, e2e=False):
     peak, peak_kind = measured_peak()
     avg_launch_ms = ms / steps / stages
     achieved = alg / (avg_launch_ms / 1e3) / 1e9
-    launches = stages * steps * (1 if cfg["form"] == "persistent" else 3)
+    launches = stages * steps * (3 if cfg["form"] == "grouped" else 1)
     out = dict(value=dof * stages * steps / (ms / 1e3), unit=UNIT, ms_per_step=ms / steps, steps=steps,
                nodes=dof, problems=len(meshes), autotuned=cfg, autotune_s=t_tune, gpu_launches=launches,
                roofline=dict(bound="hbm",
-                             kernel="k_batch_stage" if cfg["form"] == "persistent" else "k_batch_phase<0,1,2>",
+                             kernel="k_batch_phase<0,1,2>" if cfg["form"] == "grouped" else "k_batch_stage",
                              achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, peak_kind=peak_kind,
                              alg_bytes_per_launch=alg, avg_launch_ms=avg_launch_ms, traffic=None,
                              note="per RK stage: one persistent launch, or the three grouped phase launches; "
