@@ -153,6 +153,12 @@ __device__ __forceinline__ void store_line(R *f, int base, int stride, const R y
 // ---- packed float arithmetic: fma.rn.f32x2 / mul.rn.f32x2 on two floats side by side
 // in a 64-bit register pair, rounded as the two scalar operations are.  The line
 // contractions below are instruction-issue bound; packing halves their FMA instructions.
+// A translation unit may switch it off before including this header: the batched
+// ensemble's grouped kernels (three degrees' bodies per kernel) ran 15% slower packed
+// (17.9 against 15.6 ms per step), the single-problem kernels 2-5% faster.
+#ifndef DGK_PACKED_LINES
+#define DGK_PACKED_LINES 1
+#endif
 __device__ __forceinline__ unsigned long long f2_pack(float a, float b)
 {
     unsigned long long r;
@@ -238,7 +244,7 @@ __device__ __forceinline__ void store_line_d(int dir, R *f, int base, int stride
 template <int P, typename R>
 __device__ __forceinline__ void lift_line(const OpsR<R> &o, const R x[P], R qm, R qp, R s, R y[P])
 {
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (sizeof(R) == 4 && DGK_PACKED_LINES) {
         unsigned long long xb[P];
 #pragma unroll
         for (int l = 0; l < P; ++l) xb[l] = f2_pack(x[l], x[l]);
@@ -277,7 +283,7 @@ __device__ __forceinline__ void lift_line(const OpsR<R> &o, const R x[P], R qm, 
 template <int P, typename R>
 __device__ __forceinline__ void dhat_line(const OpsR<R> &o, const R x[P], R s, R y[P])
 {
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (sizeof(R) == 4 && DGK_PACKED_LINES) {
         unsigned long long xb[P];
 #pragma unroll
         for (int l = 0; l < P; ++l) xb[l] = f2_pack(x[l], x[l]);
@@ -311,7 +317,7 @@ __device__ __forceinline__ void dhat_line(const OpsR<R> &o, const R x[P], R s, R
 template <int P, typename R>
 __device__ __forceinline__ void trace_pair(const OpsR<R> &o, const R x[P], R &tm, R &tp)
 {
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (sizeof(R) == 4 && DGK_PACKED_LINES) {
         unsigned long long acc = f2_pack(0.0f, 0.0f);
 #pragma unroll
         for (int l = 0; l < P; ++l) acc = f2_fma(f2_at(&o.lmp[2 * l]), f2_pack(x[l], x[l]), acc);
