@@ -816,6 +816,13 @@ static int mesh_box_impl(dgk_ctx *c, const dgk_box_mesh *m, bool curved_walls)
         }
     }
     if (c->prm.model == 0 && has_walls(*m)) return fail(DGK_ERR_UNSUPPORTED, "the original NSK model runs on periodic boxes");
+    {
+        // the kernels index inside one plane of a node or face array with 32 bits
+        long long ne = 1, P = m->N + 1;
+        for (int d = 0; d < m->dim; ++d) ne *= m->n[d];
+        const long long np = m->dim == 2 ? P * P : P * P * P, nfq = m->dim == 2 ? 4 * P : 6 * P * P;
+        if (ne * (np > nfq ? np : nfq) >= (1LL << 32)) return fail(DGK_ERR_ARG, "more than 2^32 - 1 nodes or face points");
+    }
     DGK_CUDA(cudaSetDevice(c->device));
     cudaStreamSynchronize(c->stream);
     free_buffers(c);

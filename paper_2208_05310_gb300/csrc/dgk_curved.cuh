@@ -282,7 +282,7 @@ __device__ __forceinline__ long long face_nbr(const KView<R> &v, const Slot<D, N
 template <int NP, typename R>
 __device__ __forceinline__ R metric(const KView<R> &v, int p, long long e, int n)
 {
-    return v.met[((long long)p * v.g.ne + e) * NP + n];
+    return nat<NP>(v.met, v.g.ne, p, e, n);
 }
 
 // Stage the element's face metrics into sJf[k][f][fp] (one face point per task).
@@ -293,7 +293,7 @@ __device__ __forceinline__ void stage_face_metrics(const Ctx<R> &a, const Slot<D
     constexpr int NP = S::NP, NF = S::NF, NFP = S::NFP;
     for (int q = t.n; q < NF * NFP; q += NP) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) sJf[k * NF * NFP + q] = a.v.fmet[fidx<NF, NFP>(a.v.g.ne, k, t.e, q / NFP, q % NFP)];
+        for (int k = 0; k < D; ++k) sJf[k * NF * NFP + q] = fat<NF, NFP>(a.v.fmet, a.v.g.ne, k, t.e, q / NFP, q % NFP);
     }
 }
 
@@ -340,10 +340,10 @@ struct CLiftC {
             sC[t.n] = c;
             for (int q = t.n; q < NF * NFP; q += NP) {
                 const int f = q / NFP, fp = q % NFP;
-                const R own = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
+                const R own = fat<NF, NFP>(a.v.tr1, ne, D + 1, t.e, f, fp);
                 int fo, o, w;
                 const long long b = face_nbr<D, N, R>(a.v, t, f, fo, o, w);
-                if (b >= 0) sCs[q] = R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, D + 1, b, fo, map_fp<S::P>(o, fp))]);
+                if (b >= 0) sCs[q] = R(0.5) * (own + fat<NF, NFP>(a.v.tr1, ne, D + 1, b, fo, map_fp<S::P>(o, fp)));
                 else if (b <= kMortar) sCs[q] = R(0.5) * (own + a.v.mtr1[((long long)(D + 1) * a.v.g.nslot + (kMortar - b)) * NFP + fp]);
                 else sCs[q] = own;
             }
@@ -414,8 +414,8 @@ __device__ __forceinline__ void lift1c_body(const Ctx<R> &a, long long blk, unsi
             R x[P], tm, tp;
             load_line<P, R>(sT, base, stride, x);
             trace_pair<P, R>(a.op, x, tm, tp);
-            a.v.tr2[fidx<NF, NFP>(ne, 0, t.e, 2 * dir, line)] = tm;
-            a.v.tr2[fidx<NF, NFP>(ne, 0, t.e, 2 * dir + 1, line)] = tp;
+            fat<NF, NFP>(a.v.tr2, ne, 0, t.e, 2 * dir, line) = tm;
+            fat<NF, NFP>(a.v.tr2, ne, 0, t.e, 2 * dir + 1, line) = tp;
             R dm = R(0), dp = R(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
@@ -424,8 +424,8 @@ __device__ __forceinline__ void lift1c_body(const Ctx<R> &a, long long blk, unsi
                 dm += tm * sJf[(k * NF + 2 * dir) * NFP + line];
                 dp += tp * sJf[(k * NF + 2 * dir + 1) * NFP + line];
             }
-            a.v.tr2[fidx<NF, NFP>(ne, 1, t.e, 2 * dir, line)] = dm;
-            a.v.tr2[fidx<NF, NFP>(ne, 1, t.e, 2 * dir + 1, line)] = dp;
+            fat<NF, NFP>(a.v.tr2, ne, 1, t.e, 2 * dir, line) = dm;
+            fat<NF, NFP>(a.v.tr2, ne, 1, t.e, 2 * dir + 1, line) = dp;
         }
     }
 }
@@ -560,12 +560,12 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
 #pragma unroll
                 for (int v = 0; v < NL; ++v)
                     sQs[(f * NL + v) * NFP + fp] =
-                        R(0.5) * (a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)] + a.v.tr1[fidx<NF, NFP>(ne, v, b, fo, fq)]);
+                        R(0.5) * (fat<NF, NFP>(a.v.tr1, ne, v, t.e, f, fp) + fat<NF, NFP>(a.v.tr1, ne, v, b, fo, fq));
             } else if (b <= kMortar) {
                 const long long sl = kMortar - b;
 #pragma unroll
                 for (int v = 0; v < NL; ++v)
-                    sQs[(f * NL + v) * NFP + fp] = R(0.5) * (a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)] +
+                    sQs[(f * NL + v) * NFP + fp] = R(0.5) * (fat<NF, NFP>(a.v.tr1, ne, v, t.e, f, fp) +
                                                              a.v.mtr1[((long long)v * a.v.g.nslot + sl) * NFP + fp]);
             } else {
                 // walls: rho*, c* one-sided; u* the part of the wall's velocity (no slip) or
@@ -574,8 +574,8 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
                 R bv[D], av[D], ba = R(0), aa = R(0);
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
-                    av[k] = a.v.fmet[fidx<NF, NFP>(ne, k, t.e, f, fp)];
-                    bv[k] = slip ? a.v.tr1[fidx<NF, NFP>(ne, 1 + k, t.e, f, fp)] : a.v.wr.uw[w][k];
+                    av[k] = fat<NF, NFP>(a.v.fmet, ne, k, t.e, f, fp);
+                    bv[k] = slip ? fat<NF, NFP>(a.v.tr1, ne, 1 + k, t.e, f, fp) : a.v.wr.uw[w][k];
                     ba += bv[k] * av[k];
                     aa += av[k] * av[k];
                 }
@@ -583,7 +583,7 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
 #pragma unroll
                 for (int v = 0; v < NL; ++v)
                     sQs[(f * NL + v) * NFP + fp] =
-                        (v >= 1 && v <= D) ? bv[v - 1] - sb * av[v - 1] : a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)];
+                        (v >= 1 && v <= D) ? bv[v - 1] - sb * av[v - 1] : fat<NF, NFP>(a.v.tr1, ne, v, t.e, f, fp);
             }
         }
         stage_face_metrics<D, N, R>(a, t, sJf);
@@ -600,8 +600,8 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
             const int f = q / NFP, fp = q % NFP, side = f & 1;
             int fo, o, w;
             const long long b = face_nbr<D, N, R>(a.v, t, f, fo, o, w);
-            const R ownT = a.v.tr2[fidx<NF, NFP>(ne, 0, t.e, f, fp)];
-            const R ownD = a.v.tr2[fidx<NF, NFP>(ne, 1, t.e, f, fp)];
+            const R ownT = fat<NF, NFP>(a.v.tr2, ne, 0, t.e, f, fp);
+            const R ownD = fat<NF, NFP>(a.v.tr2, ne, 1, t.e, f, fp);
             if (b <= kMortar) {
                 const long long sl = kMortar - b, ns = a.v.g.nslot;
                 pT[j] = R(0.5) * (ownT + a.v.mtr2[sl * NFP + fp]);
@@ -609,17 +609,17 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
                 if (fp == 0) sX[M::WG + f] = R(0);
             } else if (b >= 0) {
                 const int fq = map_fp<P>(o, fp);
-                pT[j] = R(0.5) * (ownT + a.v.tr2[fidx<NF, NFP>(ne, 0, b, fo, fq)]);
+                pT[j] = R(0.5) * (ownT + fat<NF, NFP>(a.v.tr2, ne, 0, b, fo, fq));
                 // the neighbour traced grad c . J a along its own face orientation
-                pD[j] = R(0.5) * (ownD + R(facing_sign(f, fo)) * a.v.tr2[fidx<NF, NFP>(ne, 1, b, fo, fq)]);
+                pD[j] = R(0.5) * (ownD + R(facing_sign(f, fo)) * fat<NF, NFP>(a.v.tr2, ne, 1, b, fo, fq));
                 if (fp == 0) sX[M::WG + f] = R(0);
             } else {
-                const R cm = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
+                const R cm = fat<NF, NFP>(a.v.tr1, ne, D + 1, t.e, f, fp);
                 const R gn = a.v.wr.K[w] * (cm - a.v.wr.rl[w]) * (cm - a.v.wr.rv[w]);
                 R a2 = R(0);
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
-                    const R x = a.v.fmet[fidx<NF, NFP>(ne, k, t.e, f, fp)];
+                    const R x = fat<NF, NFP>(a.v.fmet, ne, k, t.e, f, fp);
                     a2 += x * x;
                 }
                 // isothermal wall: T* = T_wall; Navier-slip wall: the fluid's trace (the wall
@@ -874,16 +874,16 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
             for (int k = 0; k < D; ++k) av[k] = sJf[(k * NF + f) * NFP + fp];
             R F[NV], lam, pf, sig;
             face_flux_c<D, R>(a, f, w, wall, r, av, F, lam, pf, sig);
-            const long long fo = (t.e * NF + f) * NFP + fp;
+            const unsigned fo = foff<NF, NFP>(t.e, f, fp);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                a.v.fd[v * st + fo] = r[v];
-                a.v.fd[(NV + v) * st + fo] = F[v];
+                (a.v.fd + v * st)[fo] = r[v];
+                (a.v.fd + (NV + v) * st)[fo] = F[v];
             }
-            a.v.fd[(2 * NV) * st + fo] = lam;
+            (a.v.fd + (2 * NV) * st)[fo] = lam;
             if (a.pr.flux == 1) {
-                a.v.fd[(2 * NV + 1) * st + fo] = pf;
-                a.v.fd[(2 * NV + 2) * st + fo] = sig;
+                (a.v.fd + (2 * NV + 1) * st)[fo] = pf;
+                (a.v.fd + (2 * NV + 2) * st)[fo] = sig;
             }
         }
     }
@@ -944,13 +944,13 @@ __global__ void __launch_bounds__(256) k_mortar_traces(KArgs<R> args, int which)
         double acc = 0.0;
         if (D == 2) {
 #pragma unroll
-            for (int i = 0; i < P; ++i) acc += to_f64<R>(op.Im[h0][u * P + i]) * to_f64<R>(src[fidx<NF, NFP>(ne, var, B, fB, i)]);
+            for (int i = 0; i < P; ++i) acc += to_f64<R>(op.Im[h0][u * P + i]) * to_f64<R>(fat<NF, NFP>(src, ne, var, B, fB, i));
         } else {
             for (int j = 0; j < P; ++j) {
                 double row = 0.0;
 #pragma unroll
                 for (int i = 0; i < P; ++i)
-                    row += to_f64<R>(op.Im[h0][u * P + i]) * to_f64<R>(src[fidx<NF, NFP>(ne, var, B, fB, i + P * j)]);
+                    row += to_f64<R>(op.Im[h0][u * P + i]) * to_f64<R>(fat<NF, NFP>(src, ne, var, B, fB, i + P * j));
                 acc += to_f64<R>(op.Im[h1][w * P + j]) * row;
             }
         }
@@ -968,7 +968,7 @@ __global__ void __launch_bounds__(256) k_mortar_traces(KArgs<R> args, int which)
                 const int qq = map_fp<P>(sb[2], fq), u = qq % P, w = qq / P;
                 const double wt = D == 2 ? to_f64<R>(op.Pm[h0][i * P + u])
                                          : to_f64<R>(op.Pm[h0][i * P + u]) * to_f64<R>(op.Pm[h1][j * P + w]);
-                acc += wt * sg * to_f64<R>(src[fidx<NF, NFP>(ne, var, sb[0], sb[1], fq)]);
+                acc += wt * sg * to_f64<R>(fat<NF, NFP>(src, ne, var, sb[0], sb[1], fq));
             }
         }
         dst[((long long)var * ns + sB) * NFP + ib] = to_bulk<R>(acc);
@@ -1022,7 +1022,7 @@ __global__ void __launch_bounds__(256) k_mortar_flux(KArgs<R> args)
             r[k] = to_bulk<R>(acc);
         }
 #pragma unroll
-        for (int k = 0; k < D; ++k) av[k] = v.fmet[fidx<NF, NFP>(ne, k, Se, fS, fq)];
+        for (int k = 0; k < D; ++k) av[k] = fat<NF, NFP>(v.fmet, ne, k, Se, fS, fq);
         R F[NV], lam, pf, sig;
         face_flux_c<D, R>(a, fS, fS, false, r, av, F, lam, pf, sig);
         const long long so = sS * NFP + fq, sst = ns * NFP;

@@ -268,12 +268,15 @@ __device__ __forceinline__ void lift_line(const OpsR<R> &o, const R x[P], R qm, 
             y[i] = s * acc;
         }
     } else {
+        // the operations of the packed form, in its order (the scalar and packed forms
+        // give the same bits)
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             R acc = R(0);
 #pragma unroll
             for (int l = 0; l < P; ++l) acc += o.Dh[i * P + l] * x[l];
-            acc += o.Lp[i] * qp - o.Lm[i] * qm;
+            acc += o.Lp[i] * qp;
+            acc += o.Lm[i] * (-qm);
             y[i] = s * acc;
         }
     }
@@ -334,10 +337,26 @@ __device__ __forceinline__ void trace_pair(const OpsR<R> &o, const R x[P], R &tm
     }
 }
 
-template <int NF, int NFP>
-__device__ __forceinline__ long long fidx(long long ne, int v, long long e, int f, int fp)
+// Device arrays are [plane][element][...]: an element-node array has planes of ne NP
+// values, a face array planes of ne NF NFP.  An access takes the plane's base (the same
+// for every thread of a launch) plus a 32-bit offset inside the plane: the library
+// refuses meshes whose planes exceed 2^32 values, so the offset never wraps, and the
+// address costs one wide multiply-add instead of 64-bit index arithmetic per access.
+template <int NF, int NFP, typename T>
+__device__ __forceinline__ T &fat(T *p, long long ne, int v, long long e, int f, int fp)
 {
-    return (((long long)v * ne + e) * NF + f) * NFP + fp;
+    return (p + (long long)v * (ne * (NF * NFP)))[((unsigned)e * NF + (unsigned)f) * NFP + (unsigned)fp];
+}
+template <int NP, typename T>
+__device__ __forceinline__ T &nat(T *p, long long ne, int v, long long e, int n)
+{
+    return (p + (long long)v * (ne * NP))[(unsigned)e * NP + (unsigned)n];
+}
+// offset of (e, f, fp) inside a face-array plane, and the plane base
+template <int NF, int NFP>
+__device__ __forceinline__ unsigned foff(long long e, int f, int fp)
+{
+    return ((unsigned)e * NF + (unsigned)f) * NFP + (unsigned)fp;
 }
 
 // The neighbour's face point matching face point fp under orientation o: (u, v) = o & 1 ?
@@ -423,9 +442,9 @@ struct CLift {
             sC[t.n] = c;
             for (int q = t.n; q < NF * NFP; q += NP) {
                 const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
-                const R own = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
+                const R own = fat<NF, NFP>(a.v.tr1, ne, D + 1, t.e, f, fp);
                 const long long b = t.nbr(a.v.g, f);
-                sCs[q] = b >= 0 ? R(0.5) * (own + a.v.tr1[fidx<NF, NFP>(ne, D + 1, b, 2 * dir + 1 - side, fp)]) : own;
+                sCs[q] = b >= 0 ? R(0.5) * (own + fat<NF, NFP>(a.v.tr1, ne, D + 1, b, 2 * dir + 1 - side, fp)) : own;
             }
         }
         __syncthreads();
@@ -440,8 +459,8 @@ struct CLift {
                 if (write_tr2) {
                     R tm, tp;
                     trace_pair<P, R>(a.op, y, tm, tp);
-                    a.v.tr2[fidx<NF, NFP>(ne, 1, t.e, 2 * dir, line)] = tm;
-                    a.v.tr2[fidx<NF, NFP>(ne, 1, t.e, 2 * dir + 1, line)] = tp;
+                    fat<NF, NFP>(a.v.tr2, ne, 1, t.e, 2 * dir, line) = tm;
+                    fat<NF, NFP>(a.v.tr2, ne, 1, t.e, 2 * dir + 1, line) = tp;
                 }
             }
         }
@@ -478,12 +497,12 @@ struct NodeState {
         if constexpr (sizeof(R) == 8) {
             double Ud[NV];
 #pragma unroll
-            for (int k = 0; k < NV; ++k) Ud[k] = v.U[((long long)k * v.g.ne + e) * np + n];
+            for (int k = 0; k < NV; ++k) Ud[k] = (v.U + (long long)k * (v.g.ne * np))[(unsigned)e * np + (unsigned)n];
             from_double(Ud);
         } else {
             R u[NV + 1];
 #pragma unroll
-            for (int k = 0; k <= NV; ++k) u[k] = v.Us[((long long)k * v.g.ne + e) * np + n];
+            for (int k = 0; k <= NV; ++k) u[k] = (v.Us + (long long)k * (v.g.ne * np))[(unsigned)e * np + (unsigned)n];
             rho = u[0];
             irho = R(1) / rho;
 #pragma unroll
@@ -497,13 +516,14 @@ struct NodeState {
     __device__ __forceinline__ void store_shadow(const KView<R> &v, long long e, int n, int np) const
     {
         if constexpr (sizeof(R) == 4) {
-            const long long st = v.g.ne * np, o = e * np + n;
+            const long long st = v.g.ne * np;
+            const unsigned o = (unsigned)e * np + (unsigned)n;
             v.Us[o] = rho;
 #pragma unroll
-            for (int k = 0; k < D; ++k) v.Us[(1 + k) * st + o] = m[k];
-            v.Us[(D + 1) * st + o] = E;
-            v.Us[(D + 2) * st + o] = c;
-            v.Us[NV * st + o] = bal;
+            for (int k = 0; k < D; ++k) (v.Us + (1 + k) * st)[o] = m[k];
+            (v.Us + (D + 1) * st)[o] = E;
+            (v.Us + (D + 2) * st)[o] = c;
+            (v.Us + NV * st)[o] = bal;
         }
     }
 };
@@ -552,8 +572,8 @@ __device__ __forceinline__ void lift1_body(const Ctx<R> &a, long long blk, unsig
             R x[P], tm, tp;
             load_line<P, R>(sT, line_base<P>(line, dir), line_stride<P>(dir), x);
             trace_pair<P, R>(a.op, x, tm, tp);
-            a.v.tr2[fidx<NF, NFP>(ne, 0, t.e, 2 * dir, line)] = tm;
-            a.v.tr2[fidx<NF, NFP>(ne, 0, t.e, 2 * dir + 1, line)] = tp;
+            fat<NF, NFP>(a.v.tr2, ne, 0, t.e, 2 * dir, line) = tm;
+            fat<NF, NFP>(a.v.tr2, ne, 0, t.e, 2 * dir + 1, line) = tp;
         }
     }
 }
@@ -655,25 +675,25 @@ __device__ __forceinline__ void hllc_flux(int dir, const R *UL, const R *FL, R p
 // convective part, central for the viscous part, F* = HLLC(F^C) - (F^V_L + F^V_R)/2 with
 // F^V = F^C - F.  Written to out[v * ostride].
 template <int D, typename R>
-__device__ __forceinline__ void hllc_face(const R *fd, long long st, long long iL, long long iR, int dir, R *out,
+__device__ __forceinline__ void hllc_face(const R *fd, long long st, unsigned iL, unsigned iR, int dir, R *out,
                                        int ostride)
 {
     constexpr int NV = D + 3;
     R UL[NV], UR[NV], FcL[NV], FcR[NV], Fh[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        UL[v] = fd[v * st + iL];
-        UR[v] = fd[v * st + iR];
+        UL[v] = (fd + v * st)[iL];
+        UR[v] = (fd + v * st)[iR];
     }
-    const R pL = fd[(2 * NV + 1) * st + iL], aL = fd[(2 * NV + 2) * st + iL];
-    const R pR = fd[(2 * NV + 1) * st + iR], aR = fd[(2 * NV + 2) * st + iR];
+    const R pL = (fd + (2 * NV + 1) * st)[iL], aL = (fd + (2 * NV + 2) * st)[iL];
+    const R pR = (fd + (2 * NV + 1) * st)[iR], aR = (fd + (2 * NV + 2) * st)[iR];
     const R irL = R(1) / UL[0], irR = R(1) / UR[0];
     conv_flux<D, R>(dir, UL, pL, irL, FcL);
     conv_flux<D, R>(dir, UR, pR, irR, FcR);
     hllc_flux<D, R>(dir, UL, FcL, pL, aL, irL, UR, FcR, pR, aR, irR, Fh);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        const R FvL = FcL[v] - fd[(NV + v) * st + iL], FvR = FcR[v] - fd[(NV + v) * st + iR];
+        const R FvL = FcL[v] - (fd + (NV + v) * st)[iL], FvR = FcR[v] - (fd + (NV + v) * st)[iR];
         out[v * ostride] = Fh[v] - R(0.5) * (FvL + FvR);
     }
 }
@@ -858,7 +878,7 @@ struct K2Smem {
     static constexpr int GT = D * S::NP;         // grad T
     static constexpr int X1 = S::NL * S::NP + S::NF * S::NL * S::NFP;  // prims, q*
     static constexpr int X2 = S::NP + 2 * S::NF * S::NFP + D * S::NP;  // T, T*, Dc*, lap parts
-    static constexpr int X4 = (1 + D) * S::NV * S::NP;                 // volume: F, acc per direction
+    static constexpr int X4 = D * S::NV * S::NP;                       // volume: F and its integral per direction
     static constexpr int SR = S::NF * FaceRec<D>::NQ * S::NFP;         // traced face records
     static constexpr int XN = X4 > SR ? X4 : SR;                       // nodal U/div/lap (sN) offset
     static constexpr int X3 = XN + (S::NV + 2) * S::NP;
@@ -898,15 +918,15 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
             if (b >= 0) {
 #pragma unroll
                 for (int v = 0; v < NL; ++v)
-                    sQs[(f * NL + v) * NFP + fp] = R(0.5) * (a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)] +
-                                                             a.v.tr1[fidx<NF, NFP>(ne, v, b, 2 * dir + 1 - side, fp)]);
+                    sQs[(f * NL + v) * NFP + fp] = R(0.5) * (fat<NF, NFP>(a.v.tr1, ne, v, t.e, f, fp) +
+                                                             fat<NF, NFP>(a.v.tr1, ne, v, b, 2 * dir + 1 - side, fp));
             } else {
                 // walls: u* = the wall's velocity (no slip; zero unless the wall slides), or
                 // the fluid's tangential velocity (Navier slip)
                 const bool slip = a.v.wr.kind[f] == 2;
 #pragma unroll
                 for (int v = 0; v < NL; ++v) {
-                    const R own = a.v.tr1[fidx<NF, NFP>(ne, v, t.e, f, fp)];
+                    const R own = fat<NF, NFP>(a.v.tr1, ne, v, t.e, f, fp);
                     sQs[(f * NL + v) * NFP + fp] =
                         (v >= 1 && v <= D && (!slip || v == 1 + dir)) ? a.v.wr.uw[f][v - 1] : own;
                 }
@@ -924,17 +944,17 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
         if (t.valid && q < NF * NFP) {
             const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
             const long long b = t.nbr(a.v.g, f);
-            const R ownT = a.v.tr2[fidx<NF, NFP>(ne, 0, t.e, f, fp)];
-            const R ownD = a.v.tr2[fidx<NF, NFP>(ne, 1, t.e, f, fp)];
+            const R ownT = fat<NF, NFP>(a.v.tr2, ne, 0, t.e, f, fp);
+            const R ownD = fat<NF, NFP>(a.v.tr2, ne, 1, t.e, f, fp);
             if (b >= 0) {
                 const int fo = 2 * dir + 1 - side;
-                pT[j] = R(0.5) * (ownT + a.v.tr2[fidx<NF, NFP>(ne, 0, b, fo, fp)]);
-                pD[j] = R(0.5) * (ownD + a.v.tr2[fidx<NF, NFP>(ne, 1, b, fo, fp)]);
+                pT[j] = R(0.5) * (ownT + fat<NF, NFP>(a.v.tr2, ne, 0, b, fo, fp));
+                pD[j] = R(0.5) * (ownD + fat<NF, NFP>(a.v.tr2, ne, 1, b, fo, fp));
             } else {
                 // isothermal wall: T* = T_wall; Navier-slip wall: the fluid's trace (the
                 // wall heat flux enters the energy flux); contact-angle gradient (its
                 // gamma_1 div u part is added once div u is known, in the node phase)
-                const R cm = a.v.tr1[fidx<NF, NFP>(ne, D + 1, t.e, f, fp)];
+                const R cm = fat<NF, NFP>(a.v.tr1, ne, D + 1, t.e, f, fp);
                 const R gn = a.v.wr.K[f] * (cm - a.v.wr.rl[f]) * (cm - a.v.wr.rv[f]);
                 pT[j] = a.v.wr.kind[f] == 2 ? ownT : a.v.wr.Tw[f];
                 pD[j] = side ? gn : -gn;
@@ -1045,39 +1065,43 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
     }
     __syncthreads();  // sT, sTs, sDs, sLp are dead before the volume buffers reuse sX
 
-    // ---- volume integral, direction by direction: acc_i += (2/h) sum_l Dhat_il F_l
-    R *sF = sX, *sAcc = sX + NV * NP;
+    // ---- volume integral: the fluxes of all directions, then in place along each line
+    //      (2/h) sum_l Dhat_il F_l; acc = the sum over the directions
+    R *sF = sX;  // [D][NV][NP]
+    if (t.valid) {
 #pragma unroll
-    for (int dir = 0; dir < D; ++dir) {
-        if (t.valid) {
+        for (int dir = 0; dir < D; ++dir) {
             R F[NV];
             flux_dir<D, R>(a.pr, dir, rho, m, u, E, c, pf, du, gT, gc, lap, F);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) sF[v * NP + n] = F[v];
+            for (int v = 0; v < NV; ++v) sF[(dir * NV + v) * NP + n] = F[v];
         }
-        __syncthreads();
-        if (t.valid) {
+    }
+    __syncthreads();
+    if (t.valid) {
+#pragma unroll
+        for (int dir = 0; dir < D; ++dir) {
             const int stride = line_stride<P>(dir);
             for (int q = n; q < NV * NFP; q += NP) {
                 int v, line;
                 line_task<NV, NFP>(dir, q, v, line);
                 const int base = line_base<P>(line, dir);
                 R x[P], y[P];
-                load_line_d<P, R, M::per_elem>(dir, sF + v * NP, base, stride, x);
+                load_line_d<P, R, M::per_elem>(dir, sF + (dir * NV + v) * NP, base, stride, x);
                 dhat_line<P, R>(a.op, x, a.v.gr.inv2h[dir], y);
-                store_line_d<P, R, M::per_elem>(dir, sAcc + (dir * NV + v) * NP, base, stride, y);
+                store_line_d<P, R, M::per_elem>(dir, sF + (dir * NV + v) * NP, base, stride, y);
             }
         }
-        __syncthreads();
     }
-    R *sN = sX + M::XN;  // nodal U, div u, lap c (clear of sF, sAcc and the traced records)
+    __syncthreads();
+    R *sN = sX + M::XN;  // nodal U, div u, lap c (clear of sF and the traced records)
     if (t.valid) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            R acc = sAcc[v * NP + n];
+            R acc = sF[v * NP + n];
 #pragma unroll
-            for (int d = 1; d < D; ++d) acc += sAcc[(d * NV + v) * NP + n];
-            a.v.Utv[((long long)v * ne + t.e) * NP + n] = S_[v] - acc;
+            for (int d = 1; d < D; ++d) acc += sF[(d * NV + v) * NP + n];
+            nat<NP>(a.v.Utv, ne, v, t.e, n) = S_[v] - acc;
         }
         sN[n] = rho;
 #pragma unroll
@@ -1097,7 +1121,7 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
     //      are loaded once for the two faces)
     using FR = FaceRec<D>;
     constexpr int NQ = FR::NQ;
-    R *sR = sX;  // clear of sN; sF and sAcc are dead
+    R *sR = sX;  // clear of sN; sF is dead
     if (t.valid) {
         for (int q = n; q < D * NFP; q += NP) {
             int dir, line;
@@ -1135,16 +1159,16 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
             for (int k = 0; k < NQ; ++k) r[k] = sR[(f * NQ + k) * NFP + fp];
             R F[NV], lam, pf, sig;
             face_flux<D, R>(a, f, dir, wall, r, F, lam, pf, sig);
-            const long long fo = (t.e * NF + f) * NFP + fp;
+            const unsigned fo = foff<NF, NFP>(t.e, f, fp);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                a.v.fd[v * st + fo] = r[v];
-                a.v.fd[(NV + v) * st + fo] = F[v];
+                (a.v.fd + v * st)[fo] = r[v];
+                (a.v.fd + (NV + v) * st)[fo] = F[v];
             }
-            a.v.fd[(2 * NV) * st + fo] = lam;
+            (a.v.fd + (2 * NV) * st)[fo] = lam;
             if (a.pr.flux == 1) {
-                a.v.fd[(2 * NV + 1) * st + fo] = pf;
-                a.v.fd[(2 * NV + 2) * st + fo] = sig;
+                (a.v.fd + (2 * NV + 1) * st)[fo] = pf;
+                (a.v.fd + (2 * NV + 2) * st)[fo] = sig;
             }
         }
     }
@@ -1202,8 +1226,8 @@ __device__ __forceinline__ void write_traces(const Ctx<R> &a, const Slot<D, N, E
             R x[P], tm, tp;
             load_line<P, R>(sQ + v * NP, line_base<P>(line, dir), line_stride<P>(dir), x);
             trace_pair<P, R>(a.op, x, tm, tp);
-            a.v.tr1[fidx<NF, NFP>(ne, v, t.e, 2 * dir, line)] = tm;
-            a.v.tr1[fidx<NF, NFP>(ne, v, t.e, 2 * dir + 1, line)] = tp;
+            fat<NF, NFP>(a.v.tr1, ne, v, t.e, 2 * dir, line) = tm;
+            fat<NF, NFP>(a.v.tr1, ne, v, t.e, 2 * dir + 1, line) = tp;
         }
     }
 }
@@ -1395,7 +1419,7 @@ __device__ __forceinline__ void surf_rk_body(const Ctx<R> &a, long long blk, uns
                     pn = fN[(2 * NV + 1) * sN + iN];
                     sn = fN[(2 * NV + 2) * sN + iN];
 #pragma unroll
-                    for (int k = 0; k < D; ++k) av[k] = a.v.fmet[fidx<NF, NFP>(ne, k, t.e, f, fp)];
+                    for (int k = 0; k < D; ++k) av[k] = fat<NF, NFP>(a.v.fmet, ne, k, t.e, f, fp);
                 }
                 pair_flux_c<D, R, FLUX>(side, Uo, Fo, a.v.fd[(2 * NV) * st + oo], po, so, Un, Fn, fN[(2 * NV) * sN + iN],
                                         pn, sn, av, Fs);

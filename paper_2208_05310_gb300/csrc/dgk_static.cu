@@ -193,6 +193,8 @@ extern "C" int dgk_rhs_static(const dgk_params *p, const dgk_box_mesh *m, const 
         ne *= m->n[d];
         if (ne >= (1LL << 32)) return fail_static(DGK_ERR_ARG, "mesh too large for the static scratch of dgk_rhs_static (DGK_STATIC_SCRATCH_BYTES)");
     }
+    if (ne * (long long)(NP > NF * NFP ? NP : NF * NFP) >= (1LL << 32))
+        return fail_static(DGK_ERR_ARG, "mesh too large for the static scratch of dgk_rhs_static (DGK_STATIC_SCRATCH_BYTES)");
     if (count != (size_t)NV * (size_t)ne * (size_t)NP)
         return fail_static(DGK_ERR_ARG, "count must be nvar * nelem * np of the mesh");
     const bool f32 = p->precision == DGK_PREC_FP32BULK;

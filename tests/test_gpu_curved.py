@@ -204,13 +204,24 @@ def test_curved_free_stream(precision, tol):
 CURVED32 = 2.0
 
 
-# Curved mortar meshes with model 2: the convective pressure carries alpha/2 rho^2 ~ 160
-# (alpha = 100, rho ~ 1.8), and in FP32 the face metrics of a big face and of its curved
-# sub-faces cancel that term only to FP32 rounding (~1e-5 absolute per flux value), which
-# the energy accumulates.  Measured rho e errors after 10 steps: flat mortars 6e-8 (Rusanov)
-# and 1.3e-7 (HLLC), curved conforming 5e-8, curved mortars 4.6e-7 (Rusanov), 3.9e-6
-# (HLLC) and 8.2e-6 (HLLC, random frames); FP64 parity stays at 1e-12.
-MORTAR_M2_ENERGY = 50.0
+# The 10-step bound is the larger of twice the box bound and twice the oracle's own
+# response to perturbations of FP32 size: before each step every value is multiplied by
+# 1 + 2^-24 u (u uniform in [-1, 1]), largest response over three seeded sequences.  The
+# FP32-bulk kernels evaluate each stage at the state rounded to float, so no FP32 form
+# can follow the oracle more closely than the problem's conditioning allows.  On the
+# refined curved mesh with model 2 at the full step (3d_N4_g2_walls_m2_hllc_mortar_unstr)
+# the FP64 oracle's rho e response ranges from 5e-7 to 7e-6 over the seeds, and the
+# FP32-bulk error there is 7e-6; the other cases keep the box bound.
+def _fp32_sensitivity(o, Uo, nsteps, dt, seeds=(1, 2, 3)):
+    ref = o.run(Uo, nsteps, dt, rk=4)
+    worst = np.zeros(Uo.shape[0])
+    for seed in seeds:
+        rng = np.random.default_rng(seed)
+        U = Uo.copy()
+        for _ in range(nsteps):
+            U = o.run(U * (1.0 + 2.0 ** -24 * rng.uniform(-1.0, 1.0, U.shape)), 1, dt, rk=4)
+        worst = np.maximum(worst, rel_l2(U, ref))
+    return worst, ref
 
 
 @pytest.mark.parametrize("name", ["2d_N3_g3_walls_m2", "3d_N3_g1_walls", "3d_N5_g2_walls", "3d_N3_g1_walls_unstr",
@@ -225,12 +236,12 @@ def test_curved_fp32_bulk_against_oracle(orc, name):
     dt = o.max_dt(Uo)
     g.run(10, dt)
     g.status()
-    e_st = rel_l2(g.download_state(), o.run(Uo, 10, dt, rk=4))
-    print(f"{name}: FP32-bulk after 10 steps {np.array2string(e_st, precision=2)}")
-    tol = CURVED32 * tol32_step(ms["dim"])
-    if ms["geometry"].get("refine") and ps.get("model", 1) == 2:
-        tol[ms["dim"] + 1] *= MORTAR_M2_ENERGY
-    assert np.all(e_st < tol), e_st
+    sens, ref = _fp32_sensitivity(o, Uo, 10, dt)
+    e_st = rel_l2(g.download_state(), ref)
+    print(f"{name}: FP32-bulk after 10 steps {np.array2string(e_st, precision=2)}, "
+          f"oracle response to FP32-size noise {np.array2string(sens, precision=2)}")
+    tol = np.maximum(CURVED32 * tol32_step(ms["dim"]), 2.0 * sens)
+    assert np.all(e_st < tol), (e_st, tol)
 
 
 def test_curved_refusals():
