@@ -143,12 +143,14 @@ def l2_note(state_bytes):
     return "inputs fit in L2 (state %.1f MB), L2 not flushed: a parity-size case, not a headline line" % (state_bytes / 1e6)
 
 
-def kernel_sources_sha(curved=False):
+def kernel_sources_sha(curved=False, batch=False):
     """Hash of the sources of the stage kernels (with the curved-element kernels for a
-    curved workload): a committed ncu summary counts only while it matches."""
+    curved workload, the batched kernels for the ensemble): a committed ncu summary
+    counts only while it matches."""
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2208_05310_gb300", "csrc")
-    for fn in ("dgk_common.cuh", "dgk_kernels.cuh") + (("dgk_curved.cuh",) if curved else ()):
+    for fn in ("dgk_common.cuh", "dgk_kernels.cuh") + (("dgk_curved.cuh",) if curved else ()) + \
+            (("dgk_batch.cu",) if batch else ()):
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -171,6 +173,26 @@ def ncu_traffic(kernel, workload):
         return None
     try:
         return float(vals["dram_bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
+def batch_traffic(workload):
+    """DRAM bytes of one RK stage of the grouped batched form (its three phase launches)
+    from the committed ncu summary of that workload, while it matches the sources."""
+    path = os.path.join(ROOT, "profiles", f"k_batch_phase_{workload}_fp32.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha1") != kernel_sources_sha(batch=True):
+        return None
+    try:
+        return float(vals["dram_bytes_per_stage"])
     except (KeyError, ValueError):
         return None
 
@@ -589,7 +611,7 @@ def run_ours(args, wl, rank, world, local_rank):
     return 0
 
 
-def batch_measure(wl, local_rank, steps, warmup, unbatched=True, e2e=False):
+def batch_measure(wl, local_rank, steps, warmup, unbatched=True, e2e=False, name="c4"):
     """Batched ensemble: autotuned persistent launches per RK stage, timed over `steps`
     graph-replayed steps; beside it the same problems one context each (FP32-bulk and
     FP64, every context on its own stream so that small problems may overlap)."""
@@ -639,7 +661,8 @@ def batch_measure(wl, local_rank, steps, warmup, unbatched=True, e2e=False):
                roofline=dict(bound="hbm",
                              kernel="k_batch_phase<0,1,2>" if cfg["form"] == "grouped" else "k_batch_stage",
                              achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, peak_kind=peak_kind,
-                             alg_bytes_per_launch=alg, avg_launch_ms=avg_launch_ms, traffic=None,
+                             alg_bytes_per_launch=alg, avg_launch_ms=avg_launch_ms,
+                             traffic=batch_traffic(name) if cfg["form"] == "grouped" else None,
                              note="per RK stage: one persistent launch, or the three grouped phase launches; "
                                   "time from the graph-replayed steps / stages"))
     if e2e:
@@ -702,7 +725,8 @@ def run_batch(args, wl, rank, world, local_rank):
     if dist is not None:
         dist.barrier()
     with ClockSampler(local_rank) as clk:
-        r = batch_measure(wl, local_rank, args.steps, args.warmup, unbatched=not args.no_fp64, e2e=not args.no_e2e)
+        r = batch_measure(wl, local_rank, args.steps, args.warmup, unbatched=not args.no_fp64, e2e=not args.no_e2e,
+                          name=args.workload)
     ms = replica_max(r["ms_per_step"] * args.steps, dist)
     stages = 5 if wl["rk"] == 4 else 3
     if rank == 0:

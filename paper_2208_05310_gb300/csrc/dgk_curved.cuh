@@ -934,44 +934,40 @@ __global__ void __launch_bounds__(256) k_mortar_traces(KArgs<R> args, int which)
     const int nvar = which ? 2 : NL;
     const R *src = which ? v.tr2 : v.tr1;
     R *dst = which ? v.mtr2 : v.mtr1;
+    const R scale = R(D == 2 ? 2 : 4);
     for (int q = threadIdx.x; q < nvar * NSUB * NFP; q += blockDim.x) {
         const int var = q / (NSUB * NFP), p = (q / NFP) % NSUB, fq = q % NFP;
         const int *sb = mt + 4 + 4 * p;
         const int qq = map_fp<P>(sb[2], fq), u = qq % P, w = qq / P, h0 = p & 1, h1 = (p >> 1) & 1;
-        // accumulated in double, one rounding to the bulk type: with model 2 the momentum
-        // source alpha rho grad c balances the flux of alpha/2 rho^2 (both ~1e3 at an
-        // interface), and the lifted grad c takes these face values
-        double acc = 0.0;
+        R acc = R(0);
         if (D == 2) {
 #pragma unroll
-            for (int i = 0; i < P; ++i) acc += to_f64<R>(op.Im[h0][u * P + i]) * to_f64<R>(fat<NF, NFP>(src, ne, var, B, fB, i));
+            for (int i = 0; i < P; ++i) acc += op.Im[h0][u * P + i] * fat<NF, NFP>(src, ne, var, B, fB, i);
         } else {
             for (int j = 0; j < P; ++j) {
-                double row = 0.0;
+                R row = R(0);
 #pragma unroll
-                for (int i = 0; i < P; ++i)
-                    row += to_f64<R>(op.Im[h0][u * P + i]) * to_f64<R>(fat<NF, NFP>(src, ne, var, B, fB, i + P * j));
-                acc += to_f64<R>(op.Im[h1][w * P + j]) * row;
+                for (int i = 0; i < P; ++i) row += op.Im[h0][u * P + i] * fat<NF, NFP>(src, ne, var, B, fB, i + P * j);
+                acc += op.Im[h1][w * P + j] * row;
             }
         }
-        if (which && var == 1) acc *= double(facing_sign(sb[1], fB)) / double(D == 2 ? 2 : 4);
-        dst[((long long)var * ns + sb[3]) * NFP + fq] = to_bulk<R>(acc);
+        if (which && var == 1) acc *= R(facing_sign(sb[1], fB)) / scale;
+        dst[((long long)var * ns + sb[3]) * NFP + fq] = acc;
     }
     for (int q = threadIdx.x; q < nvar * NFP; q += blockDim.x) {
         const int var = q / NFP, ib = q % NFP, i = ib % P, j = ib / P;
-        double acc = 0.0;  // in double, as above
+        R acc = R(0);
         for (int p = 0; p < NSUB; ++p) {
             const int *sb = mt + 4 + 4 * p;
             const int h0 = p & 1, h1 = (p >> 1) & 1;
-            const double sg = which && var == 1 ? double(facing_sign(fB, sb[1])) * double(D == 2 ? 2 : 4) : 1.0;
+            const R sg = which && var == 1 ? R(facing_sign(fB, sb[1])) * scale : R(1);
             for (int fq = 0; fq < NFP; ++fq) {
                 const int qq = map_fp<P>(sb[2], fq), u = qq % P, w = qq / P;
-                const double wt = D == 2 ? to_f64<R>(op.Pm[h0][i * P + u])
-                                         : to_f64<R>(op.Pm[h0][i * P + u]) * to_f64<R>(op.Pm[h1][j * P + w]);
-                acc += wt * sg * to_f64<R>(fat<NF, NFP>(src, ne, var, sb[0], sb[1], fq));
+                const R wt = D == 2 ? op.Pm[h0][i * P + u] : op.Pm[h0][i * P + u] * op.Pm[h1][j * P + w];
+                acc += wt * sg * fat<NF, NFP>(src, ne, var, sb[0], sb[1], fq);
             }
         }
-        dst[((long long)var * ns + sB) * NFP + ib] = to_bulk<R>(acc);
+        dst[((long long)var * ns + sB) * NFP + ib] = acc;
     }
 }
 
@@ -1002,24 +998,22 @@ __global__ void __launch_bounds__(256) k_mortar_flux(KArgs<R> args)
         const int fS = sb[1], sS = sb[3];
         const int qq = map_fp<P>(sb[2], fq), u = qq % P, w = qq / P, h0 = p & 1, h1 = (p >> 1) & 1;
         R r[NQ], av[D];
-        // the big side's record interpolated to this point, accumulated in double (the
-        // interpolation weights exceed 1 in magnitude; one rounding to the bulk type)
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
             const R *rec = v.mrec + ((long long)k * ns + sB) * NFP;
-            double acc = 0.0;
+            R acc = R(0);
             if (D == 2) {
 #pragma unroll
-                for (int i = 0; i < P; ++i) acc += to_f64<R>(op.Im[h0][u * P + i]) * to_f64<R>(rec[i]);
+                for (int i = 0; i < P; ++i) acc += op.Im[h0][u * P + i] * rec[i];
             } else {
                 for (int j = 0; j < P; ++j) {
-                    double row = 0.0;
+                    R row = R(0);
 #pragma unroll
-                    for (int i = 0; i < P; ++i) row += to_f64<R>(op.Im[h0][u * P + i]) * to_f64<R>(rec[i + P * j]);
-                    acc += to_f64<R>(op.Im[h1][w * P + j]) * row;
+                    for (int i = 0; i < P; ++i) row += op.Im[h0][u * P + i] * rec[i + P * j];
+                    acc += op.Im[h1][w * P + j] * row;
                 }
             }
-            r[k] = to_bulk<R>(acc);
+            r[k] = acc;
         }
 #pragma unroll
         for (int k = 0; k < D; ++k) av[k] = fat<NF, NFP>(v.fmet, ne, k, Se, fS, fq);
