@@ -497,7 +497,7 @@ struct K2CSmem {
     static constexpr int JF = D * S::NF * S::NFP;  // face metrics [k][f][fp]
     static constexpr int X1 = S::NL * S::NP + S::NF * S::NL * S::NFP;                // prims, q*/jumps
     static constexpr int X2 = S::NP + 2 * S::NF * S::NFP + D * S::NP + D * D * S::NP;  // T, jumps, D T, D grad c
-    static constexpr int X4 = 2 * S::NV * S::NP;                                       // volume: F, acc
+    static constexpr int X4 = D * S::NV * S::NP;                                       // volume: F and its integral per direction
     static constexpr int SR = S::NF * FaceRecC<D>::NQ * S::NFP;                        // traced records
     static constexpr int XN = X4 > SR ? X4 : SR;                                       // nodal U, lap (sN)
     static constexpr int X3 = XN + (S::NV + 1) * S::NP;
@@ -792,38 +792,44 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
     }
     __syncthreads();  // pass-2 buffers dead before the volume buffers reuse sX
 
-    // ---- volume integral of the contravariant fluxes: acc_i = sum_dir sum_l Dhat_il (F.Ja^dir)_l
-    R *sF = sX, *sAcc = sX + NV * NP;
+    // ---- volume integral of the contravariant fluxes: acc_i = sum_dir sum_l Dhat_il (F.Ja^dir)_l;
+    //      the fluxes of all directions first, then every line contracted in place
+    R *sF = sX;  // [D][NV][NP]
+    if (t.valid) {
 #pragma unroll
-    for (int dir = 0; dir < D; ++dir) {
-        if (t.valid) {
+        for (int dir = 0; dir < D; ++dir) {
             R F[NV];
             flux_vec<D, R>(a.pr, Ja[dir], rho, m, u, E, c, pf, du, gT, gc, lap, F);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) sF[v * NP + n] = F[v];
+            for (int v = 0; v < NV; ++v) sF[(dir * NV + v) * NP + n] = F[v];
         }
-        __syncthreads();
-        if (t.valid) {
+    }
+    __syncthreads();
+    if (t.valid) {
+#pragma unroll
+        for (int dir = 0; dir < D; ++dir) {
             const int stride = line_stride<P>(dir);
             for (int q = n; q < NV * NFP; q += NP) {
-                const int v = q / NFP, line = q % NFP;
+                int v, line;
+                line_task<NV, NFP>(dir, q, v, line);
                 const int base = line_base<P>(line, dir);
                 R x[P], y[P];
-                load_line<P, R>(sF + v * NP, base, stride, x);
+                load_line_d<P, R, M::per_elem>(dir, sF + (dir * NV + v) * NP, base, stride, x);
                 dhat_line<P, R>(a.op, x, R(1), y);
-                if (dir > 0) {
-#pragma unroll
-                    for (int l = 0; l < P; ++l) y[l] += sAcc[v * NP + base + l * stride];
-                }
-                store_line<P, R>(sAcc + v * NP, base, stride, y);
+                store_line_d<P, R, M::per_elem>(dir, sF + (dir * NV + v) * NP, base, stride, y);
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
     R *sN = sX + M::XN;
     if (t.valid) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) a.v.Utv[((long long)v * ne + t.e) * NP + n] = S_[v] - iJ * sAcc[v * NP + n];
+        for (int v = 0; v < NV; ++v) {
+            R acc = sF[v * NP + n];
+#pragma unroll
+            for (int d = 1; d < D; ++d) acc = sF[(d * NV + v) * NP + n] + acc;
+            nat<NP>(a.v.Utv, ne, v, t.e, n) = S_[v] - iJ * acc;
+        }
         sN[n] = rho;
 #pragma unroll
         for (int k = 0; k < D; ++k) sN[(1 + k) * NP + n] = m[k];
