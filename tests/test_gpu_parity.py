@@ -274,8 +274,8 @@ def test_sliding_wall_refusals():
 def test_box_mesh_and_call_refusals():
     """Input checks of the C ABI (no kernel runs for a refused call): polynomial degree and
     dimension ranges, walls on every non-periodic face, wall parameters, wall
-    temperatures with saturation states, the element-count limit (refused before any
-    allocation), call order, array sizes and step sizes."""
+    temperatures with saturation states, the element-count and plane-size limits (refused
+    before any allocation), call order, array sizes and step sizes."""
     from paper_2208_05310_gb300 import dgk, inputs
 
     def ctx():
@@ -300,6 +300,10 @@ def test_box_mesh_and_call_refusals():
         ctx().mesh_box(2, 3, [2, 2, 1], [0, 0, 0], [1, 1, 1], [1, 0, 1], {2: (1.2, 90.0), 3: (0.85, 90.0)})
     with pytest.raises(dgk.DgkError):  # 2^33 elements
         ctx().mesh_box(3, 3, [2 ** 16, 2 ** 16, 2], [0, 0, 0], [1, 1, 1], [1, 1, 1])
+    # fewer than 2^32 elements, but a node plane of 2^25 * 216 > 2^32 values: the kernels
+    # index inside a plane with 32 bits
+    with pytest.raises(dgk.DgkError, match="2\\^32 - 1 nodes"):
+        ctx().mesh_box(3, 5, [1024, 1024, 32], [0, 0, 0], [1, 1, 1], [1, 1, 1])
     with pytest.raises(dgk.DgkError):  # an empty extent
         ctx().mesh_box(2, 3, [2, 2, 1], [0, 0, 0], [1, 0, 1], [1, 1, 1])
     g = ctx()
