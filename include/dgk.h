@@ -221,16 +221,16 @@ int dgk_rk_step(dgk_ctx *ctx, double dt);
    NULL: no samples.  Device buffers for the samples are allocated on first use. */
 int dgk_run(dgk_ctx *ctx, int nsteps, double dt, int diag_every, double *diag_out);
 /* Independent problems through host memory, pipelined: for i = 0..nitems-1 the state
-   becomes in[i] (as dgk_upload_state: the RK register is reset), advances nsteps RK
-   steps of size dt (as dgk_run), and is read into out[i].  in[i] and out[i] are host
-   pointers of count = nvar*nelem*np doubles each (page-locked memory lets the copies
-   run asynchronously; the same pointer may appear in several entries, and an out[i]
-   may alias an in[j] with j <= i only if the caller does not need in[j] afterwards:
-   out[i] is written while item i+1 is copied in).  The copy of item i+1 into the
-   device and of item i-1 out of it run on two copy streams of the context, overlapped
-   with the steps of item i; two device staging buffers of count doubles are allocated
-   on the first call and kept.  Blocks until out[nitems-1] is written; afterwards the
-   context holds the last item's state.  Errors: DGK_ERR_ARG for null arrays or
+   becomes in[i] (as dgk_upload_state), advances nsteps RK steps of size dt (as dgk_run),
+   and is read into out[i].  in[i] and out[i] are host pointers of count =
+   nvar*nelem*np doubles each (page-locked memory lets the copies run asynchronously;
+   the same pointer may appear in several entries, and an out[i] may alias an in[j] with
+   j <= i only if the caller does not need in[j] afterwards: out[i] is written while
+   item i+1 is copied in).  Item i steps in device buffer i mod 3 while item i+1 is
+   copied into the next buffer and item i-1 out of the previous one, on two copy streams
+   of the context; the three buffers of count doubles and a captured step graph per
+   buffer are made on the first call and kept.  Blocks until out[nitems-1] is written;
+   afterwards the context holds the last item's state.  Errors: DGK_ERR_ARG for null arrays or
    entries, a wrong count, nitems < 0, nsteps < 0 or dt <= 0; device-detected errors
    are latched as for dgk_run (check dgk_status()). */
 int dgk_run_host(dgk_ctx *ctx, const double *const *in, double *const *out, int nitems, size_t count, int nsteps,

@@ -328,11 +328,13 @@ struct dgk_ctx {
     double coef_h[12] = {0};  // A_0..A_4, B_0..B_4, dt, number of stages
     bool coef_valid = false;
     cudaGraphExec_t graph = nullptr;
-    // dgk_run_host: staging buffers, copy streams and their events
-    double *stage_in = nullptr, *stage_out = nullptr;
+    // dgk_run_host: three item buffers (item i steps in hbuf[i % 3] while item i+1 is
+    // copied in and item i-1 out), a captured step graph per buffer, copy streams and events
+    double *hbuf[3] = {nullptr, nullptr, nullptr};
     size_t stage_count = 0;
+    cudaGraphExec_t hgraph[3] = {nullptr, nullptr, nullptr};
     cudaStream_t s_in = nullptr, s_out = nullptr;
-    cudaEvent_t ev_in_ready = nullptr, ev_in_free = nullptr, ev_out_ready = nullptr, ev_out_free = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_in_ready[3] = {}, ev_done[3] = {}, ev_out_done[3] = {};
     bool timing = false;
     std::vector<cudaEvent_t> events;
     size_t events_used = 0;
@@ -373,9 +375,12 @@ void free_buffers(dgk_ctx *c)
     c->graph = nullptr;
     if (c->diag_graph) cudaGraphExecDestroy(c->diag_graph);
     c->diag_graph = nullptr;
-    if (c->stage_in) cudaFree(c->stage_in);
-    if (c->stage_out) cudaFree(c->stage_out);
-    c->stage_in = c->stage_out = nullptr;
+    for (int k = 0; k < 3; ++k) {
+        if (c->hgraph[k]) cudaGraphExecDestroy(c->hgraph[k]);
+        c->hgraph[k] = nullptr;
+        if (c->hbuf[k]) cudaFree(c->hbuf[k]);
+        c->hbuf[k] = nullptr;
+    }
     c->stage_count = 0;
 }
 
@@ -385,6 +390,10 @@ void drop_graph(dgk_ctx *c)
     c->graph = nullptr;
     if (c->diag_graph) cudaGraphExecDestroy(c->diag_graph);
     c->diag_graph = nullptr;
+    for (int k = 0; k < 3; ++k) {
+        if (c->hgraph[k]) cudaGraphExecDestroy(c->hgraph[k]);
+        c->hgraph[k] = nullptr;
+    }
 }
 
 template <typename R>
@@ -751,8 +760,10 @@ void dgk_destroy(dgk_ctx *c)
     if (c->s_out) cudaStreamSynchronize(c->s_out);
     free_buffers(c);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
-    for (cudaEvent_t e : {c->ev_in_ready, c->ev_in_free, c->ev_out_ready, c->ev_out_free})
-        if (e) cudaEventDestroy(e);
+    if (c->ev_start) cudaEventDestroy(c->ev_start);
+    for (int k = 0; k < 3; ++k)
+        for (cudaEvent_t e : {c->ev_in_ready[k], c->ev_done[k], c->ev_out_done[k]})
+            if (e) cudaEventDestroy(e);
     if (c->s_in) cudaStreamDestroy(c->s_in);
     if (c->s_out) cudaStreamDestroy(c->s_out);
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -1231,6 +1242,13 @@ int dgk_run(dgk_ctx *c, int nsteps, double dt, int diag_every, double *diag_out)
     return DGK_OK;
 }
 
+// the state array the kernels of both argument blocks work on
+static void set_state_ptr(dgk_ctx *c, double *U)
+{
+    c->a64.v.U = U;
+    c->a32.v.U = U;
+}
+
 int dgk_run_host(dgk_ctx *c, const double *const *in, double *const *out, int nitems, size_t count, int nsteps,
                  double dt)
 {
@@ -1243,54 +1261,92 @@ int dgk_run_host(dgk_ctx *c, const double *const *in, double *const *out, int ni
         if (!in[i] || !out[i]) return fail(DGK_ERR_ARG, "null host pointer");
     if (nitems == 0) return DGK_OK;
     DGK_CUDA(cudaSetDevice(c->device));
+    if ((rc = set_coef(c, dt))) return rc;
     if (c->stage_count != nstate) {
-        if (c->stage_in) cudaFree(c->stage_in);
-        if (c->stage_out) cudaFree(c->stage_out);
-        c->stage_in = c->stage_out = nullptr;
+        for (int k = 0; k < 3; ++k) {
+            if (c->hgraph[k]) cudaGraphExecDestroy(c->hgraph[k]);
+            c->hgraph[k] = nullptr;
+            if (c->hbuf[k]) cudaFree(c->hbuf[k]);
+            c->hbuf[k] = nullptr;
+        }
         c->stage_count = 0;
-        DGK_CUDA(cudaMalloc(&c->stage_in, nstate * sizeof(double)));
-        DGK_CUDA(cudaMalloc(&c->stage_out, nstate * sizeof(double)));
+        for (int k = 0; k < 3; ++k) DGK_CUDA(cudaMalloc(&c->hbuf[k], nstate * sizeof(double)));
         c->stage_count = nstate;
     }
     for (cudaStream_t *st : {&c->s_in, &c->s_out})
         if (!*st) DGK_CUDA(cudaStreamCreateWithFlags(st, cudaStreamNonBlocking));
-    for (cudaEvent_t *e : {&c->ev_in_ready, &c->ev_in_free, &c->ev_out_ready, &c->ev_out_free})
-        if (!*e) DGK_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    if (!c->ev_start) DGK_CUDA(cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming));
+    for (int k = 0; k < 3; ++k)
+        for (cudaEvent_t *e : {&c->ev_in_ready[k], &c->ev_done[k], &c->ev_out_done[k]})
+            if (!*e) DGK_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     const size_t bytes = nstate * sizeof(double);
-    // the pipeline; on an error it stops enqueueing, and the streams are drained below so
-    // that no copy touches the caller's buffers after the return
-    auto pipeline = [&]() -> int {
-        // the copy streams start after the work already queued on the context's stream
-        DGK_CUDA(cudaEventRecord(c->ev_in_free, c->stream));
-        DGK_CUDA(cudaEventRecord(c->ev_out_free, c->stream));
-        DGK_CUDA(cudaStreamWaitEvent(c->s_in, c->ev_in_free, 0));
-        DGK_CUDA(cudaStreamWaitEvent(c->s_out, c->ev_out_free, 0));
-        DGK_CUDA(cudaMemcpyAsync(c->stage_in, in[0], bytes, cudaMemcpyHostToDevice, c->s_in));
-        DGK_CUDA(cudaEventRecord(c->ev_in_ready, c->s_in));
-        for (int i = 0; i < nitems; ++i) {
-            // item i in: staging -> state (the staging buffer is then free for item i+1)
-            DGK_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in_ready, 0));
-            DGK_CUDA(cudaMemcpyAsync(c->U, c->stage_in, bytes, cudaMemcpyDeviceToDevice, c->stream));
-            DGK_CUDA(cudaEventRecord(c->ev_in_free, c->stream));
-            int r = after_state_change(c);
-            if (r) return r;
-            if (i + 1 < nitems) {
-                DGK_CUDA(cudaStreamWaitEvent(c->s_in, c->ev_in_free, 0));
-                DGK_CUDA(cudaMemcpyAsync(c->stage_in, in[i + 1], bytes, cudaMemcpyHostToDevice, c->s_in));
-                DGK_CUDA(cudaEventRecord(c->ev_in_ready, c->s_in));
+    const int nbuf = nitems < 3 ? nitems : 3;
+    // one captured step graph per item buffer (the arrays are kernel parameters)
+    if (nsteps > 0 && !c->timing) {
+        for (int k = 0; k < nbuf; ++k) {
+            if (c->hgraph[k]) continue;
+            set_state_ptr(c, c->hbuf[k]);
+            cudaGraph_t g;
+            cudaError_t err = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+            if (err == cudaSuccess) {
+                rc = launch_step(c, false);
+                err = cudaStreamEndCapture(c->stream, &g);
             }
-            if ((r = dgk_run(c, nsteps, dt, 0, nullptr))) return r;
-            // item i out: state -> staging once the previous item has left it, then to the host
-            DGK_CUDA(cudaStreamWaitEvent(c->stream, c->ev_out_free, 0));
-            DGK_CUDA(cudaMemcpyAsync(c->stage_out, c->U, bytes, cudaMemcpyDeviceToDevice, c->stream));
-            DGK_CUDA(cudaEventRecord(c->ev_out_ready, c->stream));
-            DGK_CUDA(cudaStreamWaitEvent(c->s_out, c->ev_out_ready, 0));
-            DGK_CUDA(cudaMemcpyAsync(out[i], c->stage_out, bytes, cudaMemcpyDeviceToHost, c->s_out));
-            DGK_CUDA(cudaEventRecord(c->ev_out_free, c->s_out));
+            set_state_ptr(c, c->U);
+            if (rc) return rc;
+            if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(err));
+            err = cudaGraphInstantiate(&c->hgraph[k], g, 0);
+            cudaGraphDestroy(g);
+            if (err != cudaSuccess) {
+                c->hgraph[k] = nullptr;
+                return fail(DGK_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(err));
+            }
         }
+    }
+    // The pipeline: item i steps in buffer i % 3 on the context's stream while item i+1 is
+    // copied in on s_in and item i-1 out on s_out; a buffer takes a new item once its
+    // previous item has left it.  No device-to-device copies: the step graphs work on the
+    // buffers themselves.  On an error it stops enqueueing; the streams are drained below
+    // so that no copy touches the caller's buffers after the return.
+    auto pipeline = [&]() -> int {
+        DGK_CUDA(cudaEventRecord(c->ev_start, c->stream));  // after the work already queued
+        DGK_CUDA(cudaStreamWaitEvent(c->s_in, c->ev_start, 0));
+        DGK_CUDA(cudaStreamWaitEvent(c->s_out, c->ev_start, 0));
+        DGK_CUDA(cudaMemcpyAsync(c->hbuf[0], in[0], bytes, cudaMemcpyHostToDevice, c->s_in));
+        DGK_CUDA(cudaEventRecord(c->ev_in_ready[0], c->s_in));
+        for (int i = 0; i < nitems; ++i) {
+            const int b = i % 3;
+            if (i + 1 < nitems) {
+                const int nb = (i + 1) % 3;
+                if (i + 1 >= 3) DGK_CUDA(cudaStreamWaitEvent(c->s_in, c->ev_out_done[nb], 0));
+                DGK_CUDA(cudaMemcpyAsync(c->hbuf[nb], in[i + 1], bytes, cudaMemcpyHostToDevice, c->s_in));
+                DGK_CUDA(cudaEventRecord(c->ev_in_ready[nb], c->s_in));
+            }
+            DGK_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in_ready[b], 0));
+            set_state_ptr(c, c->hbuf[b]);
+            // the new state's traces (as dgk_upload_state; the first RK stage of both
+            // schemes does not read the RK register, so it needs no reset)
+            cudaError_t err = run_traces(c);
+            if (err != cudaSuccess) return fail(DGK_ERR_CUDA, std::string("trace kernel: ") + cudaGetErrorString(err));
+            for (int st = 0; st < nsteps; ++st) {
+                if (c->timing) {
+                    int r = launch_step(c, true);
+                    if (r) return r;
+                } else {
+                    DGK_CUDA(cudaGraphLaunch(c->hgraph[b], c->stream));
+                }
+            }
+            DGK_CUDA(cudaEventRecord(c->ev_done[b], c->stream));
+            DGK_CUDA(cudaStreamWaitEvent(c->s_out, c->ev_done[b], 0));
+            DGK_CUDA(cudaMemcpyAsync(out[i], c->hbuf[b], bytes, cudaMemcpyDeviceToHost, c->s_out));
+            DGK_CUDA(cudaEventRecord(c->ev_out_done[b], c->s_out));
+        }
+        // the context keeps the last item's state
+        DGK_CUDA(cudaMemcpyAsync(c->U, c->hbuf[(nitems - 1) % 3], bytes, cudaMemcpyDeviceToDevice, c->stream));
         return DGK_OK;
     };
     rc = pipeline();
+    set_state_ptr(c, c->U);
     const cudaError_t e1 = cudaStreamSynchronize(c->s_in), e2 = cudaStreamSynchronize(c->s_out),
                       e3 = cudaStreamSynchronize(c->stream);
     if (rc) return rc;

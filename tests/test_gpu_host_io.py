@@ -24,7 +24,7 @@ def _inputs(g, n):
 def test_run_host_equals_sequential(precision):
     import torch
     g = dgk_context(MS, PAPER_PARAMS, precision=precision)
-    ins = _inputs(g, 4)
+    ins = _inputs(g, 7)  # every one of the three item buffers takes two or three items
     dt = 0.5 * g.max_dt()
     ref = []
     for u in ins:
