@@ -539,6 +539,9 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
     R *sGT = sG + M::G, *sJf = sGT + M::GT, *sX = sJf + M::JF;
     const long long ne = a.v.g.ne;
     const int n = t.n;
+    // one face point per thread when NF NFP = NP (3D, N = 5): its neighbour once
+    int fo0 = 0, o0 = 0, w0 = 0;
+    const long long b0 = (NF * NFP == NP && t.valid) ? face_nbr<D, N, R>(a.v, t, n / NFP, fo0, o0, w0) : -1;
 
     // ---- pass 1 inputs: prims (rho, u, c), central face values (walls: rho*, c* one-sided,
     //      u* = 0), face metrics
@@ -552,8 +555,8 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
         sQ[(D + 1) * NP + n] = ns.c;
         for (int q = n; q < NF * NFP; q += NP) {
             const int f = q / NFP, fp = q % NFP;
-            int fo, o, w;
-            const long long b = face_nbr<D, N, R>(a.v, t, f, fo, o, w);
+            int fo = fo0, o = o0, w = w0;
+            const long long b = NF * NFP == NP ? b0 : face_nbr<D, N, R>(a.v, t, f, fo, o, w);
             // one branch per kind of face, so that each point issues only its own loads
             if (b >= 0) {
                 const int fq = map_fp<P>(o, fp);
@@ -598,8 +601,8 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
         pT[j] = pD[j] = R(0);
         if (t.valid && q < NF * NFP) {
             const int f = q / NFP, fp = q % NFP, side = f & 1;
-            int fo, o, w;
-            const long long b = face_nbr<D, N, R>(a.v, t, f, fo, o, w);
+            int fo = fo0, o = o0, w = w0;
+            const long long b = NF * NFP == NP ? b0 : face_nbr<D, N, R>(a.v, t, f, fo, o, w);
             const R ownT = fat<NF, NFP>(a.v.tr2, ne, 0, t.e, f, fp);
             const R ownD = fat<NF, NFP>(a.v.tr2, ne, 1, t.e, f, fp);
             if (b <= kMortar) {
@@ -864,8 +867,8 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
         const long long st = ne * NF * NFP;
         for (int q = n; q < NF * NFP; q += NP) {
             const int f = q / NFP, fp = q % NFP;
-            int f_nb, o_nb, w;
-            const long long bn = face_nbr<D, N, R>(a.v, t, f, f_nb, o_nb, w);
+            int f_nb = fo0, o_nb = o0, w = w0;
+            const long long bn = NF * NFP == NP ? b0 : face_nbr<D, N, R>(a.v, t, f, f_nb, o_nb, w);
             const bool wall = bn < 0 && bn > kMortar;
             R r[NQ], av[D];
 #pragma unroll

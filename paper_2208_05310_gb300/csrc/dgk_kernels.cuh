@@ -896,6 +896,8 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
     using M = K2Smem<D, N, R, EB>;
     constexpr int P = S::P, NP = S::NP, NFP = S::NFP, NF = S::NF, NL = S::NL, NV = S::NV;
         const Slot<D, N, EB> t(a.v.g, blk);
+    // one face point per thread when NF NFP = NP (3D, N = 5): its neighbour once
+    const long long bn = (NF * NFP == NP && t.valid) ? t.nbr(a.v.g, t.n / NFP) : -1;
     R *sG = reinterpret_cast<R *>(smraw) + (size_t)t.le * M::per_elem;
     R *sGT = sG + M::G, *sX = sGT + M::GT;
     const long long ne = a.v.g.ne;
@@ -912,7 +914,7 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
         sQ[(D + 1) * NP + n] = ns.c;
         for (int q = n; q < NF * NFP; q += NP) {
             const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
-            const long long b = t.nbr(a.v.g, f);
+            const long long b = NF * NFP == NP ? bn : t.nbr(a.v.g, f);
             // two branches, so that interior points issue no loads of wall constants (a
             // select over both would cost 13% of the kernel)
             if (b >= 0) {
@@ -943,7 +945,7 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
         pT[j] = pD[j] = R(0);
         if (t.valid && q < NF * NFP) {
             const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
-            const long long b = t.nbr(a.v.g, f);
+            const long long b = NF * NFP == NP ? bn : t.nbr(a.v.g, f);
             const R ownT = fat<NF, NFP>(a.v.tr2, ne, 0, t.e, f, fp);
             const R ownD = fat<NF, NFP>(a.v.tr2, ne, 1, t.e, f, fp);
             if (b >= 0) {
@@ -1001,7 +1003,7 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
                 sTs[q] = pT[j];
                 R dD = R(0);
                 const int f = q / NFP;
-                if (a.v.wr.kind[f] == 2 && a.v.wr.g1gK[f] != R(0) && t.nbr(a.v.g, f) < 0) {
+                if (a.v.wr.kind[f] == 2 && a.v.wr.g1gK[f] != R(0) && (NF * NFP == NP ? bn : t.nbr(a.v.g, f)) < 0) {
                     // Eq. bc_contactangle_alpha: + (gamma_1/gamma_K) div u- at the face point
                     const int dir = f >> 1, fp = q % NFP;
                     const int base = line_base<P>(fp, dir), stride = line_stride<P>(dir);
@@ -1153,7 +1155,7 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
         const long long st = ne * NF * NFP;
         for (int q = n; q < NF * NFP; q += NP) {
             const int f = q / NFP, fp = q % NFP, dir = f >> 1;
-            const bool wall = t.nbr(a.v.g, f) < 0;
+            const bool wall = (NF * NFP == NP ? bn : t.nbr(a.v.g, f)) < 0;
             R r[NQ];
 #pragma unroll
             for (int k = 0; k < NQ; ++k) r[k] = sR[(f * NQ + k) * NFP + fp];
