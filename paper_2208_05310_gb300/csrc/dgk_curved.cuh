@@ -332,7 +332,8 @@ struct CLiftC {
     static constexpr int smem_per_elem = S::NP + S::NF * S::NFP + D * S::NP + D * S::NP + D * S::NF * S::NFP + S::NP;
     // c, c*/jumps, reference derivatives, grad c, face metrics, T
 
-    __device__ static void run(const Ctx<R> &a, const Slot<D, N> &t, R c, R *sC, R *sCs, R *sR, R *sJf, R *sDc)
+    __device__ static void run(const Ctx<R> &a, const Slot<D, N> &t, R c, R *sC, R *sCs, R *sR, R *sJf, R *sDc,
+                               const R (*Jpre)[D] = nullptr, R iJpre = R(0))
     {
         constexpr int P = S::P, NP = S::NP, NF = S::NF, NFP = S::NFP;
         const long long ne = a.v.g.ne;
@@ -370,9 +371,9 @@ struct CLiftC {
             for (int dir = 0; dir < D; ++dir) {
                 r[dir] = sR[dir * NP + t.n];
 #pragma unroll
-                for (int k = 0; k < D; ++k) Ja[dir][k] = metric<NP, R>(a.v, dir * D + k, t.e, t.n);
+                for (int k = 0; k < D; ++k) Ja[dir][k] = Jpre ? Jpre[dir][k] : metric<NP, R>(a.v, dir * D + k, t.e, t.n);
             }
-            chain_gradient<D, N, R>(a, t.n, Ja, metric<NP, R>(a.v, D * D, t.e, t.n), r, sCs, NFP, sJf, gc);
+            chain_gradient<D, N, R>(a, t.n, Ja, Jpre ? iJpre : metric<NP, R>(a.v, D * D, t.e, t.n), r, sCs, NFP, sJf, gc);
 #pragma unroll
             for (int k = 0; k < D; ++k) sDc[k * NP + t.n] = gc[k];
         }
@@ -394,9 +395,19 @@ __device__ __forceinline__ void lift1c_body(const Ctx<R> &a, long long blk, unsi
     const Slot<D, N> t(a.v.g, blk);
     R *sC = reinterpret_cast<R *>(smraw) + (size_t)t.le * L::smem_per_elem;
     R *sCs = sC + NP, *sR = sCs + NF * NFP, *sDc = sR + D * NP, *sJf = sDc + D * NP, *sT = sJf + D * NF * NFP;
+    // the node's metric terms are loaded with the state: their latency then overlaps the
+    // face values and the line derivatives instead of stalling the chain rule
     NodeState<D, R> q;
-    if (t.valid) q.load(a.v, t.e, t.n, NP);
-    L::run(a, t, q.c, sC, sCs, sR, sJf, sDc);
+    R Jm[D][D], iJm = R(0);
+    if (t.valid) {
+        q.load(a.v, t.e, t.n, NP);
+#pragma unroll
+        for (int dir = 0; dir < D; ++dir)
+#pragma unroll
+            for (int k = 0; k < D; ++k) Jm[dir][k] = metric<NP, R>(a.v, dir * D + k, t.e, t.n);
+        iJm = metric<NP, R>(a.v, D * D, t.e, t.n);
+    }
+    L::run(a, t, q.c, sC, sCs, sR, sJf, sDc, Jm, iJm);
     if (t.valid) {
         R gc[D];
 #pragma unroll
@@ -542,6 +553,15 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
     // one face point per thread when NF NFP = NP (3D, N = 5): its neighbour once
     int fo0 = 0, o0 = 0, w0 = 0;
     const long long b0 = (NF * NFP == NP && t.valid) ? face_nbr<D, N, R>(a.v, t, n / NFP, fo0, o0, w0) : -1;
+    // the node's metric terms, loaded first so that their latency overlaps pass 1
+    R Ja[D][D], iJ = R(0);
+    if (t.valid) {
+#pragma unroll
+        for (int dir = 0; dir < D; ++dir)
+#pragma unroll
+            for (int k = 0; k < D; ++k) Ja[dir][k] = metric<NP, R>(a.v, dir * D + k, t.e, n);
+        iJ = metric<NP, R>(a.v, D * D, t.e, n);
+    }
 
     // ---- pass 1 inputs: prims (rho, u, c), central face values (walls: rho*, c* one-sided,
     //      u* = 0), face metrics
@@ -656,16 +676,10 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
     }
     __syncthreads();
 
-    // ---- node: metric terms, physical gradients, temperature
-    R Ja[D][D], iJ = R(0);
+    // ---- node: physical gradients, temperature
     R g[D][D + 2];
     R T = R(0);
     if (t.valid) {
-#pragma unroll
-        for (int dir = 0; dir < D; ++dir)
-#pragma unroll
-            for (int k = 0; k < D; ++k) Ja[dir][k] = metric<NP, R>(a.v, dir * D + k, t.e, n);
-        iJ = metric<NP, R>(a.v, D * D, t.e, n);
 #pragma unroll
         for (int v = 0; v < NL; ++v) {
             R r[D], gv[D];
