@@ -439,13 +439,13 @@ struct CLift {
         constexpr int P = S::P, NP = S::NP, NF = S::NF, NFP = S::NFP;
         const long long ne = a.v.g.ne;
         if (t.valid) {
-            sC[t.n] = c;
             for (int q = t.n; q < NF * NFP; q += NP) {
                 const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
                 const R own = fat<NF, NFP>(a.v.tr1, ne, D + 1, t.e, f, fp);
                 const long long b = t.nbr(a.v.g, f);
                 sCs[q] = b >= 0 ? R(0.5) * (own + fat<NF, NFP>(a.v.tr1, ne, D + 1, b, 2 * dir + 1 - side, fp)) : own;
             }
+            sC[t.n] = c;  // after the face loads, so that c's own load is not waited for first
         }
         __syncthreads();
         if (t.valid) {
@@ -908,20 +908,20 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
     NodeState<D, R> ns;
     if (t.valid) {
         ns.load(a.v, t.e, n, NP);
-        sQ[n] = ns.rho;
-#pragma unroll
-        for (int k = 0; k < D; ++k) sQ[(1 + k) * NP + n] = ns.m[k] * ns.irho;
-        sQ[(D + 1) * NP + n] = ns.c;
         for (int q = n; q < NF * NFP; q += NP) {
             const int f = q / NFP, fp = q % NFP, dir = f >> 1, side = f & 1;
             const long long b = NF * NFP == NP ? bn : t.nbr(a.v.g, f);
             // two branches, so that interior points issue no loads of wall constants (a
             // select over both would cost 13% of the kernel)
             if (b >= 0) {
+                R own[NL], nbv[NL];  // all loads issued before the first use
 #pragma unroll
-                for (int v = 0; v < NL; ++v)
-                    sQs[(f * NL + v) * NFP + fp] = R(0.5) * (fat<NF, NFP>(a.v.tr1, ne, v, t.e, f, fp) +
-                                                             fat<NF, NFP>(a.v.tr1, ne, v, b, 2 * dir + 1 - side, fp));
+                for (int v = 0; v < NL; ++v) {
+                    own[v] = fat<NF, NFP>(a.v.tr1, ne, v, t.e, f, fp);
+                    nbv[v] = fat<NF, NFP>(a.v.tr1, ne, v, b, 2 * dir + 1 - side, fp);
+                }
+#pragma unroll
+                for (int v = 0; v < NL; ++v) sQs[(f * NL + v) * NFP + fp] = R(0.5) * (own[v] + nbv[v]);
             } else {
                 // walls: u* = the wall's velocity (no slip; zero unless the wall slides), or
                 // the fluid's tangential velocity (Navier slip)
@@ -934,6 +934,10 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
                 }
             }
         }
+        sQ[n] = ns.rho;
+#pragma unroll
+        for (int k = 0; k < D; ++k) sQ[(1 + k) * NP + n] = ns.m[k] * ns.irho;
+        sQ[(D + 1) * NP + n] = ns.c;
     }
     // pass-2 central face values (T*, and dc/dx_dir* for the lap c lifting; at walls T_wall
     // and the contact-angle gradient), loaded now so that their latency overlaps pass 1
