@@ -338,7 +338,6 @@ struct CLiftC {
         constexpr int P = S::P, NP = S::NP, NF = S::NF, NFP = S::NFP;
         const long long ne = a.v.g.ne;
         if (t.valid) {
-            sC[t.n] = c;
             for (int q = t.n; q < NF * NFP; q += NP) {
                 const int f = q / NFP, fp = q % NFP;
                 const R own = fat<NF, NFP>(a.v.tr1, ne, D + 1, t.e, f, fp);
@@ -349,6 +348,7 @@ struct CLiftC {
                 else sCs[q] = own;
             }
             stage_face_metrics<D, N, R>(a, t, sJf);
+            sC[t.n] = c;  // after the face loads, so that c's own load is not waited for first
         }
         __syncthreads();
         if (t.valid) {
@@ -569,10 +569,6 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
     NodeState<D, R> ns;
     if (t.valid) {
         ns.load(a.v, t.e, n, NP);
-        sQ[n] = ns.rho;
-#pragma unroll
-        for (int k = 0; k < D; ++k) sQ[(1 + k) * NP + n] = ns.m[k] * ns.irho;
-        sQ[(D + 1) * NP + n] = ns.c;
         for (int q = n; q < NF * NFP; q += NP) {
             const int f = q / NFP, fp = q % NFP;
             int fo = fo0, o = o0, w = w0;
@@ -580,10 +576,14 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
             // one branch per kind of face, so that each point issues only its own loads
             if (b >= 0) {
                 const int fq = map_fp<P>(o, fp);
+                R own[NL], nbv[NL];  // all loads issued before the first use
 #pragma unroll
-                for (int v = 0; v < NL; ++v)
-                    sQs[(f * NL + v) * NFP + fp] =
-                        R(0.5) * (fat<NF, NFP>(a.v.tr1, ne, v, t.e, f, fp) + fat<NF, NFP>(a.v.tr1, ne, v, b, fo, fq));
+                for (int v = 0; v < NL; ++v) {
+                    own[v] = fat<NF, NFP>(a.v.tr1, ne, v, t.e, f, fp);
+                    nbv[v] = fat<NF, NFP>(a.v.tr1, ne, v, b, fo, fq);
+                }
+#pragma unroll
+                for (int v = 0; v < NL; ++v) sQs[(f * NL + v) * NFP + fp] = R(0.5) * (own[v] + nbv[v]);
             } else if (b <= kMortar) {
                 const long long sl = kMortar - b;
 #pragma unroll
@@ -610,6 +610,10 @@ __device__ __forceinline__ void lift2volc_body(const Ctx<R> &a, long long blk, u
             }
         }
         stage_face_metrics<D, N, R>(a, t, sJf);
+        sQ[n] = ns.rho;  // the state's shared copies after the face loads
+#pragma unroll
+        for (int k = 0; k < D; ++k) sQ[(1 + k) * NP + n] = ns.m[k] * ns.irho;
+        sQ[(D + 1) * NP + n] = ns.c;
     }
     // pass-2 face values: T* (T_wall at walls) and (grad c)* . J a^dir (at walls
     // nsign |J a^dir| g_n from the contact angle)
