@@ -63,3 +63,25 @@ def test_ncu_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
     (csrc / "dgk_kernels.cuh").write_text("// changed\n")
     assert bench.ncu_traffic("k_lift2vol", "c5_fp32") is None
     assert bench.ncu_traffic("k_surf_rk", "c5_fp32") is None
+
+
+def test_batch_traffic_follows_the_batched_sources(tmp_path, monkeypatch):
+    """The batched form's DRAM bytes per stage count only while the stage kernels and the
+    batched kernels are the sources the summary was taken on."""
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    os.makedirs(tmp_path / "profiles")
+    csrc = tmp_path / "paper_2208_05310_gb300" / "csrc"
+    os.makedirs(csrc)
+    for fn in ("dgk_common.cuh", "dgk_kernels.cuh", "dgk_batch.cu"):
+        (csrc / fn).write_text("// " + fn + "\n")
+    body = f"kernel_source_sha1: {bench.kernel_sources_sha(batch=True)}\ndram_bytes_per_stage: 777\n"
+    (tmp_path / "profiles" / "k_batch_phase_c4_fp32.txt").write_text(body)
+    assert bench.batch_traffic("c4") == pytest.approx(777)
+    assert bench.batch_traffic("c4s") is None  # no summary of that workload
+    (csrc / "dgk_batch.cu").write_text("// changed\n")
+    assert bench.batch_traffic("c4") is None
+
+
+def test_l2_note_says_when_a_workload_fits_in_l2():
+    assert bench.l2_note(1.36e9).startswith("inputs larger than L2")
+    assert "fit in L2" in bench.l2_note(4.1e6)
