@@ -70,3 +70,39 @@ def test_run_host_edge_cases_and_refusals():
         g.run_host([u], [out], 1, 0.0)
     with pytest.raises(dgk.DgkError):
         g.run_host([u], [out, out], 1, dt)
+
+
+def test_run_host_with_kernel_timing_and_after_a_parameter_change():
+    """With per-kernel timing on, dgk_run_host launches the stage kernels one by one
+    instead of replaying its step graphs; after new parameters it captures new graphs.
+    Both give the sequential results bit for bit."""
+    from paper_2208_05310_gb300 import dgk
+    g = dgk_context(MS, PAPER_PARAMS, precision="fp32bulk")
+    ins = _inputs(g, 4)
+    dt = 0.5 * g.max_dt()
+
+    def sequential():
+        ref = []
+        for u in ins:
+            g.upload_state(u)
+            g.run(2, dt)
+            g.status()
+            ref.append(g.download_state())
+        return ref
+
+    ref = sequential()
+    g.set_timing(True)
+    outs = [np.zeros_like(u) for u in ins]
+    g.run_host(ins, outs, 2, dt)
+    g.status()
+    assert all(np.array_equal(o, r) for o, r in zip(outs, ref))
+    assert g.kernel_time(1)[1] > 0  # the k_lift2vol launches were timed
+    g.set_timing(False)
+    g.run_host(ins, outs, 2, dt)  # graphs of the three buffers
+    assert all(np.array_equal(o, r) for o, r in zip(outs, ref))
+    g.set_params(rk=4, precision="fp32bulk", **dict(PAPER_PARAMS, beta=50.0))  # drops the graphs
+    ref2 = sequential()
+    g.run_host(ins, outs, 2, dt)
+    g.status()
+    assert all(np.array_equal(o, r) for o, r in zip(outs, ref2))
+    assert not all(np.array_equal(a, b) for a, b in zip(ref, ref2))
