@@ -1227,13 +1227,30 @@ __device__ __forceinline__ void write_traces(const Ctx<R> &a, const Slot<D, N, E
     __syncthreads();
     if (t.valid) {
         const long long ne = a.v.g.ne;
-        for (int q = t.n; q < D * NL * NFP; q += NP) {
-            const int dir = q / (NL * NFP), v = (q / NFP) % NL, line = q % NFP;
-            R x[P], tm, tp;
-            load_line<P, R>(sQ + v * NP, line_base<P>(line, dir), line_stride<P>(dir), x);
-            trace_pair<P, R>(a.op, x, tm, tp);
-            fat<NF, NFP>(a.v.tr1, ne, v, t.e, 2 * dir, line) = tm;
-            fat<NF, NFP>(a.v.tr1, ne, v, t.e, 2 * dir + 1, line) = tp;
+        // One loop per direction (compile-time line base and stride: no run-time
+        // direction selects or strided address arithmetic) where that takes no more
+        // rounds of NP tasks than one loop over all directions does.
+        constexpr int RD = (NL * NFP + NP - 1) / NP, RA = (D * NL * NFP + NP - 1) / NP;
+        if constexpr (D * RD <= RA) {
+#pragma unroll
+            for (int dir = 0; dir < D; ++dir)
+                for (int q = t.n; q < NL * NFP; q += NP) {
+                    const int v = q / NFP, line = q % NFP;
+                    R x[P], tm, tp;
+                    load_line<P, R>(sQ + v * NP, line_base<P>(line, dir), line_stride<P>(dir), x);
+                    trace_pair<P, R>(a.op, x, tm, tp);
+                    fat<NF, NFP>(a.v.tr1, ne, v, t.e, 2 * dir, line) = tm;
+                    fat<NF, NFP>(a.v.tr1, ne, v, t.e, 2 * dir + 1, line) = tp;
+                }
+        } else {
+            for (int q = t.n; q < D * NL * NFP; q += NP) {
+                const int dir = q / (NL * NFP), v = (q / NFP) % NL, line = q % NFP;
+                R x[P], tm, tp;
+                load_line<P, R>(sQ + v * NP, line_base<P>(line, dir), line_stride<P>(dir), x);
+                trace_pair<P, R>(a.op, x, tm, tp);
+                fat<NF, NFP>(a.v.tr1, ne, v, t.e, 2 * dir, line) = tm;
+                fat<NF, NFP>(a.v.tr1, ne, v, t.e, 2 * dir + 1, line) = tp;
+            }
         }
     }
 }
