@@ -871,6 +871,27 @@ __device__ __forceinline__ const R *face_source(int k, int dir, const R *sG, con
 
 // ------------------------------------------------------------------ kernel 2
 
+// One line of BR1 pass 2 along the compile-time direction DIR: q < NFP lifts T along
+// line q into grad T, otherwise dc/dx_DIR along line q - NFP into the DIR part of lap c.
+// (A compile-time direction turns the line's base, stride and buffer offsets into
+// constants: one loop per direction over 2 NFP tasks ran faster than one loop over all
+// 2 D NFP tasks with a run-time direction, although it takes D rounds instead of one.)
+template <int DIR, int P, int NP, int NFP, int NL, int D, typename R>
+__device__ __forceinline__ void pass2_line(const Ctx<R> &a, int q, const R *sT, const R *sTs, const R *sDs, const R *sG,
+                                           R *sGT, R *sLp)
+{
+    const bool isT = q < NFP;
+    const int line = isT ? q : q - NFP;
+    const int base = line_base<P>(line, DIR), stride = line_stride<P>(DIR);
+    const R *src = isT ? sT : sG + (DIR * NL + D + 1) * NP;
+    const R *qs = isT ? sTs : sDs;
+    R *dst = isT ? sGT + DIR * NP : sLp + DIR * NP;
+    R x[P], y[P];
+    load_line<P, R>(src, base, stride, x);
+    lift_line<P, R>(a.op, x, qs[(2 * DIR) * NFP + line], qs[(2 * DIR + 1) * NFP + line], a.v.gr.inv2h[DIR], y);
+    store_line<P, R>(dst, base, stride, y);
+}
+
 template <int D, int N, typename R, int EB = 0>
 struct K2Smem {
     using S = Shape<D, N, EB>;
@@ -989,7 +1010,9 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
     // ---- node: gradients, temperature; pass-2 central face values
     R g[D][D + 2];
     R T = R(0);
-    R *sT = sX, *sTs = sX + NP, *sDs = sTs + NF * NFP, *sLp = sDs + NF * NFP;
+    // the nodal region: written only after the volume integral, which reuses sX
+    static_assert(M::X2 <= (NV + 2) * NP, "pass-2 buffers fit the nodal region");
+    R *sT = sX + M::XN, *sTs = sT + NP, *sDs = sTs + NF * NFP, *sLp = sDs + NF * NFP;
     if (t.valid) {
 #pragma unroll
         for (int d = 0; d < D; ++d)
@@ -1026,21 +1049,12 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
     __syncthreads();
 
     // ---- pass 2: grad T (-> sGT) and the per-direction parts of lap c (-> sLp);
-    //      tasks 0..D*NFP-1 lift T, the next D*NFP lift dc/dx_dir along dir
+    //      per direction, tasks 0..NFP-1 lift T, the next NFP lift dc/dx_dir along dir
     if (t.valid) {
-        for (int q = n; q < 2 * D * NFP; q += NP) {
-            const bool isT = q < D * NFP;
-            const int qq = isT ? q : q - D * NFP;
-            const int dir = qq / NFP, line = qq % NFP;
-            const int base = line_base<P>(line, dir), stride = line_stride<P>(dir);
-            const R *src = isT ? sT : sG + (dir * NL + D + 1) * NP;
-            const R *qs = isT ? sTs : sDs;
-            R *dst = isT ? sGT + dir * NP : sLp + dir * NP;
-            R x[P], y[P];
-            load_line<P, R>(src, base, stride, x);
-            lift_line<P, R>(a.op, x, qs[(2 * dir) * NFP + line], qs[(2 * dir + 1) * NFP + line], a.v.gr.inv2h[dir], y);
-            store_line<P, R>(dst, base, stride, y);
-        }
+        for (int q = n; q < 2 * NFP; q += NP) pass2_line<0, P, NP, NFP, NL, D, R>(a, q, sT, sTs, sDs, sG, sGT, sLp);
+        for (int q = n; q < 2 * NFP; q += NP) pass2_line<1, P, NP, NFP, NL, D, R>(a, q, sT, sTs, sDs, sG, sGT, sLp);
+        if constexpr (D == 3)
+            for (int q = n; q < 2 * NFP; q += NP) pass2_line<D - 1, P, NP, NFP, NL, D, R>(a, q, sT, sTs, sDs, sG, sGT, sLp);
     }
     __syncthreads();
     R gT[D], lap = R(0);
@@ -1069,7 +1083,6 @@ __device__ __forceinline__ void lift2vol_body(const Ctx<R> &a, long long blk, un
         if (t.valid) a.v.out[t.e * NP + n] = to_f64<R>(entropy_production<D, R>(a.pr, rho, c, T, du, gT, lap));
         return;
     }
-    __syncthreads();  // sT, sTs, sDs, sLp are dead before the volume buffers reuse sX
 
     // ---- volume integral: the fluxes of all directions, then in place along each line
     //      (2/h) sum_l Dhat_il F_l; acc = the sum over the directions
